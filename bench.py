@@ -1,0 +1,401 @@
+#!/usr/bin/env python
+"""Benchmark of the BSE hot path on one GB300 (or N, one process per GPU).
+
+One step = one pass of the whole path over one momentum transfer of the
+optical-limit workload (Q = 0, full BSE, Nk = 64 on a 4x4x4 grid, Nv = Nc = 4,
+N = 1024, NG = 181): the Hamiltonian build (exchange + direct W^rr + direct
+W^ra + assembly of A and B), the Cholesky-form reduction, the FP64
+eigensolve and the oscillator-strength / eps_M spectrum.  Inputs are seeded
+synthetic arrays resident in HBM (0.61 GB, larger than the 129 MB L2).
+
+value: algorithmic build TFLOP/s (8 flops per complex multiply-add, no
+padding) of the build phase, timed with CUDA events on the launching stream.
+ms_per_step: the whole step (time to spectrum).  N > 1: every rank builds
+and solves its own momentum transfer (Q replicas, no collective), value sums
+the flops of all ranks over the slowest rank's time.
+
+--impl reference times the CPU oracle (the plain FP64 restatement of the
+paper the CUDA path is checked against) on the host cores, same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("BSE kernel-build TFLOP/s and time-to-spectrum, mixed vs FP64 GPU at "
+          "≤1 meV error")
+WORKLOAD = ("optical limit Q=0, full (non-TDA) BSE, Nk=64 (4x4x4), Nv=4, Nc=4, N=1024 "
+            "(2048 full), NG=181")
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+FP64_PEAK_TFLOPS = 1.25     # GB300 FP64 (CUDA-core and tensor) nominal rate
+
+
+def build_flops(nk, nv, nc, ng, coupling=True):
+    """Algorithmic flops of one build: 8 per complex multiply-add, no padding.
+    exchange 8 N^2 NG; W^rr stage 1 8 Nk^2 NG^2 min(nv^2, nc^2) + stage 2 8 NG N^2;
+    W^ra stage 1 8 Nk^2 NG^2 nv nc + stage 2 8 NG N^2."""
+    n = nk * nv * nc
+    f = 8.0 * n * n * ng
+    f += 8.0 * nk * nk * ng * ng * min(nv * nv, nc * nc) + 8.0 * ng * n * n
+    if coupling:
+        f += 8.0 * nk * nk * ng * ng * nv * nc + 8.0 * ng * n * n
+    return f
+
+
+def stage1_flops(nk, nv, nc, ng):
+    return 8.0 * nk * nk * ng * ng * min(nv * nv, nc * nc), 8.0 * nk * nk * ng * ng * nv * nc
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            out = {"source": "measured"}
+            for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained"):
+                if k in d:
+                    out[k] = float(d[k])
+            for k, v in FALLBACK_PEAKS.items():
+                out.setdefault(k, v)
+            return out
+        except Exception:
+            pass
+    out = dict(FALLBACK_PEAKS)
+    out["source"] = "fallback"
+    return out
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def oracle_step(p, O):
+    """One oracle pass over the workload: build, reduce, spectrum (seconds)."""
+    t0 = time.perf_counter()
+    A, B = O.build_A_B(p)
+    t1 = time.perf_counter()
+    O.spectrum(A, B, p)
+    t2 = time.perf_counter()
+    return t1 - t0, t2 - t0
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return 0
+    import bse_inputs as bi
+    from oracle import bse_oracle as O
+    p = bi.make_problem(args.config)
+    flops = build_flops(p["nk"], p["nv"], p["nc"], p["ng"])
+    for _ in range(args.warmup):
+        oracle_step(p, O)
+    tb, tt = [], []
+    for _ in range(args.steps):
+        b, t = oracle_step(p, O)
+        tb.append(b)
+        tt.append(t)
+    value = flops / statistics.mean(tb) / 1e12
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * statistics.mean(tt), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": "fp64 (numpy, host)"},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cpu_cores(),
+                         "kind": "oracle",
+                         "sample": f"full workload, {args.steps} steps of build+reduce+spectrum"},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c2")
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "bf16x6", "bf16x3"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    args.warmup = max(args.warmup, 3)
+
+    import numpy as np
+    import torch
+
+    import bse_inputs as bi
+    import paper_1904_05575_gb300 as bse
+    from paper_1904_05575_gb300 import build as _build
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        dist.barrier()
+    bse.load()
+
+    prec_map = {"fp64": bse.BSE_PREC_FP64, "bf16x6": bse.BSE_PREC_BF16X6,
+                "bf16x3": bse.BSE_PREC_BF16X3}
+    if args.precision == "auto":
+        args.precision = "bf16x6" if bse.mixed_available() else "fp64"
+    prec = prec_map[args.precision]
+
+    # each rank: its own momentum transfer (Q replica), resident in HBM
+    p = bi.make_problem(args.config, seed=20190411 + rank)
+    nk, nv, nc, ng = p["nk"], p["nv"], p["nc"], p["ng"]
+    n = nk * nv * nc
+    flops = build_flops(nk, nv, nc, ng)
+    d = bse.upload_problem(p)
+    st = bse.make_problem_struct(d)
+    dev = "cuda"
+    S = torch.empty((n, n), dtype=torch.complex128, device=dev)
+    L = torch.empty_like(S)
+    E = torch.empty(n, dtype=torch.float64, device=dev)
+    osc = torch.empty_like(E)
+    om = torch.as_tensor(p["omega"]).to(dev)
+    eps = torch.empty(len(p["omega"]), dtype=torch.complex128, device=dev)
+    rho = torch.as_tensor(p["rho"]).to(dev)
+    vc = nk * p["omega_cell"]
+    stream = torch.cuda.current_stream()
+
+    def step(precision, ev=None):
+        if ev:
+            ev[0].record(stream)
+        bse.bse_build_kernel([st], precision)
+        if ev:
+            ev[1].record(stream)
+        bse.bse_reduce(n, d["A"], d["B"], S, L)
+        bse.bse_spectrum(n, S, L, rho, p["c_q"], vc, om, p["delta"], E, osc, eps)
+        if ev:
+            ev[2].record(stream)
+
+    for _ in range(args.warmup):
+        step(prec)
+    torch.cuda.synchronize()
+
+    # ---- timed region ----
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = bse.bse_kernel_launches()
+    bse.bse_phase_timing(True)
+    for i in range(args.steps):
+        step(prec, evs[i])
+    torch.cuda.synchronize()
+    bse.bse_phase_timing(False)
+    launches = bse.bse_kernel_launches() - launches0
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    phases = bse.bse_phase_report()
+    build_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    step_ms = [e[0].elapsed_time(e[2]) for e in evs]
+    t_build = statistics.mean(build_ms)
+    t_step = statistics.mean(step_ms)
+    if world > 1:
+        t = torch.tensor([t_build, t_step], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_build, t_step = t.tolist()
+    value = world * flops / (t_build * 1e-3) / 1e12
+
+    # accuracy of this precision against the FP64 GPU build (same inputs)
+    E_this = E.clone()
+    A_this = d["A"].clone()
+    extra = {}
+    if prec != bse.BSE_PREC_FP64:
+        fp_ms = []
+        for i in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            bse.bse_build_kernel([st], bse.BSE_PREC_FP64)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            fp_ms.append(e0.elapsed_time(e1))
+        bse.bse_reduce(n, d["A"], d["B"], S, L)
+        bse.bse_spectrum(n, S, L, rho, p["c_q"], vc, om, p["delta"], E, osc, eps)
+        torch.cuda.synchronize()
+        dA = (torch.linalg.norm(A_this - d["A"]) / torch.linalg.norm(d["A"])).item()
+        dE = (E_this - E).abs().max().item() * 1e3
+        extra = {"fp64_build_ms": statistics.mean(fp_ms),
+                 "fp64_build_tflops": flops / (statistics.mean(fp_ms) * 1e-3) / 1e12,
+                 "speedup_vs_fp64_build": statistics.mean(fp_ms) / t_build,
+                 "A_rel_fro_vs_fp64": dA, "max_dE_meV_vs_fp64": dE}
+
+    # ---- roofline of the dominant build kernel (phase timing, live) ----
+    peaks = load_peaks()
+    s1_rr, s1_ra = stage1_flops(nk, nv, nc, ng)
+    if prec == bse.BSE_PREC_FP64:
+        name = "fp64_wra_stage1"
+        cnt, ms = phases.get(name, (1, float("nan")))
+        achieved = s1_ra / (ms / cnt * 1e-3) / 1e12
+        roofline = {"kernel": name, "bound": "alu", "achieved": achieved,
+                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                    "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak)",
+                    "flops_per_launch": s1_ra}
+    else:
+        name = "mixed_stage1_gemm"
+        cnt, ms = phases.get(name, (1, float("nan")))
+        per = (s1_rr + s1_ra) / max(cnt, 1) * cnt / args.steps   # both direct terms per step
+        products = 6 if prec == bse.BSE_PREC_BF16X6 else 3
+        peak = peaks["bf16_tflops"] / products
+        achieved = (s1_rr + s1_ra) / (ms / args.steps * 1e-3) / 1e12
+        roofline = {"kernel": name, "bound": "tensor", "achieved": achieved, "peak": peak,
+                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                    "peak_source": f"{peaks['source']} bf16 burst / {products} piece products",
+                    "flops_per_step": s1_rr + s1_ra}
+
+    # ---- end to end through the public API with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        host = {k: d[k].cpu().pin_memory() for k in
+                ("e_v", "e_c", "m_x", "m_vv", "m_cc", "n_vc", "w", "q_minus", "q_plus", "v_bar")}
+        h2d = sum(t.numel() * t.element_size() for t in host.values())
+        E_h = torch.empty(n, dtype=torch.float64).pin_memory()
+        osc_h = torch.empty_like(E_h).pin_memory()
+        eps_h = torch.empty(len(p["omega"]), dtype=torch.complex128).pin_memory()
+        d2h = (E_h.numel() + osc_h.numel()) * 8 + eps_h.numel() * 16
+        e2e_ms = []
+        for i in range(args.warmup + args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for k, t in host.items():
+                d[k].copy_(t, non_blocking=True)
+            step(prec)
+            E_h.copy_(E, non_blocking=True)
+            osc_h.copy_(osc, non_blocking=True)
+            eps_h.copy_(eps, non_blocking=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                e2e_ms.append(e0.elapsed_time(e1))
+        t_e2e = statistics.mean(e2e_ms)
+        if world > 1:
+            t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = t.item()
+        e2e = {"value": world * flops / (t_e2e * 1e-3) / 1e12, "unit": "TFLOP/s",
+               "ms_per_step": t_e2e, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    # ---- CPU oracle on the host cores (rank 0, N = 1 only), bounded sample ----
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import bse_oracle as O
+        tb, _ = oracle_step(p, O)
+        cpu = {"value": flops / tb / 1e12, "unit": "TFLOP/s", "cores": cpu_cores(),
+               "kind": "oracle", "sample": "one full build of the same workload (numpy FP64)",
+               "build_s": tb}
+
+    if rank == 0:
+        phase_ms = {k: v[1] / args.steps for k, v in phases.items()}
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "bf16x6": "bf16x6(f32 acc)", "bf16x3": "bf16x3(f32 acc)"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": args.precision,
+                       "l2": "inputs larger than L2 (0.61 GB resident per step)",
+                       "parallelism": f"Q replicas x{world}"},
+            "build_ms": t_build, "time_to_spectrum_ms": t_step,
+            "phase_ms_per_step": phase_ms,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": launches, "peaks": peaks,
+        }
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

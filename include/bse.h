@@ -1,0 +1,169 @@
+/*
+ * bse.h - C ABI of the GB300 Bethe-Salpeter Hamiltonian library (libbse.so).
+ *
+ * The library builds the two-particle BSE Hamiltonian of Vorwerk, Aurich,
+ * Cocchi, Draxl, "Bethe-Salpeter equation for absorption and scattering
+ * spectroscopy: Implementation in the exciting code" (arXiv:1904.05575),
+ * forms its half-size Hermitian reduction, solves it, and sums oscillator
+ * strengths into the macroscopic dielectric function.  Equation names below
+ * are the paper's labels.
+ *
+ * Conventions shared by every entry point
+ *   - All array pointers are DEVICE pointers (cudaMalloc / torch CUDA
+ *     memory) owned by the caller, unless a comment says "host".  The
+ *     library never frees caller memory and keeps no pointer after return.
+ *   - Complex numbers are bse_c128 = interleaved {double re, im}.
+ *   - N x N matrices are column-major with leading dimension ld >= N;
+ *     element (i, j) is at M[i + j * ld].  The full matrix is written.
+ *   - Transition index alpha = (k * nv + v) * nc + c, N = nk * nv * nc.
+ *   - Energies are in eV; v and W are in Hartree atomic units
+ *     (Ha * bohr^3); kappa = Ha / (nk * omega_cell) with Ha = 27.211386245988
+ *     eV multiplies the exchange and both direct terms.
+ *   - Functions return a bse_status and never throw across the ABI.
+ *     Argument errors are detected on the host before any launch and leave
+ *     outputs untouched.  bse_last_error() returns a thread-local message
+ *     describing the last non-OK status.
+ *   - cuda_stream is a cudaStream_t (NULL = legacy default stream).  Work is
+ *     enqueued on it; functions documented as "syncs" wait for it.
+ *   - Workspace is allocated with cudaMallocAsync on cuda_stream and freed
+ *     before return (stream-ordered).
+ */
+#ifndef BSE_H
+#define BSE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { double re, im; } bse_c128;
+
+typedef enum {
+  BSE_OK = 0,
+  BSE_ERR_ARG = -1,          /* invalid argument (message says which) */
+  BSE_ERR_CUDA = -2,         /* a CUDA runtime / library call failed */
+  BSE_ERR_NOMEM = -3,        /* workspace allocation failed */
+  BSE_ERR_NOT_PD = -4,       /* A-B or A+B not positive definite */
+  BSE_ERR_NO_CONV = -5,      /* iterative solver did not converge */
+  BSE_ERR_TIMEOUT = -6,      /* a bounded device-side wait gave up */
+  BSE_ERR_UNSUPPORTED = -7   /* valid request this build cannot serve */
+} bse_status;
+
+/* Arithmetic of the M / W / v contractions of bse_build_kernel.  The
+ * diagonal energies, the reduction, the eigensolve and the spectrum are
+ * always FP64. */
+typedef enum {
+  BSE_PREC_FP64 = 0,     /* plain FP64 on CUDA cores */
+  BSE_PREC_BF16X6 = 2,   /* each real operand split into 3 BF16 pieces, the 6
+                            leading piece products on tcgen05 tensor cores,
+                            FP32 accumulation */
+  BSE_PREC_BF16X3 = 3    /* 2 BF16 pieces, 3 products: lower precision */
+} bse_precision;
+
+/* One momentum transfer Q.  All pointers are device pointers.
+ *   e_v   [nk][nv]             valence energies eps_{v,k} (eV)
+ *   e_c   [nk][nc]             conduction energies eps_{c,k} (eV), scissor applied
+ *   m_x   [nk][nv][nc][ng]     M_{cv,k}(G, Q) of Eq. vrrofM
+ *   m_vv  [nk][nk][nv][nv][ng] m_vv[k][k'][v][v'] = M_{v'v,k'}(G, k-k') of Eq. wrrm
+ *   m_cc  [nk][nk][nc][nc][ng] m_cc[k][k'][c][c'] = M_{c'c,k'}(G', k-k') of Eq. wrrm
+ *   n_vc  [nk][nk][nv][nc][ng] n_vc[k][k'][v][c'] = N_{v c',k}(G', -k'-k) of Eq.
+ *                              wrabar; the first factor N_{c v'} of that equation
+ *                              is read as n_vc[k'][k][v'][c].  Unused (may be
+ *                              NULL) when coupling == 0.
+ *   w     [nq_w][ng][ng]       W_GG'(q), Hermitian, row-major (G' contiguous)
+ *   q_minus, q_plus [nk][nk]   index of k-k' and of -k-k' into w, in [0, nq_w)
+ *   v_bar [ng]                 4 pi / |G+Q|^2 with the G = 0 term set to 0
+ *                              (Eq. vbar_def), non-negative
+ * Output (device, column-major, ld >= N):
+ *   A = E^ip + 2 gamma_x V^rr - gamma_c W^rr     (Eq. diagonalblock)
+ *   B = 2 gamma_x V^rr - gamma_c W^ra            (Eq. couplingblock)
+ * with V^rr_{aa'} = kappa sum_G v_bar_G conj(m_x[a][G]) m_x[a'][G]   (Eq. vrrofM)
+ *      W^rr_{(kvc)(k'v'c')} = kappa sum_GG' conj(m_vv[k][k'][v][v'][G])
+ *                             w[q_minus[k][k']][G][G'] m_cc[k][k'][c][c'][G']   (Eq. wrrm)
+ *      W^ra_{(kvc)(k'v'c')} = kappa sum_GG' conj(n_vc[k'][k][v'][c][G])
+ *                             w[q_plus[k][k']][G][G'] n_vc[k][k'][v][c'][G']    (Eq. wrabar)
+ * B is not touched when coupling == 0 (Tamm-Dancoff, Eq. tdaevp) and may be NULL. */
+typedef struct {
+  int32_t nk, nv, nc, ng, nq_w;
+  double omega_cell;                  /* Omega in bohr^3; V_c = nk * Omega */
+  double gamma_x, gamma_c;            /* spin factors, Table tab:approx */
+  int32_t coupling;                   /* 1 = full BSE (fill B), 0 = TDA */
+  const double *e_v, *e_c;
+  const bse_c128 *m_x, *m_vv, *m_cc, *n_vc, *w;
+  const int32_t *q_minus, *q_plus;
+  const double *v_bar;
+  bse_c128 *A, *B;
+  int64_t ld;
+} bse_problem;
+
+/* Build A and B for nprob independent momentum transfers (each Q is its own
+ * BSE, Sec. "BSE in matrix form", Eq. chimatrixq).  probs is a HOST array of
+ * nprob descriptors (device pointers inside).  precision selects the
+ * contraction arithmetic.  Reads q_minus / q_plus back to the host to check
+ * their range (a sync on cuda_stream); the rest is asynchronous.
+ * Errors: BSE_ERR_ARG (sizes, NULL pointers, ld < N, q index out of range,
+ * unknown precision), BSE_ERR_NOMEM, BSE_ERR_CUDA, BSE_ERR_UNSUPPORTED. */
+int bse_build_kernel(const bse_problem* probs, int32_t nprob, int32_t precision,
+                     void* cuda_stream);
+
+/* Half-size reduction of Eq. auxham in its Cholesky form.  A-B = L L^H (L
+ * lower triangular, written to L with the strict upper triangle zeroed) and
+ * S = L^H (A+B) L, which is unitarily similar to (A-B)^{1/2}(A+B)(A-B)^{1/2}
+ * and has the eigenvalues E^2 of Eq. auxevp.  A, B are read only; S and L
+ * are N x N with the same ld.  For the TDA pass B = NULL (then S = L^H A L
+ * with A = L L^H, eigenvalues E^2 of the TDA problem Eq. tdaevp).
+ * failed_minor: HOST pointer (may be NULL) receiving the order of the
+ * leading minor of A-B that is not positive definite (0 on success).
+ * Syncs.  Errors: BSE_ERR_ARG, BSE_ERR_NOT_PD, BSE_ERR_NOMEM, BSE_ERR_CUDA. */
+int bse_reduce(int32_t n, const bse_c128* A, const bse_c128* B, int64_t ld,
+               bse_c128* S, bse_c128* L, int32_t* failed_minor, void* cuda_stream);
+
+/* Eigensolve S Z = E^2 Z (Eq. auxevp, FP64 Hermitian solver; S is
+ * overwritten by Z) and the spectrum:
+ *   E_lambda = sqrt(E^2_lambda), ascending                       -> E_out [n]
+ *   X+Y = E^{-1/2} L Z (from A-B = L L^H)
+ *   |t_lambda|^2 = |sum_alpha (X+Y)_{alpha lambda} rho_alpha|^2 / vc  (Eq. osci) -> osc_out [n]
+ *   eps(w) = 1 - c_q Ha sum_lambda |t_lambda|^2
+ *              [1/(w - E_lambda + i delta) - 1/(w + E_lambda + i delta)]
+ *            (Eq. chir and Eq. epsmtensor for one direction)   -> eps_out [n_omega]
+ * rho [n] = M_alpha(G=0, Q) (q.D in the optical limit, Eq. mofd); c_q = 4 pi
+ * at Q = 0 and 4 pi / |Q|^2 otherwise; vc = nk * Omega (bohr^3); omega
+ * [n_omega] and delta (half width) in eV.  All arrays are device pointers.
+ * Syncs (reads the eigensolver status).  Errors: BSE_ERR_ARG,
+ * BSE_ERR_NOT_PD (an eigenvalue E^2 <= 0), BSE_ERR_NOMEM, BSE_ERR_CUDA. */
+int bse_spectrum(int32_t n, bse_c128* S_inout, const bse_c128* L, int64_t ld,
+                 const bse_c128* rho, double c_q, double vc, int32_t n_omega,
+                 const double* omega, double delta, double* E_out, double* osc_out,
+                 bse_c128* eps_out, void* cuda_stream);
+
+/* Per-phase timing for measurement.  bse_phase_timing(1) makes the library
+ * record a CUDA event pair on the launching stream around each of its
+ * phases (one or more kernels, or one cuSOLVER / cuBLAS call);
+ * bse_phase_timing(0) stops recording.  bse_phase_report synchronizes the
+ * recorded events, writes one line "name launches total_ms\n" per phase into
+ * buf (host, buflen bytes, NUL-terminated, truncated if short), clears the
+ * record and returns the number of bytes written (or a negative status). */
+int bse_phase_timing(int32_t enable);
+int bse_phase_report(char* buf, int64_t buflen);
+
+/* 1 if this build serves the given bse_precision in bse_build_kernel, else 0.
+ * Host only; no CUDA call. */
+int bse_precision_supported(int32_t precision);
+
+/* Thread-local description of the last non-OK status ("" if none). */
+const char* bse_last_error(void);
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int bse_version(void);
+
+/* Number of CUDA kernels this library has launched in the calling process
+ * (its own kernels only; kernels inside cuSOLVER / cuBLAS calls are not
+ * counted).  Monotonic; for measurement. */
+int64_t bse_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BSE_H */

@@ -1,0 +1,228 @@
+"""Python binding of libbse.so: ctypes marshalling of torch CUDA tensors onto
+the C ABI declared in include/bse.h.  Every step of the computation runs in
+the library's CUDA kernels (and the cuSOLVER / cuBLAS calls it makes); this
+module only checks tensor placement and passes pointers.  It raises if the
+library is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Dict, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbse.so")
+
+BSE_OK, BSE_ERR_ARG, BSE_ERR_CUDA, BSE_ERR_NOMEM = 0, -1, -2, -3
+BSE_ERR_NOT_PD, BSE_ERR_NO_CONV, BSE_ERR_TIMEOUT, BSE_ERR_UNSUPPORTED = -4, -5, -6, -7
+BSE_PREC_FP64, BSE_PREC_BF16X6, BSE_PREC_BF16X3 = 0, 2, 3
+HARTREE_EV = 27.211386245988
+
+STATUS_NAMES = {0: "BSE_OK", -1: "BSE_ERR_ARG", -2: "BSE_ERR_CUDA", -3: "BSE_ERR_NOMEM",
+                -4: "BSE_ERR_NOT_PD", -5: "BSE_ERR_NO_CONV", -6: "BSE_ERR_TIMEOUT",
+                -7: "BSE_ERR_UNSUPPORTED"}
+
+
+class BSEError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+        self.message = message
+
+
+class bse_problem(ctypes.Structure):
+    _fields_ = [
+        ("nk", ctypes.c_int32), ("nv", ctypes.c_int32), ("nc", ctypes.c_int32),
+        ("ng", ctypes.c_int32), ("nq_w", ctypes.c_int32),
+        ("omega_cell", ctypes.c_double), ("gamma_x", ctypes.c_double),
+        ("gamma_c", ctypes.c_double), ("coupling", ctypes.c_int32),
+        ("e_v", ctypes.c_void_p), ("e_c", ctypes.c_void_p),
+        ("m_x", ctypes.c_void_p), ("m_vv", ctypes.c_void_p), ("m_cc", ctypes.c_void_p),
+        ("n_vc", ctypes.c_void_p), ("w", ctypes.c_void_p),
+        ("q_minus", ctypes.c_void_p), ("q_plus", ctypes.c_void_p),
+        ("v_bar", ctypes.c_void_p),
+        ("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("ld", ctypes.c_int64),
+    ]
+
+
+_lib: Optional[ctypes.CDLL] = None
+
+EXPORTED = ("bse_build_kernel", "bse_reduce", "bse_spectrum", "bse_last_error", "bse_version",
+            "bse_kernel_launches", "bse_precision_supported", "bse_phase_timing",
+            "bse_phase_report")
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libbse.so (built by build.py / __graft_entry__.build()); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with __graft_entry__.build() "
+                          "(there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    lib.bse_build_kernel.argtypes = [ctypes.POINTER(bse_problem), i32, i32, vp]
+    lib.bse_reduce.argtypes = [i32, vp, vp, i64, vp, vp, ctypes.POINTER(i32), vp]
+    lib.bse_spectrum.argtypes = [i32, vp, vp, i64, vp, dbl, dbl, i32, vp, dbl, vp, vp, vp, vp]
+    lib.bse_last_error.restype = ctypes.c_char_p
+    lib.bse_kernel_launches.restype = ctypes.c_int64
+    lib.bse_phase_timing.argtypes = [i32]
+    lib.bse_phase_report.argtypes = [ctypes.c_char_p, i64]
+    lib.bse_precision_supported.argtypes = [i32]
+    lib.bse_precision_supported.restype = ctypes.c_int
+    for name in ("bse_build_kernel", "bse_reduce", "bse_spectrum", "bse_version"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != BSE_OK:
+        msg = load().bse_last_error().decode(errors="replace")
+        raise BSEError(status, msg)
+
+
+def _ptr(t, dtype=None, name="tensor"):
+    if t is None:
+        return None
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda):
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _matrix_ptr(t, n, name):
+    """Column-major N x N with ld: a torch tensor of shape [n_cols, ld] (row r of
+    the tensor is column r of the matrix)."""
+    import torch
+    if t.dim() != 2 or t.shape[0] != n or t.shape[1] < n:
+        raise ValueError(f"{name} must have shape [n, ld] with ld >= n")
+    return _ptr(t, torch.complex128, name), t.shape[1]
+
+
+def make_problem_struct(d: Dict, gamma_x: float = 1.0, gamma_c: float = 1.0,
+                        coupling: bool = True) -> bse_problem:
+    """bse_problem from a dict of CUDA tensors (see upload_problem) and outputs A, B."""
+    import torch
+    c128, f64, i32 = torch.complex128, torch.float64, torch.int32
+    n = d["nk"] * d["nv"] * d["nc"]
+    a_ptr, ld = _matrix_ptr(d["A"], n, "A")
+    b_ptr = None
+    if coupling:
+        b_ptr, ldb = _matrix_ptr(d["B"], n, "B")
+        if ldb != ld:
+            raise ValueError("A and B must share ld")
+    return bse_problem(
+        nk=d["nk"], nv=d["nv"], nc=d["nc"], ng=d["ng"], nq_w=d["w"].shape[0],
+        omega_cell=float(d["omega_cell"]), gamma_x=float(gamma_x), gamma_c=float(gamma_c),
+        coupling=1 if coupling else 0,
+        e_v=_ptr(d["e_v"], f64, "e_v"), e_c=_ptr(d["e_c"], f64, "e_c"),
+        m_x=_ptr(d["m_x"], c128, "m_x"), m_vv=_ptr(d["m_vv"], c128, "m_vv"),
+        m_cc=_ptr(d["m_cc"], c128, "m_cc"),
+        n_vc=_ptr(d["n_vc"], c128, "n_vc") if coupling else None,
+        w=_ptr(d["w"], c128, "w"), q_minus=_ptr(d["q_minus"], i32, "q_minus"),
+        q_plus=_ptr(d["q_plus"], i32, "q_plus") if coupling else None,
+        v_bar=_ptr(d["v_bar"], f64, "v_bar"), A=a_ptr, B=b_ptr, ld=ld)
+
+
+def bse_build_kernel(problems: Sequence[bse_problem], precision: int = BSE_PREC_FP64,
+                     stream=None) -> None:
+    lib = load()
+    arr = (bse_problem * len(problems))(*problems)
+    _check(lib.bse_build_kernel(arr, len(problems), int(precision), _stream(stream)))
+
+
+def bse_reduce(n: int, A, B, S, L, stream=None) -> int:
+    """A-B = L L^H, S = L^H (A+B) L.  B may be None (TDA).  Returns 0 or raises
+    BSEError (status BSE_ERR_NOT_PD carries the failing minor in .minor)."""
+    lib = load()
+    a, ld = _matrix_ptr(A, n, "A")
+    b = _matrix_ptr(B, n, "B")[0] if B is not None else None
+    s, _ = _matrix_ptr(S, n, "S")
+    l, _ = _matrix_ptr(L, n, "L")
+    minor = ctypes.c_int32(0)
+    st = lib.bse_reduce(n, a, b, ld, s, l, ctypes.byref(minor), _stream(stream))
+    if st != BSE_OK:
+        err = BSEError(st, lib.bse_last_error().decode(errors="replace"))
+        err.minor = minor.value
+        raise err
+    return 0
+
+
+def bse_spectrum(n: int, S, L, rho, c_q: float, vc: float, omega, delta: float,
+                 E_out, osc_out, eps_out, stream=None) -> None:
+    import torch
+    lib = load()
+    s, ld = _matrix_ptr(S, n, "S")
+    l, _ = _matrix_ptr(L, n, "L")
+    n_omega = 0 if omega is None else omega.numel()
+    _check(lib.bse_spectrum(n, s, l, ld, _ptr(rho, torch.complex128, "rho"), float(c_q),
+                            float(vc), n_omega, _ptr(omega, torch.float64, "omega"),
+                            float(delta), _ptr(E_out, torch.float64, "E_out"),
+                            _ptr(osc_out, torch.float64, "osc_out"),
+                            _ptr(eps_out, torch.complex128, "eps_out"), _stream(stream)))
+
+
+def bse_phase_timing(enable: bool) -> None:
+    load().bse_phase_timing(1 if enable else 0)
+
+
+def bse_phase_report() -> Dict[str, tuple]:
+    """{phase: (launches, total_ms)} since the last report; clears the record."""
+    buf = ctypes.create_string_buffer(1 << 16)
+    n = load().bse_phase_report(buf, len(buf))
+    if n < 0:
+        _check(n)
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, cnt, ms = line.split()
+        out[name] = (int(cnt), float(ms))
+    return out
+
+
+def bse_kernel_launches() -> int:
+    return int(load().bse_kernel_launches())
+
+
+def upload_problem(p: Dict, device="cuda", ld: Optional[int] = None, pin: bool = False) -> Dict:
+    """Copy a bse_inputs problem (numpy) to CUDA tensors and allocate A, B [n, ld]."""
+    import torch
+    out = {}
+    for k in ("e_v", "e_c", "v_bar"):
+        out[k] = torch.as_tensor(np.ascontiguousarray(p[k], np.float64)).to(device)
+    for k in ("m_x", "m_vv", "m_cc", "n_vc", "w"):
+        out[k] = torch.as_tensor(np.ascontiguousarray(p[k], np.complex128)).to(device)
+    for k in ("q_minus", "q_plus"):
+        out[k] = torch.as_tensor(np.ascontiguousarray(p[k], np.int32)).to(device)
+    for k in ("nk", "nv", "nc", "ng"):
+        out[k] = int(p[k])
+    out["omega_cell"] = float(p["omega_cell"])
+    n = out["nk"] * out["nv"] * out["nc"]
+    ld = ld or n
+    out["A"] = torch.zeros((n, ld), dtype=torch.complex128, device=device)
+    out["B"] = torch.zeros((n, ld), dtype=torch.complex128, device=device)
+    return out
+
+
+def matrix_to_numpy(t, n: int) -> np.ndarray:
+    """Column-major [n, ld] tensor -> numpy N x N (row i, column j)."""
+    return t[:, :n].cpu().numpy().T.copy()
+
+
+def mixed_available() -> bool:
+    """True when this build serves the split-precision tensor-core build."""
+    return bool(load().bse_precision_supported(BSE_PREC_BF16X6))

@@ -1,0 +1,237 @@
+// The extern "C" entry points of libbse.so: argument checks on the host,
+// then dispatch to the build / reduction / spectrum launchers.  No C++
+// exception crosses this boundary.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "bse_internal.h"
+
+namespace bse {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+namespace {
+std::atomic<int64_t> g_launches{0};
+}
+void note_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+namespace {
+struct PhaseRecord {
+  std::string name;
+  cudaEvent_t start, stop;
+};
+std::atomic<bool> g_timing{false};
+std::mutex g_phase_mutex;
+std::vector<PhaseRecord> g_phases;
+}  // namespace
+
+Phase::Phase(const char* name, cudaStream_t s) : name_(name), s_(s) {
+  if (!g_timing.load()) return;
+  if (cudaEventCreate(&start_) != cudaSuccess || cudaEventRecord(start_, s_) != cudaSuccess) {
+    (void)cudaGetLastError();
+    start_ = nullptr;
+  }
+}
+
+Phase::~Phase() {
+  if (!start_) return;
+  cudaEvent_t stop = nullptr;
+  if (cudaEventCreate(&stop) != cudaSuccess || cudaEventRecord(stop, s_) != cudaSuccess) {
+    (void)cudaGetLastError();
+    cudaEventDestroy(start_);
+    if (stop) cudaEventDestroy(stop);
+    return;
+  }
+  std::lock_guard<std::mutex> lock(g_phase_mutex);
+  g_phases.push_back({name_, start_, stop});
+}
+
+template <class F>
+int guarded(F&& f) {
+  try {
+    f();
+    g_last_error.clear();
+    return BSE_OK;
+  } catch (const Error& e) {
+    g_last_error = e.what();
+    return e.status;
+  } catch (const std::bad_alloc&) {
+    g_last_error = "host allocation failed";
+    return BSE_ERR_NOMEM;
+  } catch (const std::exception& e) {
+    g_last_error = e.what();
+    return BSE_ERR_CUDA;
+  } catch (...) {
+    g_last_error = "unknown error";
+    return BSE_ERR_CUDA;
+  }
+}
+
+namespace {
+
+void check_q_map(const int32_t* dmap, int nk, int nq_w, const char* name, cudaStream_t s) {
+  std::vector<int32_t> h((size_t)nk * nk);
+  BSE_CUDA(cudaMemcpyAsync(h.data(), dmap, h.size() * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                           s));
+  BSE_CUDA(cudaStreamSynchronize(s));
+  for (size_t i = 0; i < h.size(); ++i)
+    if (h[i] < 0 || h[i] >= nq_w)
+      throw Error(BSE_ERR_ARG, std::string(name) + "[" + std::to_string(i / nk) + "][" +
+                                   std::to_string(i % nk) + "] = " + std::to_string(h[i]) +
+                                   " is outside [0, nq_w = " + std::to_string(nq_w) + ")");
+}
+
+Problem validate(const bse_problem& p, int index, cudaStream_t s) {
+  const std::string at = "probs[" + std::to_string(index) + "]: ";
+  BSE_CHECK_ARG(p.nk >= 1 && p.nv >= 1 && p.nc >= 1 && p.ng >= 1 && p.nq_w >= 1,
+                at + "nk, nv, nc, ng and nq_w must all be >= 1");
+  const int64_t n = (int64_t)p.nk * p.nv * p.nc;
+  BSE_CHECK_ARG(n <= 2147483647LL / 2, at + "N = nk*nv*nc is too large");
+  BSE_CHECK_ARG(p.ld >= n, at + "ld (" + std::to_string(p.ld) + ") < N (" + std::to_string(n) + ")");
+  BSE_CHECK_ARG(std::isfinite(p.omega_cell) && p.omega_cell > 0.0, at + "omega_cell must be > 0");
+  BSE_CHECK_ARG(std::isfinite(p.gamma_x) && std::isfinite(p.gamma_c),
+                at + "gamma_x and gamma_c must be finite");
+  BSE_CHECK_ARG(p.coupling == 0 || p.coupling == 1, at + "coupling must be 0 or 1");
+  BSE_CHECK_ARG(p.e_v && p.e_c && p.m_x && p.v_bar && p.A, at + "NULL e_v, e_c, m_x, v_bar or A");
+  if (p.gamma_c != 0.0) {
+    BSE_CHECK_ARG(p.m_vv && p.m_cc && p.w && p.q_minus, at + "NULL m_vv, m_cc, w or q_minus");
+    if (p.coupling) BSE_CHECK_ARG(p.n_vc && p.q_plus, at + "NULL n_vc or q_plus");
+  }
+  if (p.coupling) BSE_CHECK_ARG(p.B, at + "coupling = 1 needs B");
+  if (p.gamma_c != 0.0) {
+    check_q_map(p.q_minus, p.nk, p.nq_w, "q_minus", s);
+    if (p.coupling) check_q_map(p.q_plus, p.nk, p.nq_w, "q_plus", s);
+  }
+  Problem pr;
+  pr.p = p;
+  pr.n = n;
+  pr.kappa = kHartreeEv / ((double)p.nk * p.omega_cell);
+  return pr;
+}
+
+}  // namespace
+}  // namespace bse
+
+using namespace bse;
+
+extern "C" int bse_build_kernel(const bse_problem* probs, int32_t nprob, int32_t precision,
+                                void* cuda_stream) {
+  return guarded([&] {
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    BSE_CHECK_ARG(nprob >= 0, "nprob must be >= 0");
+    if (nprob == 0) return;
+    BSE_CHECK_ARG(probs != nullptr, "probs is NULL");
+    BSE_CHECK_ARG(precision == BSE_PREC_FP64 || precision == BSE_PREC_BF16X6 ||
+                      precision == BSE_PREC_BF16X3,
+                  "unknown precision " + std::to_string(precision));
+    std::vector<Problem> prs;
+    prs.reserve(nprob);
+    for (int i = 0; i < nprob; ++i) prs.push_back(validate(probs[i], i, s));
+    for (const Problem& pr : prs) {
+      if (precision == BSE_PREC_FP64)
+        build_fp64(pr, s);
+      else
+        build_mixed(pr, precision, s);
+    }
+  });
+}
+
+extern "C" int bse_reduce(int32_t n, const bse_c128* A, const bse_c128* B, int64_t ld,
+                          bse_c128* S, bse_c128* L, int32_t* failed_minor, void* cuda_stream) {
+  return guarded([&] {
+    if (failed_minor) *failed_minor = 0;
+    BSE_CHECK_ARG(n >= 1, "n must be >= 1");
+    BSE_CHECK_ARG(ld >= n, "ld < n");
+    BSE_CHECK_ARG(A && S && L, "NULL A, S or L");
+    BSE_CHECK_ARG(S != L && S != A && L != A && (B == nullptr || (S != B && L != B)),
+                  "S and L must not alias A, B or each other");
+    reduce_fp64(n, A, B, ld, S, L, failed_minor, static_cast<cudaStream_t>(cuda_stream));
+  });
+}
+
+extern "C" int bse_spectrum(int32_t n, bse_c128* S_inout, const bse_c128* L, int64_t ld,
+                            const bse_c128* rho, double c_q, double vc, int32_t n_omega,
+                            const double* omega, double delta, double* E_out, double* osc_out,
+                            bse_c128* eps_out, void* cuda_stream) {
+  return guarded([&] {
+    BSE_CHECK_ARG(n >= 1, "n must be >= 1");
+    BSE_CHECK_ARG(ld >= n, "ld < n");
+    BSE_CHECK_ARG(n_omega >= 0, "n_omega must be >= 0");
+    BSE_CHECK_ARG(S_inout && L && rho && E_out && osc_out, "NULL S, L, rho, E_out or osc_out");
+    BSE_CHECK_ARG(n_omega == 0 || (omega && eps_out), "NULL omega or eps_out");
+    BSE_CHECK_ARG(std::isfinite(vc) && vc > 0.0, "vc must be > 0");
+    BSE_CHECK_ARG(std::isfinite(c_q) && std::isfinite(delta) && delta >= 0.0,
+                  "c_q must be finite and delta >= 0");
+    spectrum_fp64(n, S_inout, L, ld, rho, c_q, vc, n_omega, omega, delta, E_out, osc_out,
+                  eps_out, static_cast<cudaStream_t>(cuda_stream));
+  });
+}
+
+extern "C" int bse_phase_timing(int32_t enable) {
+  g_timing.store(enable != 0);
+  return BSE_OK;
+}
+
+extern "C" int bse_phase_report(char* buf, int64_t buflen) {
+  int written = 0;
+  int st = guarded([&] {
+    BSE_CHECK_ARG(buf && buflen > 0, "NULL buf or buflen <= 0");
+    std::vector<PhaseRecord> recs;
+    {
+      std::lock_guard<std::mutex> lock(g_phase_mutex);
+      recs.swap(g_phases);
+    }
+    std::map<std::string, std::pair<int64_t, double>> acc;
+    std::vector<std::string> order;
+    std::string err;
+    for (auto& r : recs) {
+      float ms = 0.f;
+      cudaError_t e = cudaEventSynchronize(r.stop);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.start, r.stop);
+      if (e != cudaSuccess && err.empty()) err = cudaGetErrorString(e);
+      cudaEventDestroy(r.start);
+      cudaEventDestroy(r.stop);
+      if (!acc.count(r.name)) order.push_back(r.name);
+      auto& a = acc[r.name];
+      a.first += 1;
+      a.second += ms;
+    }
+    if (!err.empty()) throw Error(BSE_ERR_CUDA, "phase events: " + err);
+    std::string out;
+    for (auto& n : order) {
+      char line[256];
+      snprintf(line, sizeof(line), "%s %lld %.6f\n", n.c_str(), (long long)acc[n].first,
+               acc[n].second);
+      out += line;
+    }
+    size_t nb = out.size() < (size_t)(buflen - 1) ? out.size() : (size_t)(buflen - 1);
+    memcpy(buf, out.data(), nb);
+    buf[nb] = 0;
+    written = (int)nb;
+  });
+  return st == BSE_OK ? written : st;
+}
+
+extern "C" int bse_precision_supported(int32_t precision) {
+  if (precision == BSE_PREC_FP64) return 1;
+  if (precision == BSE_PREC_BF16X6 || precision == BSE_PREC_BF16X3)
+    return mixed_supported(precision) ? 1 : 0;
+  return 0;
+}
+
+extern "C" const char* bse_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" int bse_version(void) { return 100; }
+
+extern "C" int64_t bse_kernel_launches(void) { return g_launches.load(); }

@@ -1,0 +1,104 @@
+// Internal declarations shared by the translation units of libbse.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <stdexcept>
+#include <string>
+
+#include "../../include/bse.h"
+
+namespace bse {
+
+constexpr double kHartreeEv = 27.211386245988;   // CODATA 2018
+
+// Error carried from deep inside a launcher to the ABI boundary.
+struct Error : std::runtime_error {
+  int status;
+  Error(int s, const std::string& m) : std::runtime_error(m), status(s) {}
+};
+
+void set_last_error(const std::string& msg);
+
+// Count of kernels launched by this library (see bse_kernel_launches).
+void note_launches(int64_t n);
+
+// RAII phase timer: when bse_phase_timing(1) is on, records a start event on
+// construction and a stop event on destruction, both on the given stream.
+class Phase {
+ public:
+  Phase(const char* name, cudaStream_t s);
+  ~Phase();
+  Phase(const Phase&) = delete;
+  Phase& operator=(const Phase&) = delete;
+
+ private:
+  const char* name_;
+  cudaStream_t s_;
+  cudaEvent_t start_ = nullptr;
+};
+
+#define BSE_CUDA(call)                                                           \
+  do {                                                                           \
+    cudaError_t e_ = (call);                                                     \
+    if (e_ != cudaSuccess) {                                                     \
+      throw ::bse::Error(BSE_ERR_CUDA, std::string(#call) + ": " +               \
+                                           cudaGetErrorString(e_) + " at " +     \
+                                           __FILE__ + ":" + std::to_string(__LINE__)); \
+    }                                                                            \
+  } while (0)
+
+#define BSE_CHECK_ARG(cond, msg)                                                 \
+  do {                                                                           \
+    if (!(cond)) throw ::bse::Error(BSE_ERR_ARG, msg);                           \
+  } while (0)
+
+// Stream-ordered scratch buffer (cudaMallocAsync / cudaFreeAsync).
+struct DeviceBuffer {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  cudaStream_t stream = nullptr;
+  DeviceBuffer() = default;
+  DeviceBuffer(size_t n, cudaStream_t s) : bytes(n), stream(s) {
+    if (n == 0) return;
+    cudaError_t e = cudaMallocAsync(&ptr, n, s);
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      throw Error(BSE_ERR_NOMEM, "cudaMallocAsync of " + std::to_string(n) +
+                                     " bytes failed: " + cudaGetErrorString(e));
+    }
+  }
+  DeviceBuffer(const DeviceBuffer&) = delete;
+  DeviceBuffer& operator=(const DeviceBuffer&) = delete;
+  ~DeviceBuffer() {
+    if (ptr) cudaFreeAsync(ptr, stream);
+  }
+  template <class T>
+  T* as() const { return static_cast<T*>(ptr); }
+};
+
+// One problem after host-side validation, with derived sizes.
+struct Problem {
+  bse_problem p;
+  int64_t n;          // nk * nv * nc
+  double kappa;       // Ha / (nk * omega_cell)
+};
+
+// FP64 build (CUDA cores).  Writes A (and B when coupling) completely.
+void build_fp64(const Problem& pr, cudaStream_t stream);
+
+// True when build_mixed serves the precision.
+bool mixed_supported(int precision);
+
+// Split-precision tensor-core build (tcgen05).  Writes A (and B) completely.
+void build_mixed(const Problem& pr, int precision, cudaStream_t stream);
+
+// Reduction and spectrum.
+void reduce_fp64(int n, const bse_c128* A, const bse_c128* B, int64_t ld, bse_c128* S,
+                 bse_c128* L, int32_t* failed_minor, cudaStream_t stream);
+void spectrum_fp64(int n, bse_c128* S, const bse_c128* L, int64_t ld, const bse_c128* rho,
+                   double c_q, double vc, int n_omega, const double* omega, double delta,
+                   double* E_out, double* osc_out, bse_c128* eps_out, cudaStream_t stream);
+
+}  // namespace bse

@@ -1,0 +1,291 @@
+// Plain FP64 build of the BSE Hamiltonian on CUDA cores.
+//
+// Exchange (Eq. vrrofM), direct resonant-resonant (Eq. wrrm) and direct
+// resonant-antiresonant (Eq. wrabar) terms are batched complex GEMMs over
+// the plane-wave index; the assembly of Eqs. diagonalblock / couplingblock
+// happens in their epilogues:
+//   1. exchange GEMM       V = M_x^H diag(v_bar) M_x   -> writes A = E + 2 gx k V, B = 2 gx k V
+//   2. direct, stage 1     T_p = M_side(p) W(q(p))^T   (one small GEMM per k-pair p)
+//   3. direct, stage 2     P_p = M_other(p)^* T_p^T    -> A (or B) -= gc k P_p, scattered
+// Stage 1 applies W to whichever pair side is smaller (s_rr = min(nv^2, nc^2)).
+#include <cuda_runtime.h>
+
+#include "bse_internal.h"
+
+namespace bse {
+namespace {
+
+struct cplx {
+  double x, y;
+};
+__device__ __forceinline__ cplx cmake(double a, double b) { return {a, b}; }
+__device__ __forceinline__ cplx ldc(const bse_c128* p) {
+  double2 v = __ldg(reinterpret_cast<const double2*>(p));
+  return {v.x, v.y};
+}
+__device__ __forceinline__ cplx conj(cplx a) { return {a.x, -a.y}; }
+
+__device__ __forceinline__ double trans_energy(const double* e_v, const double* e_c, int nv,
+                                               int nc, int64_t alpha) {
+  int64_t k = alpha / (nv * nc);
+  int v = (int)((alpha / nc) % nv);
+  int c = (int)(alpha % nc);
+  return e_c[k * nc + c] - e_v[k * nv + v];
+}
+
+// Batched complex GEMM C_b[m][n] = sum_k a(b, m, k) * b(b, n, k), result
+// handed to P.store(b, m, n, value).  TM x TN tile per block, each thread
+// RM x RN outputs, K staged through shared memory TK at a time.
+template <int TM, int TN, int TK, int RM, int RN, class Prob>
+__global__ void __launch_bounds__((TM / RM) * (TN / RN))
+zgemm_batched(Prob P, int b0) {
+  constexpr int NTM = TM / RM, NTN = TN / RN, NT = NTM * NTN;
+  __shared__ double2 As[TK][TM];
+  __shared__ double2 Bs[TK][TN];
+  const int b = b0 + blockIdx.z;
+  const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+  const int tid = threadIdx.x;
+  const int tn = tid % NTN, tm = tid / NTN;
+  double accx[RM][RN], accy[RM][RN];
+#pragma unroll
+  for (int i = 0; i < RM; ++i)
+#pragma unroll
+    for (int j = 0; j < RN; ++j) accx[i][j] = accy[i][j] = 0.0;
+
+  for (int k0 = 0; k0 < P.K; k0 += TK) {
+    for (int i = tid; i < TM * TK; i += NT) {
+      int mm = i / TK, kk = i % TK;
+      cplx v = {0.0, 0.0};
+      if (m0 + mm < P.M && k0 + kk < P.K) v = P.a(b, m0 + mm, k0 + kk);
+      As[kk][mm] = make_double2(v.x, v.y);
+    }
+    for (int i = tid; i < TN * TK; i += NT) {
+      int nn = i / TK, kk = i % TK;
+      cplx v = {0.0, 0.0};
+      if (n0 + nn < P.N && k0 + kk < P.K) v = P.b(b, n0 + nn, k0 + kk);
+      Bs[kk][nn] = make_double2(v.x, v.y);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < TK; ++kk) {
+      double2 av[RM], bv[RN];
+#pragma unroll
+      for (int i = 0; i < RM; ++i) av[i] = As[kk][tm + i * NTM];
+#pragma unroll
+      for (int j = 0; j < RN; ++j) bv[j] = Bs[kk][tn + j * NTN];
+#pragma unroll
+      for (int i = 0; i < RM; ++i)
+#pragma unroll
+        for (int j = 0; j < RN; ++j) {
+          accx[i][j] = fma(av[i].x, bv[j].x, accx[i][j]);
+          accx[i][j] = fma(-av[i].y, bv[j].y, accx[i][j]);
+          accy[i][j] = fma(av[i].x, bv[j].y, accy[i][j]);
+          accy[i][j] = fma(av[i].y, bv[j].x, accy[i][j]);
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < RM; ++i)
+#pragma unroll
+    for (int j = 0; j < RN; ++j) {
+      int m = m0 + tm + i * NTM, n = n0 + tn + j * NTN;
+      if (m < P.M && n < P.N) P.store(b, m, n, cmake(accx[i][j], accy[i][j]));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// problem functors
+// ---------------------------------------------------------------------------
+struct ExchangeProb {     // Eq. vrrofM; epilogue initialises A and B
+  int M, N, K;
+  const bse_c128* mx;     // [n][ng]
+  const double* vbar;
+  const double *e_v, *e_c;
+  int nv, nc;
+  double scale;           // 2 gamma_x kappa
+  bse_c128 *A, *B;
+  int64_t ld;
+  __device__ cplx a(int, int m, int k) const {
+    cplx v = conj(ldc(mx + (int64_t)m * K + k));
+    double s = vbar[k];
+    return {v.x * s, v.y * s};
+  }
+  __device__ cplx b(int, int n, int k) const { return ldc(mx + (int64_t)n * K + k); }
+  __device__ void store(int, int m, int n, cplx v) const {
+    double2 val = make_double2(scale * v.x, scale * v.y);
+    int64_t off = (int64_t)m + (int64_t)n * ld;
+    if (B) reinterpret_cast<double2*>(B)[off] = val;
+    if (m == n) val.x += trans_energy(e_v, e_c, nv, nc, m);
+    reinterpret_cast<double2*>(A)[off] = val;
+  }
+};
+
+// Stage 1, W applied to rows of X (K = G' contiguous): T[p][r][G] = sum_G' W_q[G][G'] X_p[r][G']
+struct Stage1WProb {
+  int M, N, K;            // M = rows per pair, N = K = ng
+  const bse_c128* x;      // [npair][M][ng]
+  const bse_c128* w;      // [nq][ng][ng]
+  const int32_t* qmap;    // [npair]
+  bse_c128* t;            // [npair][M][ng]
+  __device__ cplx a(int p, int m, int k) const { return ldc(x + ((int64_t)p * M + m) * K + k); }
+  __device__ cplx b(int p, int n, int k) const {
+    return ldc(w + ((int64_t)qmap[p] * N + n) * K + k);
+  }
+  __device__ void store(int p, int m, int n, cplx v) const {
+    reinterpret_cast<double2*>(t)[((int64_t)p * M + m) * N + n] = make_double2(v.x, v.y);
+  }
+};
+
+// Stage 1, W^H applied: U[p][r][G'] = sum_G conj(W_q[G][G']) X_p[r][G]
+struct Stage1WHProb {
+  int M, N, K;
+  const bse_c128* x;
+  const bse_c128* w;
+  const int32_t* qmap;
+  bse_c128* t;
+  __device__ cplx a(int p, int m, int k) const { return ldc(x + ((int64_t)p * M + m) * K + k); }
+  __device__ cplx b(int p, int n, int k) const {
+    return conj(ldc(w + ((int64_t)qmap[p] * K + k) * N + n));
+  }
+  __device__ void store(int p, int m, int n, cplx v) const {
+    reinterpret_cast<double2*>(t)[((int64_t)p * M + m) * N + n] = make_double2(v.x, v.y);
+  }
+};
+
+// Stage 2 of W^rr: out[(v v')][(c c')] = sum_G conj(L_p[row][G]) R_p[col][G]
+//   cc-side T:  L = m_vv (rows v v'), R = T   (cols c c')
+//   vv-side U:  L = U    (rows v v'), R = m_cc (cols c c')
+// and A[(k v c)][(k' v' c')] -= gamma_c kappa out.
+struct Stage2RRProb {
+  int M, N, K;            // M = nv^2, N = nc^2, K = ng
+  const bse_c128* l;      // [npair][M][ng]
+  const bse_c128* r;      // [npair][N][ng]
+  int nk, nv, nc;
+  double scale;           // gamma_c kappa
+  bse_c128* A;
+  int64_t ld;
+  __device__ cplx a(int p, int m, int k) const {
+    return conj(ldc(l + ((int64_t)p * M + m) * K + k));
+  }
+  __device__ cplx b(int p, int n, int k) const { return ldc(r + ((int64_t)p * N + n) * K + k); }
+  __device__ void store(int p, int m, int n, cplx v) const {
+    int k = p / nk, kp = p % nk;
+    int vi = m / nv, vp = m % nv, ci = n / nc, cp = n % nc;
+    int64_t al = ((int64_t)k * nv + vi) * nc + ci;
+    int64_t ap = ((int64_t)kp * nv + vp) * nc + cp;
+    double2* dst = reinterpret_cast<double2*>(A) + al + ap * ld;
+    double2 o = *dst;
+    o.x -= scale * v.x;
+    o.y -= scale * v.y;
+    *dst = o;
+  }
+};
+
+// Stage 2 of W^ra: out[(v' c)][(v c')] = sum_G conj(n_vc[k'][k][v'][c][G]) T_p[(v c')][G]
+// and B[(k v c)][(k' v' c')] -= gamma_c kappa out.
+struct Stage2RAProb {
+  int M, N, K;            // M = N = nv * nc
+  const bse_c128* nvc;    // [nk][nk][nv*nc][ng]
+  const bse_c128* t;      // [npair][nv*nc][ng]
+  int nk, nv, nc;
+  double scale;
+  bse_c128* B;
+  int64_t ld;
+  __device__ cplx a(int p, int m, int k) const {
+    int kk = p / nk, kp = p % nk;
+    int64_t pt = (int64_t)kp * nk + kk;
+    return conj(ldc(nvc + (pt * M + m) * K + k));
+  }
+  __device__ cplx b(int p, int n, int k) const { return ldc(t + ((int64_t)p * N + n) * K + k); }
+  __device__ void store(int p, int m, int n, cplx v) const {
+    int k = p / nk, kp = p % nk;
+    int vp = m / nc, ci = m % nc;     // row (v', c)
+    int vi = n / nc, cp = n % nc;     // col (v, c')
+    int64_t al = ((int64_t)k * nv + vi) * nc + ci;
+    int64_t ap = ((int64_t)kp * nv + vp) * nc + cp;
+    double2* dst = reinterpret_cast<double2*>(B) + al + ap * ld;
+    double2 o = *dst;
+    o.x -= scale * v.x;
+    o.y -= scale * v.y;
+    *dst = o;
+  }
+};
+
+template <class Prob>
+void launch_zgemm(const Prob& P, int batch, cudaStream_t s) {
+  // tile shape from the output shape; every config is 128 or 256 threads.
+  // gridDim.z is capped at 65535, so large batches go in chunks.
+  for (int b0 = 0; b0 < batch; b0 += 65535) {
+    const int nb = batch - b0 < 65535 ? batch - b0 : 65535;
+    if (P.M >= 48 && P.N >= 48) {
+      dim3 grid((P.N + 63) / 64, (P.M + 63) / 64, nb);
+      zgemm_batched<64, 64, 8, 4, 4, Prob><<<grid, 256, 0, s>>>(P, b0);
+    } else if (P.M <= 16) {
+      dim3 grid((P.N + 63) / 64, (P.M + 15) / 16, nb);
+      zgemm_batched<16, 64, 16, 2, 4, Prob><<<grid, 128, 0, s>>>(P, b0);
+    } else {
+      dim3 grid((P.N + 31) / 32, (P.M + 31) / 32, nb);
+      zgemm_batched<32, 32, 16, 2, 4, Prob><<<grid, 128, 0, s>>>(P, b0);
+    }
+    BSE_CUDA(cudaGetLastError());
+    note_launches(1);
+  }
+}
+
+}  // namespace
+
+void build_fp64(const Problem& pr, cudaStream_t s) {
+  const bse_problem& p = pr.p;
+  const int nk = p.nk, nv = p.nv, nc = p.nc, ng = p.ng;
+  const int npair = nk * nk;
+  const double kap = pr.kappa;
+
+  // 1. exchange: initialises A and B
+  {
+    ExchangeProb P{(int)pr.n, (int)pr.n, ng, p.m_x, p.v_bar, p.e_v, p.e_c, nv, nc,
+                   2.0 * p.gamma_x * kap, p.A, p.coupling ? p.B : nullptr, p.ld};
+    Phase ph("fp64_exchange", s);
+    launch_zgemm(P, 1, s);
+  }
+  if (p.gamma_c == 0.0) return;
+
+  const int s_rr = nv * nv < nc * nc ? nv * nv : nc * nc;
+  const int rows_max = s_rr > nv * nc ? s_rr : (p.coupling ? nv * nc : s_rr);
+  DeviceBuffer tbuf((size_t)npair * rows_max * ng * sizeof(bse_c128), s);
+  bse_c128* t = tbuf.as<bse_c128>();
+
+  // 2./3. W^rr (Eq. wrrm)
+  if (nc * nc <= nv * nv) {
+    Stage1WProb P1{nc * nc, ng, ng, p.m_cc, p.w, p.q_minus, t};
+    {
+      Phase ph("fp64_wrr_stage1", s);
+      launch_zgemm(P1, npair, s);
+    }
+    Stage2RRProb P2{nv * nv, nc * nc, ng, p.m_vv, t, nk, nv, nc, p.gamma_c * kap, p.A, p.ld};
+    Phase ph("fp64_wrr_stage2", s);
+    launch_zgemm(P2, npair, s);
+  } else {
+    Stage1WHProb P1{nv * nv, ng, ng, p.m_vv, p.w, p.q_minus, t};
+    {
+      Phase ph("fp64_wrr_stage1", s);
+      launch_zgemm(P1, npair, s);
+    }
+    Stage2RRProb P2{nv * nv, nc * nc, ng, t, p.m_cc, nk, nv, nc, p.gamma_c * kap, p.A, p.ld};
+    Phase ph("fp64_wrr_stage2", s);
+    launch_zgemm(P2, npair, s);
+  }
+  if (!p.coupling) return;
+
+  // 2./3. W^ra (Eq. wrabar)
+  Stage1WProb P1{nv * nc, ng, ng, p.n_vc, p.w, p.q_plus, t};
+  {
+    Phase ph("fp64_wra_stage1", s);
+    launch_zgemm(P1, npair, s);
+  }
+  Stage2RAProb P2{nv * nc, nv * nc, ng, p.n_vc, t, nk, nv, nc, p.gamma_c * kap, p.B, p.ld};
+  Phase ph("fp64_wra_stage2", s);
+  launch_zgemm(P2, npair, s);
+}
+
+}  // namespace bse

@@ -1,0 +1,279 @@
+// Half-size reduction (Eq. auxham, Cholesky form), eigensolve (Eq. auxevp)
+// and the spectrum (Eqs. osci, chir, epsmtensor), all FP64.
+//
+// The dense Cholesky factorisation and the Hermitian eigensolver are
+// cuSOLVER calls and the two triangular products cuBLAS ZTRMM; the
+// element-wise set-up, the oscillator strengths and the eps_M sum are the
+// kernels below.
+#include <cublas_v2.h>
+#include <cuda_runtime.h>
+#include <cusolverDn.h>
+
+#include <mutex>
+#include <vector>
+
+#include "bse_internal.h"
+
+namespace bse {
+namespace {
+
+#define BSE_CUSOLVER(call)                                                        \
+  do {                                                                            \
+    cusolverStatus_t st_ = (call);                                                \
+    if (st_ != CUSOLVER_STATUS_SUCCESS)                                           \
+      throw ::bse::Error(BSE_ERR_CUDA, std::string(#call) + " failed with status " + \
+                                           std::to_string((int)st_));             \
+  } while (0)
+#define BSE_CUBLAS(call)                                                          \
+  do {                                                                            \
+    cublasStatus_t st_ = (call);                                                  \
+    if (st_ != CUBLAS_STATUS_SUCCESS)                                             \
+      throw ::bse::Error(BSE_ERR_CUDA, std::string(#call) + " failed with status " + \
+                                           std::to_string((int)st_));             \
+  } while (0)
+
+// One cuSOLVER and one cuBLAS handle per device, created on first use and
+// kept until exit; calls on them are serialised by a mutex.
+struct Handles {
+  cusolverDnHandle_t solver = nullptr;
+  cublasHandle_t blas = nullptr;
+};
+std::mutex g_handle_mutex;
+std::vector<Handles> g_handles;
+
+Handles& handles_for_current_device() {
+  int dev = 0;
+  BSE_CUDA(cudaGetDevice(&dev));
+  if ((int)g_handles.size() <= dev) g_handles.resize(dev + 1);
+  Handles& h = g_handles[dev];
+  if (!h.solver) BSE_CUSOLVER(cusolverDnCreate(&h.solver));
+  if (!h.blas) BSE_CUBLAS(cublasCreate(&h.blas));
+  return h;
+}
+
+__global__ void k_plus_minus(int n, const double2* A, const double2* B, int64_t ld,
+                             double2* S, double2* L) {
+  int64_t total = (int64_t)n * n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = i % n, c = i / n;
+    int64_t off = r + c * ld;
+    double2 a = A[off];
+    double2 b = B ? B[off] : make_double2(0.0, 0.0);
+    S[off] = make_double2(a.x + b.x, a.y + b.y);
+    L[off] = make_double2(a.x - b.x, a.y - b.y);
+  }
+}
+
+__global__ void k_zero_upper(int n, double2* L, int64_t ld) {
+  int64_t total = (int64_t)n * n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = i % n, c = i / n;
+    if (r < c) L[r + c * ld] = make_double2(0.0, 0.0);
+  }
+}
+
+// E = sqrt(E^2) in place; flag any E^2 <= 0.
+__global__ void k_sqrt_energies(int n, double* e, int* bad) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    double v = e[i];
+    if (!(v > 0.0)) {
+      atomicExch(bad, 1);
+      e[i] = 0.0;
+    } else {
+      e[i] = sqrt(v);
+    }
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// r_j = sum_i L_ij rho_i  (r = L^T rho, no conjugate): one warp per column j.
+__global__ void k_lt_rho(int n, const double2* L, int64_t ld, const double2* rho, double2* r) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const double2* col = L + (int64_t)warp * ld;
+  double sx = 0.0, sy = 0.0;
+  for (int i = warp + lane; i < n; i += 32) {   // L is lower triangular
+    double2 l = col[i], p = rho[i];
+    sx = fma(l.x, p.x, fma(-l.y, p.y, sx));
+    sy = fma(l.x, p.y, fma(l.y, p.x, sy));
+  }
+  sx = warp_sum(sx);
+  sy = warp_sum(sy);
+  if (lane == 0) r[warp] = make_double2(sx, sy);
+}
+
+// u_lambda = sum_j Z_{j lambda} r_j, |t_lambda|^2 = |u|^2 / (E_lambda vc): one warp per lambda.
+__global__ void k_oscillators(int n, const double2* Z, int64_t ld, const double2* r,
+                              const double* e, double vc, double* osc) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const double2* col = Z + (int64_t)warp * ld;
+  double sx = 0.0, sy = 0.0;
+  for (int j = lane; j < n; j += 32) {
+    double2 z = col[j], q = r[j];
+    sx = fma(z.x, q.x, fma(-z.y, q.y, sx));
+    sy = fma(z.x, q.y, fma(z.y, q.x, sy));
+  }
+  sx = warp_sum(sx);
+  sy = warp_sum(sy);
+  if (lane == 0) osc[warp] = (sx * sx + sy * sy) / (e[warp] * vc);
+}
+
+// eps(w) = 1 - c Ha sum_l osc_l [1/(w - E_l + i d) - 1/(w + E_l + i d)]: one block per w.
+__global__ void k_eps(int n, const double* e, const double* osc, int n_omega,
+                      const double* omega, double delta, double pref, double2* eps) {
+  __shared__ double sx[32], sy[32];
+  int iw = blockIdx.x;
+  if (iw >= n_omega) return;
+  double w = omega[iw];
+  double d2 = delta * delta;
+  double ax = 0.0, ay = 0.0;
+  for (int l = threadIdx.x; l < n; l += blockDim.x) {
+    double el = e[l], f = osc[l];
+    double a = w - el, b = w + el;
+    double ia = 1.0 / (a * a + d2), ib = 1.0 / (b * b + d2);
+    // 1/(a + i d) = (a - i d)/(a^2 + d^2)
+    ax += f * (a * ia - b * ib);
+    ay += f * (-delta * ia + delta * ib);
+  }
+  ax = warp_sum(ax);
+  ay = warp_sum(ay);
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    sx[wid] = ax;
+    sy[wid] = ay;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    int nw = blockDim.x >> 5;
+    ax = lane < nw ? sx[lane] : 0.0;
+    ay = lane < nw ? sy[lane] : 0.0;
+    ax = warp_sum(ax);
+    ay = warp_sum(ay);
+    if (lane == 0) eps[iw] = make_double2(1.0 - pref * ax, -pref * ay);
+  }
+}
+
+int grid_for(int64_t total, int threads) {
+  int64_t b = (total + threads - 1) / threads;
+  return (int)(b < 152 * 32 ? (b < 1 ? 1 : b) : 152 * 32);
+}
+
+}  // namespace
+
+void reduce_fp64(int n, const bse_c128* A, const bse_c128* B, int64_t ld, bse_c128* S,
+                 bse_c128* L, int32_t* failed_minor, cudaStream_t s) {
+  std::lock_guard<std::mutex> lock(g_handle_mutex);
+  Handles& h = handles_for_current_device();
+  BSE_CUSOLVER(cusolverDnSetStream(h.solver, s));
+  BSE_CUBLAS(cublasSetStream(h.blas, s));
+
+  // S <- A + B, L <- A - B
+  k_plus_minus<<<grid_for((int64_t)n * n, 256), 256, 0, s>>>(
+      n, reinterpret_cast<const double2*>(A), reinterpret_cast<const double2*>(B), ld,
+      reinterpret_cast<double2*>(S), reinterpret_cast<double2*>(L));
+  BSE_CUDA(cudaGetLastError());
+  note_launches(1);
+
+  // A - B = L L^H
+  int lwork = 0;
+  BSE_CUSOLVER(cusolverDnZpotrf_bufferSize(h.solver, CUBLAS_FILL_MODE_LOWER, n,
+                                           reinterpret_cast<cuDoubleComplex*>(L), (int)ld,
+                                           &lwork));
+  DeviceBuffer work((size_t)(lwork > 0 ? lwork : 1) * sizeof(cuDoubleComplex), s);
+  DeviceBuffer info(sizeof(int), s);
+  {
+    Phase ph("reduce_potrf", s);
+    BSE_CUSOLVER(cusolverDnZpotrf(h.solver, CUBLAS_FILL_MODE_LOWER, n,
+                                  reinterpret_cast<cuDoubleComplex*>(L), (int)ld,
+                                  work.as<cuDoubleComplex>(), lwork, info.as<int>()));
+  }
+  int hinfo = 0;
+  BSE_CUDA(cudaMemcpyAsync(&hinfo, info.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+  BSE_CUDA(cudaStreamSynchronize(s));
+  if (failed_minor) *failed_minor = hinfo > 0 ? hinfo : 0;
+  if (hinfo > 0)
+    throw Error(BSE_ERR_NOT_PD, "A-B is not positive definite: leading minor " +
+                                    std::to_string(hinfo) + " failed");
+  if (hinfo < 0) throw Error(BSE_ERR_CUDA, "zpotrf: invalid parameter " + std::to_string(-hinfo));
+  k_zero_upper<<<grid_for((int64_t)n * n, 256), 256, 0, s>>>(n, reinterpret_cast<double2*>(L),
+                                                               ld);
+  BSE_CUDA(cudaGetLastError());
+  note_launches(1);
+
+  // S = L^H (A+B) L:  C = (A+B) L, then S = L^H C
+  DeviceBuffer c((size_t)ld * n * sizeof(bse_c128), s);
+  const cuDoubleComplex one = make_cuDoubleComplex(1.0, 0.0);
+  Phase ph("reduce_trmm", s);
+  BSE_CUBLAS(cublasZtrmm(h.blas, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N,
+                         CUBLAS_DIAG_NON_UNIT, n, n, &one,
+                         reinterpret_cast<const cuDoubleComplex*>(L), (int)ld,
+                         reinterpret_cast<const cuDoubleComplex*>(S), (int)ld,
+                         c.as<cuDoubleComplex>(), (int)ld));
+  BSE_CUBLAS(cublasZtrmm(h.blas, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_C,
+                         CUBLAS_DIAG_NON_UNIT, n, n, &one,
+                         reinterpret_cast<const cuDoubleComplex*>(L), (int)ld,
+                         c.as<const cuDoubleComplex>(), (int)ld,
+                         reinterpret_cast<cuDoubleComplex*>(S), (int)ld));
+  BSE_CUDA(cudaStreamSynchronize(s));
+}
+
+void spectrum_fp64(int n, bse_c128* S, const bse_c128* L, int64_t ld, const bse_c128* rho,
+                   double c_q, double vc, int n_omega, const double* omega, double delta,
+                   double* E_out, double* osc_out, bse_c128* eps_out, cudaStream_t s) {
+  std::lock_guard<std::mutex> lock(g_handle_mutex);
+  Handles& h = handles_for_current_device();
+  BSE_CUSOLVER(cusolverDnSetStream(h.solver, s));
+
+  int lwork = 0;
+  BSE_CUSOLVER(cusolverDnZheevd_bufferSize(h.solver, CUSOLVER_EIG_MODE_VECTOR,
+                                           CUBLAS_FILL_MODE_LOWER, n,
+                                           reinterpret_cast<cuDoubleComplex*>(S), (int)ld,
+                                           E_out, &lwork));
+  DeviceBuffer work((size_t)(lwork > 0 ? lwork : 1) * sizeof(cuDoubleComplex), s);
+  DeviceBuffer flags(2 * sizeof(int), s);
+  BSE_CUDA(cudaMemsetAsync(flags.ptr, 0, 2 * sizeof(int), s));
+  {
+    Phase ph("eig_heevd", s);
+    BSE_CUSOLVER(cusolverDnZheevd(h.solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER,
+                                  n, reinterpret_cast<cuDoubleComplex*>(S), (int)ld, E_out,
+                                  work.as<cuDoubleComplex>(), lwork, flags.as<int>()));
+  }
+  Phase ph("spectrum_kernels", s);
+  k_sqrt_energies<<<(n + 255) / 256, 256, 0, s>>>(n, E_out, flags.as<int>() + 1);
+  BSE_CUDA(cudaGetLastError());
+
+  DeviceBuffer r((size_t)n * sizeof(bse_c128), s);
+  const int warps_per_block = 8;
+  int blocks = (n + warps_per_block - 1) / warps_per_block;
+  k_lt_rho<<<blocks, 32 * warps_per_block, 0, s>>>(
+      n, reinterpret_cast<const double2*>(L), ld, reinterpret_cast<const double2*>(rho),
+      r.as<double2>());
+  k_oscillators<<<blocks, 32 * warps_per_block, 0, s>>>(
+      n, reinterpret_cast<const double2*>(S), ld, r.as<const double2>(), E_out, vc, osc_out);
+  if (n_omega > 0)
+    k_eps<<<n_omega, 256, 0, s>>>(n, E_out, osc_out, n_omega, omega, delta,
+                                  c_q * kHartreeEv, reinterpret_cast<double2*>(eps_out));
+  BSE_CUDA(cudaGetLastError());
+  note_launches(n_omega > 0 ? 4 : 3);
+
+  int hflags[2] = {0, 0};
+  BSE_CUDA(cudaMemcpyAsync(hflags, flags.ptr, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  BSE_CUDA(cudaStreamSynchronize(s));
+  if (hflags[0] != 0)
+    throw Error(BSE_ERR_CUDA, "zheevd failed, info = " + std::to_string(hflags[0]));
+  if (hflags[1] != 0)
+    throw Error(BSE_ERR_NOT_PD, "an eigenvalue E^2 <= 0: A+B is not positive definite");
+}
+
+}  // namespace bse

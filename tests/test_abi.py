@@ -1,0 +1,62 @@
+"""The C-ABI library builds, loads, and exports every symbol include/bse.h
+declares (CPU only: no compute call)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(bse_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1904_05575_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_boundary():
+    names = _declared()
+    for required in ("bse_build_kernel", "bse_reduce", "bse_spectrum", "bse_last_error"):
+        assert required in names
+
+
+def test_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), f"libbse.so does not export {name}"
+
+
+def test_version_and_error_without_gpu(lib):
+    lib.bse_version.restype = ctypes.c_int
+    assert lib.bse_version() >= 100
+    lib.bse_last_error.restype = ctypes.c_char_p
+    assert isinstance(lib.bse_last_error(), bytes)
+
+
+def test_host_side_argument_errors(lib):
+    """Argument checks run on the host before any CUDA call."""
+    import paper_1904_05575_gb300 as bse
+    lib2 = bse.load()
+    # nprob = 0 is a no-op
+    assert lib2.bse_build_kernel(None, 0, 0, None) == bse.BSE_OK
+    # unknown precision / NULL probs / bad sizes are BSE_ERR_ARG
+    assert lib2.bse_build_kernel(None, 1, 0, None) == bse.BSE_ERR_ARG
+    p = bse.bse_problem(nk=0, nv=1, nc=1, ng=1, nq_w=1, omega_cell=1.0, ld=1)
+    arr = (bse.bse_problem * 1)(p)
+    assert lib2.bse_build_kernel(arr, 1, 0, None) == bse.BSE_ERR_ARG
+    assert b"nk" in lib2.bse_last_error()
+    assert lib2.bse_build_kernel(arr, 1, 99, None) == bse.BSE_ERR_ARG
+    assert lib2.bse_reduce(0, None, None, 1, None, None, None, None) == bse.BSE_ERR_ARG
+    assert lib2.bse_spectrum(4, None, None, 2, None, 1.0, 1.0, 0, None, 0.1,
+                             None, None, None, None) == bse.BSE_ERR_ARG
