@@ -1,10 +1,530 @@
-// Split-precision tensor-core build (tcgen05).  Placeholder until the
-// tensor-core kernels land: the request is refused, never served by another path.
+// Split-precision build of the BSE Hamiltonian on tcgen05 tensor cores.
+//
+// Same algebra as the FP64 build (exchange Eq. vrrofM, direct Eqs. wrrm and
+// wrabar, assembly Eqs. diagonalblock / couplingblock), with the two large
+// contractions on tensor cores:
+//   1. split      complex128 rows -> BF16 planes (Re/Im x P pieces), K padded
+//                 to 16; stage-1 rows are gathered in pairs-sorted-by-q order
+//                 so every 128-row tile shares one W(q)
+//   2. exchange   tensor-core GEMM conj(M_x) diag(v_bar) M_x^T; the epilogue
+//                 writes A = E + 2 gx k V and B = 2 gx k V (FP64)
+//   3. stage 1    tensor-core GEMM T = X_side W(q)^T per q group -> FP32 T[G][row]
+//   4. stage 2    FP32 CUDA-core contraction of T with the other pair side over
+//                 G, read straight from the complex128 input, subtracted from
+//                 A (W^rr) or B (W^ra) in FP64
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+#include <numeric>
+#include <vector>
+
 #include "bse_internal.h"
+#include "tc_gemm.cuh"
 
 namespace bse {
-bool mixed_supported(int) { return false; }
-void build_mixed(const Problem&, int, cudaStream_t) {
-  throw Error(BSE_ERR_UNSUPPORTED, "split-precision build is not available in this build");
+namespace {
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// ---------------------------------------------------------------------------
+// split: one thread per (output row, k); P pieces per real number
+// ---------------------------------------------------------------------------
+struct SplitArgs {
+  const double2* src;
+  const int64_t* row_off;   // output row -> element offset of its k = 0 entry (-1: zero row);
+                            // NULL: row * K (dense rows)
+  int64_t k_stride;         // elements between consecutive k of one row
+  int K;                    // real K
+  int Kp;                   // padded K (multiple of 16)
+  int rows;                 // output rows
+  int pieces;
+  int conj;                 // store the conjugate
+  const double* kscale;     // per-k real factor or NULL
+  __nv_bfloat16* out;       // [2 * pieces][rows][Kp]
+};
+
+__device__ __forceinline__ void split_real(double x, int pieces, __nv_bfloat16* out, int64_t plane) {
+  double r = x;
+  for (int i = 0; i < pieces; ++i) {
+    __nv_bfloat16 h = __float2bfloat16_rn((float)r);
+    out[i * plane] = h;
+    r -= (double)__bfloat162float(h);
+  }
 }
+
+__global__ void k_split(SplitArgs a) {
+  const int64_t total = (int64_t)a.rows * a.Kp;
+  const int64_t plane = total;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int row = (int)(i / a.Kp), k = (int)(i % a.Kp);
+    double2 x = make_double2(0.0, 0.0);
+    const int64_t off = a.row_off ? a.row_off[row] : (int64_t)row * a.K;
+    if (k < a.K && off >= 0) {
+      x = a.src[off + (int64_t)k * a.k_stride];
+      if (a.conj) x.y = -x.y;
+      if (a.kscale) {
+        const double s = a.kscale[k];
+        x.x *= s;
+        x.y *= s;
+      }
+    }
+    split_real(x.x, a.pieces, a.out + i, plane);
+    split_real(x.y, a.pieces, a.out + (int64_t)a.pieces * plane + i, plane);
+  }
+}
+
+void launch_split(const SplitArgs& a, cudaStream_t s) {
+  const int64_t total = (int64_t)a.rows * a.Kp;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  k_split<<<(int)std::max<int64_t>(blocks, 1), 256, 0, s>>>(a);
+  BSE_CUDA(cudaGetLastError());
+  note_launches(1);
+}
+
+// ---------------------------------------------------------------------------
+// epilogues of the tensor-core GEMM
+// ---------------------------------------------------------------------------
+struct ExchangeEpi {   // V[alpha][alpha'] -> A, B (column-major FP64)
+  double2 *A, *B;
+  int64_t ld;
+  double scale;
+  const double *e_v, *e_c;
+  int nv, nc;
+  __device__ void operator()(const tc::Tile& t, int row, int c0, const float* re,
+                             const float* im) const {
+    const int64_t al = t.out_row0 + row;
+    const int64_t kk = al / (nv * nc);
+    const int v = (int)((al / nc) % nv), c = (int)(al % nc);
+    const double e = e_c[kk * nc + c] - e_v[kk * nv + v];
+#pragma unroll 4
+    for (int j = 0; j < 32; ++j) {
+      const int col = c0 + j;
+      if (col >= t.n_valid) break;
+      const int64_t ap = t.n0 + col;
+      double2 val = make_double2(scale * (double)re[j], scale * (double)im[j]);
+      const int64_t off = al + ap * ld;
+      if (B) B[off] = val;
+      if (al == ap) val.x += e;
+      A[off] = val;
+    }
+  }
+};
+
+struct TEpi {          // T[G][row] (FP32 complex), G-major so a warp's stores coalesce
+  float2* T;
+  int64_t t_ld;        // rows in T
+  __device__ void operator()(const tc::Tile& t, int row, int c0, const float* re,
+                             const float* im) const {
+    const int64_t r = t.out_row0 + row;
+#pragma unroll 4
+    for (int j = 0; j < 32; ++j) {
+      const int col = c0 + j;
+      if (col >= t.n_valid) break;
+      T[(int64_t)(t.n0 + col) * t_ld + r] = make_float2(re[j], im[j]);
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// stage 2: P[rx][rt] = sum_G opX(X_p[rx][G]) * opT(T[G][slot * rows_t + rt])
+// ---------------------------------------------------------------------------
+enum Stage2Mode { S2_RR_CC = 0, S2_RR_VV = 1, S2_RA = 2 };
+
+struct Stage2Args {
+  int mode;
+  const double2* x;      // complex128 pair array, [nk][nk][rows_x][ng]
+  int x_transpose_pair;  // read X of pair (k', k) (W^ra)
+  int conj_x, conj_t;
+  const float2* T;
+  int64_t t_ld;
+  const int* slot_of_pair;
+  int rows_x, rows_t, ng, nk, nv, nc;
+  double scale;          // gamma_c kappa
+  double2* out;          // A or B
+  int64_t ld;
+};
+
+template <int TS, int R>   // TS x TS output tile per block, R x R outputs per thread
+__global__ void __launch_bounds__((TS / R) * (TS / R)) k_stage2(Stage2Args a) {
+  constexpr int NTH = (TS / R) * (TS / R);
+  constexpr int GC = 32;
+  __shared__ float2 Xs[TS][GC + 1];
+  __shared__ float2 Ts[GC][TS + 1];
+  const int p = blockIdx.x;
+  const int k = p / a.nk, kp = p % a.nk;
+  const int rx0 = blockIdx.y * TS, rt0 = blockIdx.z * TS;
+  const int64_t xp = a.x_transpose_pair ? (int64_t)kp * a.nk + k : (int64_t)p;
+  const double2* X = a.x + xp * a.rows_x * a.ng;
+  const int64_t trow0 = (int64_t)a.slot_of_pair[p] * a.rows_t;
+  const int tid = threadIdx.x;
+  const int tx = tid % (TS / R), ty = tid / (TS / R);
+  float accx[R][R], accy[R][R];
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+#pragma unroll
+    for (int j = 0; j < R; ++j) accx[i][j] = accy[i][j] = 0.f;
+
+  for (int g0 = 0; g0 < a.ng; g0 += GC) {
+    for (int i = tid; i < TS * GC; i += NTH) {
+      const int r = i / GC, g = i % GC;
+      float2 v = make_float2(0.f, 0.f);
+      if (rx0 + r < a.rows_x && g0 + g < a.ng) {
+        const double2 d = X[(int64_t)(rx0 + r) * a.ng + g0 + g];
+        v = make_float2((float)d.x, a.conj_x ? -(float)d.y : (float)d.y);
+      }
+      Xs[r][g] = v;
+    }
+    for (int i = tid; i < TS * GC; i += NTH) {
+      const int g = i / TS, r = i % TS;
+      float2 v = make_float2(0.f, 0.f);
+      if (rt0 + r < a.rows_t && g0 + g < a.ng) {
+        v = a.T[(int64_t)(g0 + g) * a.t_ld + trow0 + rt0 + r];
+        if (a.conj_t) v.y = -v.y;
+      }
+      Ts[g][r] = v;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int g = 0; g < GC; ++g) {
+      float2 xv[R], tv[R];
+#pragma unroll
+      for (int i = 0; i < R; ++i) xv[i] = Xs[ty + i * (TS / R)][g];
+#pragma unroll
+      for (int j = 0; j < R; ++j) tv[j] = Ts[g][tx + j * (TS / R)];
+#pragma unroll
+      for (int i = 0; i < R; ++i)
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+          accx[i][j] = fmaf(xv[i].x, tv[j].x, accx[i][j]);
+          accx[i][j] = fmaf(-xv[i].y, tv[j].y, accx[i][j]);
+          accy[i][j] = fmaf(xv[i].x, tv[j].y, accy[i][j]);
+          accy[i][j] = fmaf(xv[i].y, tv[j].x, accy[i][j]);
+        }
+    }
+    __syncthreads();
+  }
+
+  const int nv = a.nv, nc = a.nc;
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int rx = rx0 + ty + i * (TS / R), rt = rt0 + tx + j * (TS / R);
+      if (rx >= a.rows_x || rt >= a.rows_t) continue;
+      int vi, ci, vp, cp;
+      if (a.mode == S2_RR_CC) {          // rx = (v, v'), rt = (c, c')
+        vi = rx / nv; vp = rx % nv; ci = rt / nc; cp = rt % nc;
+      } else if (a.mode == S2_RR_VV) {   // rx = (c, c'), rt = (v, v')
+        ci = rx / nc; cp = rx % nc; vi = rt / nv; vp = rt % nv;
+      } else {                           // rx = (v', c), rt = (v, c')
+        vp = rx / nc; ci = rx % nc; vi = rt / nc; cp = rt % nc;
+      }
+      const int64_t al = ((int64_t)k * nv + vi) * nc + ci;
+      const int64_t ap = ((int64_t)kp * nv + vp) * nc + cp;
+      double2* dst = a.out + al + ap * a.ld;
+      double2 o = *dst;
+      o.x -= a.scale * (double)accx[i][j];
+      o.y -= a.scale * (double)accy[i][j];
+      *dst = o;
+    }
+}
+
+void launch_stage2(const Stage2Args& a, int npair, cudaStream_t s) {
+  if (a.rows_x <= 16 && a.rows_t <= 16) {
+    dim3 grid(npair, 1, 1);
+    k_stage2<16, 1><<<grid, 256, 0, s>>>(a);
+  } else {
+    dim3 grid(npair, (a.rows_x + 31) / 32, (a.rows_t + 31) / 32);
+    k_stage2<32, 2><<<grid, 256, 0, s>>>(a);
+  }
+  BSE_CUDA(cudaGetLastError());
+  note_launches(1);
+}
+
+// ---------------------------------------------------------------------------
+// tensor maps and the GEMM launcher
+// ---------------------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  if (!fn) throw Error(BSE_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  return fn;
+}
+
+// 3-D map over planes [planes][rows][Kp] of BF16, box {16, box_rows, planes}, 32-byte swizzle.
+CUtensorMap make_plane_map(const __nv_bfloat16* base, int Kp, int rows, int planes, int box_rows) {
+  CUtensorMap m;
+  cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)planes};
+  cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)Kp * 2 * rows};
+  cuuint32_t box[3] = {(cuuint32_t)tc::BK, (cuuint32_t)box_rows, (cuuint32_t)planes};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)base, dims, strides,
+                           box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    throw Error(BSE_ERR_CUDA, "cuTensorMapEncodeTiled failed with " + std::to_string((int)r));
+  return m;
+}
+
+int num_sms() {
+  int dev = 0, n = 0;
+  BSE_CUDA(cudaGetDevice(&dev));
+  BSE_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+  return n;
+}
+
+template <class Epi>
+void launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb, const std::vector<tc::Tile>& tiles,
+                 const tc::GemmShape& sh, const Epi& epi, int* d_err, cudaStream_t s) {
+  if (tiles.empty()) return;
+  DeviceBuffer dt(tiles.size() * sizeof(tc::Tile), s);
+  BSE_CUDA(cudaMemcpyAsync(dt.ptr, tiles.data(), tiles.size() * sizeof(tc::Tile),
+                           cudaMemcpyHostToDevice, s));
+  const size_t smem = tc::gemm_smem_bytes(sh);
+  auto kern = tc::gemm_split_bf16<Epi>;
+  BSE_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int grid = std::min<int>((int)tiles.size(), num_sms());
+  kern<<<grid, tc::NUM_THREADS, smem, s>>>(ma, mb, dt.as<tc::Tile>(), (int)tiles.size(), sh, epi,
+                                           d_err);
+  BSE_CUDA(cudaGetLastError());
+  note_launches(1);
+}
+
+tc::GemmShape make_shape(int nt, int Kp, int pieces) {
+  tc::GemmShape sh;
+  sh.nt = nt;
+  sh.kchunks = Kp / tc::BK;
+  sh.pieces = pieces;
+  sh.tmem_cols = 2 * nt <= 32 ? 32 : 2 * nt <= 64 ? 64 : 2 * nt <= 128 ? 128 : 2 * nt <= 256 ? 256 : 512;
+  const uint32_t sb = 2u * pieces * (tc::a_plane_bytes() + tc::b_plane_bytes(nt));
+  const size_t budget = 220 * 1024;
+  int st = (int)((budget - 2048) / sb);
+  sh.stages = std::max(1, std::min(st, 6));
+  return sh;
+}
+
+// output columns per tile: the padded N split into equal multiples of 32, each <= 256
+int tile_cols(int n_pad) {
+  int ntiles = (n_pad + 255) / 256;
+  return round_up((n_pad + ntiles - 1) / ntiles, 32);
+}
+
+// Pairs sorted by q (stable in pair order); returns perm (slot -> pair) and group bounds.
+void group_pairs(const std::vector<int32_t>& qmap, int nq, std::vector<int>& perm,
+                 std::vector<int>& group_start) {
+  const int npair = (int)qmap.size();
+  std::vector<int> count(nq + 1, 0);
+  for (int p = 0; p < npair; ++p) count[qmap[p] + 1]++;
+  for (int q = 0; q < nq; ++q) count[q + 1] += count[q];
+  group_start = count;
+  perm.assign(npair, 0);
+  std::vector<int> fill(count.begin(), count.end() - 1);
+  for (int p = 0; p < npair; ++p) perm[fill[qmap[p]]++] = p;
+}
+
+std::vector<int32_t> read_map(const int32_t* dmap, size_t n, cudaStream_t s) {
+  std::vector<int32_t> h(n);
+  BSE_CUDA(cudaMemcpyAsync(h.data(), dmap, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  BSE_CUDA(cudaStreamSynchronize(s));
+  return h;
+}
+
+struct DirectTerm {
+  const bse_c128* side;     // stage-1 operand pair array
+  int rows_side;            // rows per pair of it
+  bool w_conj_transpose;    // stage 1 with W^H instead of W
+  const int32_t* qmap;      // device
+  Stage2Args s2;            // stage-2 description (T, slots filled in here)
+};
+
+}  // namespace
+
+bool mixed_supported(int precision) {
+  return precision == BSE_PREC_BF16X6 || precision == BSE_PREC_BF16X3;
+}
+
+void build_mixed(const Problem& pr, int precision, cudaStream_t s) {
+  const bse_problem& p = pr.p;
+  const int nk = p.nk, nv = p.nv, nc = p.nc, ng = p.ng, nq = p.nq_w;
+  const int n = (int)pr.n, npair = nk * nk;
+  const int pieces = precision == BSE_PREC_BF16X6 ? 3 : 2;
+  const int planes = 2 * pieces;
+  const int Kp = round_up(ng, tc::BK);
+  const double kap = pr.kappa;
+
+  DeviceBuffer err(sizeof(int), s);
+  BSE_CUDA(cudaMemsetAsync(err.ptr, 0, sizeof(int), s));
+
+  // ---- exchange: A = E + 2 gx k V, B = 2 gx k V ----
+  {
+    Phase ph("mixed_exchange", s);
+    DeviceBuffer xa((size_t)planes * n * Kp * 2, s), xb((size_t)planes * n * Kp * 2, s);
+    SplitArgs sa{reinterpret_cast<const double2*>(p.m_x), nullptr, 1, ng, Kp, n, pieces,
+                 1, p.v_bar, xa.as<__nv_bfloat16>()};
+    launch_split(sa, s);
+    SplitArgs sb{reinterpret_cast<const double2*>(p.m_x), nullptr, 1, ng, Kp, n, pieces,
+                 0, nullptr, xb.as<__nv_bfloat16>()};
+    launch_split(sb, s);
+    const int n_pad = round_up(n, 32);
+    const int nt = tile_cols(n_pad);
+    tc::GemmShape sh = make_shape(nt, Kp, pieces);
+    CUtensorMap ma = make_plane_map(xa.as<__nv_bfloat16>(), Kp, n, planes, tc::BM);
+    CUtensorMap mb = make_plane_map(xb.as<__nv_bfloat16>(), Kp, n, planes, nt);
+    std::vector<tc::Tile> tiles;
+    for (int m0 = 0; m0 < n; m0 += tc::BM)
+      for (int n0 = 0; n0 < n; n0 += nt)
+        tiles.push_back({m0, std::min(tc::BM, n - m0), n0, n0, std::min(nt, n - n0), m0});
+    ExchangeEpi epi{reinterpret_cast<double2*>(p.A),
+                    p.coupling ? reinterpret_cast<double2*>(p.B) : nullptr,
+                    p.ld, 2.0 * p.gamma_x * kap, p.e_v, p.e_c, nv, nc};
+    launch_gemm(ma, mb, tiles, sh, epi, err.as<int>(), s);
+  }
+
+  if (p.gamma_c != 0.0) {
+    std::vector<DirectTerm> terms;
+    const bool cc_side = nc * nc <= nv * nv;
+    {
+      DirectTerm t;
+      t.side = cc_side ? p.m_cc : p.m_vv;
+      t.rows_side = cc_side ? nc * nc : nv * nv;
+      t.w_conj_transpose = !cc_side;
+      t.qmap = p.q_minus;
+      Stage2Args& a = t.s2;
+      a = Stage2Args{};
+      a.mode = cc_side ? S2_RR_CC : S2_RR_VV;
+      a.x = reinterpret_cast<const double2*>(cc_side ? p.m_vv : p.m_cc);
+      a.x_transpose_pair = 0;
+      a.conj_x = cc_side ? 1 : 0;
+      a.conj_t = cc_side ? 0 : 1;
+      a.rows_x = cc_side ? nv * nv : nc * nc;
+      a.rows_t = t.rows_side;
+      a.out = reinterpret_cast<double2*>(p.A);
+      terms.push_back(t);
+    }
+    if (p.coupling) {
+      DirectTerm t;
+      t.side = p.n_vc;
+      t.rows_side = nv * nc;
+      t.w_conj_transpose = false;
+      t.qmap = p.q_plus;
+      Stage2Args& a = t.s2;
+      a = Stage2Args{};
+      a.mode = S2_RA;
+      a.x = reinterpret_cast<const double2*>(p.n_vc);
+      a.x_transpose_pair = 1;
+      a.conj_x = 1;
+      a.conj_t = 0;
+      a.rows_x = nv * nc;
+      a.rows_t = nv * nc;
+      a.out = reinterpret_cast<double2*>(p.B);
+      terms.push_back(t);
+    }
+
+    const int ng_pad = round_up(ng, 32);
+    const int nt = tile_cols(ng_pad);
+    const int rows_max = std::max(terms[0].rows_side, terms.size() > 1 ? terms[1].rows_side : 0);
+    const int64_t side_rows_max = (int64_t)npair * rows_max;
+    DeviceBuffer wsplit((size_t)planes * nq * ng_pad * Kp * 2, s);
+    DeviceBuffer asplit((size_t)planes * side_rows_max * Kp * 2, s);
+    DeviceBuffer tbuf((size_t)ng_pad * side_rows_max * sizeof(float2), s);
+    DeviceBuffer dmap((size_t)nq * ng_pad * sizeof(int64_t), s);
+    DeviceBuffer dmap2((size_t)side_rows_max * sizeof(int64_t), s);
+    DeviceBuffer dslot((size_t)npair * sizeof(int), s);
+
+    for (const DirectTerm& t : terms) {
+      // host-side grouping of the k pairs by q
+      std::vector<int32_t> qh = read_map(t.qmap, (size_t)npair, s);
+      std::vector<int> perm, gstart;
+      group_pairs(qh, nq, perm, gstart);
+      std::vector<int> slot(npair);
+      for (int i = 0; i < npair; ++i) slot[perm[i]] = i;
+      const int64_t side_rows = (int64_t)npair * t.rows_side;
+
+      // W planes: row (q, n) holds W[q][n][.] (or W^H: conj(W[q][.][n])), zero beyond ng
+      {
+        Phase ph("mixed_split", s);
+        std::vector<int64_t> wmap((size_t)nq * ng_pad);
+        for (int q = 0; q < nq; ++q)
+          for (int g = 0; g < ng_pad; ++g)
+            wmap[(size_t)q * ng_pad + g] =
+                g >= ng ? -1
+                        : (int64_t)q * ng * ng + (t.w_conj_transpose ? (int64_t)g : (int64_t)g * ng);
+        BSE_CUDA(cudaMemcpyAsync(dmap.ptr, wmap.data(), wmap.size() * sizeof(int64_t),
+                                 cudaMemcpyHostToDevice, s));
+        SplitArgs sw{reinterpret_cast<const double2*>(p.w), dmap.as<int64_t>(),
+                     t.w_conj_transpose ? (int64_t)ng : 1, ng, Kp, nq * ng_pad, pieces,
+                     t.w_conj_transpose ? 1 : 0, nullptr, wsplit.as<__nv_bfloat16>()};
+        launch_split(sw, s);
+
+        // stage-1 operand rows in slot order: row (slot, r) <- pair perm[slot], row r
+        std::vector<int64_t> amap((size_t)side_rows);
+        for (int sl = 0; sl < npair; ++sl)
+          for (int r = 0; r < t.rows_side; ++r)
+            amap[(size_t)sl * t.rows_side + r] = ((int64_t)perm[sl] * t.rows_side + r) * ng;
+        BSE_CUDA(cudaMemcpyAsync(dmap2.ptr, amap.data(), amap.size() * sizeof(int64_t),
+                                 cudaMemcpyHostToDevice, s));
+        SplitArgs sa{reinterpret_cast<const double2*>(t.side), dmap2.as<int64_t>(), 1, ng, Kp,
+                     (int)side_rows, pieces, 0, nullptr, asplit.as<__nv_bfloat16>()};
+        launch_split(sa, s);
+        BSE_CUDA(cudaMemcpyAsync(dslot.ptr, slot.data(), slot.size() * sizeof(int),
+                                 cudaMemcpyHostToDevice, s));
+      }
+
+      // stage 1: per q group, 128-row tiles x nt-column tiles
+      {
+        Phase ph("mixed_stage1_gemm", s);
+        tc::GemmShape sh = make_shape(nt, Kp, pieces);
+        CUtensorMap ma = make_plane_map(asplit.as<__nv_bfloat16>(), Kp, (int)side_rows, planes, tc::BM);
+        CUtensorMap mb = make_plane_map(wsplit.as<__nv_bfloat16>(), Kp, nq * ng_pad, planes, nt);
+        std::vector<tc::Tile> tiles;
+        for (int q = 0; q < nq; ++q) {
+          const int64_t r0 = (int64_t)gstart[q] * t.rows_side;
+          const int64_t r1 = (int64_t)gstart[q + 1] * t.rows_side;
+          for (int64_t m0 = r0; m0 < r1; m0 += tc::BM)
+            for (int n0 = 0; n0 < ng; n0 += nt)
+              tiles.push_back({(int)m0, (int)std::min<int64_t>(tc::BM, r1 - m0), q * ng_pad + n0,
+                               n0, std::min(nt, ng - n0), (int)m0});
+        }
+        TEpi epi{tbuf.as<float2>(), side_rows};
+        launch_gemm(ma, mb, tiles, sh, epi, err.as<int>(), s);
+      }
+
+      // stage 2
+      {
+        Phase ph("mixed_stage2", s);
+        Stage2Args a = t.s2;
+        a.T = tbuf.as<float2>();
+        a.t_ld = side_rows;
+        a.slot_of_pair = dslot.as<int>();
+        a.ng = ng;
+        a.nk = nk;
+        a.nv = nv;
+        a.nc = nc;
+        a.scale = p.gamma_c * kap;
+        a.ld = p.ld;
+        launch_stage2(a, npair, s);
+      }
+    }
+  }
+
+  int herr = 0;
+  BSE_CUDA(cudaMemcpyAsync(&herr, err.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+  BSE_CUDA(cudaStreamSynchronize(s));
+  if (herr) throw Error(BSE_ERR_TIMEOUT, "tensor-core GEMM: a bounded pipeline wait expired");
+}
+
 }  // namespace bse

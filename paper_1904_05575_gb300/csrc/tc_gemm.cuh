@@ -1,0 +1,355 @@
+// Split-precision complex GEMM on the 5th-generation tensor cores (tcgen05).
+//
+//   C[m][n] = sum_k A[m][k] * B[n][k]      (complex, FP32 accumulation)
+//
+// Both operands are stored pre-split as BF16 planes: plane (comp * P + piece)
+// holds piece `piece` of the real (comp 0) or imaginary (comp 1) part, so
+// x = x_0 + x_1 + x_2 with each x_i a BF16 number.  For each K step of 16 the
+// kernel issues, for every piece pair (i, j) with i + j < P, the four real
+// products of a complex multiply-add into two TMEM accumulators:
+//   D_re += A_re,i B_re,j - A_im,i B_im,j        D_im += A_re,i B_im,j + A_im,i B_re,j
+// (the minus sign through the instruction descriptor's negate-A bit).
+// Conjugation of an operand is applied when it is split (Im stored negated).
+//
+// One CTA per SM, persistent over a list of 128-row tiles:
+//   warp 0     TMA producer: one 3-D box per operand per stage (all planes)
+//   warp 1     TMEM allocation and MMA issue (one elected thread)
+//   warps 2-5  epilogue: tcgen05.ld of D_re / D_im, then the store functor
+// Shared-memory tiles are K-major with the 32-byte swizzle (one K step of 16
+// BF16 = 32 bytes per row), the layout TMA writes and the MMA descriptor
+// reads.  Every wait on an mbarrier is bounded by a clock budget; on expiry
+// the thread records BSE_TC_TIMEOUT in *err and every role winds down.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace bse {
+namespace tc {
+
+constexpr int BM = 128;             // tile rows (UMMA M)
+constexpr int BK = 16;              // K elements per stage (32 bytes of BF16)
+constexpr int NUM_THREADS = 192;    // 6 warps
+constexpr int ERR_TIMEOUT = 1;
+constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
+
+struct Tile {
+  int a_row0;    // first row in the A planes
+  int m_valid;   // real rows of this tile (<= 128)
+  int b_row0;    // first row in the B planes
+  int n0;        // first output column
+  int n_valid;   // real output columns (<= nt)
+  int out_row0;  // first output row
+};
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity.  Returns false (after
+// recording the timeout) if the budget runs out or another role has already
+// failed.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          int* err) {
+  long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > WAIT_CYCLES) {
+      *abort_flag = 1;
+      atomicOr(err, ERR_TIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(slot)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 32-byte swizzle, 8-row groups
+// 256 bytes apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc_sw32(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);          // start address
+  d |= (uint64_t)1 << 16;                            // leading byte offset (unused here)
+  d |= (uint64_t)(256 >> 4) << 32;                   // stride byte offset
+  d |= (uint64_t)1 << 46;                            // version
+  d |= (uint64_t)6 << 61;                            // layout: 32-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: BF16 x BF16 -> F32, both K-major, M = 128.
+__host__ __device__ constexpr uint32_t idesc_bf16(int n, bool neg_a) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((neg_a ? 1u : 0u) << 13) |
+         ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct GemmShape {    // stages <= 8
+  int nt;          // output columns per tile (multiple of 32, <= 256)
+  int kchunks;     // padded K / 16
+  int pieces;      // BF16 pieces per real number (2 or 3)
+  int stages;      // pipeline depth
+  uint32_t tmem_cols;
+};
+
+__host__ __device__ inline uint32_t a_plane_bytes() { return BM * BK * 2; }
+__host__ __device__ inline uint32_t b_plane_bytes(int nt) { return (uint32_t)nt * BK * 2; }
+__host__ __device__ inline uint32_t stage_bytes(const GemmShape& s) {
+  return 2u * s.pieces * (a_plane_bytes() + b_plane_bytes(s.nt));
+}
+__host__ inline size_t gemm_smem_bytes(const GemmShape& s) {
+  return 1024 /* alignment slack */ + (size_t)s.stages * stage_bytes(s) + 64 * 8;
+}
+
+// ---------------------------------------------------------------------------
+// The kernel.  Epi provides: __device__ void operator()(const Tile&, int row,
+// int col0, const float* re, const float* im) const  for 32 columns at col0.
+// ---------------------------------------------------------------------------
+template <class Epi>
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+gemm_split_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                const Tile* __restrict__ tiles, int ntiles, GemmShape sh, Epi epi, int* err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  const uint32_t sbytes = stage_bytes(sh);
+  const uint32_t a_bytes = 2u * sh.pieces * a_plane_bytes();
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)sh.stages * sbytes);
+  uint64_t* empty = full + sh.stages;
+  uint64_t* tmem_full = empty + sh.stages;
+  uint64_t* tmem_empty = tmem_full + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tmem_empty + 1);
+  __shared__ volatile int abort_flag;
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int P = sh.pieces;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < sh.stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(tmem_full, 1);
+    mbar_init(tmem_empty, 4);
+    abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, sh.tmem_cols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int pending[8];   // parity of the latest arming of each stage, -1 = never armed
+      for (int s = 0; s < 8; ++s) pending[s] = -1;
+      for (int t = blockIdx.x; t < ntiles && !abort_flag; t += gridDim.x) {
+        const Tile tl = tiles[t];
+        for (int kc = 0; kc < sh.kchunks; ++kc) {
+          if (!mbar_wait(&empty[stage], phase ^ 1, &abort_flag, err)) break;
+          mbar_expect_tx(&full[stage], sbytes);
+          uint8_t* sa = smem + (size_t)stage * sbytes;
+          tma_load_3d(sa, &tmA, kc * BK, tl.a_row0, 0, &full[stage]);
+          tma_load_3d(sa + a_bytes, &tmB, kc * BK, tl.b_row0, 0, &full[stage]);
+          pending[stage] = (int)phase;
+          if (++stage == sh.stages) {
+            stage = 0;
+            phase ^= 1;
+          }
+        }
+      }
+      if (abort_flag) {
+        // let the copies this thread issued land before shared memory goes away:
+        // the latest arming of each stage completes when its bytes have arrived
+        long long t0 = clock64();
+        for (int s = 0; s < sh.stages; ++s)
+          if (pending[s] >= 0)
+            while (!mbar_try_wait(&full[s], (uint32_t)pending[s]) &&
+                   clock64() - t0 < WAIT_CYCLES) {
+            }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int local = 0;
+      const uint32_t d_re = tmem_base, d_im = tmem_base + (uint32_t)sh.nt;
+      const uint32_t id_pos = idesc_bf16(sh.nt, false), id_neg = idesc_bf16(sh.nt, true);
+      const uint32_t bpb = b_plane_bytes(sh.nt);
+      for (int t = blockIdx.x; t < ntiles && !abort_flag; t += gridDim.x, ++local) {
+        if (local > 0 && !mbar_wait(tmem_empty, (local - 1) & 1, &abort_flag, err)) break;
+        tc_fence_after();
+        bool ok = true;
+        for (int kc = 0; kc < sh.kchunks; ++kc) {
+          if (!mbar_wait(&full[stage], phase, &abort_flag, err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + (size_t)stage * sbytes);
+          const uint32_t sb = sa + a_bytes;
+          uint32_t acc_re = kc > 0, acc_im = kc > 0;
+          for (int i = 0; i < P; ++i) {
+            for (int j = 0; i + j < P; ++j) {
+              const uint64_t a_re = smem_desc_sw32(sa + (uint32_t)i * a_plane_bytes());
+              const uint64_t a_im = smem_desc_sw32(sa + (uint32_t)(P + i) * a_plane_bytes());
+              const uint64_t b_re = smem_desc_sw32(sb + (uint32_t)j * bpb);
+              const uint64_t b_im = smem_desc_sw32(sb + (uint32_t)(P + j) * bpb);
+              mma_bf16(d_re, a_re, b_re, id_pos, acc_re);
+              acc_re = 1;
+              mma_bf16(d_re, a_im, b_im, id_neg, 1);
+              mma_bf16(d_im, a_re, b_im, id_pos, acc_im);
+              acc_im = 1;
+              mma_bf16(d_im, a_im, b_re, id_pos, 1);
+            }
+          }
+          mma_commit(&empty[stage]);   // frees this stage once its MMAs complete
+          if (++stage == sh.stages) {
+            stage = 0;
+            phase ^= 1;
+          }
+        }
+        if (!ok) break;
+        mma_commit(tmem_full);
+      }
+    }
+  } else {
+    // ---------------- epilogue (warps 2..5) ----------------
+    const int quarter = warp & 3;    // TMEM lanes this warp may access
+    const int row = quarter * 32 + lane;
+    int local = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++local) {
+      // one lane waits, the warp follows (the tcgen05.ld below is warp-collective)
+      int ok = 0;
+      if (lane == 0) ok = mbar_wait(tmem_full, local & 1, &abort_flag, err) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      __syncwarp();
+      tc_fence_after();
+      const Tile tl = tiles[t];
+      float re[32], im[32];
+      const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
+      for (int c0 = 0; c0 < sh.nt; c0 += 32) {
+        tmem_ld32(lane_base + (uint32_t)c0, re);
+        tmem_ld32(lane_base + (uint32_t)(sh.nt + c0), im);
+        if (row < tl.m_valid && c0 < tl.n_valid) epi(tl, row, c0, re, im);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tmem_empty);
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, sh.tmem_cols);
+  }
+}
+
+}  // namespace tc
+}  // namespace bse
