@@ -26,7 +26,11 @@
  *   - cuda_stream is a cudaStream_t (NULL = legacy default stream).  Work is
  *     enqueued on it; functions documented as "syncs" wait for it.
  *   - Workspace is allocated with cudaMallocAsync on cuda_stream and freed
- *     before return (stream-ordered).
+ *     before return (stream-ordered).  On first use of a device the library
+ *     raises the release threshold of that device's default memory pool so
+ *     that freed workspace stays in the pool for the next call.  Small
+ *     grouping plans of bse_build_kernel (k pairs sorted by q, tile lists)
+ *     are cached in device memory per shape and q map until process exit.
  */
 #ifndef BSE_H
 #define BSE_H

@@ -80,7 +80,8 @@ int guarded(F&& f) {
 
 namespace {
 
-void check_q_map(const int32_t* dmap, int nk, int nq_w, const char* name, cudaStream_t s) {
+std::vector<int32_t> check_q_map(const int32_t* dmap, int nk, int nq_w, const char* name,
+                                 cudaStream_t s) {
   std::vector<int32_t> h((size_t)nk * nk);
   BSE_CUDA(cudaMemcpyAsync(h.data(), dmap, h.size() * sizeof(int32_t), cudaMemcpyDeviceToHost,
                            s));
@@ -90,6 +91,26 @@ void check_q_map(const int32_t* dmap, int nk, int nq_w, const char* name, cudaSt
       throw Error(BSE_ERR_ARG, std::string(name) + "[" + std::to_string(i / nk) + "][" +
                                    std::to_string(i % nk) + "] = " + std::to_string(h[i]) +
                                    " is outside [0, nq_w = " + std::to_string(nq_w) + ")");
+  return h;
+}
+
+// Keep stream-ordered workspace in the device's default pool between calls
+// instead of returning it to the driver at every synchronization.
+void keep_pool_memory() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  static std::mutex m;
+  static std::vector<bool> done;
+  std::lock_guard<std::mutex> lock(m);
+  if ((int)done.size() <= dev) done.resize(dev + 1, false);
+  if (done[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  (void)cudaGetLastError();
+  done[dev] = true;
 }
 
 Problem validate(const bse_problem& p, int index, cudaStream_t s) {
@@ -109,11 +130,11 @@ Problem validate(const bse_problem& p, int index, cudaStream_t s) {
     if (p.coupling) BSE_CHECK_ARG(p.n_vc && p.q_plus, at + "NULL n_vc or q_plus");
   }
   if (p.coupling) BSE_CHECK_ARG(p.B, at + "coupling = 1 needs B");
-  if (p.gamma_c != 0.0) {
-    check_q_map(p.q_minus, p.nk, p.nq_w, "q_minus", s);
-    if (p.coupling) check_q_map(p.q_plus, p.nk, p.nq_w, "q_plus", s);
-  }
   Problem pr;
+  if (p.gamma_c != 0.0) {
+    pr.qm_host = check_q_map(p.q_minus, p.nk, p.nq_w, "q_minus", s);
+    if (p.coupling) pr.qp_host = check_q_map(p.q_plus, p.nk, p.nq_w, "q_plus", s);
+  }
   pr.p = p;
   pr.n = n;
   pr.kappa = kHartreeEv / ((double)p.nk * p.omega_cell);
@@ -135,6 +156,7 @@ extern "C" int bse_build_kernel(const bse_problem* probs, int32_t nprob, int32_t
     BSE_CHECK_ARG(precision == BSE_PREC_FP64 || precision == BSE_PREC_BF16X6 ||
                       precision == BSE_PREC_BF16X3,
                   "unknown precision " + std::to_string(precision));
+    keep_pool_memory();
     std::vector<Problem> prs;
     prs.reserve(nprob);
     for (int i = 0; i < nprob; ++i) prs.push_back(validate(probs[i], i, s));
@@ -156,6 +178,7 @@ extern "C" int bse_reduce(int32_t n, const bse_c128* A, const bse_c128* B, int64
     BSE_CHECK_ARG(A && S && L, "NULL A, S or L");
     BSE_CHECK_ARG(S != L && S != A && L != A && (B == nullptr || (S != B && L != B)),
                   "S and L must not alias A, B or each other");
+    keep_pool_memory();
     reduce_fp64(n, A, B, ld, S, L, failed_minor, static_cast<cudaStream_t>(cuda_stream));
   });
 }
@@ -173,6 +196,7 @@ extern "C" int bse_spectrum(int32_t n, bse_c128* S_inout, const bse_c128* L, int
     BSE_CHECK_ARG(std::isfinite(vc) && vc > 0.0, "vc must be > 0");
     BSE_CHECK_ARG(std::isfinite(c_q) && std::isfinite(delta) && delta >= 0.0,
                   "c_q must be finite and delta >= 0");
+    keep_pool_memory();
     spectrum_fp64(n, S_inout, L, ld, rho, c_q, vc, n_omega, omega, delta, E_out, osc_out,
                   eps_out, static_cast<cudaStream_t>(cuda_stream));
   });

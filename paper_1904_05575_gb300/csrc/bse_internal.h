@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <stdexcept>
 #include <string>
+#include <vector>
 
 #include "../../include/bse.h"
 
@@ -83,6 +84,7 @@ struct Problem {
   bse_problem p;
   int64_t n;          // nk * nv * nc
   double kappa;       // Ha / (nk * omega_cell)
+  std::vector<int32_t> qm_host, qp_host;   // host copies of q_minus / q_plus (checked)
 };
 
 // FP64 build (CUDA cores).  Writes A (and B when coupling) completely.

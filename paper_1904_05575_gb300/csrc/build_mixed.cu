@@ -18,10 +18,13 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <numeric>
 #include <vector>
 
+#include "bits.cuh"
 #include "bse_internal.h"
 #include "tc_gemm.cuh"
 
@@ -33,11 +36,19 @@ int round_up(int x, int m) { return (x + m - 1) / m * m; }
 // ---------------------------------------------------------------------------
 // split: one thread per (output row, k); P pieces per real number
 // ---------------------------------------------------------------------------
+enum SplitMode { SPLIT_DENSE = 0, SPLIT_PAIRS = 1, SPLIT_W = 2 };
+
 struct SplitArgs {
   const double2* src;
-  const int64_t* row_off;   // output row -> element offset of its k = 0 entry (-1: zero row);
-                            // NULL: row * K (dense rows)
-  int64_t k_stride;         // elements between consecutive k of one row
+  int mode;
+  // SPLIT_DENSE: row r is src[r * K + k]
+  // SPLIT_PAIRS: row r = (slot, j) with rows_per rows per slot is the j-th row of
+  //              pair perm[slot]: src[(perm[slot] * rows_per + j) * K + k]
+  // SPLIT_W:     row r = (q, g) with rows_per = padded G per q; g >= K is a zero
+  //              row; W[q][g][k] (or, transposed, W[q][k][g])
+  const int* perm;
+  int rows_per;
+  int transpose;
   int K;                    // real K
   int Kp;                   // padded K (multiple of 16)
   int rows;                 // output rows
@@ -47,41 +58,65 @@ struct SplitArgs {
   __nv_bfloat16* out;       // [2 * pieces][rows][Kp]
 };
 
-__device__ __forceinline__ void split_real(double x, int pieces, __nv_bfloat16* out, int64_t plane) {
-  double r = x;
-  for (int i = 0; i < pieces; ++i) {
-    __nv_bfloat16 h = __float2bfloat16_rn((float)r);
-    out[i * plane] = h;
-    r -= (double)__bfloat162float(h);
+// 8 consecutive reals -> P planes of 8 BF16 each (16-byte stores), integer split
+__device__ __forceinline__ void split_real8(const double* x, int pieces, __nv_bfloat16* out,
+                                            int64_t plane) {
+  __align__(16) uint16_t h[3][8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    uint16_t t[3];
+    split_bf16_bits(x[e], pieces, t);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) h[i][e] = t[i];
   }
+  for (int i = 0; i < pieces; ++i)
+    *reinterpret_cast<uint4*>(out + i * plane) = *reinterpret_cast<const uint4*>(h[i]);
 }
 
+// one thread per (output row, 8 consecutive k): 16-byte stores into every plane
 __global__ void k_split(SplitArgs a) {
-  const int64_t total = (int64_t)a.rows * a.Kp;
-  const int64_t plane = total;
+  const int kg = a.Kp / 8;
+  const int64_t total = (int64_t)a.rows * kg;
+  const int64_t plane = (int64_t)a.rows * a.Kp;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int row = (int)(i / a.Kp), k = (int)(i % a.Kp);
-    double2 x = make_double2(0.0, 0.0);
-    const int64_t off = a.row_off ? a.row_off[row] : (int64_t)row * a.K;
-    if (k < a.K && off >= 0) {
-      x = a.src[off + (int64_t)k * a.k_stride];
-      if (a.conj) x.y = -x.y;
-      if (a.kscale) {
-        const double s = a.kscale[k];
-        x.x *= s;
-        x.y *= s;
-      }
+    const int row = (int)(i / kg), k0 = (int)(i % kg) * 8;
+    int64_t off = (int64_t)row * a.K, kstride = 1;
+    if (a.mode == SPLIT_PAIRS) {
+      const int slot = row / a.rows_per, j = row % a.rows_per;
+      off = ((int64_t)a.perm[slot] * a.rows_per + j) * a.K;
+    } else if (a.mode == SPLIT_W) {
+      const int q = row / a.rows_per, g = row % a.rows_per;
+      off = g >= a.K ? -1 : (int64_t)q * a.K * a.K + (a.transpose ? g : (int64_t)g * a.K);
+      kstride = a.transpose ? a.K : 1;
     }
-    split_real(x.x, a.pieces, a.out + i, plane);
-    split_real(x.y, a.pieces, a.out + (int64_t)a.pieces * plane + i, plane);
+    double xr[8], xi[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int k = k0 + e;
+      double2 x = make_double2(0.0, 0.0);
+      if (k < a.K && off >= 0) {
+        x = __ldg(a.src + off + (int64_t)k * kstride);
+        if (a.conj) x.y = -x.y;
+        if (a.kscale) {
+          const double s = a.kscale[k];
+          x.x *= s;
+          x.y *= s;
+        }
+      }
+      xr[e] = x.x;
+      xi[e] = x.y;
+    }
+    const int64_t o = (int64_t)row * a.Kp + k0;
+    split_real8(xr, a.pieces, a.out + o, plane);
+    split_real8(xi, a.pieces, a.out + (int64_t)a.pieces * plane + o, plane);
   }
 }
 
 void launch_split(const SplitArgs& a, cudaStream_t s) {
-  const int64_t total = (int64_t)a.rows * a.Kp;
+  const int64_t total = (int64_t)a.rows * (a.Kp / 8);
   int64_t blocks = (total + 255) / 256;
-  if (blocks > 152 * 64) blocks = 152 * 64;
+  if (blocks > 152 * 16) blocks = 152 * 16;
   k_split<<<(int)std::max<int64_t>(blocks, 1), 256, 0, s>>>(a);
   BSE_CUDA(cudaGetLastError());
   note_launches(1);
@@ -164,19 +199,26 @@ __global__ void __launch_bounds__((TS / R) * (TS / R)) k_stage2(Stage2Args a) {
   const int64_t trow0 = (int64_t)a.slot_of_pair[p] * a.rows_t;
   const int tid = threadIdx.x;
   const int tx = tid % (TS / R), ty = tid / (TS / R);
-  float accx[R][R], accy[R][R];
+  // FP32 sums over one chunk of 32 plane waves, promoted to FP64 between chunks
+  double sumx[R][R], sumy[R][R];
 #pragma unroll
   for (int i = 0; i < R; ++i)
 #pragma unroll
-    for (int j = 0; j < R; ++j) accx[i][j] = accy[i][j] = 0.f;
+    for (int j = 0; j < R; ++j) sumx[i][j] = sumy[i][j] = 0.0;
 
   for (int g0 = 0; g0 < a.ng; g0 += GC) {
+    float accx[R][R], accy[R][R];
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+      for (int j = 0; j < R; ++j) accx[i][j] = accy[i][j] = 0.f;
     for (int i = tid; i < TS * GC; i += NTH) {
       const int r = i / GC, g = i % GC;
       float2 v = make_float2(0.f, 0.f);
       if (rx0 + r < a.rows_x && g0 + g < a.ng) {
-        const double2 d = X[(int64_t)(rx0 + r) * a.ng + g0 + g];
-        v = make_float2((float)d.x, a.conj_x ? -(float)d.y : (float)d.y);
+        const double2 d = __ldg(X + (int64_t)(rx0 + r) * a.ng + g0 + g);
+        const float dy = f64_to_f32_bits(d.y);
+        v = make_float2(f64_to_f32_bits(d.x), a.conj_x ? -dy : dy);
       }
       Xs[r][g] = v;
     }
@@ -207,6 +249,13 @@ __global__ void __launch_bounds__((TS / R) * (TS / R)) k_stage2(Stage2Args a) {
           accy[i][j] = fmaf(xv[i].y, tv[j].x, accy[i][j]);
         }
     }
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        sumx[i][j] += (double)accx[i][j];
+        sumy[i][j] += (double)accy[i][j];
+      }
     __syncthreads();
   }
 
@@ -229,8 +278,8 @@ __global__ void __launch_bounds__((TS / R) * (TS / R)) k_stage2(Stage2Args a) {
       const int64_t ap = ((int64_t)kp * nv + vp) * nc + cp;
       double2* dst = a.out + al + ap * a.ld;
       double2 o = *dst;
-      o.x -= a.scale * (double)accx[i][j];
-      o.y -= a.scale * (double)accy[i][j];
+      o.x -= a.scale * sumx[i][j];
+      o.y -= a.scale * sumy[i][j];
       *dst = o;
     }
 }
@@ -288,18 +337,14 @@ int num_sms() {
 }
 
 template <class Epi>
-void launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb, const std::vector<tc::Tile>& tiles,
+void launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb, const tc::Tile* d_tiles, int ntiles,
                  const tc::GemmShape& sh, const Epi& epi, int* d_err, cudaStream_t s) {
-  if (tiles.empty()) return;
-  DeviceBuffer dt(tiles.size() * sizeof(tc::Tile), s);
-  BSE_CUDA(cudaMemcpyAsync(dt.ptr, tiles.data(), tiles.size() * sizeof(tc::Tile),
-                           cudaMemcpyHostToDevice, s));
+  if (ntiles == 0) return;
   const size_t smem = tc::gemm_smem_bytes(sh);
   auto kern = tc::gemm_split_bf16<Epi>;
   BSE_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const int grid = std::min<int>((int)tiles.size(), num_sms());
-  kern<<<grid, tc::NUM_THREADS, smem, s>>>(ma, mb, dt.as<tc::Tile>(), (int)tiles.size(), sh, epi,
-                                           d_err);
+  const int grid = std::min<int>(ntiles, num_sms());
+  kern<<<grid, tc::NUM_THREADS, smem, s>>>(ma, mb, d_tiles, ntiles, sh, epi, d_err);
   BSE_CUDA(cudaGetLastError());
   note_launches(1);
 }
@@ -309,7 +354,7 @@ tc::GemmShape make_shape(int nt, int Kp, int pieces) {
   sh.nt = nt;
   sh.kchunks = Kp / tc::BK;
   sh.pieces = pieces;
-  sh.tmem_cols = 2 * nt <= 32 ? 32 : 2 * nt <= 64 ? 64 : 2 * nt <= 128 ? 128 : 2 * nt <= 256 ? 256 : 512;
+  sh.tmem_cols = 4 * nt <= 128 ? 128 : 4 * nt <= 256 ? 256 : 512;
   const uint32_t sb = 2u * pieces * (tc::a_plane_bytes() + tc::b_plane_bytes(nt));
   const size_t budget = 220 * 1024;
   int st = (int)((budget - 2048) / sb);
@@ -317,9 +362,9 @@ tc::GemmShape make_shape(int nt, int Kp, int pieces) {
   return sh;
 }
 
-// output columns per tile: the padded N split into equal multiples of 32, each <= 256
+// output columns per tile: the padded N split into equal multiples of 32, each <= 128
 int tile_cols(int n_pad) {
-  int ntiles = (n_pad + 255) / 256;
+  int ntiles = (n_pad + 127) / 128;
   return round_up((n_pad + ntiles - 1) / ntiles, 32);
 }
 
@@ -336,20 +381,118 @@ void group_pairs(const std::vector<int32_t>& qmap, int nq, std::vector<int>& per
   for (int p = 0; p < npair; ++p) perm[fill[qmap[p]]++] = p;
 }
 
-std::vector<int32_t> read_map(const int32_t* dmap, size_t n, cudaStream_t s) {
-  std::vector<int32_t> h(n);
-  BSE_CUDA(cudaMemcpyAsync(h.data(), dmap, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  BSE_CUDA(cudaStreamSynchronize(s));
+// ---------------------------------------------------------------------------
+// plan: grouping of the k pairs by q and the tile lists, cached per shape and
+// q-map content (device copies kept until exit)
+// ---------------------------------------------------------------------------
+struct TermPlan {
+  int rows_side = 0;
+  int ntiles = 0;
+  int* perm = nullptr;         // slot -> pair
+  int* slot = nullptr;         // pair -> slot
+  tc::Tile* tiles = nullptr;
+};
+
+struct Plan {
+  int exchange_tiles = 0;
+  tc::Tile* xtiles = nullptr;
+  TermPlan rr, ra;
+};
+
+struct PlanKey {
+  int dev, nk, nv, nc, ng, nq, coupling, direct;
+  uint64_t hash;
+  bool operator<(const PlanKey& o) const {
+    return std::tie(dev, nk, nv, nc, ng, nq, coupling, direct, hash) <
+           std::tie(o.dev, o.nk, o.nv, o.nc, o.ng, o.nq, o.coupling, o.direct, o.hash);
+  }
+};
+
+std::mutex g_plan_mutex;
+std::map<PlanKey, Plan> g_plans;
+
+uint64_t fnv1a(const std::vector<int32_t>& v, uint64_t h = 1469598103934665603ull) {
+  for (int32_t x : v) {
+    h ^= (uint32_t)x;
+    h *= 1099511628211ull;
+  }
   return h;
 }
 
-struct DirectTerm {
-  const bse_c128* side;     // stage-1 operand pair array
-  int rows_side;            // rows per pair of it
-  bool w_conj_transpose;    // stage 1 with W^H instead of W
-  const int32_t* qmap;      // device
-  Stage2Args s2;            // stage-2 description (T, slots filled in here)
-};
+template <class T>
+T* upload_persistent(const std::vector<T>& v) {
+  T* d = nullptr;
+  if (v.empty()) return nullptr;
+  BSE_CUDA(cudaMalloc(&d, v.size() * sizeof(T)));
+  BSE_CUDA(cudaMemcpy(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return d;
+}
+
+TermPlan make_term_plan(const std::vector<int32_t>& qh, int nq, int npair, int rows_side, int ng,
+                        int ng_pad, int nt) {
+  TermPlan tp;
+  tp.rows_side = rows_side;
+  std::vector<int> perm, gstart;
+  group_pairs(qh, nq, perm, gstart);
+  std::vector<int> slot(npair);
+  for (int i = 0; i < npair; ++i) slot[perm[i]] = i;
+  // 128-row tiles inside each q group; the n tiles of one m tile are adjacent in
+  // the list so the second read of the A rows hits L2
+  std::vector<tc::Tile> tiles;
+  for (int q = 0; q < nq; ++q) {
+    const int64_t r0 = (int64_t)gstart[q] * rows_side, r1 = (int64_t)gstart[q + 1] * rows_side;
+    for (int64_t m0 = r0; m0 < r1; m0 += tc::BM)
+      for (int n0 = 0; n0 < ng; n0 += nt)
+        tiles.push_back({(int)m0, (int)std::min<int64_t>(tc::BM, r1 - m0), q * ng_pad + n0, n0,
+                         std::min(nt, ng - n0), (int)m0});
+  }
+  tp.ntiles = (int)tiles.size();
+  tp.perm = upload_persistent(perm);
+  tp.slot = upload_persistent(slot);
+  tp.tiles = upload_persistent(tiles);
+  return tp;
+}
+
+const Plan& get_plan(const Problem& pr, bool direct, int nt_x, int nt_g, int ng_pad) {
+  const bse_problem& p = pr.p;
+  int dev = 0;
+  BSE_CUDA(cudaGetDevice(&dev));
+  uint64_t h = fnv1a(pr.qm_host);
+  h = fnv1a(pr.qp_host, h);
+  PlanKey key{dev, p.nk, p.nv, p.nc, p.ng, p.nq_w, p.coupling, direct ? 1 : 0, h};
+  std::lock_guard<std::mutex> lock(g_plan_mutex);
+  auto it = g_plans.find(key);
+  if (it != g_plans.end()) return it->second;
+  if (g_plans.size() >= 32) {     // bounded: drop everything, plans are cheap to rebuild
+    for (auto& kv : g_plans) {
+      Plan& q = kv.second;
+      cudaFree(q.xtiles);
+      for (TermPlan* t : {&q.rr, &q.ra}) {
+        cudaFree(t->perm);
+        cudaFree(t->slot);
+        cudaFree(t->tiles);
+      }
+    }
+    g_plans.clear();
+  }
+  Plan plan;
+  const int n = (int)pr.n;
+  std::vector<tc::Tile> xt;
+  for (int m0 = 0; m0 < n; m0 += tc::BM)
+    for (int n0 = 0; n0 < n; n0 += nt_x)
+      xt.push_back({m0, std::min(tc::BM, n - m0), n0, n0, std::min(nt_x, n - n0), m0});
+  plan.exchange_tiles = (int)xt.size();
+  plan.xtiles = upload_persistent(xt);
+  if (direct) {
+    const int npair = p.nk * p.nk;
+    const bool cc_side = p.nc * p.nc <= p.nv * p.nv;
+    plan.rr = make_term_plan(pr.qm_host, p.nq_w, npair, cc_side ? p.nc * p.nc : p.nv * p.nv,
+                             p.ng, ng_pad, nt_g);
+    if (p.coupling)
+      plan.ra = make_term_plan(pr.qp_host, p.nq_w, npair, p.nv * p.nc, p.ng, ng_pad, nt_g);
+  }
+  return g_plans.emplace(key, plan).first->second;
+}
 
 }  // namespace
 
@@ -364,7 +507,12 @@ void build_mixed(const Problem& pr, int precision, cudaStream_t s) {
   const int pieces = precision == BSE_PREC_BF16X6 ? 3 : 2;
   const int planes = 2 * pieces;
   const int Kp = round_up(ng, tc::BK);
+  const int ng_pad = round_up(ng, 32);
+  const int nt_x = tile_cols(round_up(n, 32));
+  const int nt_g = tile_cols(ng_pad);
   const double kap = pr.kappa;
+  const bool direct = p.gamma_c != 0.0;
+  const Plan plan = get_plan(pr, direct, nt_x, nt_g, ng_pad);   // copy: the cache may evict
 
   DeviceBuffer err(sizeof(int), s);
   BSE_CUDA(cudaMemsetAsync(err.ptr, 0, sizeof(int), s));
@@ -373,56 +521,48 @@ void build_mixed(const Problem& pr, int precision, cudaStream_t s) {
   {
     Phase ph("mixed_exchange", s);
     DeviceBuffer xa((size_t)planes * n * Kp * 2, s), xb((size_t)planes * n * Kp * 2, s);
-    SplitArgs sa{reinterpret_cast<const double2*>(p.m_x), nullptr, 1, ng, Kp, n, pieces,
-                 1, p.v_bar, xa.as<__nv_bfloat16>()};
+    SplitArgs sa{reinterpret_cast<const double2*>(p.m_x), SPLIT_DENSE, nullptr, 0, 0, ng, Kp, n,
+                 pieces, 1, p.v_bar, xa.as<__nv_bfloat16>()};
     launch_split(sa, s);
-    SplitArgs sb{reinterpret_cast<const double2*>(p.m_x), nullptr, 1, ng, Kp, n, pieces,
-                 0, nullptr, xb.as<__nv_bfloat16>()};
+    SplitArgs sb = sa;
+    sb.conj = 0;
+    sb.kscale = nullptr;
+    sb.out = xb.as<__nv_bfloat16>();
     launch_split(sb, s);
-    const int n_pad = round_up(n, 32);
-    const int nt = tile_cols(n_pad);
-    tc::GemmShape sh = make_shape(nt, Kp, pieces);
+    tc::GemmShape sh = make_shape(nt_x, Kp, pieces);
     CUtensorMap ma = make_plane_map(xa.as<__nv_bfloat16>(), Kp, n, planes, tc::BM);
-    CUtensorMap mb = make_plane_map(xb.as<__nv_bfloat16>(), Kp, n, planes, nt);
-    std::vector<tc::Tile> tiles;
-    for (int m0 = 0; m0 < n; m0 += tc::BM)
-      for (int n0 = 0; n0 < n; n0 += nt)
-        tiles.push_back({m0, std::min(tc::BM, n - m0), n0, n0, std::min(nt, n - n0), m0});
+    CUtensorMap mb = make_plane_map(xb.as<__nv_bfloat16>(), Kp, n, planes, nt_x);
     ExchangeEpi epi{reinterpret_cast<double2*>(p.A),
                     p.coupling ? reinterpret_cast<double2*>(p.B) : nullptr,
                     p.ld, 2.0 * p.gamma_x * kap, p.e_v, p.e_c, nv, nc};
-    launch_gemm(ma, mb, tiles, sh, epi, err.as<int>(), s);
+    launch_gemm(ma, mb, plan.xtiles, plan.exchange_tiles, sh, epi, err.as<int>(), s);
   }
 
-  if (p.gamma_c != 0.0) {
-    std::vector<DirectTerm> terms;
+  if (direct) {
     const bool cc_side = nc * nc <= nv * nv;
+    struct Term {
+      const TermPlan* tp;
+      const bse_c128* side;
+      bool w_conj_transpose;
+      Stage2Args s2;
+    };
+    std::vector<Term> terms;
     {
-      DirectTerm t;
-      t.side = cc_side ? p.m_cc : p.m_vv;
-      t.rows_side = cc_side ? nc * nc : nv * nv;
-      t.w_conj_transpose = !cc_side;
-      t.qmap = p.q_minus;
+      Term t{&plan.rr, cc_side ? p.m_cc : p.m_vv, !cc_side, Stage2Args{}};
       Stage2Args& a = t.s2;
-      a = Stage2Args{};
       a.mode = cc_side ? S2_RR_CC : S2_RR_VV;
       a.x = reinterpret_cast<const double2*>(cc_side ? p.m_vv : p.m_cc);
       a.x_transpose_pair = 0;
       a.conj_x = cc_side ? 1 : 0;
       a.conj_t = cc_side ? 0 : 1;
       a.rows_x = cc_side ? nv * nv : nc * nc;
-      a.rows_t = t.rows_side;
+      a.rows_t = plan.rr.rows_side;
       a.out = reinterpret_cast<double2*>(p.A);
       terms.push_back(t);
     }
     if (p.coupling) {
-      DirectTerm t;
-      t.side = p.n_vc;
-      t.rows_side = nv * nc;
-      t.w_conj_transpose = false;
-      t.qmap = p.q_plus;
+      Term t{&plan.ra, p.n_vc, false, Stage2Args{}};
       Stage2Args& a = t.s2;
-      a = Stage2Args{};
       a.mode = S2_RA;
       a.x = reinterpret_cast<const double2*>(p.n_vc);
       a.x_transpose_pair = 1;
@@ -433,83 +573,42 @@ void build_mixed(const Problem& pr, int precision, cudaStream_t s) {
       a.out = reinterpret_cast<double2*>(p.B);
       terms.push_back(t);
     }
-
-    const int ng_pad = round_up(ng, 32);
-    const int nt = tile_cols(ng_pad);
-    const int rows_max = std::max(terms[0].rows_side, terms.size() > 1 ? terms[1].rows_side : 0);
+    int rows_max = 0;
+    for (const Term& t : terms) rows_max = std::max(rows_max, t.tp->rows_side);
     const int64_t side_rows_max = (int64_t)npair * rows_max;
     DeviceBuffer wsplit((size_t)planes * nq * ng_pad * Kp * 2, s);
     DeviceBuffer asplit((size_t)planes * side_rows_max * Kp * 2, s);
     DeviceBuffer tbuf((size_t)ng_pad * side_rows_max * sizeof(float2), s);
-    DeviceBuffer dmap((size_t)nq * ng_pad * sizeof(int64_t), s);
-    DeviceBuffer dmap2((size_t)side_rows_max * sizeof(int64_t), s);
-    DeviceBuffer dslot((size_t)npair * sizeof(int), s);
+    tc::GemmShape sh = make_shape(nt_g, Kp, pieces);
 
-    for (const DirectTerm& t : terms) {
-      // host-side grouping of the k pairs by q
-      std::vector<int32_t> qh = read_map(t.qmap, (size_t)npair, s);
-      std::vector<int> perm, gstart;
-      group_pairs(qh, nq, perm, gstart);
-      std::vector<int> slot(npair);
-      for (int i = 0; i < npair; ++i) slot[perm[i]] = i;
-      const int64_t side_rows = (int64_t)npair * t.rows_side;
-
-      // W planes: row (q, n) holds W[q][n][.] (or W^H: conj(W[q][.][n])), zero beyond ng
+    for (const Term& t : terms) {
+      const int64_t side_rows = (int64_t)npair * t.tp->rows_side;
       {
         Phase ph("mixed_split", s);
-        std::vector<int64_t> wmap((size_t)nq * ng_pad);
-        for (int q = 0; q < nq; ++q)
-          for (int g = 0; g < ng_pad; ++g)
-            wmap[(size_t)q * ng_pad + g] =
-                g >= ng ? -1
-                        : (int64_t)q * ng * ng + (t.w_conj_transpose ? (int64_t)g : (int64_t)g * ng);
-        BSE_CUDA(cudaMemcpyAsync(dmap.ptr, wmap.data(), wmap.size() * sizeof(int64_t),
-                                 cudaMemcpyHostToDevice, s));
-        SplitArgs sw{reinterpret_cast<const double2*>(p.w), dmap.as<int64_t>(),
-                     t.w_conj_transpose ? (int64_t)ng : 1, ng, Kp, nq * ng_pad, pieces,
+        // W planes: row (q, g) = W[q][g][.] (or W^H: conj(W[q][.][g])), zero beyond ng
+        SplitArgs sw{reinterpret_cast<const double2*>(p.w), SPLIT_W, nullptr, ng_pad,
+                     t.w_conj_transpose ? 1 : 0, ng, Kp, nq * ng_pad, pieces,
                      t.w_conj_transpose ? 1 : 0, nullptr, wsplit.as<__nv_bfloat16>()};
         launch_split(sw, s);
-
-        // stage-1 operand rows in slot order: row (slot, r) <- pair perm[slot], row r
-        std::vector<int64_t> amap((size_t)side_rows);
-        for (int sl = 0; sl < npair; ++sl)
-          for (int r = 0; r < t.rows_side; ++r)
-            amap[(size_t)sl * t.rows_side + r] = ((int64_t)perm[sl] * t.rows_side + r) * ng;
-        BSE_CUDA(cudaMemcpyAsync(dmap2.ptr, amap.data(), amap.size() * sizeof(int64_t),
-                                 cudaMemcpyHostToDevice, s));
-        SplitArgs sa{reinterpret_cast<const double2*>(t.side), dmap2.as<int64_t>(), 1, ng, Kp,
-                     (int)side_rows, pieces, 0, nullptr, asplit.as<__nv_bfloat16>()};
+        // stage-1 operand rows in slot order (pairs grouped by q)
+        SplitArgs sa{reinterpret_cast<const double2*>(t.side), SPLIT_PAIRS, t.tp->perm,
+                     t.tp->rows_side, 0, ng, Kp, (int)side_rows, pieces, 0, nullptr,
+                     asplit.as<__nv_bfloat16>()};
         launch_split(sa, s);
-        BSE_CUDA(cudaMemcpyAsync(dslot.ptr, slot.data(), slot.size() * sizeof(int),
-                                 cudaMemcpyHostToDevice, s));
       }
-
-      // stage 1: per q group, 128-row tiles x nt-column tiles
       {
         Phase ph("mixed_stage1_gemm", s);
-        tc::GemmShape sh = make_shape(nt, Kp, pieces);
         CUtensorMap ma = make_plane_map(asplit.as<__nv_bfloat16>(), Kp, (int)side_rows, planes, tc::BM);
-        CUtensorMap mb = make_plane_map(wsplit.as<__nv_bfloat16>(), Kp, nq * ng_pad, planes, nt);
-        std::vector<tc::Tile> tiles;
-        for (int q = 0; q < nq; ++q) {
-          const int64_t r0 = (int64_t)gstart[q] * t.rows_side;
-          const int64_t r1 = (int64_t)gstart[q + 1] * t.rows_side;
-          for (int64_t m0 = r0; m0 < r1; m0 += tc::BM)
-            for (int n0 = 0; n0 < ng; n0 += nt)
-              tiles.push_back({(int)m0, (int)std::min<int64_t>(tc::BM, r1 - m0), q * ng_pad + n0,
-                               n0, std::min(nt, ng - n0), (int)m0});
-        }
+        CUtensorMap mb = make_plane_map(wsplit.as<__nv_bfloat16>(), Kp, nq * ng_pad, planes, nt_g);
         TEpi epi{tbuf.as<float2>(), side_rows};
-        launch_gemm(ma, mb, tiles, sh, epi, err.as<int>(), s);
+        launch_gemm(ma, mb, t.tp->tiles, t.tp->ntiles, sh, epi, err.as<int>(), s);
       }
-
-      // stage 2
       {
         Phase ph("mixed_stage2", s);
         Stage2Args a = t.s2;
         a.T = tbuf.as<float2>();
         a.t_ld = side_rows;
-        a.slot_of_pair = dslot.as<int>();
+        a.slot_of_pair = t.tp->slot;
         a.ng = ng;
         a.nk = nk;
         a.nv = nv;

@@ -6,9 +6,14 @@
 // holds piece `piece` of the real (comp 0) or imaginary (comp 1) part, so
 // x = x_0 + x_1 + x_2 with each x_i a BF16 number.  For each K step of 16 the
 // kernel issues, for every piece pair (i, j) with i + j < P, the four real
-// products of a complex multiply-add into two TMEM accumulators:
-//   D_re += A_re,i B_re,j - A_im,i B_im,j        D_im += A_re,i B_im,j + A_im,i B_re,j
+// products of a complex multiply-add:
+//   re += A_re,i B_re,j - A_im,i B_im,j        im += A_re,i B_im,j + A_im,i B_re,j
 // (the minus sign through the instruction descriptor's negate-A bit).
+// The leading products (i = j = 0) go to a "main" pair of TMEM accumulators
+// and all correction products (i + j > 0, 2^-8 smaller) to a separate pair:
+// the tensor core's FP32 accumulation loses low bits at every accumulate
+// event, and this keeps the large accumulator at 2 events per K step instead
+// of 2 * (number of products).  The epilogue adds main + correction.
 // Conjugation of an operand is applied when it is split (Im stored negated).
 //
 // One CTA per SM, persistent over a list of 128-row tiles:
@@ -181,7 +186,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 }
 
 struct GemmShape {    // stages <= 8
-  int nt;          // output columns per tile (multiple of 32, <= 256)
+  int nt;          // output columns per tile (multiple of 32, <= 128: 4 accumulators in TMEM)
   int kchunks;     // padded K / 16
   int pieces;      // BF16 pieces per real number (2 or 3)
   int stages;      // pipeline depth
@@ -276,7 +281,9 @@ gemm_split_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       int stage = 0;
       uint32_t phase = 0;
       int local = 0;
-      const uint32_t d_re = tmem_base, d_im = tmem_base + (uint32_t)sh.nt;
+      const uint32_t nt = (uint32_t)sh.nt;
+      const uint32_t m_re = tmem_base, m_im = tmem_base + nt;            // main
+      const uint32_t c_re = tmem_base + 2 * nt, c_im = tmem_base + 3 * nt;  // corrections
       const uint32_t id_pos = idesc_bf16(sh.nt, false), id_neg = idesc_bf16(sh.nt, true);
       const uint32_t bpb = b_plane_bytes(sh.nt);
       for (int t = blockIdx.x; t < ntiles && !abort_flag; t += gridDim.x, ++local) {
@@ -291,19 +298,27 @@ gemm_split_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
           tc_fence_after();
           const uint32_t sa = smem_u32(smem + (size_t)stage * sbytes);
           const uint32_t sb = sa + a_bytes;
-          uint32_t acc_re = kc > 0, acc_im = kc > 0;
+          const uint32_t first = kc == 0 ? 0u : 1u;
+          uint32_t acc_cre = first, acc_cim = first;
           for (int i = 0; i < P; ++i) {
             for (int j = 0; i + j < P; ++j) {
               const uint64_t a_re = smem_desc_sw32(sa + (uint32_t)i * a_plane_bytes());
               const uint64_t a_im = smem_desc_sw32(sa + (uint32_t)(P + i) * a_plane_bytes());
               const uint64_t b_re = smem_desc_sw32(sb + (uint32_t)j * bpb);
               const uint64_t b_im = smem_desc_sw32(sb + (uint32_t)(P + j) * bpb);
-              mma_bf16(d_re, a_re, b_re, id_pos, acc_re);
-              acc_re = 1;
-              mma_bf16(d_re, a_im, b_im, id_neg, 1);
-              mma_bf16(d_im, a_re, b_im, id_pos, acc_im);
-              acc_im = 1;
-              mma_bf16(d_im, a_im, b_re, id_pos, 1);
+              if (i + j == 0) {
+                mma_bf16(m_re, a_re, b_re, id_pos, first);
+                mma_bf16(m_re, a_im, b_im, id_neg, 1);
+                mma_bf16(m_im, a_re, b_im, id_pos, first);
+                mma_bf16(m_im, a_im, b_re, id_pos, 1);
+              } else {
+                mma_bf16(c_re, a_re, b_re, id_pos, acc_cre);
+                acc_cre = 1;
+                mma_bf16(c_re, a_im, b_im, id_neg, 1);
+                mma_bf16(c_im, a_re, b_im, id_pos, acc_cim);
+                acc_cim = 1;
+                mma_bf16(c_im, a_im, b_re, id_pos, 1);
+              }
             }
           }
           mma_commit(&empty[stage]);   // frees this stage once its MMAs complete
@@ -330,11 +345,18 @@ gemm_split_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       __syncwarp();
       tc_fence_after();
       const Tile tl = tiles[t];
-      float re[32], im[32];
+      float re[32], im[32], cr[32], ci[32];
       const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
       for (int c0 = 0; c0 < sh.nt; c0 += 32) {
         tmem_ld32(lane_base + (uint32_t)c0, re);
         tmem_ld32(lane_base + (uint32_t)(sh.nt + c0), im);
+        tmem_ld32(lane_base + (uint32_t)(2 * sh.nt + c0), cr);
+        tmem_ld32(lane_base + (uint32_t)(3 * sh.nt + c0), ci);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          re[j] += cr[j];
+          im[j] += ci[j];
+        }
         if (row < tl.m_valid && c0 < tl.n_valid) epi(tl, row, c0, re, im);
       }
       tc_fence_before();
