@@ -69,3 +69,58 @@ __device__ __forceinline__ float f64_to_f32_bits(double x) {
 }
 
 }  // namespace bse
+
+namespace bse {
+
+// FP32 -> FP64 with integer instructions (exact; FP32 subnormals become zero).
+__device__ __forceinline__ double f32_to_f64_bits(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint64_t sign = (uint64_t)(u & 0x80000000u) << 32;
+  const uint32_t e = (u >> 23) & 0xFFu;
+  if (e == 0) return __longlong_as_double((long long)sign);
+  const uint64_t be = e == 0xFFu ? 0x7FFull : (uint64_t)(e + 896u);
+  return __longlong_as_double((long long)(sign | (be << 52) | ((uint64_t)(u & 0x7FFFFFu) << 29)));
+}
+
+// Error-free sum of two FP32 numbers (Knuth's TwoSum): s + err == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& err) {
+  s = a + b;
+  const float bp = s - a;
+  err = (a - (s - bp)) + (b - bp);
+}
+
+}  // namespace bse
+
+namespace bse {
+
+// FP64 (given as its two 32-bit words) -> FP32, round half up, 32-bit
+// integer instructions only.  |x| < 2^-126 becomes a signed zero.
+__device__ __forceinline__ uint32_t f64w_to_f32_bits(uint32_t lo, uint32_t hi) {
+  const uint32_t sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7FFu);
+  const int be = e - 896;                                     // FP32 biased exponent
+  uint32_t m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);            // top 23 fraction bits
+  uint32_t f = ((uint32_t)be << 23) + m + ((lo >> 28) & 1u);   // rounding carries into the exponent
+  f = be <= 0 ? 0u : (be >= 255 ? 0x7F800000u : f);
+  return sign | f;
+}
+
+// FP32 -> BF16 bit pattern, round to nearest even (finite inputs).
+__device__ __forceinline__ uint32_t f32_to_bf16_rn_bits(uint32_t u) {
+  return (u + 0x7FFFu + ((u >> 16) & 1u)) >> 16;
+}
+
+// x (FP32) = h_0 + ... + h_{P-1} + r with every h_i a BF16 number taken to
+// nearest from what remains; the remainders are exact in FP32.
+template <int P>
+__device__ __forceinline__ void split_f32_bf16(uint32_t u, uint32_t* h) {
+  float r = __uint_as_float(u);
+#pragma unroll
+  for (int i = 0; i < P; ++i) {
+    const uint32_t b = f32_to_bf16_rn_bits(__float_as_uint(r));
+    h[i] = b;
+    if (i + 1 < P) r -= __uint_as_float(b << 16);
+  }
+}
+
+}  // namespace bse

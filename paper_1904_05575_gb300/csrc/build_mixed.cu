@@ -18,6 +18,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -58,26 +59,15 @@ struct SplitArgs {
   __nv_bfloat16* out;       // [2 * pieces][rows][Kp]
 };
 
-// 8 consecutive reals -> P planes of 8 BF16 each (16-byte stores), integer split
-__device__ __forceinline__ void split_real8(const double* x, int pieces, __nv_bfloat16* out,
-                                            int64_t plane) {
-  __align__(16) uint16_t h[3][8];
-#pragma unroll
-  for (int e = 0; e < 8; ++e) {
-    uint16_t t[3];
-    split_bf16_bits(x[e], pieces, t);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) h[i][e] = t[i];
-  }
-  for (int i = 0; i < pieces; ++i)
-    *reinterpret_cast<uint4*>(out + i * plane) = *reinterpret_cast<const uint4*>(h[i]);
-}
-
-// one thread per (output row, 8 consecutive k): 16-byte stores into every plane
-__global__ void k_split(SplitArgs a) {
+// One thread per (output row, 8 consecutive k): every element is read as two
+// 32-bit words, rounded to FP32 with integer instructions and split in FP32
+// into P BF16 pieces; each plane gets one 16-byte store of 8 pieces.
+template <int P>
+__global__ void __launch_bounds__(256) k_split(SplitArgs a) {
   const int kg = a.Kp / 8;
   const int64_t total = (int64_t)a.rows * kg;
   const int64_t plane = (int64_t)a.rows * a.Kp;
+  const uint4* src = reinterpret_cast<const uint4*>(a.src);   // one complex128 per uint4
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int row = (int)(i / kg), k0 = (int)(i % kg) * 8;
@@ -90,34 +80,50 @@ __global__ void k_split(SplitArgs a) {
       off = g >= a.K ? -1 : (int64_t)q * a.K * a.K + (a.transpose ? g : (int64_t)g * a.K);
       kstride = a.transpose ? a.K : 1;
     }
-    double xr[8], xi[8];
+    uint32_t hr[P][8], hi[P][8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const int k = k0 + e;
-      double2 x = make_double2(0.0, 0.0);
-      if (k < a.K && off >= 0) {
-        x = __ldg(a.src + off + (int64_t)k * kstride);
-        if (a.conj) x.y = -x.y;
-        if (a.kscale) {
-          const double s = a.kscale[k];
-          x.x *= s;
-          x.y *= s;
-        }
+      uint4 x = make_uint4(0u, 0u, 0u, 0u);
+      if (k < a.K && off >= 0) x = __ldg(src + off + (int64_t)k * kstride);
+      uint32_t fr = f64w_to_f32_bits(x.x, x.y), fi = f64w_to_f32_bits(x.z, x.w);
+      if (a.kscale && k < a.K) {   // exchange operand only: scale in FP32
+        const float sc = (float)a.kscale[k];
+        fr = __float_as_uint(__uint_as_float(fr) * sc);
+        fi = __float_as_uint(__uint_as_float(fi) * sc);
       }
-      xr[e] = x.x;
-      xi[e] = x.y;
+      if (a.conj) fi ^= 0x80000000u;
+      uint32_t tr[P], ti[P];
+      split_f32_bf16<P>(fr, tr);
+      split_f32_bf16<P>(fi, ti);
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        hr[p][e] = tr[p];
+        hi[p][e] = ti[p];
+      }
     }
     const int64_t o = (int64_t)row * a.Kp + k0;
-    split_real8(xr, a.pieces, a.out + o, plane);
-    split_real8(xi, a.pieces, a.out + (int64_t)a.pieces * plane + o, plane);
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      uint4 vr, vi;
+      vr.x = hr[p][0] | (hr[p][1] << 16); vr.y = hr[p][2] | (hr[p][3] << 16);
+      vr.z = hr[p][4] | (hr[p][5] << 16); vr.w = hr[p][6] | (hr[p][7] << 16);
+      vi.x = hi[p][0] | (hi[p][1] << 16); vi.y = hi[p][2] | (hi[p][3] << 16);
+      vi.z = hi[p][4] | (hi[p][5] << 16); vi.w = hi[p][6] | (hi[p][7] << 16);
+      *reinterpret_cast<uint4*>(a.out + (int64_t)p * plane + o) = vr;
+      *reinterpret_cast<uint4*>(a.out + (int64_t)(P + p) * plane + o) = vi;
+    }
   }
 }
 
 void launch_split(const SplitArgs& a, cudaStream_t s) {
   const int64_t total = (int64_t)a.rows * (a.Kp / 8);
   int64_t blocks = (total + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  k_split<<<(int)std::max<int64_t>(blocks, 1), 256, 0, s>>>(a);
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (a.pieces == 3)
+    k_split<3><<<(int)std::max<int64_t>(blocks, 1), 256, 0, s>>>(a);
+  else
+    k_split<2><<<(int)std::max<int64_t>(blocks, 1), 256, 0, s>>>(a);
   BSE_CUDA(cudaGetLastError());
   note_launches(1);
 }
@@ -128,25 +134,27 @@ void launch_split(const SplitArgs& a, cudaStream_t s) {
 struct ExchangeEpi {   // V[alpha][alpha'] -> A, B (column-major FP64)
   double2 *A, *B;
   int64_t ld;
-  double scale;
+  float scale;         // 2 gamma_x kappa (the product is formed in FP32, then widened exactly)
   const double *e_v, *e_c;
   int nv, nc;
-  __device__ void operator()(const tc::Tile& t, int row, int c0, const float* re,
-                             const float* im) const {
+  __device__ __forceinline__ void operator()(const tc::Tile& t, int row, int c0, const float* re,
+                                             const float* im) const {
     const int64_t al = t.out_row0 + row;
-    const int64_t kk = al / (nv * nc);
-    const int v = (int)((al / nc) % nv), c = (int)(al % nc);
-    const double e = e_c[kk * nc + c] - e_v[kk * nv + v];
-#pragma unroll 4
+#pragma unroll
     for (int j = 0; j < 32; ++j) {
       const int col = c0 + j;
-      if (col >= t.n_valid) break;
-      const int64_t ap = t.n0 + col;
-      double2 val = make_double2(scale * (double)re[j], scale * (double)im[j]);
-      const int64_t off = al + ap * ld;
-      if (B) B[off] = val;
-      if (al == ap) val.x += e;
-      A[off] = val;
+      if (col < t.n_valid) {
+        const int64_t ap = t.n0 + col;
+        double2 val = make_double2(f32_to_f64_bits(scale * re[j]), f32_to_f64_bits(scale * im[j]));
+        const int64_t off = al + ap * ld;
+        if (B) B[off] = val;
+        if (al == ap) {
+          const int64_t kk = al / (nv * nc);
+          const int v = (int)((al / nc) % nv), c = (int)(al % nc);
+          val.x += e_c[kk * nc + c] - e_v[kk * nv + v];
+        }
+        A[off] = val;
+      }
     }
   }
 };
@@ -154,15 +162,12 @@ struct ExchangeEpi {   // V[alpha][alpha'] -> A, B (column-major FP64)
 struct TEpi {          // T[G][row] (FP32 complex), G-major so a warp's stores coalesce
   float2* T;
   int64_t t_ld;        // rows in T
-  __device__ void operator()(const tc::Tile& t, int row, int c0, const float* re,
-                             const float* im) const {
+  __device__ __forceinline__ void operator()(const tc::Tile& t, int row, int c0, const float* re,
+                                             const float* im) const {
     const int64_t r = t.out_row0 + row;
-#pragma unroll 4
-    for (int j = 0; j < 32; ++j) {
-      const int col = c0 + j;
-      if (col >= t.n_valid) break;
-      T[(int64_t)(t.n0 + col) * t_ld + r] = make_float2(re[j], im[j]);
-    }
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (c0 + j < t.n_valid) T[(int64_t)(t.n0 + c0 + j) * t_ld + r] = make_float2(re[j], im[j]);
   }
 };
 
@@ -199,26 +204,22 @@ __global__ void __launch_bounds__((TS / R) * (TS / R)) k_stage2(Stage2Args a) {
   const int64_t trow0 = (int64_t)a.slot_of_pair[p] * a.rows_t;
   const int tid = threadIdx.x;
   const int tx = tid % (TS / R), ty = tid / (TS / R);
-  // FP32 sums over one chunk of 32 plane waves, promoted to FP64 between chunks
-  double sumx[R][R], sumy[R][R];
+  // compensated FP32: sums over 8 plane waves in FMA, folded into (hi, lo) pairs
+  // with TwoSum, so no FP64 instruction runs inside the loop
+  float hx[R][R], hy[R][R], lx[R][R], ly[R][R];
 #pragma unroll
   for (int i = 0; i < R; ++i)
 #pragma unroll
-    for (int j = 0; j < R; ++j) sumx[i][j] = sumy[i][j] = 0.0;
+    for (int j = 0; j < R; ++j) hx[i][j] = hy[i][j] = lx[i][j] = ly[i][j] = 0.f;
 
   for (int g0 = 0; g0 < a.ng; g0 += GC) {
-    float accx[R][R], accy[R][R];
-#pragma unroll
-    for (int i = 0; i < R; ++i)
-#pragma unroll
-      for (int j = 0; j < R; ++j) accx[i][j] = accy[i][j] = 0.f;
     for (int i = tid; i < TS * GC; i += NTH) {
       const int r = i / GC, g = i % GC;
       float2 v = make_float2(0.f, 0.f);
       if (rx0 + r < a.rows_x && g0 + g < a.ng) {
-        const double2 d = __ldg(X + (int64_t)(rx0 + r) * a.ng + g0 + g);
-        const float dy = f64_to_f32_bits(d.y);
-        v = make_float2(f64_to_f32_bits(d.x), a.conj_x ? -dy : dy);
+        const uint4 d = __ldg(reinterpret_cast<const uint4*>(X) + (int64_t)(rx0 + r) * a.ng + g0 + g);
+        const uint32_t dy = f64w_to_f32_bits(d.z, d.w) ^ (a.conj_x ? 0x80000000u : 0u);
+        v = make_float2(__uint_as_float(f64w_to_f32_bits(d.x, d.y)), __uint_as_float(dy));
       }
       Xs[r][g] = v;
     }
@@ -232,30 +233,43 @@ __global__ void __launch_bounds__((TS / R) * (TS / R)) k_stage2(Stage2Args a) {
       Ts[g][r] = v;
     }
     __syncthreads();
-#pragma unroll 8
-    for (int g = 0; g < GC; ++g) {
-      float2 xv[R], tv[R];
 #pragma unroll
-      for (int i = 0; i < R; ++i) xv[i] = Xs[ty + i * (TS / R)][g];
+    for (int g8 = 0; g8 < GC; g8 += 8) {
+      float accx[R][R], accy[R][R];
 #pragma unroll
-      for (int j = 0; j < R; ++j) tv[j] = Ts[g][tx + j * (TS / R)];
+      for (int i = 0; i < R; ++i)
+#pragma unroll
+        for (int j = 0; j < R; ++j) accx[i][j] = accy[i][j] = 0.f;
+#pragma unroll
+      for (int g = g8; g < g8 + 8; ++g) {
+        float2 xv[R], tv[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) xv[i] = Xs[ty + i * (TS / R)][g];
+#pragma unroll
+        for (int j = 0; j < R; ++j) tv[j] = Ts[g][tx + j * (TS / R)];
+#pragma unroll
+        for (int i = 0; i < R; ++i)
+#pragma unroll
+          for (int j = 0; j < R; ++j) {
+            accx[i][j] = fmaf(xv[i].x, tv[j].x, accx[i][j]);
+            accx[i][j] = fmaf(-xv[i].y, tv[j].y, accx[i][j]);
+            accy[i][j] = fmaf(xv[i].x, tv[j].y, accy[i][j]);
+            accy[i][j] = fmaf(xv[i].y, tv[j].x, accy[i][j]);
+          }
+      }
 #pragma unroll
       for (int i = 0; i < R; ++i)
 #pragma unroll
         for (int j = 0; j < R; ++j) {
-          accx[i][j] = fmaf(xv[i].x, tv[j].x, accx[i][j]);
-          accx[i][j] = fmaf(-xv[i].y, tv[j].y, accx[i][j]);
-          accy[i][j] = fmaf(xv[i].x, tv[j].y, accy[i][j]);
-          accy[i][j] = fmaf(xv[i].y, tv[j].x, accy[i][j]);
+          float s, e;
+          two_sum(hx[i][j], accx[i][j], s, e);
+          hx[i][j] = s;
+          lx[i][j] += e;
+          two_sum(hy[i][j], accy[i][j], s, e);
+          hy[i][j] = s;
+          ly[i][j] += e;
         }
     }
-#pragma unroll
-    for (int i = 0; i < R; ++i)
-#pragma unroll
-      for (int j = 0; j < R; ++j) {
-        sumx[i][j] += (double)accx[i][j];
-        sumy[i][j] += (double)accy[i][j];
-      }
     __syncthreads();
   }
 
@@ -278,8 +292,8 @@ __global__ void __launch_bounds__((TS / R) * (TS / R)) k_stage2(Stage2Args a) {
       const int64_t ap = ((int64_t)kp * nv + vp) * nc + cp;
       double2* dst = a.out + al + ap * a.ld;
       double2 o = *dst;
-      o.x -= a.scale * sumx[i][j];
-      o.y -= a.scale * sumy[i][j];
+      o.x -= a.scale * (f32_to_f64_bits(hx[i][j]) + f32_to_f64_bits(lx[i][j]));
+      o.y -= a.scale * (f32_to_f64_bits(hy[i][j]) + f32_to_f64_bits(ly[i][j]));
       *dst = o;
     }
 }
@@ -341,7 +355,7 @@ void launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb, const tc::Tile* d
                  const tc::GemmShape& sh, const Epi& epi, int* d_err, cudaStream_t s) {
   if (ntiles == 0) return;
   const size_t smem = tc::gemm_smem_bytes(sh);
-  auto kern = tc::gemm_split_bf16<Epi>;
+  auto kern = sh.pieces == 3 ? tc::gemm_split_bf16<3, Epi> : tc::gemm_split_bf16<2, Epi>;
   BSE_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int grid = std::min<int>(ntiles, num_sms());
   kern<<<grid, tc::NUM_THREADS, smem, s>>>(ma, mb, d_tiles, ntiles, sh, epi, d_err);
@@ -354,7 +368,9 @@ tc::GemmShape make_shape(int nt, int Kp, int pieces) {
   sh.nt = nt;
   sh.kchunks = Kp / tc::BK;
   sh.pieces = pieces;
-  sh.tmem_cols = 4 * nt <= 128 ? 128 : 4 * nt <= 256 ? 256 : 512;
+  sh.acc_bufs = 8 * nt <= 512 ? 2 : 1;
+  const int cols = 4 * nt * sh.acc_bufs;
+  sh.tmem_cols = cols <= 128 ? 128 : cols <= 256 ? 256 : 512;
   const uint32_t sb = 2u * pieces * (tc::a_plane_bytes() + tc::b_plane_bytes(nt));
   const size_t budget = 220 * 1024;
   int st = (int)((budget - 2048) / sb);
@@ -362,9 +378,21 @@ tc::GemmShape make_shape(int nt, int Kp, int pieces) {
   return sh;
 }
 
-// output columns per tile: the padded N split into equal multiples of 32, each <= 128
+// Largest output-column tile (multiple of 32, <= 128).  Tiles of <= 64 columns
+// leave room for two accumulator sets in TMEM (epilogue overlapped with the
+// next tile's MMAs); wider tiles read shared memory more efficiently.  The
+// environment variable BSE_TC_NT_MAX overrides the default for tuning.
+int nt_max() {
+  const char* e = getenv("BSE_TC_NT_MAX");
+  int v = e ? atoi(e) : 128;
+  if (v != 32 && v != 64 && v != 96 && v != 128) v = 128;
+  return v;
+}
+
+// output columns per tile: the padded N split into equal multiples of 32, each <= nt_max()
 int tile_cols(int n_pad) {
-  int ntiles = (n_pad + 127) / 128;
+  const int mx = nt_max();
+  int ntiles = (n_pad + mx - 1) / mx;
   return round_up((n_pad + ntiles - 1) / ntiles, 32);
 }
 
@@ -534,7 +562,7 @@ void build_mixed(const Problem& pr, int precision, cudaStream_t s) {
     CUtensorMap mb = make_plane_map(xb.as<__nv_bfloat16>(), Kp, n, planes, nt_x);
     ExchangeEpi epi{reinterpret_cast<double2*>(p.A),
                     p.coupling ? reinterpret_cast<double2*>(p.B) : nullptr,
-                    p.ld, 2.0 * p.gamma_x * kap, p.e_v, p.e_c, nv, nc};
+                    p.ld, (float)(2.0 * p.gamma_x * kap), p.e_v, p.e_c, nv, nc};
     launch_gemm(ma, mb, plan.xtiles, plan.exchange_tiles, sh, epi, err.as<int>(), s);
   }
 

@@ -190,6 +190,7 @@ struct GemmShape {    // stages <= 8
   int kchunks;     // padded K / 16
   int pieces;      // BF16 pieces per real number (2 or 3)
   int stages;      // pipeline depth
+  int acc_bufs;    // accumulator sets in TMEM (2: epilogue of one tile overlaps the next)
   uint32_t tmem_cols;
 };
 
@@ -199,14 +200,14 @@ __host__ __device__ inline uint32_t stage_bytes(const GemmShape& s) {
   return 2u * s.pieces * (a_plane_bytes() + b_plane_bytes(s.nt));
 }
 __host__ inline size_t gemm_smem_bytes(const GemmShape& s) {
-  return 1024 /* alignment slack */ + (size_t)s.stages * stage_bytes(s) + 64 * 8;
+  return 1024 /* alignment slack */ + (size_t)s.stages * stage_bytes(s) + 64 * 8;   // + barriers
 }
 
 // ---------------------------------------------------------------------------
 // The kernel.  Epi provides: __device__ void operator()(const Tile&, int row,
 // int col0, const float* re, const float* im) const  for 32 columns at col0.
 // ---------------------------------------------------------------------------
-template <class Epi>
+template <int P, class Epi>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
 gemm_split_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 const Tile* __restrict__ tiles, int ntiles, GemmShape sh, Epi epi, int* err) {
@@ -217,22 +218,24 @@ gemm_split_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
   const uint32_t a_bytes = 2u * sh.pieces * a_plane_bytes();
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)sh.stages * sbytes);
   uint64_t* empty = full + sh.stages;
-  uint64_t* tmem_full = empty + sh.stages;
-  uint64_t* tmem_empty = tmem_full + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tmem_empty + 1);
+  uint64_t* tmem_full = empty + sh.stages;      // [2]: one per accumulator buffer
+  uint64_t* tmem_empty = tmem_full + 2;         // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tmem_empty + 2);
   __shared__ volatile int abort_flag;
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int P = sh.pieces;
+  const int nbuf = sh.acc_bufs;                 // 1 or 2 accumulator sets of 4 * nt columns
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < sh.stages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(tmem_full, 1);
-    mbar_init(tmem_empty, 4);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tmem_full[b], 1);
+      mbar_init(&tmem_empty[b], 4);
+    }
     abort_flag = 0;
     fence_barrier_init();
   }
@@ -282,13 +285,21 @@ gemm_split_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       uint32_t phase = 0;
       int local = 0;
       const uint32_t nt = (uint32_t)sh.nt;
-      const uint32_t m_re = tmem_base, m_im = tmem_base + nt;            // main
-      const uint32_t c_re = tmem_base + 2 * nt, c_im = tmem_base + 3 * nt;  // corrections
       const uint32_t id_pos = idesc_bf16(sh.nt, false), id_neg = idesc_bf16(sh.nt, true);
-      const uint32_t bpb = b_plane_bytes(sh.nt);
+      // descriptors of stage 0, plane 0; the start-address field (bytes >> 4, 14 bits)
+      // is advanced by plain adds for other stages and planes (all below 256 KB)
+      const uint32_t sa0 = smem_u32(smem);
+      const uint64_t da0 = smem_desc_sw32(sa0), db0 = smem_desc_sw32(sa0 + a_bytes);
+      const uint64_t dstage = sbytes >> 4, dpa = a_plane_bytes() >> 4,
+                     dpb = b_plane_bytes(sh.nt) >> 4;
       for (int t = blockIdx.x; t < ntiles && !abort_flag; t += gridDim.x, ++local) {
-        if (local > 0 && !mbar_wait(tmem_empty, (local - 1) & 1, &abort_flag, err)) break;
+        const int buf = nbuf == 2 ? (local & 1) : 0;
+        const int use = nbuf == 2 ? (local >> 1) : local;    // earlier uses of this buffer
+        if (use > 0 && !mbar_wait(&tmem_empty[buf], (use - 1) & 1, &abort_flag, err)) break;
         tc_fence_after();
+        const uint32_t base = tmem_base + (uint32_t)buf * 4u * nt;
+        const uint32_t m_re = base, m_im = base + nt;               // main
+        const uint32_t c_re = base + 2 * nt, c_im = base + 3 * nt;  // corrections
         bool ok = true;
         for (int kc = 0; kc < sh.kchunks; ++kc) {
           if (!mbar_wait(&full[stage], phase, &abort_flag, err)) {
@@ -296,29 +307,27 @@ gemm_split_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             break;
           }
           tc_fence_after();
-          const uint32_t sa = smem_u32(smem + (size_t)stage * sbytes);
-          const uint32_t sb = sa + a_bytes;
+          const uint64_t da = da0 + (uint64_t)stage * dstage, db = db0 + (uint64_t)stage * dstage;
           const uint32_t first = kc == 0 ? 0u : 1u;
-          uint32_t acc_cre = first, acc_cim = first;
+          // leading products
+          mma_bf16(m_re, da, db, id_pos, first);
+          mma_bf16(m_re, da + P * dpa, db + P * dpb, id_neg, 1);
+          mma_bf16(m_im, da, db + P * dpb, id_pos, first);
+          mma_bf16(m_im, da + P * dpa, db, id_pos, 1);
+          // correction products i + j in [1, P)
+          uint32_t acc_c = first;
+#pragma unroll
           for (int i = 0; i < P; ++i) {
+#pragma unroll
             for (int j = 0; i + j < P; ++j) {
-              const uint64_t a_re = smem_desc_sw32(sa + (uint32_t)i * a_plane_bytes());
-              const uint64_t a_im = smem_desc_sw32(sa + (uint32_t)(P + i) * a_plane_bytes());
-              const uint64_t b_re = smem_desc_sw32(sb + (uint32_t)j * bpb);
-              const uint64_t b_im = smem_desc_sw32(sb + (uint32_t)(P + j) * bpb);
-              if (i + j == 0) {
-                mma_bf16(m_re, a_re, b_re, id_pos, first);
-                mma_bf16(m_re, a_im, b_im, id_neg, 1);
-                mma_bf16(m_im, a_re, b_im, id_pos, first);
-                mma_bf16(m_im, a_im, b_re, id_pos, 1);
-              } else {
-                mma_bf16(c_re, a_re, b_re, id_pos, acc_cre);
-                acc_cre = 1;
-                mma_bf16(c_re, a_im, b_im, id_neg, 1);
-                mma_bf16(c_im, a_re, b_im, id_pos, acc_cim);
-                acc_cim = 1;
-                mma_bf16(c_im, a_im, b_re, id_pos, 1);
-              }
+              if (i + j == 0) continue;
+              const uint64_t a_re = da + i * dpa, a_im = da + (P + i) * dpa;
+              const uint64_t b_re = db + j * dpb, b_im = db + (P + j) * dpb;
+              mma_bf16(c_re, a_re, b_re, id_pos, acc_c);
+              mma_bf16(c_re, a_im, b_im, id_neg, 1);
+              mma_bf16(c_im, a_re, b_im, id_pos, acc_c);
+              mma_bf16(c_im, a_im, b_re, id_pos, 1);
+              acc_c = 1;
             }
           }
           mma_commit(&empty[stage]);   // frees this stage once its MMAs complete
@@ -328,7 +337,7 @@ gemm_split_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
           }
         }
         if (!ok) break;
-        mma_commit(tmem_full);
+        mma_commit(&tmem_full[buf]);
       }
     }
   } else {
@@ -338,15 +347,18 @@ gemm_split_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     int local = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++local) {
       // one lane waits, the warp follows (the tcgen05.ld below is warp-collective)
+      const int buf = nbuf == 2 ? (local & 1) : 0;
+      const int use = nbuf == 2 ? (local >> 1) : local;
       int ok = 0;
-      if (lane == 0) ok = mbar_wait(tmem_full, local & 1, &abort_flag, err) ? 1 : 0;
+      if (lane == 0) ok = mbar_wait(&tmem_full[buf], use & 1, &abort_flag, err) ? 1 : 0;
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (!ok) break;
       __syncwarp();
       tc_fence_after();
       const Tile tl = tiles[t];
       float re[32], im[32], cr[32], ci[32];
-      const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
+      const uint32_t lane_base =
+          tmem_base + (uint32_t)buf * 4u * (uint32_t)sh.nt + ((uint32_t)(quarter * 32) << 16);
       for (int c0 = 0; c0 < sh.nt; c0 += 32) {
         tmem_ld32(lane_base + (uint32_t)c0, re);
         tmem_ld32(lane_base + (uint32_t)(sh.nt + c0), im);
@@ -361,7 +373,7 @@ gemm_split_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(tmem_empty);
+      if (lane == 0) mbar_arrive(&tmem_empty[buf]);
     }
   }
 
