@@ -292,8 +292,10 @@ __global__ void __launch_bounds__((TS / R) * (TS / R)) k_stage2(Stage2Args a) {
       const int64_t ap = ((int64_t)kp * nv + vp) * nc + cp;
       double2* dst = a.out + al + ap * a.ld;
       double2 o = *dst;
-      o.x -= a.scale * (f32_to_f64_bits(hx[i][j]) + f32_to_f64_bits(lx[i][j]));
-      o.y -= a.scale * (f32_to_f64_bits(hy[i][j]) + f32_to_f64_bits(ly[i][j]));
+      // contribution formed in FP32 (hi + lo carries the compensated sum), widened exactly
+      const float sc = (float)a.scale;
+      o.x -= f32_to_f64_bits(sc * hx[i][j] + sc * lx[i][j]);
+      o.y -= f32_to_f64_bits(sc * hy[i][j] + sc * ly[i][j]);
       *dst = o;
     }
 }
