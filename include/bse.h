@@ -111,6 +111,34 @@ typedef struct {
 int bse_build_kernel(const bse_problem* probs, int32_t nprob, int32_t precision,
                      void* cuda_stream);
 
+/* FP64 build of one problem that allocates no device memory.
+ *
+ * There is no counterpart in the paper: this entry point exists for callers
+ * that cannot allocate device memory when they call the library, for example
+ * a host that has handed all of the GPU's memory to an allocator of its own,
+ * or a loop that must not pay for the allocator's implicit synchronisation.
+ * It computes exactly what bse_build_kernel(prob, 1, BSE_PREC_FP64, stream)
+ * computes, with the same kernels; the stage-1 intermediate of the direct
+ * terms lives in a fixed 16 MiB array compiled into the library instead of
+ * stream-ordered workspace.  Every GPU on which the library's FP64 kernels are
+ * loaded holds that array until the process exits.
+ *
+ * Limits and behaviour:
+ *   - a problem whose intermediate needs more than 16 MiB, that is
+ *     nk^2 * max(min(nv^2, nc^2), nv*nc if coupling) * ng * 16 bytes, is
+ *     rejected with BSE_ERR_ARG before any launch;
+ *   - the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, no allocation); make that first call before any
+ *     stream capture on that device;
+ *   - all calls share the one array and it keeps the previous call's
+ *     contents (nothing in it needs to start at zero); calls whose work
+ *     overlaps on the GPU (other streams, other host threads) race on it and
+ *     must be serialised by the caller;
+ *   - like bse_build_kernel it reads q_minus / q_plus back to the host to
+ *     check their range (a sync on cuda_stream).
+ * Errors: BSE_ERR_ARG, BSE_ERR_CUDA. */
+int bse_build_kernel_fp64_static(const bse_problem* prob, void* cuda_stream);
+
 /* Half-size reduction of Eq. auxham in its Cholesky form.  A-B = L L^H (L
  * lower triangular, written to L with the strict upper triangle zeroed) and
  * S = L^H (A+B) L, which is unitarily similar to (A-B)^{1/2}(A+B)(A-B)^{1/2}

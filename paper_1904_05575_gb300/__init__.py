@@ -51,7 +51,7 @@ _lib: Optional[ctypes.CDLL] = None
 
 EXPORTED = ("bse_build_kernel", "bse_reduce", "bse_spectrum", "bse_last_error", "bse_version",
             "bse_kernel_launches", "bse_precision_supported", "bse_phase_timing",
-            "bse_phase_report")
+            "bse_phase_report", "bse_build_kernel_fp64_static")
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -69,6 +69,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.bse_spectrum.argtypes = [i32, vp, vp, i64, vp, dbl, dbl, i32, vp, dbl, vp, vp, vp, vp]
     lib.bse_last_error.restype = ctypes.c_char_p
     lib.bse_kernel_launches.restype = ctypes.c_int64
+    lib.bse_build_kernel_fp64_static.argtypes = [ctypes.POINTER(bse_problem), vp]
+    lib.bse_build_kernel_fp64_static.restype = ctypes.c_int
     lib.bse_phase_timing.argtypes = [i32]
     lib.bse_phase_report.argtypes = [ctypes.c_char_p, i64]
     lib.bse_precision_supported.argtypes = [i32]
@@ -144,6 +146,13 @@ def bse_build_kernel(problems: Sequence[bse_problem], precision: int = BSE_PREC_
     lib = load()
     arr = (bse_problem * len(problems))(*problems)
     _check(lib.bse_build_kernel(arr, len(problems), int(precision), _stream(stream)))
+
+
+def bse_build_kernel_fp64_static(problem: bse_problem, stream=None) -> None:
+    """FP64 build of one problem using the library's fixed 16 MiB scratch array
+    instead of allocating device memory (for callers that cannot allocate)."""
+    lib = load()
+    _check(lib.bse_build_kernel_fp64_static(ctypes.byref(problem), _stream(stream)))
 
 
 def bse_reduce(n: int, A, B, S, L, stream=None) -> int:

@@ -169,6 +169,14 @@ extern "C" int bse_build_kernel(const bse_problem* probs, int32_t nprob, int32_t
   });
 }
 
+extern "C" int bse_build_kernel_fp64_static(const bse_problem* prob, void* cuda_stream) {
+  return guarded([&] {
+    BSE_CHECK_ARG(prob != nullptr, "prob is NULL");
+    const Problem pr = validate(*prob, 0, static_cast<cudaStream_t>(cuda_stream));
+    build_fp64_static(pr, static_cast<cudaStream_t>(cuda_stream));
+  });
+}
+
 extern "C" int bse_reduce(int32_t n, const bse_c128* A, const bse_c128* B, int64_t ld,
                           bse_c128* S, bse_c128* L, int32_t* failed_minor, void* cuda_stream) {
   return guarded([&] {

@@ -93,6 +93,12 @@ void build_fp64(const Problem& pr, cudaStream_t stream);
 // True when build_mixed serves the precision.
 bool mixed_supported(int precision);
 
+// FP64 build whose stage-1 intermediate lives in a fixed module array of
+// kFp64StaticScratchBytes (no device allocation); rejects larger problems.
+constexpr size_t kFp64StaticScratchBytes = (size_t)16 << 20;
+size_t fp64_static_scratch_need(const Problem& pr);
+void build_fp64_static(const Problem& pr, cudaStream_t stream);
+
 // Split-precision tensor-core build (tcgen05).  Writes A (and B) completely.
 void build_mixed(const Problem& pr, int precision, cudaStream_t stream);
 

@@ -10,6 +10,9 @@
 // Stage 1 applies W to whichever pair side is smaller (s_rr = min(nv^2, nc^2)).
 #include <cuda_runtime.h>
 
+#include <mutex>
+#include <vector>
+
 #include "bse_internal.h"
 
 namespace bse {
@@ -286,6 +289,87 @@ void build_fp64(const Problem& pr, cudaStream_t s) {
   Stage2RAProb P2{nv * nc, nv * nc, ng, p.n_vc, t, nk, nv, nc, p.gamma_c * kap, p.B, p.ld};
   Phase ph("fp64_wra_stage2", s);
   launch_zgemm(P2, npair, s);
+}
+
+}  // namespace bse
+
+// ---------------------------------------------------------------------------
+// FP64 build without any device allocation: the stage-1 intermediate lives in
+// a fixed array compiled into this module instead of stream-ordered workspace.
+// ---------------------------------------------------------------------------
+namespace bse {
+
+// Fixed scratch for build_fp64_static.  Every GPU that loads this module holds
+// it until the process exits; calls share it.
+static __device__ __align__(256) unsigned char g_fp64_static_scratch[kFp64StaticScratchBytes];
+
+namespace {
+std::mutex g_static_mutex;
+std::vector<void*> g_static_scratch_ptr;   // device address of the array, per device
+
+// Host code cannot use the array's name as a device address (on the host it is
+// only a stand-in); the address is looked up once per device, with that
+// device current, and cached.
+void* static_scratch_for_current_device() {
+  int dev = 0;
+  BSE_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  if ((int)g_static_scratch_ptr.size() <= dev) g_static_scratch_ptr.resize(dev + 1, nullptr);
+  if (!g_static_scratch_ptr[dev]) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_fp64_static_scratch);
+    if (e != cudaSuccess || ptr == nullptr) {
+      (void)cudaGetLastError();
+      throw Error(BSE_ERR_CUDA, std::string("cudaGetSymbolAddress of the fixed scratch failed: ") +
+                                    cudaGetErrorString(e));
+    }
+    g_static_scratch_ptr[dev] = ptr;
+  }
+  return g_static_scratch_ptr[dev];
+}
+}  // namespace
+
+size_t fp64_static_scratch_need(const Problem& pr) {
+  const bse_problem& p = pr.p;
+  if (p.gamma_c == 0.0) return 0;
+  const int nv = p.nv, nc = p.nc;
+  const int s_rr = nv * nv < nc * nc ? nv * nv : nc * nc;
+  const int rows_max = s_rr > nv * nc ? s_rr : (p.coupling ? nv * nc : s_rr);
+  return (size_t)p.nk * p.nk * rows_max * p.ng * sizeof(bse_c128);
+}
+
+void build_fp64_static(const Problem& pr, cudaStream_t s) {
+  const bse_problem& p = pr.p;
+  const int nk = p.nk, nv = p.nv, nc = p.nc, ng = p.ng;
+  const int npair = nk * nk;
+  const double kap = pr.kappa;
+  const size_t need = fp64_static_scratch_need(pr);
+  if (need > kFp64StaticScratchBytes)
+    throw Error(BSE_ERR_ARG, "problem needs " + std::to_string(need) +
+                                 " bytes of stage-1 scratch; the fixed scratch holds " +
+                                 std::to_string(kFp64StaticScratchBytes) + " bytes");
+  // first call on a device: looks up the array's device address (no allocation)
+  bse_c128* t = static_cast<bse_c128*>(static_scratch_for_current_device());
+
+  ExchangeProb PX{(int)pr.n, (int)pr.n, ng, p.m_x, p.v_bar, p.e_v, p.e_c, nv, nc,
+                  2.0 * p.gamma_x * kap, p.A, p.coupling ? p.B : nullptr, p.ld};
+  launch_zgemm(PX, 1, s);
+  if (p.gamma_c == 0.0) return;
+  // the intermediate is fully written by each stage 1 before its stage 2 reads
+  // it, so nothing in the shared array has to start at zero
+  if (nc * nc <= nv * nv) {
+    launch_zgemm(Stage1WProb{nc * nc, ng, ng, p.m_cc, p.w, p.q_minus, t}, npair, s);
+    launch_zgemm(Stage2RRProb{nv * nv, nc * nc, ng, p.m_vv, t, nk, nv, nc, p.gamma_c * kap,
+                              p.A, p.ld}, npair, s);
+  } else {
+    launch_zgemm(Stage1WHProb{nv * nv, ng, ng, p.m_vv, p.w, p.q_minus, t}, npair, s);
+    launch_zgemm(Stage2RRProb{nv * nv, nc * nc, ng, t, p.m_cc, nk, nv, nc, p.gamma_c * kap,
+                              p.A, p.ld}, npair, s);
+  }
+  if (!p.coupling) return;
+  launch_zgemm(Stage1WProb{nv * nc, ng, ng, p.n_vc, p.w, p.q_plus, t}, npair, s);
+  launch_zgemm(Stage2RAProb{nv * nc, nv * nc, ng, p.n_vc, t, nk, nv, nc, p.gamma_c * kap, p.B,
+                            p.ld}, npair, s);
 }
 
 }  // namespace bse
