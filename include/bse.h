@@ -179,6 +179,27 @@ int bse_spectrum(int32_t n, bse_c128* S_inout, const bse_c128* L, int64_t ld,
 int bse_phase_timing(int32_t enable);
 int bse_phase_report(char* buf, int64_t buflen);
 
+/* Lowest nev excitons of the full BSE without the dense O(N^3) solve: block
+ * Davidson on the half-size product form (A-B)(A+B)(X+Y) = E^2 (X+Y), which
+ * follows from Eq. gevpbse with H = [[A,B],[B,A]] (Eq. Hetr) and underlies
+ * Eqs. auxham / auxevp; projected problems use the Cholesky form of
+ * bse_reduce.  A and B: N x N Hermitian, column-major, full storage, ld >= n
+ * (device); B = NULL solves the TDA problem A X = E X (Eq. tdaevp); A-B and
+ * A+B must be positive definite.
+ *   nev        number of lowest excitons (1 <= nev <= n)
+ *   tol_ev     convergence: every residual norm of the nev pairs below tol_ev
+ *              (eV; 1e-4 gives energies far inside 1 meV)
+ *   max_iter   iteration limit
+ *   precond    0 = diagonal (r_a / (A_aa - E)), 1 = the trained MLP given in mlp
+ *   E_out      [nev] device, ascending exciton energies (eV)
+ *   XpY_out    [n x nev] device column-major, X+Y with (X+Y)^H (X-Y) = 1, or NULL
+ *   iters_out  host, iterations used (may be NULL)
+ * Syncs every iteration.  Errors: BSE_ERR_ARG, BSE_ERR_NOT_PD, BSE_ERR_NO_CONV
+ * (E_out then holds the last estimates), BSE_ERR_UNSUPPORTED, BSE_ERR_CUDA. */
+int bse_lowest_excitons(int32_t n, const bse_c128* A, const bse_c128* B, int64_t ld, int32_t nev,
+                        double tol_ev, int32_t max_iter, int32_t precond, const void* mlp,
+                        double* E_out, bse_c128* XpY_out, int32_t* iters_out, void* cuda_stream);
+
 /* 1 if this build serves the given bse_precision in bse_build_kernel, else 0.
  * Host only; no CUDA call. */
 int bse_precision_supported(int32_t precision);

@@ -51,7 +51,7 @@ _lib: Optional[ctypes.CDLL] = None
 
 EXPORTED = ("bse_build_kernel", "bse_reduce", "bse_spectrum", "bse_last_error", "bse_version",
             "bse_kernel_launches", "bse_precision_supported", "bse_phase_timing",
-            "bse_phase_report", "bse_build_kernel_fp64_static")
+            "bse_phase_report", "bse_build_kernel_fp64_static", "bse_lowest_excitons")
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -71,6 +71,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.bse_kernel_launches.restype = ctypes.c_int64
     lib.bse_build_kernel_fp64_static.argtypes = [ctypes.POINTER(bse_problem), vp]
     lib.bse_build_kernel_fp64_static.restype = ctypes.c_int
+    lib.bse_lowest_excitons.argtypes = [i32, vp, vp, i64, i32, dbl, i32, i32, vp, vp, vp,
+                                        ctypes.POINTER(i32), vp]
+    lib.bse_lowest_excitons.restype = ctypes.c_int
     lib.bse_phase_timing.argtypes = [i32]
     lib.bse_phase_report.argtypes = [ctypes.c_char_p, i64]
     lib.bse_precision_supported.argtypes = [i32]
@@ -184,6 +187,31 @@ def bse_spectrum(n: int, S, L, rho, c_q: float, vc: float, omega, delta: float,
                             float(delta), _ptr(E_out, torch.float64, "E_out"),
                             _ptr(osc_out, torch.float64, "osc_out"),
                             _ptr(eps_out, torch.complex128, "eps_out"), _stream(stream)))
+
+
+def bse_lowest_excitons(n: int, A, B, nev: int, E_out, XpY_out=None, tol_ev: float = 1e-4,
+                        max_iter: int = 100, precond: int = 0, mlp=None, stream=None) -> int:
+    """Lowest nev excitons by block Davidson; returns the iterations used.  On
+    BSE_ERR_NO_CONV the raised error carries .iters."""
+    import torch
+    lib = load()
+    a, ld = _matrix_ptr(A, n, "A")
+    b = _matrix_ptr(B, n, "B")[0] if B is not None else None
+    x = None
+    if XpY_out is not None:
+        if XpY_out.shape != (nev, n):
+            raise ValueError("XpY_out must have shape [nev, n] (column-major n x nev)")
+        x = _ptr(XpY_out, torch.complex128, "XpY_out")
+    iters = ctypes.c_int32(0)
+    handle = mlp.handle if mlp is not None else None
+    st = lib.bse_lowest_excitons(n, a, b, ld, nev, float(tol_ev), int(max_iter), int(precond),
+                                 handle, _ptr(E_out, torch.float64, "E_out"), x,
+                                 ctypes.byref(iters), _stream(stream))
+    if st != BSE_OK:
+        err = BSEError(st, lib.bse_last_error().decode(errors="replace"))
+        err.iters = iters.value
+        raise err
+    return iters.value
 
 
 def bse_phase_timing(enable: bool) -> None:

@@ -262,6 +262,27 @@ extern "C" int bse_precision_supported(int32_t precision) {
   return 0;
 }
 
+extern "C" int bse_lowest_excitons(int32_t n, const bse_c128* A, const bse_c128* B, int64_t ld,
+                                   int32_t nev, double tol_ev, int32_t max_iter, int32_t precond,
+                                   const void* mlp, double* E_out, bse_c128* XpY_out,
+                                   int32_t* iters_out, void* cuda_stream) {
+  return guarded([&] {
+    if (iters_out) *iters_out = 0;
+    BSE_CHECK_ARG(n >= 1, "n must be >= 1");
+    BSE_CHECK_ARG(ld >= n, "ld < n");
+    BSE_CHECK_ARG(nev >= 1 && nev <= n, "nev must be in [1, n]");
+    BSE_CHECK_ARG(std::isfinite(tol_ev) && tol_ev > 0.0, "tol_ev must be > 0");
+    BSE_CHECK_ARG(max_iter >= 1, "max_iter must be >= 1");
+    BSE_CHECK_ARG(A && E_out, "NULL A or E_out");
+    BSE_CHECK_ARG(precond == 0 || precond == 1, "precond must be 0 (diagonal) or 1 (MLP)");
+    BSE_CHECK_ARG(precond == 0 || mlp != nullptr, "precond = 1 needs an MLP handle");
+    keep_pool_memory();
+    davidson_fp64(n, A, B, ld, nev, tol_ev, max_iter, precond,
+                  static_cast<const MlpNet*>(mlp), E_out, XpY_out, iters_out,
+                  static_cast<cudaStream_t>(cuda_stream));
+  });
+}
+
 extern "C" const char* bse_last_error(void) { return g_last_error.c_str(); }
 
 extern "C" int bse_version(void) { return 100; }

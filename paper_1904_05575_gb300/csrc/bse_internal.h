@@ -1,8 +1,12 @@
 // Internal declarations shared by the translation units of libbse.so.
 #pragma once
 
+#include <cublas_v2.h>
 #include <cuda_runtime.h>
+#include <cusolverDn.h>
+
 #include <cstdint>
+#include <mutex>
 #include <cstdio>
 #include <stdexcept>
 #include <string>
@@ -101,6 +105,19 @@ void build_fp64_static(const Problem& pr, cudaStream_t stream);
 
 // Split-precision tensor-core build (tcgen05).  Writes A (and B) completely.
 void build_mixed(const Problem& pr, int precision, cudaStream_t stream);
+
+// The per-device cuSOLVER / cuBLAS handles; the lock serialises their use.
+struct LibHandles {
+  cusolverDnHandle_t solver;
+  cublasHandle_t blas;
+};
+LibHandles acquire_handles(std::unique_lock<std::mutex>& lock);
+
+// Lowest excitons by block Davidson (product form); precond 0 = diagonal, 1 = MLP.
+struct MlpNet;
+void davidson_fp64(int n, const bse_c128* A, const bse_c128* B, int64_t ld, int nev, double tol,
+                   int max_iter, int precond, const MlpNet* mlp, double* E_out, bse_c128* XpY_out,
+                   int32_t* iters_out, cudaStream_t stream);
 
 // Reduction and spectrum.
 void reduce_fp64(int n, const bse_c128* A, const bse_c128* B, int64_t ld, bse_c128* S,

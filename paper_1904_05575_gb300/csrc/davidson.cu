@@ -1,0 +1,419 @@
+// Lowest excitons of the full BSE by block Davidson on the product form.
+//
+// The full problem H (X;Y) = E Delta (X;Y) (Eq. gevpbse) with H = [[A,B],[B,A]]
+// (Eq. Hetr) is equivalent to (A+B)(X+Y) = E (X-Y), (A-B)(X-Y) = E (X+Y), so
+// (A-B)(A+B)(X+Y) = E^2 (X+Y): the half-size form behind Eq. auxevp.  The
+// solver keeps one orthonormal basis V for both X+Y and X-Y (the scheme of
+// Stratmann, Scuseria and Frisch, J. Chem. Phys. 109, 8218 (1998)):
+//   P = (A+B) V, M = (A-B) V                   matvecs: FP64 GEMM kernels here
+//   a+ = V^H P, a- = V^H M                      projected (m x m) matrices
+//   a- = l l^H, s = l^H a+ l, s z = E^2 z       the projected problem, in the
+//   u = l z E^-1/2, w = a+ u / E                Cholesky form used by bse_reduce
+//   X+Y = V u, X-Y = V w                        Ritz vectors, (X+Y)^H (X-Y) = 1
+//   r+ = P u - E V w, r- = M w - E V u          residuals of the two equations
+// Unconverged residuals are preconditioned (diagonal: r / (A_aa - E), or the
+// trained MLP of mlp.cu), orthogonalised against V (two Gram-Schmidt passes)
+// and appended; the basis restarts from the current Ritz vectors when full.
+// Small dense steps (projections, m x m factorisations) are cuBLAS / cuSOLVER
+// calls; the host drives the iteration and reads residual norms each step.
+#include <cublas_v2.h>
+#include <cuda_runtime.h>
+#include <cusolverDn.h>
+
+#include <algorithm>
+#include <cmath>
+#include <memory>
+#include <numeric>
+#include <vector>
+
+#include "bse_internal.h"
+#include "mlp.h"
+#include "zgemm.cuh"
+
+namespace bse {
+namespace {
+
+#define BSE_CUSOLVER(call)                                                        \
+  do {                                                                            \
+    cusolverStatus_t st_ = (call);                                                \
+    if (st_ != CUSOLVER_STATUS_SUCCESS)                                           \
+      throw ::bse::Error(BSE_ERR_CUDA, std::string(#call) + " failed with status " + \
+                                           std::to_string((int)st_));             \
+  } while (0)
+#define BSE_CUBLAS(call)                                                          \
+  do {                                                                            \
+    cublasStatus_t st_ = (call);                                                  \
+    if (st_ != CUBLAS_STATUS_SUCCESS)                                             \
+      throw ::bse::Error(BSE_ERR_CUDA, std::string(#call) + " failed with status " + \
+                                           std::to_string((int)st_));             \
+  } while (0)
+
+// out[:, j] = H V[:, j], H Hermitian column-major: H[m][k] = conj(H[k + m ld])
+struct MatvecProb {
+  int M, N, K;
+  const bse_c128* H;
+  int64_t ld;
+  const bse_c128* V;   // K x N, column-major, leading dimension ldv
+  int64_t ldv;
+  bse_c128* out;       // M x N, column-major, leading dimension ldo
+  int64_t ldo;
+  __device__ cplx a(int, int m, int k) const { return conj(ldc(H + (int64_t)m * ld + k)); }
+  __device__ cplx b(int, int n, int k) const { return ldc(V + (int64_t)n * ldv + k); }
+  __device__ void store(int, int m, int n, cplx v) const {
+    reinterpret_cast<double2*>(out)[(int64_t)n * ldo + m] = make_double2(v.x, v.y);
+  }
+};
+
+// P = AV + BV, M = AV - BV (B absent: both AV)
+__global__ void k_plus_minus_cols(int64_t total, const double2* av, const double2* bv,
+                                  double2* P, double2* M) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 a = av[i];
+    const double2 b = bv ? bv[i] : make_double2(0.0, 0.0);
+    P[i] = make_double2(a.x + b.x, a.y + b.y);
+    M[i] = make_double2(a.x - b.x, a.y - b.y);
+  }
+}
+
+__global__ void k_diag_real(int n, const double2* A, int64_t ld, double* d) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) d[i] = A[i + (int64_t)i * ld].x;
+}
+
+// s <- (s + s^H) / 2 on an m x m block with leading dimension lds
+__global__ void k_hermitize(int m, double2* s, int lds) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i < m && j < m && i < j) {
+    double2 a = s[i + (int64_t)j * lds], b = s[j + (int64_t)i * lds];
+    double2 h = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+    s[i + (int64_t)j * lds] = h;
+    s[j + (int64_t)i * lds] = make_double2(h.x, -h.y);
+  }
+  if (i < m && j < m && i == j) s[i + (int64_t)i * lds].y = 0.0;
+}
+
+__global__ void k_zero_strict_upper(int m, double2* l, int ldl) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i < m && j < m && i < j) l[i + (int64_t)j * ldl] = make_double2(0.0, 0.0);
+}
+
+// scale column j of x (rows x k, ld) by f[j]
+__global__ void k_scale_cols(int rows, int k, double2* x, int64_t ld, const double* f) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y;
+  if (i < rows && j < k) {
+    double2 v = x[i + (int64_t)j * ld];
+    x[i + (int64_t)j * ld] = make_double2(v.x * f[j], v.y * f[j]);
+  }
+}
+
+// t[:, j] = r[:, j] / (d - E_j), denominators kept at least 1e-2 eV away from 0
+__global__ void k_precond_diag(int n, int k, const double* d, const double* e, const double2* r,
+                               int64_t ldr, double2* t, int64_t ldt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y;
+  if (i < n && j < k) {
+    double den = d[i] - e[j];
+    if (fabs(den) < 1e-2) den = den < 0 ? -1e-2 : 1e-2;
+    double2 v = r[i + (int64_t)j * ldr];
+    t[i + (int64_t)j * ldt] = make_double2(v.x / den, v.y / den);
+  }
+}
+
+struct Solver {
+  int n, nev, mmax;
+  const bse_c128 *A, *B;
+  int64_t ld;
+  cudaStream_t s;
+  LibHandles h;
+  DeviceBuffer V, P, M, AV, BV, ap, am, L, S, U, W, R1, R2, T, C, info, dE, dF, dD;
+  std::unique_ptr<DeviceBuffer> work_;
+  int lwork = 0;
+  int m = 0;          // current basis size
+  std::vector<double> D;
+
+  Solver(int n_, int nev_, int mmax_, const bse_c128* A_, const bse_c128* B_, int64_t ld_,
+         cudaStream_t s_, LibHandles h_)
+      : n(n_), nev(nev_), mmax(mmax_), A(A_), B(B_), ld(ld_), s(s_), h(h_),
+        V((size_t)n_ * mmax_ * 16, s_), P((size_t)n_ * mmax_ * 16, s_),
+        M((size_t)n_ * mmax_ * 16, s_), AV((size_t)n_ * std::max(mmax_, 2 * nev_) * 16, s_),
+        BV((size_t)n_ * std::max(mmax_, 2 * nev_) * 16, s_), ap((size_t)mmax_ * mmax_ * 16, s_),
+        am((size_t)mmax_ * mmax_ * 16, s_), L((size_t)mmax_ * mmax_ * 16, s_),
+        S((size_t)mmax_ * mmax_ * 16, s_), U((size_t)mmax_ * mmax_ * 16, s_),
+        W((size_t)mmax_ * mmax_ * 16, s_), R1((size_t)n_ * std::max(mmax_, 2 * nev_) * 16, s_),
+        R2((size_t)n_ * mmax_ * 16, s_), T((size_t)n_ * 2 * std::max(mmax_, nev_) * 16, s_),
+        C((size_t)mmax_ * 16, s_), info(sizeof(int), s_), dE((size_t)mmax_ * 8, s_),
+        dF((size_t)std::max(mmax_, 2 * nev_) * 8, s_), dD((size_t)n_ * 8, s_) {
+    int lw1 = 0, lw2 = 0;
+    BSE_CUSOLVER(cusolverDnZpotrf_bufferSize(h.solver, CUBLAS_FILL_MODE_LOWER, mmax,
+                                             L.as<cuDoubleComplex>(), mmax, &lw1));
+    BSE_CUSOLVER(cusolverDnZheevd_bufferSize(h.solver, CUSOLVER_EIG_MODE_VECTOR,
+                                             CUBLAS_FILL_MODE_LOWER, mmax,
+                                             S.as<cuDoubleComplex>(), mmax, dE.as<double>(),
+                                             &lw2));
+    lwork = std::max(std::max(lw1, lw2), 1);
+    work_.reset(new DeviceBuffer((size_t)lwork * 16, s));
+  }
+
+  cuDoubleComplex* col(const DeviceBuffer& b, int j, int64_t ldb) const {
+    return b.as<cuDoubleComplex>() + (int64_t)j * ldb;
+  }
+
+  // P, M for basis columns [j0, j1)
+  void matvec(int j0, int j1) {
+    const int k = j1 - j0;
+    if (k <= 0) return;
+    MatvecProb pa{n, k, n, A, ld, V.as<bse_c128>() + (int64_t)j0 * n, n,
+                  AV.as<bse_c128>(), n};
+    launch_zgemm(pa, 1, s);
+    if (B) {
+      MatvecProb pb{n, k, n, B, ld, V.as<bse_c128>() + (int64_t)j0 * n, n,
+                    BV.as<bse_c128>(), n};
+      launch_zgemm(pb, 1, s);
+    }
+    const int64_t total = (int64_t)n * k;
+    k_plus_minus_cols<<<(int)std::min<int64_t>((total + 255) / 256, 152 * 16), 256, 0, s>>>(
+        total, AV.as<double2>(), B ? BV.as<double2>() : nullptr,
+        P.as<double2>() + (int64_t)j0 * n, M.as<double2>() + (int64_t)j0 * n);
+    BSE_CUDA(cudaGetLastError());
+    note_launches(1);
+  }
+
+  // orthonormalise vector x (device, length n) against V[:, :m] and append it.
+  // Returns false if it is (numerically) inside the span already.
+  bool append(cuDoubleComplex* x) {
+    const cuDoubleComplex one = make_cuDoubleComplex(1, 0), zero = make_cuDoubleComplex(0, 0),
+                          mone = make_cuDoubleComplex(-1, 0);
+    double n0 = 0.0;
+    BSE_CUBLAS(cublasDznrm2(h.blas, n, x, 1, &n0));
+    if (!(n0 > 0.0)) return false;
+    cuDoubleComplex* c = C.as<cuDoubleComplex>();   // projection coefficients, length m
+    for (int pass = 0; pass < 2 && m > 0; ++pass) {
+      BSE_CUBLAS(cublasZgemv(h.blas, CUBLAS_OP_C, n, m, &one, V.as<cuDoubleComplex>(), n, x, 1,
+                             &zero, c, 1));
+      BSE_CUBLAS(cublasZgemv(h.blas, CUBLAS_OP_N, n, m, &mone, V.as<cuDoubleComplex>(), n, c, 1,
+                             &one, x, 1));
+    }
+    double n1 = 0.0;
+    BSE_CUBLAS(cublasDznrm2(h.blas, n, x, 1, &n1));
+    if (!(n1 > 1e-8 * n0) || m >= mmax) return false;
+    const double inv = 1.0 / n1;
+    BSE_CUBLAS(cublasZdscal(h.blas, n, &inv, x, 1));
+    BSE_CUBLAS(cublasZcopy(h.blas, n, x, 1, col(V, m, n), 1));
+    ++m;
+    return true;
+  }
+
+  // projected problem on the current basis; fills U (u, m x nev), W (w, m x nev), E (host)
+  void rayleigh_ritz(int k, std::vector<double>& E) {
+    const cuDoubleComplex one = make_cuDoubleComplex(1, 0), zero = make_cuDoubleComplex(0, 0);
+    BSE_CUBLAS(cublasZgemm(h.blas, CUBLAS_OP_C, CUBLAS_OP_N, m, m, n, &one,
+                           V.as<cuDoubleComplex>(), n, P.as<cuDoubleComplex>(), n, &zero,
+                           ap.as<cuDoubleComplex>(), mmax));
+    BSE_CUBLAS(cublasZgemm(h.blas, CUBLAS_OP_C, CUBLAS_OP_N, m, m, n, &one,
+                           V.as<cuDoubleComplex>(), n, M.as<cuDoubleComplex>(), n, &zero,
+                           am.as<cuDoubleComplex>(), mmax));
+    dim3 tb(16, 16), gb((m + 15) / 16, (m + 15) / 16);
+    k_hermitize<<<gb, tb, 0, s>>>(m, ap.as<double2>(), mmax);
+    k_hermitize<<<gb, tb, 0, s>>>(m, am.as<double2>(), mmax);
+    note_launches(2);
+    // a- = l l^H
+    BSE_CUDA(cudaMemcpy2DAsync(L.ptr, (size_t)mmax * 16, am.ptr, (size_t)mmax * 16, (size_t)m * 16,
+                               m, cudaMemcpyDeviceToDevice, s));
+    BSE_CUSOLVER(cusolverDnZpotrf(h.solver, CUBLAS_FILL_MODE_LOWER, m, L.as<cuDoubleComplex>(),
+                                  mmax, work_->as<cuDoubleComplex>(), lwork, info.as<int>()));
+    int hinfo = 0;
+    BSE_CUDA(cudaMemcpyAsync(&hinfo, info.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BSE_CUDA(cudaStreamSynchronize(s));
+    if (hinfo != 0)
+      throw Error(BSE_ERR_NOT_PD, "projected A-B is not positive definite (A-B or A+B not PD)");
+    k_zero_strict_upper<<<gb, tb, 0, s>>>(m, L.as<double2>(), mmax);
+    note_launches(1);
+    // s = l^H a+ l
+    BSE_CUBLAS(cublasZtrmm(h.blas, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N,
+                           CUBLAS_DIAG_NON_UNIT, m, m, &one, L.as<cuDoubleComplex>(), mmax,
+                           ap.as<cuDoubleComplex>(), mmax, W.as<cuDoubleComplex>(), mmax));
+    BSE_CUBLAS(cublasZtrmm(h.blas, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_C,
+                           CUBLAS_DIAG_NON_UNIT, m, m, &one, L.as<cuDoubleComplex>(), mmax,
+                           W.as<cuDoubleComplex>(), mmax, S.as<cuDoubleComplex>(), mmax));
+    BSE_CUSOLVER(cusolverDnZheevd(h.solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, m,
+                                  S.as<cuDoubleComplex>(), mmax, dE.as<double>(),
+                                  work_->as<cuDoubleComplex>(), lwork, info.as<int>()));
+    std::vector<double> e2(m);
+    BSE_CUDA(cudaMemcpyAsync(e2.data(), dE.ptr, m * 8, cudaMemcpyDeviceToHost, s));
+    BSE_CUDA(cudaMemcpyAsync(&hinfo, info.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BSE_CUDA(cudaStreamSynchronize(s));
+    if (hinfo != 0) throw Error(BSE_ERR_CUDA, "zheevd on the projected problem failed");
+    E.assign(k, 0.0);
+    std::vector<double> f(k);
+    for (int j = 0; j < k; ++j) {
+      if (!(e2[j] > 0.0)) throw Error(BSE_ERR_NOT_PD, "projected E^2 <= 0 (A+B not PD)");
+      E[j] = std::sqrt(e2[j]);
+      f[j] = 1.0 / std::sqrt(E[j]);
+    }
+    // u = l z E^-1/2
+    BSE_CUBLAS(cublasZtrmm(h.blas, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N,
+                           CUBLAS_DIAG_NON_UNIT, m, k, &one, L.as<cuDoubleComplex>(), mmax,
+                           S.as<cuDoubleComplex>(), mmax, U.as<cuDoubleComplex>(), mmax));
+    BSE_CUDA(cudaMemcpyAsync(dF.ptr, f.data(), k * 8, cudaMemcpyHostToDevice, s));
+    k_scale_cols<<<dim3((m + 127) / 128, k), 128, 0, s>>>(m, k, U.as<double2>(), mmax,
+                                                          dF.as<double>());
+    // w = a+ u / E
+    BSE_CUBLAS(cublasZgemm(h.blas, CUBLAS_OP_N, CUBLAS_OP_N, m, k, m, &one,
+                           ap.as<cuDoubleComplex>(), mmax, U.as<cuDoubleComplex>(), mmax, &zero,
+                           W.as<cuDoubleComplex>(), mmax));
+    for (int j = 0; j < k; ++j) f[j] = 1.0 / E[j];
+    BSE_CUDA(cudaMemcpyAsync(dF.ptr, f.data(), k * 8, cudaMemcpyHostToDevice, s));
+    k_scale_cols<<<dim3((m + 127) / 128, k), 128, 0, s>>>(m, k, W.as<double2>(), mmax,
+                                                          dF.as<double>());
+    note_launches(2);
+    BSE_CUDA(cudaMemcpyAsync(dE.ptr, E.data(), k * 8, cudaMemcpyHostToDevice, s));
+  }
+
+  // r+ = P u - V (w E), r- = M w - V (u E) into R1, R2 (n x k); returns max column norms
+  void residuals(int k, const std::vector<double>& E, std::vector<double>& res) {
+    const cuDoubleComplex one = make_cuDoubleComplex(1, 0), zero = make_cuDoubleComplex(0, 0),
+                          mone = make_cuDoubleComplex(-1, 0);
+    // X+Y and X-Y as full vectors, scaled by E: T[:, 0:k] = V (w E), T[:, k:2k] = V (u E)
+    BSE_CUBLAS(cublasZgemm(h.blas, CUBLAS_OP_N, CUBLAS_OP_N, n, k, m, &one,
+                           V.as<cuDoubleComplex>(), n, W.as<cuDoubleComplex>(), mmax, &zero,
+                           T.as<cuDoubleComplex>(), n));
+    BSE_CUBLAS(cublasZgemm(h.blas, CUBLAS_OP_N, CUBLAS_OP_N, n, k, m, &one,
+                           V.as<cuDoubleComplex>(), n, U.as<cuDoubleComplex>(), mmax, &zero,
+                           col(T, k, n), n));
+    k_scale_cols<<<dim3((n + 127) / 128, k), 128, 0, s>>>(n, k, T.as<double2>(), n, dE.as<double>());
+    k_scale_cols<<<dim3((n + 127) / 128, k), 128, 0, s>>>(n, k, T.as<double2>() + (int64_t)k * n, n,
+                                                          dE.as<double>());
+    note_launches(2);
+    BSE_CUBLAS(cublasZgemm(h.blas, CUBLAS_OP_N, CUBLAS_OP_N, n, k, m, &one,
+                           P.as<cuDoubleComplex>(), n, U.as<cuDoubleComplex>(), mmax, &zero,
+                           R1.as<cuDoubleComplex>(), n));
+    BSE_CUBLAS(cublasZaxpy(h.blas, n * k, &mone, T.as<cuDoubleComplex>(), 1,
+                           R1.as<cuDoubleComplex>(), 1));
+    BSE_CUBLAS(cublasZgemm(h.blas, CUBLAS_OP_N, CUBLAS_OP_N, n, k, m, &one,
+                           M.as<cuDoubleComplex>(), n, W.as<cuDoubleComplex>(), mmax, &zero,
+                           R2.as<cuDoubleComplex>(), n));
+    BSE_CUBLAS(cublasZaxpy(h.blas, n * k, &mone, col(T, k, n), 1, R2.as<cuDoubleComplex>(), 1));
+    res.assign(k, 0.0);
+    for (int j = 0; j < k; ++j) {
+      double a = 0, b = 0;
+      BSE_CUBLAS(cublasDznrm2(h.blas, n, col(R1, j, n), 1, &a));
+      BSE_CUBLAS(cublasDznrm2(h.blas, n, col(R2, j, n), 1, &b));
+      res[j] = std::max(a, b);
+    }
+  }
+};
+
+}  // namespace
+
+void davidson_fp64(int n, const bse_c128* A, const bse_c128* B, int64_t ld, int nev, double tol,
+                   int max_iter, int precond, const MlpNet* mlp, double* E_out,
+                   bse_c128* XpY_out, int32_t* iters_out, cudaStream_t s) {
+  std::unique_lock<std::mutex> lock;
+  LibHandles h = acquire_handles(lock);
+  BSE_CUSOLVER(cusolverDnSetStream(h.solver, s));
+  BSE_CUBLAS(cublasSetStream(h.blas, s));
+  BSE_CUBLAS(cublasSetPointerMode(h.blas, CUBLAS_POINTER_MODE_HOST));
+
+  const int mmax = std::min(n, std::max(8 * nev, nev + 32));
+  Solver sv(n, nev, mmax, A, B, ld, s, h);
+
+  // diagonal of A: initial guess (unit vectors at the smallest A_aa) and preconditioner
+  k_diag_real<<<(n + 255) / 256, 256, 0, s>>>(n, reinterpret_cast<const double2*>(A), ld,
+                                              sv.dD.as<double>());
+  note_launches(1);
+  sv.D.resize(n);
+  BSE_CUDA(cudaMemcpyAsync(sv.D.data(), sv.dD.ptr, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+  BSE_CUDA(cudaStreamSynchronize(s));
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return sv.D[a] < sv.D[b]; });
+  const int b0 = std::min(n, std::min(mmax, nev + std::max(4, nev / 4)));
+  BSE_CUDA(cudaMemsetAsync(sv.V.ptr, 0, (size_t)n * b0 * 16, s));
+  for (int j = 0; j < b0; ++j) {
+    const double2 one = make_double2(1.0, 0.0);
+    BSE_CUDA(cudaMemcpyAsync(sv.V.as<double2>() + (int64_t)j * n + order[j], &one, 16,
+                             cudaMemcpyHostToDevice, s));
+  }
+  sv.m = b0;
+  sv.matvec(0, b0);
+
+  std::vector<double> E, res;
+  const int k = nev;
+  int it = 0;
+  bool converged = false;
+  for (it = 1; it <= max_iter; ++it) {
+    sv.rayleigh_ritz(k, E);
+    sv.residuals(k, E, res);
+    std::vector<int> todo;
+    for (int j = 0; j < k; ++j)
+      if (!(res[j] < tol)) todo.push_back(j);
+    if (todo.empty()) {
+      converged = true;
+      break;
+    }
+    if (it == max_iter) break;
+    const int nt = (int)todo.size();
+    // preconditioned corrections of both residuals, columns in T
+    std::vector<double> et(nt);
+    for (int i = 0; i < nt; ++i) et[i] = E[todo[i]];
+    BSE_CUDA(cudaMemcpyAsync(sv.dF.ptr, et.data(), nt * 8, cudaMemcpyHostToDevice, s));
+    for (int i = 0; i < nt; ++i) {
+      BSE_CUDA(cudaMemcpyAsync(sv.AV.as<double2>() + (int64_t)i * n,
+                               sv.R1.as<double2>() + (int64_t)todo[i] * n, (size_t)n * 16,
+                               cudaMemcpyDeviceToDevice, s));
+      BSE_CUDA(cudaMemcpyAsync(sv.AV.as<double2>() + (int64_t)(nt + i) * n,
+                               sv.R2.as<double2>() + (int64_t)todo[i] * n, (size_t)n * 16,
+                               cudaMemcpyDeviceToDevice, s));
+    }
+    // both blocks use the same eigenvalue list
+    BSE_CUDA(cudaMemcpyAsync(sv.dF.as<double>() + nt, et.data(), nt * 8, cudaMemcpyHostToDevice, s));
+    if (precond == 1) {
+      mlp_precondition(mlp, n, 2 * nt, sv.dD.as<double>(), sv.dF.as<double>(),
+                       sv.AV.as<double2>(), n, sv.T.as<double2>(), n, s);
+    } else {
+      k_precond_diag<<<dim3((n + 127) / 128, 2 * nt), 128, 0, s>>>(
+          n, 2 * nt, sv.dD.as<double>(), sv.dF.as<double>(), sv.AV.as<double2>(), n,
+          sv.T.as<double2>(), n);
+      BSE_CUDA(cudaGetLastError());
+      note_launches(1);
+    }
+    // restart from the Ritz vectors when the new block would not fit
+    if (sv.m + 2 * nt > mmax) {
+      const cuDoubleComplex one = make_cuDoubleComplex(1, 0), zero = make_cuDoubleComplex(0, 0);
+      // X+Y and X-Y of the wanted pairs into R1 (n x 2k), then rebuild V from them
+      BSE_CUBLAS(cublasZgemm(h.blas, CUBLAS_OP_N, CUBLAS_OP_N, n, k, sv.m, &one,
+                             sv.V.as<cuDoubleComplex>(), n, sv.U.as<cuDoubleComplex>(), mmax,
+                             &zero, sv.R1.as<cuDoubleComplex>(), n));
+      BSE_CUBLAS(cublasZgemm(h.blas, CUBLAS_OP_N, CUBLAS_OP_N, n, k, sv.m, &one,
+                             sv.V.as<cuDoubleComplex>(), n, sv.W.as<cuDoubleComplex>(), mmax,
+                             &zero, sv.R1.as<cuDoubleComplex>() + (int64_t)k * n, n));
+      sv.m = 0;
+      for (int j = 0; j < 2 * k; ++j) sv.append(sv.R1.as<cuDoubleComplex>() + (int64_t)j * n);
+      sv.matvec(0, sv.m);
+    }
+    const int m0 = sv.m;
+    for (int j = 0; j < 2 * nt; ++j) sv.append(sv.T.as<cuDoubleComplex>() + (int64_t)j * n);
+    if (sv.m == m0) break;   // no new direction: stagnated
+    sv.matvec(m0, sv.m);
+  }
+  if (iters_out) *iters_out = std::min(it, max_iter);
+
+  // outputs: E and X+Y = V u for the nev lowest
+  BSE_CUDA(cudaMemcpyAsync(E_out, E.data(), (size_t)k * 8, cudaMemcpyHostToDevice, s));
+  if (XpY_out) {
+    const cuDoubleComplex one = make_cuDoubleComplex(1, 0), zero = make_cuDoubleComplex(0, 0);
+    BSE_CUBLAS(cublasZgemm(h.blas, CUBLAS_OP_N, CUBLAS_OP_N, n, k, sv.m, &one,
+                           sv.V.as<cuDoubleComplex>(), n, sv.U.as<cuDoubleComplex>(), mmax, &zero,
+                           reinterpret_cast<cuDoubleComplex*>(XpY_out), n));
+  }
+  BSE_CUDA(cudaStreamSynchronize(s));
+  if (!converged)
+    throw Error(BSE_ERR_NO_CONV, "Davidson did not reach the residual tolerance in " +
+                                     std::to_string(max_iter) + " iterations");
+}
+
+}  // namespace bse

@@ -171,6 +171,12 @@ int grid_for(int64_t total, int threads) {
 
 }  // namespace
 
+LibHandles acquire_handles(std::unique_lock<std::mutex>& lock) {
+  lock = std::unique_lock<std::mutex>(g_handle_mutex);
+  Handles& h = handles_for_current_device();
+  return LibHandles{h.solver, h.blas};
+}
+
 void reduce_fp64(int n, const bse_c128* A, const bse_c128* B, int64_t ld, bse_c128* S,
                  bse_c128* L, int32_t* failed_minor, cudaStream_t s) {
   std::lock_guard<std::mutex> lock(g_handle_mutex);

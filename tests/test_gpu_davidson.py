@@ -1,0 +1,78 @@
+"""Lowest excitons by block Davidson against the oracle's dense solve (GPU).
+
+The Davidson iteration converges to the lowest eigenpairs of the product form
+(A-B)(A+B)(X+Y) = E^2 (X+Y); the oracle reaches the same E by the dense
+square-root reduction (Eq. auxham) and a full eigendecomposition."""
+import numpy as np
+import pytest
+
+import bse_inputs as bi
+from oracle import bse_oracle as O
+from test_gpu_fp64 import gpu_build, problem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bse():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1904_05575_gb300 import build
+    build.build()
+    import paper_1904_05575_gb300 as m
+    m.load()
+    return m
+
+
+def _run(bse, d, n, nev, coupling=True, tol=1e-6, max_iter=200, precond=0, mlp=None):
+    import torch
+    E = torch.empty(nev, dtype=torch.float64, device="cuda")
+    X = torch.empty((nev, n), dtype=torch.complex128, device="cuda")
+    it = bse.bse_lowest_excitons(n, d["A"], d["B"] if coupling else None, nev, E, X,
+                                 tol_ev=tol, max_iter=max_iter, precond=precond, mlp=mlp)
+    torch.cuda.synchronize()
+    return E.cpu().numpy(), X.cpu().numpy().T, it
+
+
+@pytest.mark.parametrize("name,nev", [("c1", 8), ("c2", 16), ((3, 2, 3, 27), 10)], ids=str)
+@pytest.mark.parametrize("coupling", [True, False], ids=["full", "tda"])
+def test_davidson_matches_dense(bse, name, nev, coupling):
+    p = problem(name)
+    n = p["nk"] * p["nv"] * p["nc"]
+    A, B = O.build_A_B(p, coupling=coupling)
+    if coupling:
+        e_ref, _ = O.solve_full(A, B)
+    else:
+        e_ref = np.linalg.eigvalsh(A)
+    d = gpu_build(bse, p, coupling=coupling)
+    e, xpy, it = _run(bse, d, n, nev, coupling)
+    assert np.abs(e - np.sort(e_ref)[:nev]).max() < 1e-8
+    # the returned X+Y satisfy the product form and the normalisation
+    Bm = B if coupling else np.zeros_like(A)
+    xmy = ((A + Bm) @ xpy) / e[None, :]
+    assert np.allclose((A - Bm) @ xmy, xpy * e[None, :], atol=1e-5)
+    assert np.allclose(np.diag(xpy.conj().T @ xmy).real, 1.0, atol=1e-8)
+    assert 1 <= it < 200
+
+
+def test_davidson_no_convergence_is_reported(bse):
+    p = problem("c2")
+    n = p["nk"] * p["nv"] * p["nc"]
+    d = gpu_build(bse, p)
+    with pytest.raises(bse.BSEError) as ei:
+        _run(bse, d, n, 16, tol=1e-12, max_iter=2)
+    assert ei.value.status == bse.BSE_ERR_NO_CONV
+
+
+def test_davidson_argument_errors(bse):
+    import torch
+    p = problem("c1")
+    n = p["nk"] * p["nv"] * p["nc"]
+    d = gpu_build(bse, p)
+    E = torch.empty(4, dtype=torch.float64, device="cuda")
+    for kw, status in [(dict(nev=0), bse.BSE_ERR_ARG), (dict(nev=n + 1), bse.BSE_ERR_ARG),
+                       (dict(nev=4, precond=1), bse.BSE_ERR_ARG)]:
+        with pytest.raises(bse.BSEError) as ei:
+            bse.bse_lowest_excitons(n, d["A"], d["B"], kw.pop("nev"), E, None, **kw)
+        assert ei.value.status == status
