@@ -288,3 +288,13 @@ def scaled(problem: Dict[str, np.ndarray], **factors) -> Dict[str, np.ndarray]:
     for name, f in factors.items():
         out[name] = problem[name] * f
     return out
+
+
+def directions(n: int, m: int, seed: int = 7, name: str = "directions") -> np.ndarray:
+    """m seeded complex-normal unit vectors of length n, as an [n, m] array
+    (perturbation directions for preconditioner training samples)."""
+    out = np.empty((n, m), np.complex128)
+    for j in range(m):
+        v = _cnormal(_rng(seed, name, j), (n,))
+        out[:, j] = v / np.linalg.norm(v)
+    return out

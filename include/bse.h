@@ -179,6 +179,14 @@ int bse_spectrum(int32_t n, bse_c128* S_inout, const bse_c128* L, int64_t ld,
 int bse_phase_timing(int32_t enable);
 int bse_phase_report(char* buf, int64_t buflen);
 
+/* Eigenvectors of the full problem from the reduction: X+Y = L Z E^{-1/2}
+ * (the reconstruction after Eq. auxevp in the Cholesky form, A-B = L L^H), for
+ * the first k columns of Z (S_inout of bse_spectrum after it returns), L from
+ * bse_reduce, E [k] from bse_spectrum.  XpY_out: n x k column-major (ld n),
+ * normalised so that (X+Y)^H (X-Y) = 1.  All device pointers; asynchronous. */
+int bse_xpy(int32_t n, int32_t k, const bse_c128* Z, const bse_c128* L, int64_t ld,
+            const double* E, bse_c128* XpY_out, void* cuda_stream);
+
 /* Lowest nev excitons of the full BSE without the dense O(N^3) solve: block
  * Davidson on the half-size product form (A-B)(A+B)(X+Y) = E^2 (X+Y), which
  * follows from Eq. gevpbse with H = [[A,B],[B,A]] (Eq. Hetr) and underlies
@@ -199,6 +207,68 @@ int bse_phase_report(char* buf, int64_t buflen);
 int bse_lowest_excitons(int32_t n, const bse_c128* A, const bse_c128* B, int64_t ld, int32_t nev,
                         double tol_ev, int32_t max_iter, int32_t precond, const void* mlp,
                         double* E_out, bse_c128* XpY_out, int32_t* iters_out, void* cuda_stream);
+
+/* ---- learned preconditioner for bse_lowest_excitons -------------------------
+ * Not in the paper: a per-transition network (4 features -> 128 -> 128 -> 1,
+ * ReLU, FP16 weights, FP32 arithmetic) predicting a factor c that rescales the
+ * diagonal gain of the Davidson correction, t_a = c r_a / (D_a - E), D the
+ * diagonal of A+B (residual of (A+B)(X+Y) = E(X-Y)) or of A-B (the other
+ * equation); features [D_a - E, D'_a - E, off-diagonal row norm of A, E/10].
+ * An untrained network gives c ~ 1, the diagonal preconditioner.
+ * The handle owns device memory on the device current at creation. */
+
+/* Create with deterministic initial weights from seed; n_features must be 4
+ * and hidden 128 (BSE_ERR_UNSUPPORTED otherwise). */
+int bse_mlp_create(void** mlp, int32_t n_features, int32_t hidden, uint64_t seed);
+void bse_mlp_destroy(void* mlp);
+int64_t bse_mlp_num_params(const void* mlp);
+/* Parameters in the order W1 [128][4], b1 [128], W2 [128][128], b2, w3 [128],
+ * b3 [1] (row-major), as the FP16 values the network uses, to / from host. */
+int bse_mlp_get_params(const void* mlp, float* host, int64_t count);
+int bse_mlp_set_params(void* mlp, const float* host, int64_t count);
+
+/* Training samples from exact pairs (E [nev], X+Y [n x nev] column-major, both
+ * device) of the full problem: X-Y = (A+B)(X+Y)/E, both perturbed by eps p
+ * (noise [n x nev] device, column lambda the direction p of pair lambda); the
+ * residuals r of the two half-size equations give, per transition a, the gain
+ * g* = Re(conj(r_a) eps p_a)/|r_a|^2 that maps r_a onto the perturbation, the
+ * target factor c* = g* (D_a - E) and weight |r_a|^2/(D_a - E)^2 normalised
+ * over each vector.  Outputs (device, sample s = (2 lambda + eq) n + a,
+ * eq 0 = the (A+B) equation): feat_out [2 nev n][4], target_out and
+ * weight_out [2 nev n] (FP32).  B = NULL for the TDA problem. */
+int bse_mlp_samples(int32_t n, const bse_c128* A, const bse_c128* B, int64_t ld, int32_t nev,
+                    const double* E, const bse_c128* XpY, const bse_c128* noise, double eps,
+                    float* feat_out, float* target_out, float* weight_out, void* cuda_stream);
+
+/* Training samples from a Davidson trajectory: runs bse_lowest_excitons with
+ * the diagonal preconditioner on (A, B) whose exact lowest pairs (E_exact
+ * [nev], XpY_exact [n x nev], device) are known; at every iteration each
+ * unconverged pair contributes, for both half-size equations, the samples of
+ * its residual against the current error (Ritz vector minus the exact vector
+ * aligned in phase), defined as in bse_mlp_samples with that error as the
+ * step.  Stops at convergence (tol_ev), max_iter or when the next vector's
+ * samples would exceed capacity; count_out (host) receives the number
+ * written.  Outputs as in bse_mlp_samples (device).  Syncs. */
+int bse_mlp_trajectory_samples(int32_t n, const bse_c128* A, const bse_c128* B, int64_t ld,
+                               int32_t nev, const double* E_exact, const bse_c128* XpY_exact,
+                               double tol_ev, int32_t max_iter, int64_t capacity, float* feat_out,
+                               float* target_out, float* weight_out, int64_t* count_out,
+                               void* cuda_stream);
+
+/* Loss sum_s w_s (c_s - c*_s)^2 / sum_s w_s over nsamp device samples and its
+ * gradient with respect to the FP16 parameters (grad_out: host, count
+ * bse_mlp_num_params, or NULL).  Syncs. */
+int bse_mlp_loss_grad(void* mlp, const float* feat, const float* target, const float* weight,
+                      int64_t nsamp, double* loss_out, float* grad_out, void* cuda_stream);
+
+/* steps of full-batch Adam (beta1 0.9, beta2 0.999) with learning rate lr on
+ * the same loss; loss_out (host) receives the final loss.  Syncs. */
+int bse_mlp_train(void* mlp, const float* feat, const float* target, const float* weight,
+                  int64_t nsamp, int32_t steps, double lr, double* loss_out, void* cuda_stream);
+
+/* factor_out[s] = c(feat[s]) for nsamp device feature rows. */
+int bse_mlp_predict(const void* mlp, const float* feat, int64_t nsamp, float* factor_out,
+                    void* cuda_stream);
 
 /* 1 if this build serves the given bse_precision in bse_build_kernel, else 0.
  * Host only; no CUDA call. */

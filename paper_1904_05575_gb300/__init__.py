@@ -51,7 +51,10 @@ _lib: Optional[ctypes.CDLL] = None
 
 EXPORTED = ("bse_build_kernel", "bse_reduce", "bse_spectrum", "bse_last_error", "bse_version",
             "bse_kernel_launches", "bse_precision_supported", "bse_phase_timing",
-            "bse_phase_report", "bse_build_kernel_fp64_static", "bse_lowest_excitons")
+            "bse_phase_report", "bse_build_kernel_fp64_static", "bse_lowest_excitons",
+            "bse_mlp_create", "bse_mlp_destroy", "bse_mlp_num_params", "bse_mlp_get_params",
+            "bse_mlp_set_params", "bse_mlp_samples", "bse_mlp_loss_grad", "bse_mlp_train",
+            "bse_mlp_predict", "bse_xpy", "bse_mlp_trajectory_samples")
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -74,6 +77,26 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.bse_lowest_excitons.argtypes = [i32, vp, vp, i64, i32, dbl, i32, i32, vp, vp, vp,
                                         ctypes.POINTER(i32), vp]
     lib.bse_lowest_excitons.restype = ctypes.c_int
+    lib.bse_xpy.argtypes = [i32, i32, vp, vp, i64, vp, vp, vp]
+    lib.bse_xpy.restype = ctypes.c_int
+    f32p = ctypes.POINTER(ctypes.c_float)
+    lib.bse_mlp_create.argtypes = [ctypes.POINTER(vp), i32, i32, ctypes.c_uint64]
+    lib.bse_mlp_destroy.argtypes = [vp]
+    lib.bse_mlp_destroy.restype = None
+    lib.bse_mlp_num_params.argtypes = [vp]
+    lib.bse_mlp_num_params.restype = ctypes.c_int64
+    lib.bse_mlp_get_params.argtypes = [vp, f32p, i64]
+    lib.bse_mlp_set_params.argtypes = [vp, f32p, i64]
+    lib.bse_mlp_samples.argtypes = [i32, vp, vp, i64, i32, vp, vp, vp, dbl, vp, vp, vp, vp]
+    lib.bse_mlp_trajectory_samples.argtypes = [i32, vp, vp, i64, i32, vp, vp, dbl, i32, i64,
+                                               vp, vp, vp, ctypes.POINTER(i64), vp]
+    lib.bse_mlp_trajectory_samples.restype = ctypes.c_int
+    lib.bse_mlp_loss_grad.argtypes = [vp, vp, vp, vp, i64, ctypes.POINTER(dbl), f32p, vp]
+    lib.bse_mlp_train.argtypes = [vp, vp, vp, vp, i64, i32, dbl, ctypes.POINTER(dbl), vp]
+    lib.bse_mlp_predict.argtypes = [vp, vp, i64, vp, vp]
+    for name in ("bse_mlp_create", "bse_mlp_get_params", "bse_mlp_set_params", "bse_mlp_samples",
+                 "bse_mlp_loss_grad", "bse_mlp_train", "bse_mlp_predict"):
+        getattr(lib, name).restype = ctypes.c_int
     lib.bse_phase_timing.argtypes = [i32]
     lib.bse_phase_report.argtypes = [ctypes.c_char_p, i64]
     lib.bse_precision_supported.argtypes = [i32]
@@ -231,6 +254,17 @@ def bse_phase_report() -> Dict[str, tuple]:
     return out
 
 
+def bse_xpy(n: int, k: int, Z, L, E, XpY_out, stream=None) -> None:
+    """X+Y = L Z E^-1/2 for the first k eigenvectors (XpY_out [k, n] CUDA complex128)."""
+    import torch
+    z, ld = _matrix_ptr(Z, n, "Z")
+    l, _ = _matrix_ptr(L, n, "L")
+    if XpY_out.shape != (k, n):
+        raise ValueError("XpY_out must have shape [k, n]")
+    _check(load().bse_xpy(n, k, z, l, ld, _ptr(E, torch.float64, "E"),
+                          _ptr(XpY_out, torch.complex128, "XpY_out"), _stream(stream)))
+
+
 def bse_kernel_launches() -> int:
     return int(load().bse_kernel_launches())
 
@@ -263,3 +297,105 @@ def matrix_to_numpy(t, n: int) -> np.ndarray:
 def mixed_available() -> bool:
     """True when this build serves the split-precision tensor-core build."""
     return bool(load().bse_precision_supported(BSE_PREC_BF16X6))
+
+
+class MLP:
+    """Handle of the learned Davidson preconditioner (bse_mlp_* in include/bse.h)."""
+
+    def __init__(self, seed: int = 1, n_features: int = 4, hidden: int = 128):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.bse_mlp_create(ctypes.byref(h), n_features, hidden, seed))
+        self.handle = h
+        self.num_params = int(lib.bse_mlp_num_params(h))
+
+    def close(self):
+        if self.handle:
+            load().bse_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.num_params, np.float32)
+        _check(load().bse_mlp_get_params(self.handle, out.ctypes.data_as(
+            ctypes.POINTER(ctypes.c_float)), self.num_params))
+        return out
+
+    def set_params(self, v: np.ndarray) -> None:
+        v = np.ascontiguousarray(v, np.float32)
+        _check(load().bse_mlp_set_params(self.handle, v.ctypes.data_as(
+            ctypes.POINTER(ctypes.c_float)), self.num_params))
+
+    def loss_grad(self, feat, target, weight, stream=None):
+        import torch
+        g = np.empty(self.num_params, np.float32)
+        L = ctypes.c_double(0.0)
+        _check(load().bse_mlp_loss_grad(self.handle, _ptr(feat, torch.float32, "feat"),
+                                        _ptr(target, torch.float32, "target"),
+                                        _ptr(weight, torch.float32, "weight"), target.numel(),
+                                        ctypes.byref(L), g.ctypes.data_as(
+                                            ctypes.POINTER(ctypes.c_float)), _stream(stream)))
+        return L.value, g
+
+    def train(self, feat, target, weight, steps: int, lr: float, stream=None) -> float:
+        import torch
+        L = ctypes.c_double(0.0)
+        _check(load().bse_mlp_train(self.handle, _ptr(feat, torch.float32, "feat"),
+                                    _ptr(target, torch.float32, "target"),
+                                    _ptr(weight, torch.float32, "weight"), target.numel(),
+                                    int(steps), float(lr), ctypes.byref(L), _stream(stream)))
+        return L.value
+
+    def predict(self, feat, out, stream=None) -> None:
+        import torch
+        _check(load().bse_mlp_predict(self.handle, _ptr(feat, torch.float32, "feat"),
+                                      feat.shape[0], _ptr(out, torch.float32, "out"),
+                                      _stream(stream)))
+
+
+def bse_mlp_samples(n: int, A, B, E, XpY, noise, eps: float, stream=None):
+    """Training samples (feat [2 nev n, 4], target, weight: CUDA float32 tensors)."""
+    import torch
+    lib = load()
+    a, ld = _matrix_ptr(A, n, "A")
+    b = _matrix_ptr(B, n, "B")[0] if B is not None else None
+    nev = E.numel()
+    if XpY.shape != (nev, n) or noise.shape != (nev, n):
+        raise ValueError("XpY and noise must have shape [nev, n] (column-major n x nev)")
+    ns = 2 * nev * n
+    feat = torch.empty((ns, 4), dtype=torch.float32, device="cuda")
+    target = torch.empty(ns, dtype=torch.float32, device="cuda")
+    weight = torch.empty(ns, dtype=torch.float32, device="cuda")
+    _check(lib.bse_mlp_samples(n, a, b, ld, nev, _ptr(E, torch.float64, "E"),
+                               _ptr(XpY, torch.complex128, "XpY"),
+                               _ptr(noise, torch.complex128, "noise"), float(eps),
+                               _ptr(feat), _ptr(target), _ptr(weight), _stream(stream)))
+    return feat, target, weight
+
+
+def bse_mlp_trajectory_samples(n: int, A, B, E, XpY, tol_ev: float = 1e-6, max_iter: int = 60,
+                               capacity: int = 1 << 20, stream=None):
+    """Samples recorded along a diagonal-preconditioned Davidson run whose exact
+    pairs (E, XpY [nev, n]) are known; returns (feat, target, weight) trimmed."""
+    import torch
+    lib = load()
+    a, ld = _matrix_ptr(A, n, "A")
+    b = _matrix_ptr(B, n, "B")[0] if B is not None else None
+    nev = E.numel()
+    if XpY.shape != (nev, n):
+        raise ValueError("XpY must have shape [nev, n]")
+    feat = torch.empty((capacity, 4), dtype=torch.float32, device="cuda")
+    target = torch.empty(capacity, dtype=torch.float32, device="cuda")
+    weight = torch.empty(capacity, dtype=torch.float32, device="cuda")
+    cnt = ctypes.c_int64(0)
+    _check(lib.bse_mlp_trajectory_samples(n, a, b, ld, nev, _ptr(E, torch.float64, "E"),
+                                          _ptr(XpY, torch.complex128, "XpY"), float(tol_ev),
+                                          int(max_iter), int(capacity), _ptr(feat), _ptr(target),
+                                          _ptr(weight), ctypes.byref(cnt), _stream(stream)))
+    c = cnt.value
+    return feat[:c].contiguous(), target[:c].contiguous(), weight[:c].contiguous()

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "bse_internal.h"
+#include "mlp.h"
 
 namespace bse {
 
@@ -262,6 +263,15 @@ extern "C" int bse_precision_supported(int32_t precision) {
   return 0;
 }
 
+extern "C" int bse_xpy(int32_t n, int32_t k, const bse_c128* Z, const bse_c128* L, int64_t ld,
+                       const double* E, bse_c128* XpY_out, void* cuda_stream) {
+  return guarded([&] {
+    BSE_CHECK_ARG(n >= 1 && k >= 1 && k <= n && ld >= n, "bad n, k or ld");
+    BSE_CHECK_ARG(Z && L && E && XpY_out, "NULL argument");
+    xpy_fp64(n, k, Z, L, ld, E, XpY_out, n, static_cast<cudaStream_t>(cuda_stream));
+  });
+}
+
 extern "C" int bse_lowest_excitons(int32_t n, const bse_c128* A, const bse_c128* B, int64_t ld,
                                    int32_t nev, double tol_ev, int32_t max_iter, int32_t precond,
                                    const void* mlp, double* E_out, bse_c128* XpY_out,
@@ -280,6 +290,120 @@ extern "C" int bse_lowest_excitons(int32_t n, const bse_c128* A, const bse_c128*
     davidson_fp64(n, A, B, ld, nev, tol_ev, max_iter, precond,
                   static_cast<const MlpNet*>(mlp), E_out, XpY_out, iters_out,
                   static_cast<cudaStream_t>(cuda_stream));
+  });
+}
+
+extern "C" int bse_mlp_create(void** mlp, int32_t n_features, int32_t hidden, uint64_t seed) {
+  return guarded([&] {
+    BSE_CHECK_ARG(mlp != nullptr, "mlp is NULL");
+    *mlp = nullptr;
+    if (n_features != 4 || hidden != 128)
+      throw Error(BSE_ERR_UNSUPPORTED, "this build provides n_features = 4 and hidden = 128");
+    *mlp = mlp_create(seed);
+  });
+}
+
+extern "C" void bse_mlp_destroy(void* mlp) { mlp_destroy(static_cast<MlpNet*>(mlp)); }
+
+extern "C" int64_t bse_mlp_num_params(const void* mlp) {
+  return mlp ? mlp_num_params(static_cast<const MlpNet*>(mlp)) : 0;
+}
+
+extern "C" int bse_mlp_get_params(const void* mlp, float* host, int64_t count) {
+  return guarded([&] {
+    BSE_CHECK_ARG(mlp && host, "NULL mlp or host buffer");
+    BSE_CHECK_ARG(count == mlp_num_params(static_cast<const MlpNet*>(mlp)), "wrong count");
+    mlp_get_params(static_cast<const MlpNet*>(mlp), host);
+  });
+}
+
+extern "C" int bse_mlp_set_params(void* mlp, const float* host, int64_t count) {
+  return guarded([&] {
+    BSE_CHECK_ARG(mlp && host, "NULL mlp or host buffer");
+    BSE_CHECK_ARG(count == mlp_num_params(static_cast<MlpNet*>(mlp)), "wrong count");
+    mlp_set_params(static_cast<MlpNet*>(mlp), host);
+  });
+}
+
+extern "C" int bse_mlp_samples(int32_t n, const bse_c128* A, const bse_c128* B, int64_t ld,
+                               int32_t nev, const double* E, const bse_c128* XpY,
+                               const bse_c128* noise, double eps, float* feat_out,
+                               float* target_out, float* weight_out, void* cuda_stream) {
+  return guarded([&] {
+    BSE_CHECK_ARG(n >= 1 && ld >= n && nev >= 1 && nev <= n, "bad n, ld or nev");
+    BSE_CHECK_ARG(A && E && XpY && noise && feat_out && target_out && weight_out,
+                  "NULL argument");
+    BSE_CHECK_ARG(std::isfinite(eps) && eps > 0.0, "eps must be > 0");
+    keep_pool_memory();
+    mlp_samples(n, A, B, ld, nev, E, XpY, noise, eps, feat_out, target_out, weight_out,
+                static_cast<cudaStream_t>(cuda_stream));
+  });
+}
+
+extern "C" int bse_mlp_trajectory_samples(int32_t n, const bse_c128* A, const bse_c128* B,
+                                          int64_t ld, int32_t nev, const double* E_exact,
+                                          const bse_c128* XpY_exact, double tol_ev,
+                                          int32_t max_iter, int64_t capacity, float* feat_out,
+                                          float* target_out, float* weight_out,
+                                          int64_t* count_out, void* cuda_stream) {
+  return guarded([&] {
+    if (count_out) *count_out = 0;
+    BSE_CHECK_ARG(n >= 1 && ld >= n && nev >= 1 && nev <= n, "bad n, ld or nev");
+    BSE_CHECK_ARG(A && E_exact && XpY_exact && feat_out && target_out && weight_out,
+                  "NULL argument");
+    BSE_CHECK_ARG(capacity >= 0 && max_iter >= 1 && tol_ev > 0.0, "bad capacity, max_iter or tol");
+    keep_pool_memory();
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    std::vector<double> eh(nev);
+    BSE_CUDA(cudaMemcpyAsync(eh.data(), E_exact, nev * sizeof(double), cudaMemcpyDeviceToHost, s));
+    BSE_CUDA(cudaStreamSynchronize(s));
+    TrajectorySink sink;
+    sink.xpy_exact = XpY_exact;
+    sink.e_exact = eh.data();
+    sink.capacity = capacity;
+    sink.feat = feat_out;
+    sink.target = target_out;
+    sink.weight = weight_out;
+    DeviceBuffer e_out((size_t)nev * 8, s);
+    try {
+      davidson_fp64(n, A, B, ld, nev, tol_ev, max_iter, 0, nullptr, e_out.as<double>(), nullptr,
+                    nullptr, s, &sink);
+    } catch (const Error& e) {
+      if (e.status != BSE_ERR_NO_CONV) throw;   // recording ends with the iteration limit
+    }
+    if (count_out) *count_out = sink.count;
+  });
+}
+
+extern "C" int bse_mlp_loss_grad(void* mlp, const float* feat, const float* target,
+                                 const float* weight, int64_t nsamp, double* loss_out,
+                                 float* grad_out, void* cuda_stream) {
+  return guarded([&] {
+    BSE_CHECK_ARG(mlp && feat && target && weight && nsamp >= 1, "bad MLP arguments");
+    const double L = mlp_loss_grad(static_cast<MlpNet*>(mlp), feat, target, weight, nsamp,
+                                   grad_out, static_cast<cudaStream_t>(cuda_stream));
+    if (loss_out) *loss_out = L;
+  });
+}
+
+extern "C" int bse_mlp_train(void* mlp, const float* feat, const float* target,
+                             const float* weight, int64_t nsamp, int32_t steps, double lr,
+                             double* loss_out, void* cuda_stream) {
+  return guarded([&] {
+    BSE_CHECK_ARG(mlp && feat && target && weight && nsamp >= 1, "bad MLP arguments");
+    BSE_CHECK_ARG(steps >= 0 && std::isfinite(lr) && lr > 0.0, "bad steps or lr");
+    const double L = mlp_train(static_cast<MlpNet*>(mlp), feat, target, weight, nsamp, steps, lr,
+                               static_cast<cudaStream_t>(cuda_stream));
+    if (loss_out) *loss_out = L;
+  });
+}
+
+extern "C" int bse_mlp_predict(const void* mlp, const float* feat, int64_t nsamp,
+                               float* factor_out, void* cuda_stream) {
+  return guarded([&] {
+    BSE_CHECK_ARG(mlp && feat && factor_out && nsamp >= 1, "bad MLP arguments");
+    mlp_predict(static_cast<const MlpNet*>(mlp), feat, nsamp, factor_out,
+                static_cast<cudaStream_t>(cuda_stream));
   });
 }
 

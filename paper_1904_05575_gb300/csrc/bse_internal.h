@@ -115,13 +115,16 @@ LibHandles acquire_handles(std::unique_lock<std::mutex>& lock);
 
 // Lowest excitons by block Davidson (product form); precond 0 = diagonal, 1 = MLP.
 struct MlpNet;
+struct TrajectorySink;
 void davidson_fp64(int n, const bse_c128* A, const bse_c128* B, int64_t ld, int nev, double tol,
                    int max_iter, int precond, const MlpNet* mlp, double* E_out, bse_c128* XpY_out,
-                   int32_t* iters_out, cudaStream_t stream);
+                   int32_t* iters_out, cudaStream_t stream, TrajectorySink* sink = nullptr);
 
 // Reduction and spectrum.
 void reduce_fp64(int n, const bse_c128* A, const bse_c128* B, int64_t ld, bse_c128* S,
                  bse_c128* L, int32_t* failed_minor, cudaStream_t stream);
+void xpy_fp64(int n, int k, const bse_c128* Z, const bse_c128* L, int64_t ld, const double* E,
+              bse_c128* XpY, int64_t ldx, cudaStream_t stream);
 void spectrum_fp64(int n, bse_c128* S, const bse_c128* L, int64_t ld, const bse_c128* rho,
                    double c_q, double vc, int n_omega, const double* omega, double delta,
                    double* E_out, double* osc_out, bse_c128* eps_out, cudaStream_t stream);

@@ -48,22 +48,6 @@ namespace {
                                            std::to_string((int)st_));             \
   } while (0)
 
-// out[:, j] = H V[:, j], H Hermitian column-major: H[m][k] = conj(H[k + m ld])
-struct MatvecProb {
-  int M, N, K;
-  const bse_c128* H;
-  int64_t ld;
-  const bse_c128* V;   // K x N, column-major, leading dimension ldv
-  int64_t ldv;
-  bse_c128* out;       // M x N, column-major, leading dimension ldo
-  int64_t ldo;
-  __device__ cplx a(int, int m, int k) const { return conj(ldc(H + (int64_t)m * ld + k)); }
-  __device__ cplx b(int, int n, int k) const { return ldc(V + (int64_t)n * ldv + k); }
-  __device__ void store(int, int m, int n, cplx v) const {
-    reinterpret_cast<double2*>(out)[(int64_t)n * ldo + m] = make_double2(v.x, v.y);
-  }
-};
-
 // P = AV + BV, M = AV - BV (B absent: both AV)
 __global__ void k_plus_minus_cols(int64_t total, const double2* av, const double2* bv,
                                   double2* P, double2* M) {
@@ -110,13 +94,15 @@ __global__ void k_scale_cols(int rows, int k, double2* x, int64_t ld, const doub
   }
 }
 
-// t[:, j] = r[:, j] / (d - E_j), denominators kept at least 1e-2 eV away from 0
-__global__ void k_precond_diag(int n, int k, const double* d, const double* e, const double2* r,
-                               int64_t ldr, double2* t, int64_t ldt) {
+// t[:, j] = r[:, j] / (D_q - E_j) with D_q the diagonal of A+B for the first
+// k/2 columns (residuals of the (A+B) equation) and of A-B for the rest;
+// denominators kept at least 1e-2 eV away from 0
+__global__ void k_precond_diag(int n, int k, const double* dp, const double* dm, const double* e,
+                               const double2* r, int64_t ldr, double2* t, int64_t ldt) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y;
   if (i < n && j < k) {
-    double den = d[i] - e[j];
+    double den = (j < k / 2 ? dp[i] : dm[i]) - e[j];
     if (fabs(den) < 1e-2) den = den < 0 ? -1e-2 : 1e-2;
     double2 v = r[i + (int64_t)j * ldr];
     t[i + (int64_t)j * ldt] = make_double2(v.x / den, v.y / den);
@@ -129,7 +115,8 @@ struct Solver {
   int64_t ld;
   cudaStream_t s;
   LibHandles h;
-  DeviceBuffer V, P, M, AV, BV, ap, am, L, S, U, W, R1, R2, T, C, info, dE, dF, dD;
+  DeviceBuffer V, P, M, AV, BV, ap, am, L, S, U, W, R1, R2, T, C, info, dE, dF, dD, dDp, dDm,
+      dS;
   std::unique_ptr<DeviceBuffer> work_;
   int lwork = 0;
   int m = 0;          // current basis size
@@ -143,10 +130,11 @@ struct Solver {
         BV((size_t)n_ * std::max(mmax_, 2 * nev_) * 16, s_), ap((size_t)mmax_ * mmax_ * 16, s_),
         am((size_t)mmax_ * mmax_ * 16, s_), L((size_t)mmax_ * mmax_ * 16, s_),
         S((size_t)mmax_ * mmax_ * 16, s_), U((size_t)mmax_ * mmax_ * 16, s_),
-        W((size_t)mmax_ * mmax_ * 16, s_), R1((size_t)n_ * std::max(mmax_, 2 * nev_) * 16, s_),
+        W((size_t)mmax_ * mmax_ * 16, s_), R1((size_t)n_ * std::max(mmax_, 4 * nev_) * 16, s_),
         R2((size_t)n_ * mmax_ * 16, s_), T((size_t)n_ * 2 * std::max(mmax_, nev_) * 16, s_),
         C((size_t)mmax_ * 16, s_), info(sizeof(int), s_), dE((size_t)mmax_ * 8, s_),
-        dF((size_t)std::max(mmax_, 2 * nev_) * 8, s_), dD((size_t)n_ * 8, s_) {
+        dF((size_t)std::max(mmax_, 2 * nev_) * 8, s_), dD((size_t)n_ * 8, s_),
+        dDp((size_t)n_ * 8, s_), dDm((size_t)n_ * 8, s_), dS((size_t)n_ * 8, s_) {
     int lw1 = 0, lw2 = 0;
     BSE_CUSOLVER(cusolverDnZpotrf_bufferSize(h.solver, CUBLAS_FILL_MODE_LOWER, mmax,
                                              L.as<cuDoubleComplex>(), mmax, &lw1));
@@ -307,24 +295,75 @@ struct Solver {
   }
 };
 
+// Training samples from one Davidson iteration (see TrajectorySink): for every
+// unconverged pair, the Ritz vectors X+Y = V u, X-Y = V w against the exact
+// pair aligned in phase, with the residuals in R1 / R2.
+void record_trajectory(Solver& sv, TrajectorySink& sink, std::unique_ptr<DeviceBuffer>& xm_exact,
+                       const std::vector<int>& todo, const std::vector<double>& E,
+                       cudaStream_t s) {
+  const int n = sv.n;
+  const cuDoubleComplex one = make_cuDoubleComplex(1, 0), zero = make_cuDoubleComplex(0, 0);
+  DeviceBuffer xt((size_t)n * 16, s), st((size_t)n * 16, s);
+  for (int lam : todo) {
+    if (sink.count + 2 * (int64_t)n > sink.capacity) return;
+    for (int eq = 0; eq < 2; ++eq) {
+      // current vector of this equation's unknown
+      BSE_CUBLAS(cublasZgemv(sv.h.blas, CUBLAS_OP_N, n, sv.m, &one, sv.V.as<cuDoubleComplex>(), n,
+                             (eq == 0 ? sv.U : sv.W).as<cuDoubleComplex>() + (int64_t)lam * sv.mmax,
+                             1, &zero, xt.as<cuDoubleComplex>(), 1));
+      const cuDoubleComplex* xe =
+          eq == 0 ? reinterpret_cast<const cuDoubleComplex*>(sink.xpy_exact) + (int64_t)lam * n
+                  : xm_exact->as<cuDoubleComplex>() + (int64_t)lam * n;
+      cuDoubleComplex ov;
+      BSE_CUBLAS(cublasZdotc(sv.h.blas, n, xe, 1, xt.as<cuDoubleComplex>(), 1, &ov));
+      const double mag = std::hypot(ov.x, ov.y);
+      const cuDoubleComplex ph = mag > 0 ? make_cuDoubleComplex(-ov.x / mag, -ov.y / mag)
+                                         : make_cuDoubleComplex(-1, 0);
+      // step = x~ - phase * x
+      BSE_CUBLAS(cublasZcopy(sv.h.blas, n, xt.as<cuDoubleComplex>(), 1, st.as<cuDoubleComplex>(), 1));
+      BSE_CUBLAS(cublasZaxpy(sv.h.blas, n, &ph, xe, 1, st.as<cuDoubleComplex>(), 1));
+      const double2* r = (eq == 0 ? sv.R1 : sv.R2).as<double2>() + (int64_t)lam * n;
+      mlp_record(n, sv.dDp.as<double>(), sv.dDm.as<double>(), sv.dS.as<double>(), E[lam], eq == 0,
+                 r, st.as<double2>(), sink.feat + sink.count * 4, sink.target + sink.count,
+                 sink.weight + sink.count, s);
+      sink.count += n;
+    }
+  }
+}
+
+// xm = (AX + BX) / E per column (X-Y from X+Y of exact pairs)
+__global__ void k_xmy(int64_t total, int n, const double2* ax, const double2* bx, const double* e,
+                      double2* xm) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double ie = 1.0 / e[i / n];
+    const double2 a = ax[i], b = bx ? bx[i] : make_double2(0.0, 0.0);
+    xm[i] = make_double2((a.x + b.x) * ie, (a.y + b.y) * ie);
+  }
+}
+
 }  // namespace
 
 void davidson_fp64(int n, const bse_c128* A, const bse_c128* B, int64_t ld, int nev, double tol,
                    int max_iter, int precond, const MlpNet* mlp, double* E_out,
-                   bse_c128* XpY_out, int32_t* iters_out, cudaStream_t s) {
+                   bse_c128* XpY_out, int32_t* iters_out, cudaStream_t s, TrajectorySink* sink) {
   std::unique_lock<std::mutex> lock;
   LibHandles h = acquire_handles(lock);
   BSE_CUSOLVER(cusolverDnSetStream(h.solver, s));
   BSE_CUBLAS(cublasSetStream(h.blas, s));
   BSE_CUBLAS(cublasSetPointerMode(h.blas, CUBLAS_POINTER_MODE_HOST));
 
-  const int mmax = std::min(n, std::max(8 * nev, nev + 32));
+  // basis of up to 24 nev vectors; a restart keeps X+Y and X-Y of the 2 nev
+  // lowest Ritz pairs (thick restart)
+  const int mmax = std::min(n, std::max(24 * nev, nev + 96));
   Solver sv(n, nev, mmax, A, B, ld, s, h);
 
-  // diagonal of A: initial guess (unit vectors at the smallest A_aa) and preconditioner
+  // diagonal of A: initial guess (unit vectors at the smallest A_aa); diagonals
+  // of A+B and A-B and off-diagonal row norms for the preconditioners
   k_diag_real<<<(n + 255) / 256, 256, 0, s>>>(n, reinterpret_cast<const double2*>(A), ld,
                                               sv.dD.as<double>());
   note_launches(1);
+  mlp_diag_features(n, A, B, ld, sv.dDp.as<double>(), sv.dDm.as<double>(), sv.dS.as<double>(), s);
   sv.D.resize(n);
   BSE_CUDA(cudaMemcpyAsync(sv.D.data(), sv.dD.ptr, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
   BSE_CUDA(cudaStreamSynchronize(s));
@@ -341,16 +380,37 @@ void davidson_fp64(int n, const bse_c128* A, const bse_c128* B, int64_t ld, int 
   sv.m = b0;
   sv.matvec(0, b0);
 
+  // exact X-Y of the recorded problem (trajectory samples only)
+  std::unique_ptr<DeviceBuffer> xm_exact;
+  if (sink) {
+    xm_exact.reset(new DeviceBuffer((size_t)n * nev * 16, s));
+    DeviceBuffer de((size_t)nev * 8, s);
+    BSE_CUDA(cudaMemcpyAsync(de.ptr, sink->e_exact, (size_t)nev * 8, cudaMemcpyHostToDevice, s));
+    MatvecProb pa{n, nev, n, A, ld, sink->xpy_exact, n, sv.AV.as<bse_c128>(), n};
+    launch_zgemm(pa, 1, s);
+    if (B) {
+      MatvecProb pb{n, nev, n, B, ld, sink->xpy_exact, n, sv.BV.as<bse_c128>(), n};
+      launch_zgemm(pb, 1, s);
+    }
+    const int64_t tot = (int64_t)n * nev;
+    k_xmy<<<(int)std::min<int64_t>((tot + 255) / 256, 152 * 8), 256, 0, s>>>(
+        tot, n, sv.AV.as<double2>(), B ? sv.BV.as<double2>() : nullptr, de.as<double>(),
+        xm_exact->as<double2>());
+    note_launches(1);   // AV / BV are scratch: P and M of the start basis are untouched
+  }
+
   std::vector<double> E, res;
   const int k = nev;
   int it = 0;
   bool converged = false;
   for (it = 1; it <= max_iter; ++it) {
-    sv.rayleigh_ritz(k, E);
+    const int kr = std::min(sv.m, 2 * k);   // Ritz pairs kept at a restart
+    sv.rayleigh_ritz(kr, E);
     sv.residuals(k, E, res);
     std::vector<int> todo;
     for (int j = 0; j < k; ++j)
       if (!(res[j] < tol)) todo.push_back(j);
+    if (sink) record_trajectory(sv, *sink, xm_exact, todo, E, s);
     if (todo.empty()) {
       converged = true;
       break;
@@ -372,27 +432,28 @@ void davidson_fp64(int n, const bse_c128* A, const bse_c128* B, int64_t ld, int 
     // both blocks use the same eigenvalue list
     BSE_CUDA(cudaMemcpyAsync(sv.dF.as<double>() + nt, et.data(), nt * 8, cudaMemcpyHostToDevice, s));
     if (precond == 1) {
-      mlp_precondition(mlp, n, 2 * nt, sv.dD.as<double>(), sv.dF.as<double>(),
-                       sv.AV.as<double2>(), n, sv.T.as<double2>(), n, s);
+      mlp_precondition(mlp, n, 2 * nt, sv.dDp.as<double>(), sv.dDm.as<double>(),
+                       sv.dS.as<double>(), sv.dF.as<double>(), sv.AV.as<double2>(), n,
+                       sv.T.as<double2>(), n, s);
     } else {
       k_precond_diag<<<dim3((n + 127) / 128, 2 * nt), 128, 0, s>>>(
-          n, 2 * nt, sv.dD.as<double>(), sv.dF.as<double>(), sv.AV.as<double2>(), n,
-          sv.T.as<double2>(), n);
+          n, 2 * nt, sv.dDp.as<double>(), sv.dDm.as<double>(), sv.dF.as<double>(),
+          sv.AV.as<double2>(), n, sv.T.as<double2>(), n);
       BSE_CUDA(cudaGetLastError());
       note_launches(1);
     }
     // restart from the Ritz vectors when the new block would not fit
     if (sv.m + 2 * nt > mmax) {
       const cuDoubleComplex one = make_cuDoubleComplex(1, 0), zero = make_cuDoubleComplex(0, 0);
-      // X+Y and X-Y of the wanted pairs into R1 (n x 2k), then rebuild V from them
-      BSE_CUBLAS(cublasZgemm(h.blas, CUBLAS_OP_N, CUBLAS_OP_N, n, k, sv.m, &one,
+      // X+Y and X-Y of the kr lowest pairs into R1 (n x 2 kr), then rebuild V
+      BSE_CUBLAS(cublasZgemm(h.blas, CUBLAS_OP_N, CUBLAS_OP_N, n, kr, sv.m, &one,
                              sv.V.as<cuDoubleComplex>(), n, sv.U.as<cuDoubleComplex>(), mmax,
                              &zero, sv.R1.as<cuDoubleComplex>(), n));
-      BSE_CUBLAS(cublasZgemm(h.blas, CUBLAS_OP_N, CUBLAS_OP_N, n, k, sv.m, &one,
+      BSE_CUBLAS(cublasZgemm(h.blas, CUBLAS_OP_N, CUBLAS_OP_N, n, kr, sv.m, &one,
                              sv.V.as<cuDoubleComplex>(), n, sv.W.as<cuDoubleComplex>(), mmax,
-                             &zero, sv.R1.as<cuDoubleComplex>() + (int64_t)k * n, n));
+                             &zero, sv.R1.as<cuDoubleComplex>() + (int64_t)kr * n, n));
       sv.m = 0;
-      for (int j = 0; j < 2 * k; ++j) sv.append(sv.R1.as<cuDoubleComplex>() + (int64_t)j * n);
+      for (int j = 0; j < 2 * kr; ++j) sv.append(sv.R1.as<cuDoubleComplex>() + (int64_t)j * n);
       sv.matvec(0, sv.m);
     }
     const int m0 = sv.m;

@@ -234,6 +234,33 @@ void reduce_fp64(int n, const bse_c128* A, const bse_c128* B, int64_t ld, bse_c1
   BSE_CUDA(cudaStreamSynchronize(s));
 }
 
+__global__ void k_scale_cols_rsqrt(int n, int k, double2* x, int64_t ld, const double* e) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  if (i < n && j < k) {
+    const double f = 1.0 / sqrt(e[j]);
+    double2 v = x[i + (int64_t)j * ld];
+    x[i + (int64_t)j * ld] = make_double2(v.x * f, v.y * f);
+  }
+}
+
+void xpy_fp64(int n, int k, const bse_c128* Z, const bse_c128* L, int64_t ld, const double* E,
+              bse_c128* XpY, int64_t ldx, cudaStream_t s) {
+  std::lock_guard<std::mutex> lock(g_handle_mutex);
+  Handles& h = handles_for_current_device();
+  BSE_CUBLAS(cublasSetStream(h.blas, s));
+  const cuDoubleComplex one = make_cuDoubleComplex(1.0, 0.0);
+  // X+Y = L Z E^{-1/2} for the first k columns of Z
+  BSE_CUBLAS(cublasZtrmm(h.blas, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N,
+                         CUBLAS_DIAG_NON_UNIT, n, k, &one,
+                         reinterpret_cast<const cuDoubleComplex*>(L), (int)ld,
+                         reinterpret_cast<const cuDoubleComplex*>(Z), (int)ld,
+                         reinterpret_cast<cuDoubleComplex*>(XpY), (int)ldx));
+  k_scale_cols_rsqrt<<<dim3((n + 127) / 128, k), 128, 0, s>>>(
+      n, k, reinterpret_cast<double2*>(XpY), ldx, E);
+  BSE_CUDA(cudaGetLastError());
+  note_launches(1);
+}
+
 void spectrum_fp64(int n, bse_c128* S, const bse_c128* L, int64_t ld, const bse_c128* rho,
                    double c_q, double vc, int n_omega, const double* omega, double delta,
                    double* E_out, double* osc_out, bse_c128* eps_out, cudaStream_t s) {

@@ -109,5 +109,21 @@ void launch_zgemm(const Prob& P, int batch, cudaStream_t s) {
   }
 }
 
+// out[:, j] = H V[:, j], H Hermitian column-major: H[m][k] = conj(H[k + m ld])
+struct MatvecProb {
+  int M, N, K;
+  const bse_c128* H;
+  int64_t ld;
+  const bse_c128* V;   // K x N, column-major, leading dimension ldv
+  int64_t ldv;
+  bse_c128* out;       // M x N, column-major, leading dimension ldo
+  int64_t ldo;
+  __device__ cplx a(int, int m, int k) const { return conj(ldc(H + (int64_t)m * ld + k)); }
+  __device__ cplx b(int, int n, int k) const { return ldc(V + (int64_t)n * ldv + k); }
+  __device__ void store(int, int m, int n, cplx v) const {
+    reinterpret_cast<double2*>(out)[(int64_t)n * ldo + m] = make_double2(v.x, v.y);
+  }
+};
+
 }  // namespace
 }  // namespace bse

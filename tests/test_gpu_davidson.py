@@ -54,6 +54,7 @@ def test_davidson_matches_dense(bse, name, nev, coupling):
     assert np.allclose((A - Bm) @ xmy, xpy * e[None, :], atol=1e-5)
     assert np.allclose(np.diag(xpy.conj().T @ xmy).real, 1.0, atol=1e-8)
     assert 1 <= it < 200
+    print(f" [{name} nev={nev} {'full' if coupling else 'tda'}: {it} iterations]", end="")
 
 
 def test_davidson_no_convergence_is_reported(bse):
