@@ -38,6 +38,14 @@ WORKLOAD = ("optical limit Q=0, full (non-TDA) BSE, Nk=64 (4x4x4), Nv=4, Nc=4, N
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 FP64_PEAK_TFLOPS = 1.25     # GB300 FP64 (CUDA-core and tensor) nominal rate
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, or
+# dram__bytes.sum.per_second x duration) of the c2 workload's kernels, from the
+# ncu captures summarised in profiles/; to be re-taken whenever the kernel changes
+TRAFFIC_BYTES = {
+    "mixed_stage2": 315.4e6,        # k_stage2<16,1>, profiles/mixed_build_c2_kernels.md
+    "mixed_stage1_gemm": 237.3e6,   # gemm_split_bf16<3,TEpi>, same file
+}
+
 
 def build_flops(nk, nv, nc, ng, coupling=True):
     """Algorithmic flops of one build: 8 per complex multiply-add, no padding.
@@ -311,6 +319,7 @@ def main():
     # ---- roofline of the dominant build kernel (phase timing, live) ----
     peaks = load_peaks()
     s1_rr, s1_ra = stage1_flops(nk, nv, nc, ng)
+    roofline_tensor = None
     if prec == bse.BSE_PREC_FP64:
         name = "fp64_wra_stage1"
         cnt, ms = phases.get(name, (1, float("nan")))
@@ -321,16 +330,33 @@ def main():
                     "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak)",
                     "flops_per_launch": s1_ra}
     else:
-        name = "mixed_stage1_gemm"
-        cnt, ms = phases.get(name, (1, float("nan")))
-        per = (s1_rr + s1_ra) / max(cnt, 1) * cnt / args.steps   # both direct terms per step
+        # dominant by time: stage 2 of the direct terms (HBM-bound); algorithmic
+        # bytes per launch = X rows read in FP64 + T read in FP32 + A (or B)
+        # read-modify-write in FP64
+        n_pair = nk * nk
+        rows_x, rows_t = (nv * nv, nc * nc) if nc * nc <= nv * nv else (nc * nc, nv * nv)
+        bytes_rr = n_pair * ng * (16 * rows_x + 8 * rows_t) + 32 * n * n
+        bytes_ra = n_pair * ng * (16 + 8) * nv * nc + 32 * n * n
+        cnt, ms = phases.get("mixed_stage2", (1, float("nan")))
+        per_launch_bytes = (bytes_rr + bytes_ra) / 2
+        achieved = per_launch_bytes / (ms / cnt * 1e-3) / 1e9
+        roofline = {"kernel": "mixed_stage2 (k_stage2)", "bound": "hbm", "achieved": achieved,
+                    "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / peaks["hbm_gbs"],
+                    "traffic": TRAFFIC_BYTES["mixed_stage2"],
+                    "peak_source": f"{peaks['source']} HBM copy bandwidth",
+                    "bytes_per_launch": per_launch_bytes}
+        cnt, ms = phases.get("mixed_stage1_gemm", (1, float("nan")))
         products = 6 if prec == bse.BSE_PREC_BF16X6 else 3
         peak = peaks["bf16_tflops"] / products
-        achieved = (s1_rr + s1_ra) / (ms / args.steps * 1e-3) / 1e12
-        roofline = {"kernel": name, "bound": "tensor", "achieved": achieved, "peak": peak,
-                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                    "peak_source": f"{peaks['source']} bf16 burst / {products} piece products",
-                    "flops_per_step": s1_rr + s1_ra}
+        flops_launch = (s1_rr + s1_ra) / 2
+        achieved_t = flops_launch / (ms / cnt * 1e-3) / 1e12
+        roofline_tensor = {"kernel": "mixed_stage1_gemm (gemm_split_bf16, tcgen05)",
+                           "bound": "tensor", "achieved": achieved_t, "peak": peak,
+                           "unit": "TFLOP/s", "frac": achieved_t / peak,
+                           "traffic": TRAFFIC_BYTES["mixed_stage1_gemm"],
+                           "peak_source": f"{peaks['source']} bf16 burst / {products} piece products",
+                           "flops_per_launch": flops_launch}
 
     # ---- end to end through the public API with host buffers ----
     e2e = None
@@ -387,7 +413,8 @@ def main():
                        "parallelism": f"Q replicas x{world}"},
             "build_ms": t_build, "time_to_spectrum_ms": t_step,
             "phase_ms_per_step": phase_ms,
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "roofline": roofline, "roofline_tensor": roofline_tensor,
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches, "peaks": peaks,
         }
         line.update(extra)
