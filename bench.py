@@ -142,6 +142,24 @@ def dist_setup(args):
     return world, rank, local
 
 
+def max_over_ranks(values, device, world):
+    """Element-wise maximum of per-rank timings over all ranks (a no-op at
+    world size 1); the only cross-rank exchange of the benchmark."""
+    if world <= 1:
+        return list(values)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def weak_scaling_value(world, flops_per_rank, slowest_ms):
+    """Whole-job TFLOP/s: every rank builds its own Q (replicas, no collective
+    in the data path); the job takes as long as the slowest rank."""
+    return world * flops_per_rank / (slowest_ms * 1e-3) / 1e12
+
+
 def oracle_step(p, O):
     """One oracle pass over the workload: build, reduce, spectrum (seconds)."""
     t0 = time.perf_counter()
@@ -284,13 +302,9 @@ def main():
     phases = bse.bse_phase_report()
     build_ms = [e[0].elapsed_time(e[1]) for e in evs]
     step_ms = [e[0].elapsed_time(e[2]) for e in evs]
-    t_build = statistics.mean(build_ms)
-    t_step = statistics.mean(step_ms)
-    if world > 1:
-        t = torch.tensor([t_build, t_step], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_build, t_step = t.tolist()
-    value = world * flops / (t_build * 1e-3) / 1e12
+    t_build, t_step = max_over_ranks([statistics.mean(build_ms), statistics.mean(step_ms)],
+                                     dev, world)
+    value = weak_scaling_value(world, flops, t_build)
 
     # accuracy of this precision against the FP64 GPU build (same inputs)
     E_this = E.clone()
@@ -383,12 +397,8 @@ def main():
             torch.cuda.synchronize()
             if i >= args.warmup:
                 e2e_ms.append(e0.elapsed_time(e1))
-        t_e2e = statistics.mean(e2e_ms)
-        if world > 1:
-            t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = t.item()
-        e2e = {"value": world * flops / (t_e2e * 1e-3) / 1e12, "unit": "TFLOP/s",
+        t_e2e = max_over_ranks([statistics.mean(e2e_ms)], dev, world)[0]
+        e2e = {"value": weak_scaling_value(world, flops, t_e2e), "unit": "TFLOP/s",
                "ms_per_step": t_e2e, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     # ---- CPU oracle on the host cores (rank 0, N = 1 only), bounded sample ----
