@@ -111,6 +111,32 @@ typedef struct {
 int bse_build_kernel(const bse_problem* probs, int32_t nprob, int32_t precision,
                      void* cuda_stream);
 
+/* ---- batched plans ---------------------------------------------------------
+ * Many momentum transfers (each its own BSE, Eq. chimatrixq) prepared once and
+ * then built repeatedly.  bse_plan_create validates every problem (reading
+ * q_minus / q_plus back to the host: their contents are fixed for the plan's
+ * lifetime), groups the k pairs of every problem by q, allocates all scratch
+ * (cudaMalloc, owned by the plan) and, with BSE_PLAN_AUTOTUNE, times the
+ * candidate tile widths of the stage-1 tensor-core GEMM and keeps the fastest
+ * (remembered per padded NG for the process).  bse_plan_execute enqueues the
+ * build of every problem: kernel launches and memsets only, no allocation and
+ * no host synchronisation, so it may be captured into a CUDA graph.  With a
+ * tensor-core precision all problems must share ng; their exchange tiles run
+ * in one persistent GEMM launch and all their direct-term stage-1 tiles in
+ * another.  Inputs are read and A, B written at execute time through the
+ * pointers given at creation.  bse_plan_status syncs the stream and returns
+ * BSE_ERR_TIMEOUT if a bounded device wait expired in an execute since the
+ * previous status call, else BSE_OK.  Errors of create: those of
+ * bse_build_kernel, BSE_ERR_UNSUPPORTED (ng differs), BSE_ERR_NOMEM. */
+enum { BSE_PLAN_AUTOTUNE = 1 };
+int bse_plan_create(const bse_problem* probs, int32_t nprob, int32_t precision, int32_t flags,
+                    void** plan, void* cuda_stream);
+int bse_plan_execute(void* plan, void* cuda_stream);
+int bse_plan_status(void* plan, void* cuda_stream);
+/* output-column tile width the plan's stage-1 GEMM uses (0 for FP64 plans) */
+int bse_plan_tile_cols(const void* plan);
+void bse_plan_destroy(void* plan);
+
 /* FP64 build of one problem that allocates no device memory.
  *
  * There is no counterpart in the paper: this entry point exists for callers

@@ -178,6 +178,47 @@ extern "C" int bse_build_kernel_fp64_static(const bse_problem* prob, void* cuda_
   });
 }
 
+extern "C" int bse_plan_create(const bse_problem* probs, int32_t nprob, int32_t precision,
+                               int32_t flags, void** plan, void* cuda_stream) {
+  return guarded([&] {
+    BSE_CHECK_ARG(plan != nullptr, "plan is NULL");
+    *plan = nullptr;
+    BSE_CHECK_ARG(nprob >= 1 && probs != nullptr, "need at least one problem");
+    BSE_CHECK_ARG(precision == BSE_PREC_FP64 || precision == BSE_PREC_BF16X6 ||
+                      precision == BSE_PREC_BF16X3,
+                  "unknown precision " + std::to_string(precision));
+    BSE_CHECK_ARG((flags & ~BSE_PLAN_AUTOTUNE) == 0, "unknown plan flags");
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    keep_pool_memory();
+    std::vector<Problem> prs;
+    for (int i = 0; i < nprob; ++i) prs.push_back(validate(probs[i], i, s));
+    *plan = plan_create(std::move(prs), precision, (flags & BSE_PLAN_AUTOTUNE) != 0, s);
+  });
+}
+
+extern "C" int bse_plan_execute(void* plan, void* cuda_stream) {
+  return guarded([&] {
+    BSE_CHECK_ARG(plan != nullptr, "plan is NULL");
+    plan_execute(static_cast<BatchPlan*>(plan), static_cast<cudaStream_t>(cuda_stream));
+  });
+}
+
+extern "C" int bse_plan_status(void* plan, void* cuda_stream) {
+  int st = BSE_OK;
+  int rc = guarded([&] {
+    BSE_CHECK_ARG(plan != nullptr, "plan is NULL");
+    st = plan_status(static_cast<BatchPlan*>(plan), static_cast<cudaStream_t>(cuda_stream));
+    if (st != BSE_OK) throw Error(st, "a bounded device wait expired in a plan execute");
+  });
+  return rc;
+}
+
+extern "C" int bse_plan_tile_cols(const void* plan) {
+  return plan ? plan_tile_cols(static_cast<const BatchPlan*>(plan)) : 0;
+}
+
+extern "C" void bse_plan_destroy(void* plan) { plan_destroy(static_cast<BatchPlan*>(plan)); }
+
 extern "C" int bse_reduce(int32_t n, const bse_c128* A, const bse_c128* B, int64_t ld,
                           bse_c128* S, bse_c128* L, int32_t* failed_minor, void* cuda_stream) {
   return guarded([&] {

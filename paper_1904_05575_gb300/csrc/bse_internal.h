@@ -120,6 +120,14 @@ void davidson_fp64(int n, const bse_c128* A, const bse_c128* B, int64_t ld, int 
                    int max_iter, int precond, const MlpNet* mlp, double* E_out, bse_c128* XpY_out,
                    int32_t* iters_out, cudaStream_t stream, TrajectorySink* sink = nullptr);
 
+// Batched plans (build_mixed.cu).
+struct BatchPlan;
+BatchPlan* plan_create(std::vector<Problem> probs, int precision, bool autotune, cudaStream_t s);
+void plan_execute(BatchPlan* plan, cudaStream_t s);
+int plan_status(BatchPlan* plan, cudaStream_t s);
+int plan_tile_cols(const BatchPlan* plan);
+void plan_destroy(BatchPlan* plan);
+
 // Reduction and spectrum.
 void reduce_fp64(int n, const bse_c128* A, const bse_c128* B, int64_t ld, bse_c128* S,
                  bse_c128* L, int32_t* failed_minor, cudaStream_t stream);

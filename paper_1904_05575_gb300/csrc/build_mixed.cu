@@ -18,7 +18,9 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <climits>
 #include <cstdlib>
+#include <memory>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -56,7 +58,9 @@ struct SplitArgs {
   int pieces;
   int conj;                 // store the conjugate
   const double* kscale;     // per-k real factor or NULL
-  __nv_bfloat16* out;       // [2 * pieces][rows][Kp]
+  __nv_bfloat16* out;       // [2 * pieces][plane_rows][Kp]
+  int64_t plane_rows = 0;   // rows of each destination plane (0: rows)
+  int64_t row0 = 0;         // first destination row
 };
 
 // One thread per (output row, 8 consecutive k): every element is read as two
@@ -66,7 +70,7 @@ template <int P>
 __global__ void __launch_bounds__(256) k_split(SplitArgs a) {
   const int kg = a.Kp / 8;
   const int64_t total = (int64_t)a.rows * kg;
-  const int64_t plane = (int64_t)a.rows * a.Kp;
+  const int64_t plane = (a.plane_rows ? a.plane_rows : (int64_t)a.rows) * a.Kp;
   const uint4* src = reinterpret_cast<const uint4*>(a.src);   // one complex128 per uint4
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -102,7 +106,7 @@ __global__ void __launch_bounds__(256) k_split(SplitArgs a) {
         hi[p][e] = ti[p];
       }
     }
-    const int64_t o = (int64_t)row * a.Kp + k0;
+    const int64_t o = (a.row0 + row) * a.Kp + k0;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
       uint4 vr, vi;
@@ -185,6 +189,7 @@ struct Stage2Args {
   int64_t t_ld;
   const int* slot_of_pair;
   int rows_x, rows_t, ng, nk, nv, nc;
+  int64_t t_row0 = 0;    // first T row of this term (batched plans)
   double scale;          // gamma_c kappa
   double2* out;          // A or B
   int64_t ld;
@@ -201,7 +206,7 @@ __global__ void __launch_bounds__((TS / R) * (TS / R)) k_stage2(Stage2Args a) {
   const int rx0 = blockIdx.y * TS, rt0 = blockIdx.z * TS;
   const int64_t xp = a.x_transpose_pair ? (int64_t)kp * a.nk + k : (int64_t)p;
   const double2* X = a.x + xp * a.rows_x * a.ng;
-  const int64_t trow0 = (int64_t)a.slot_of_pair[p] * a.rows_t;
+  const int64_t trow0 = a.t_row0 + (int64_t)a.slot_of_pair[p] * a.rows_t;
   const int tid = threadIdx.x;
   const int tx = tid % (TS / R), ty = tid / (TS / R);
   // compensated FP32: sums over 8 plane waves in FMA, folded into (hi, lo) pairs
@@ -358,7 +363,21 @@ void launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb, const tc::Tile* d
   if (ntiles == 0) return;
   const size_t smem = tc::gemm_smem_bytes(sh);
   auto kern = sh.pieces == 3 ? tc::gemm_split_bf16<3, Epi> : tc::gemm_split_bf16<2, Epi>;
-  BSE_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // the shared-memory opt-in is set once per kernel (not per launch, so that a
+  // launch can be captured in a CUDA graph)
+  static std::once_flag once3, once2;
+  static int max_dyn3 = 0, max_dyn2 = 0;
+  int& max_dyn = sh.pieces == 3 ? max_dyn3 : max_dyn2;
+  std::call_once(sh.pieces == 3 ? once3 : once2, [&] {
+    int dev = 0, optin = 0;
+    BSE_CUDA(cudaGetDevice(&dev));
+    BSE_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa;
+    BSE_CUDA(cudaFuncGetAttributes(&fa, kern));
+    max_dyn = optin - (int)fa.sharedSizeBytes;
+    BSE_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn));
+  });
+  if ((int)smem > max_dyn) throw Error(BSE_ERR_UNSUPPORTED, "tile shape needs too much shared memory");
   const int grid = std::min<int>(ntiles, num_sms());
   kern<<<grid, tc::NUM_THREADS, smem, s>>>(ma, mb, d_tiles, ntiles, sh, epi, d_err);
   BSE_CUDA(cudaGetLastError());
@@ -655,5 +674,380 @@ void build_mixed(const Problem& pr, int precision, cudaStream_t s) {
   BSE_CUDA(cudaStreamSynchronize(s));
   if (herr) throw Error(BSE_ERR_TIMEOUT, "tensor-core GEMM: a bounded pipeline wait expired");
 }
+
+}  // namespace bse
+
+namespace bse {
+
+// ===========================================================================
+// Batched plans: many momentum transfers prepared once, then built with
+// launches only (no allocation, no host synchronisation), so that a build can
+// be captured in a CUDA graph.  All problems' exchange tiles share one
+// persistent tensor-core launch, and all direct terms' stage-1 tiles another.
+// ===========================================================================
+namespace {
+
+struct DevMem {
+  void* ptr = nullptr;
+  DevMem() = default;
+  explicit DevMem(size_t n) {
+    if (n && cudaMalloc(&ptr, n) != cudaSuccess) {
+      (void)cudaGetLastError();
+      throw Error(BSE_ERR_NOMEM, "cudaMalloc of " + std::to_string(n) + " bytes failed");
+    }
+  }
+  DevMem(const DevMem&) = delete;
+  DevMem& operator=(const DevMem&) = delete;
+  DevMem(DevMem&& o) noexcept : ptr(o.ptr) { o.ptr = nullptr; }
+  DevMem& operator=(DevMem&& o) noexcept {
+    std::swap(ptr, o.ptr);
+    return *this;
+  }
+  ~DevMem() {
+    if (ptr) cudaFree(ptr);
+  }
+  template <class T>
+  T* as() const { return static_cast<T*>(ptr); }
+};
+
+template <class T>
+DevMem upload_mem(const std::vector<T>& v) {
+  DevMem m(v.size() * sizeof(T));
+  if (!v.empty()) BSE_CUDA(cudaMemcpy(m.ptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return m;
+}
+
+struct ExParams {
+  double2 *A, *B;
+  int64_t ld;
+  float scale;
+  const double *e_v, *e_c;
+  int nv, nc;
+};
+
+struct ExchangeBatchEpi {   // ExchangeEpi with per-problem outputs
+  const ExParams* params;
+  __device__ __forceinline__ void operator()(const tc::Tile& t, int row, int c0, const float* re,
+                                             const float* im) const {
+    const ExParams q = params[t.prob];
+    ExchangeEpi e{q.A, q.B, q.ld, q.scale, q.e_v, q.e_c, q.nv, q.nc};
+    e(t, row, c0, re, im);
+  }
+};
+
+// process-wide autotuning results: padded NG -> best output-column tile width
+std::mutex g_tune_mutex;
+std::map<int, int> g_tuned_nt;
+
+}  // namespace
+
+struct BatchPlan {
+  int precision = 0, pieces = 3, planes = 6, ng = 0, Kp = 0, ng_pad = 0, nt_x = 0, nt_g = 0;
+  int device = 0;
+  std::vector<Problem> probs;
+  // exchange
+  int64_t x_rows = 0;
+  std::vector<int64_t> x_row0;
+  DevMem xa, xb, xtiles, exparams;
+  int n_xtiles = 0;
+  tc::GemmShape sh_x{}, sh_g{};
+  CUtensorMap ma_x{}, mb_x{}, ma_s{}, mb_s{};
+  // direct terms
+  struct Term {
+    int prob = 0;
+    int64_t a_row0 = 0, w_row0 = 0;
+    int rows_side = 0;
+    const bse_c128* side = nullptr;
+    bool w_conj_transpose = false;
+    DevMem perm, slot;
+    Stage2Args s2{};
+    std::vector<int32_t> qh;
+  };
+  std::vector<Term> terms;
+  int64_t a_rows = 0, w_rows = 0;
+  DevMem wsplit, asplit, tbuf, stiles;
+  int n_stiles = 0;
+  DevMem err;
+};
+
+namespace {
+
+std::vector<tc::Tile> stage1_tiles(const BatchPlan& pl, int nt) {
+  std::vector<tc::Tile> tiles;
+  for (const BatchPlan::Term& t : pl.terms) {
+    const int nq = pl.probs[t.prob].p.nq_w;
+    std::vector<int> perm, gstart;
+    group_pairs(t.qh, nq, perm, gstart);
+    for (int q = 0; q < nq; ++q) {
+      const int64_t r0 = t.a_row0 + (int64_t)gstart[q] * t.rows_side;
+      const int64_t r1 = t.a_row0 + (int64_t)gstart[q + 1] * t.rows_side;
+      for (int64_t m0 = r0; m0 < r1; m0 += tc::BM)
+        for (int n0 = 0; n0 < pl.ng; n0 += nt)
+          tiles.push_back({(int)m0, (int)std::min<int64_t>(tc::BM, r1 - m0),
+                           (int)(t.w_row0 + (int64_t)q * pl.ng_pad + n0), n0,
+                           std::min(nt, pl.ng - n0), (int)m0, t.prob});
+    }
+  }
+  return tiles;
+}
+
+void plan_splits(BatchPlan& pl, cudaStream_t s) {
+  for (size_t i = 0; i < pl.probs.size(); ++i) {
+    const bse_problem& p = pl.probs[i].p;
+    const int n = (int)pl.probs[i].n;
+    SplitArgs sa{reinterpret_cast<const double2*>(p.m_x), SPLIT_DENSE, nullptr, 0, 0, pl.ng,
+                 pl.Kp, n, pl.pieces, 1, p.v_bar, pl.xa.as<__nv_bfloat16>(), pl.x_rows,
+                 pl.x_row0[i]};
+    launch_split(sa, s);
+    SplitArgs sb = sa;
+    sb.conj = 0;
+    sb.kscale = nullptr;
+    sb.out = pl.xb.as<__nv_bfloat16>();
+    launch_split(sb, s);
+  }
+  for (BatchPlan::Term& t : pl.terms) {
+    const bse_problem& p = pl.probs[t.prob].p;
+    const int npair = p.nk * p.nk;
+    SplitArgs sw{reinterpret_cast<const double2*>(p.w), SPLIT_W, nullptr, pl.ng_pad,
+                 t.w_conj_transpose ? 1 : 0, pl.ng, pl.Kp, p.nq_w * pl.ng_pad, pl.pieces,
+                 t.w_conj_transpose ? 1 : 0, nullptr, pl.wsplit.as<__nv_bfloat16>(), pl.w_rows,
+                 t.w_row0};
+    launch_split(sw, s);
+    SplitArgs sa{reinterpret_cast<const double2*>(t.side), SPLIT_PAIRS, t.perm.as<int>(),
+                 t.rows_side, 0, pl.ng, pl.Kp, npair * t.rows_side, pl.pieces, 0, nullptr,
+                 pl.asplit.as<__nv_bfloat16>(), pl.a_rows, t.a_row0};
+    launch_split(sa, s);
+  }
+}
+
+void plan_execute_mixed(BatchPlan& pl, cudaStream_t s) {
+  BSE_CUDA(cudaMemsetAsync(pl.err.ptr, 0, sizeof(int), s));
+  {
+    Phase ph("mixed_split", s);
+    plan_splits(pl, s);
+  }
+  {
+    Phase ph("mixed_exchange", s);
+    launch_gemm(pl.ma_x, pl.mb_x, pl.xtiles.as<tc::Tile>(), pl.n_xtiles, pl.sh_x,
+                ExchangeBatchEpi{pl.exparams.as<ExParams>()}, pl.err.as<int>(), s);
+  }
+  if (pl.terms.empty()) return;
+  {
+    Phase ph("mixed_stage1_gemm", s);
+    launch_gemm(pl.ma_s, pl.mb_s, pl.stiles.as<tc::Tile>(), pl.n_stiles, pl.sh_g,
+                TEpi{pl.tbuf.as<float2>(), pl.a_rows}, pl.err.as<int>(), s);
+  }
+  Phase ph("mixed_stage2", s);
+  for (BatchPlan::Term& t : pl.terms) {
+    const bse_problem& p = pl.probs[t.prob].p;
+    launch_stage2(t.s2, p.nk * p.nk, s);
+  }
+}
+
+void plan_set_tiles(BatchPlan& pl, int nt) {
+  pl.nt_g = nt;
+  pl.sh_g = make_shape(nt, pl.Kp, pl.pieces);
+  std::vector<tc::Tile> st = stage1_tiles(pl, nt);
+  pl.n_stiles = (int)st.size();
+  pl.stiles = upload_mem(st);
+  pl.mb_s = make_plane_map(pl.wsplit.as<__nv_bfloat16>(), pl.Kp, (int)pl.w_rows, pl.planes, nt);
+}
+
+// time the stage-1 GEMM at each candidate tile width and keep the fastest
+void plan_autotune(BatchPlan& pl, cudaStream_t s) {
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tuned_nt.find(pl.ng_pad);
+    if (it != g_tuned_nt.end()) {
+      plan_set_tiles(pl, it->second);
+      return;
+    }
+  }
+  std::vector<int> cands;
+  for (int mx : {64, 128}) {
+    int nt = round_up((pl.ng_pad + ((pl.ng_pad + mx - 1) / mx) - 1) / ((pl.ng_pad + mx - 1) / mx), 32);
+    if (std::find(cands.begin(), cands.end(), nt) == cands.end()) cands.push_back(nt);
+  }
+  plan_splits(pl, s);
+  cudaEvent_t e0, e1;
+  BSE_CUDA(cudaEventCreate(&e0));
+  BSE_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_nt = cands.front();
+  for (int nt : cands) {
+    plan_set_tiles(pl, nt);
+    float ms = 0.f;
+    for (int rep = 0; rep < 3; ++rep) {
+      BSE_CUDA(cudaEventRecord(e0, s));
+      launch_gemm(pl.ma_s, pl.mb_s, pl.stiles.as<tc::Tile>(), pl.n_stiles, pl.sh_g,
+                  TEpi{pl.tbuf.as<float2>(), pl.a_rows}, pl.err.as<int>(), s);
+      BSE_CUDA(cudaEventRecord(e1, s));
+      BSE_CUDA(cudaEventSynchronize(e1));
+      float t = 0.f;
+      BSE_CUDA(cudaEventElapsedTime(&t, e0, e1));
+      if (rep > 0) ms += t;   // first launch warms up
+    }
+    if (ms < best) {
+      best = ms;
+      best_nt = nt;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  plan_set_tiles(pl, best_nt);
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_tuned_nt[pl.ng_pad] = best_nt;
+}
+
+}  // namespace
+
+BatchPlan* plan_create(std::vector<Problem> probs, int precision, bool autotune, cudaStream_t s) {
+  std::unique_ptr<BatchPlan> pl(new BatchPlan);
+  BSE_CUDA(cudaGetDevice(&pl->device));
+  pl->precision = precision;
+  pl->probs = std::move(probs);
+  if (precision == BSE_PREC_FP64) return pl.release();
+  const int ng = pl->probs.front().p.ng;
+  for (const Problem& pr : pl->probs)
+    if (pr.p.ng != ng)
+      throw Error(BSE_ERR_UNSUPPORTED, "a batched tensor-core plan needs the same ng in every problem");
+  pl->pieces = precision == BSE_PREC_BF16X6 ? 3 : 2;
+  pl->planes = 2 * pl->pieces;
+  pl->ng = ng;
+  pl->Kp = round_up(ng, tc::BK);
+  pl->ng_pad = round_up(ng, 32);
+  pl->err = DevMem(sizeof(int));
+
+  // exchange operands of all problems, stacked
+  std::vector<tc::Tile> xt;
+  std::vector<ExParams> xp;
+  int64_t nmax = 0;
+  for (const Problem& pr : pl->probs) nmax = std::max<int64_t>(nmax, pr.n);
+  pl->nt_x = tile_cols(round_up((int)nmax, 32));
+  for (size_t i = 0; i < pl->probs.size(); ++i) {
+    const bse_problem& p = pl->probs[i].p;
+    const int n = (int)pl->probs[i].n;
+    pl->x_row0.push_back(pl->x_rows);
+    for (int m0 = 0; m0 < n; m0 += tc::BM)
+      for (int n0 = 0; n0 < n; n0 += pl->nt_x)
+        xt.push_back({(int)(pl->x_rows + m0), std::min(tc::BM, n - m0), (int)(pl->x_rows + n0), n0,
+                      std::min(pl->nt_x, n - n0), m0, (int)i});
+    xp.push_back({reinterpret_cast<double2*>(p.A), p.coupling ? reinterpret_cast<double2*>(p.B) : nullptr,
+                  p.ld, (float)(2.0 * p.gamma_x * pl->probs[i].kappa), p.e_v, p.e_c, p.nv, p.nc});
+    pl->x_rows += n;
+  }
+  pl->xa = DevMem((size_t)pl->planes * pl->x_rows * pl->Kp * 2);
+  pl->xb = DevMem((size_t)pl->planes * pl->x_rows * pl->Kp * 2);
+  pl->n_xtiles = (int)xt.size();
+  pl->xtiles = upload_mem(xt);
+  pl->exparams = upload_mem(xp);
+  pl->sh_x = make_shape(pl->nt_x, pl->Kp, pl->pieces);
+  pl->ma_x = make_plane_map(pl->xa.as<__nv_bfloat16>(), pl->Kp, (int)pl->x_rows, pl->planes, tc::BM);
+  pl->mb_x = make_plane_map(pl->xb.as<__nv_bfloat16>(), pl->Kp, (int)pl->x_rows, pl->planes, pl->nt_x);
+
+  // direct terms of all problems, stacked
+  for (size_t i = 0; i < pl->probs.size(); ++i) {
+    const Problem& pr = pl->probs[i];
+    const bse_problem& p = pr.p;
+    if (p.gamma_c == 0.0) continue;
+    const int nv = p.nv, nc = p.nc, npair = p.nk * p.nk;
+    const bool cc_side = nc * nc <= nv * nv;
+    for (int term = 0; term < (p.coupling ? 2 : 1); ++term) {
+      BatchPlan::Term t;
+      t.prob = (int)i;
+      Stage2Args& a = t.s2;
+      if (term == 0) {
+        t.rows_side = cc_side ? nc * nc : nv * nv;
+        t.side = cc_side ? p.m_cc : p.m_vv;
+        t.w_conj_transpose = !cc_side;
+        t.qh = pr.qm_host;
+        a.mode = cc_side ? S2_RR_CC : S2_RR_VV;
+        a.x = reinterpret_cast<const double2*>(cc_side ? p.m_vv : p.m_cc);
+        a.x_transpose_pair = 0;
+        a.conj_x = cc_side ? 1 : 0;
+        a.conj_t = cc_side ? 0 : 1;
+        a.rows_x = cc_side ? nv * nv : nc * nc;
+        a.out = reinterpret_cast<double2*>(p.A);
+      } else {
+        t.rows_side = nv * nc;
+        t.side = p.n_vc;
+        t.w_conj_transpose = false;
+        t.qh = pr.qp_host;
+        a.mode = S2_RA;
+        a.x = reinterpret_cast<const double2*>(p.n_vc);
+        a.x_transpose_pair = 1;
+        a.conj_x = 1;
+        a.conj_t = 0;
+        a.rows_x = nv * nc;
+        a.out = reinterpret_cast<double2*>(p.B);
+      }
+      a.rows_t = t.rows_side;
+      std::vector<int> perm, gstart;
+      group_pairs(t.qh, p.nq_w, perm, gstart);
+      std::vector<int> slot(npair);
+      for (int j = 0; j < npair; ++j) slot[perm[j]] = j;
+      t.perm = upload_mem(perm);
+      t.slot = upload_mem(slot);
+      t.a_row0 = pl->a_rows;
+      t.w_row0 = pl->w_rows;
+      pl->a_rows += (int64_t)npair * t.rows_side;
+      pl->w_rows += (int64_t)p.nq_w * pl->ng_pad;
+      a.slot_of_pair = t.slot.as<int>();
+      a.ng = ng;
+      a.nk = p.nk;
+      a.nv = nv;
+      a.nc = nc;
+      a.scale = p.gamma_c * pr.kappa;
+      a.ld = p.ld;
+      a.t_row0 = t.a_row0;
+      pl->terms.push_back(std::move(t));
+    }
+  }
+  if (!pl->terms.empty()) {
+    if (pl->a_rows > INT32_MAX || pl->w_rows > INT32_MAX)
+      throw Error(BSE_ERR_UNSUPPORTED, "batched stage-1 rows exceed 2^31");
+    pl->wsplit = DevMem((size_t)pl->planes * pl->w_rows * pl->Kp * 2);
+    pl->asplit = DevMem((size_t)pl->planes * pl->a_rows * pl->Kp * 2);
+    pl->tbuf = DevMem((size_t)pl->ng_pad * pl->a_rows * sizeof(float2));
+    for (BatchPlan::Term& t : pl->terms) {
+      t.s2.T = pl->tbuf.as<float2>();
+      t.s2.t_ld = pl->a_rows;
+    }
+    pl->ma_s = make_plane_map(pl->asplit.as<__nv_bfloat16>(), pl->Kp, (int)pl->a_rows, pl->planes,
+                              tc::BM);
+    if (autotune)
+      plan_autotune(*pl, s);
+    else
+      plan_set_tiles(*pl, tile_cols(pl->ng_pad));
+  }
+  BSE_CUDA(cudaStreamSynchronize(s));
+  return pl.release();
+}
+
+void plan_execute(BatchPlan* pl, cudaStream_t s) {
+  int dev = 0;
+  BSE_CUDA(cudaGetDevice(&dev));
+  if (dev != pl->device) throw Error(BSE_ERR_ARG, "plan executed on another device");
+  if (pl->precision == BSE_PREC_FP64) {
+    for (const Problem& pr : pl->probs) build_fp64(pr, s);
+    return;
+  }
+  plan_execute_mixed(*pl, s);
+}
+
+int plan_status(BatchPlan* pl, cudaStream_t s) {
+  if (pl->precision == BSE_PREC_FP64) {
+    BSE_CUDA(cudaStreamSynchronize(s));
+    return BSE_OK;
+  }
+  int herr = 0;
+  BSE_CUDA(cudaMemcpyAsync(&herr, pl->err.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+  BSE_CUDA(cudaStreamSynchronize(s));
+  return herr ? BSE_ERR_TIMEOUT : BSE_OK;
+}
+
+int plan_tile_cols(const BatchPlan* pl) { return pl->nt_g; }
+
+void plan_destroy(BatchPlan* pl) { delete pl; }
 
 }  // namespace bse

@@ -46,6 +46,7 @@ struct Tile {
   int n0;        // first output column
   int n_valid;   // real output columns (<= nt)
   int out_row0;  // first output row
+  int prob;      // problem of a batched launch (0 otherwise)
 };
 
 // ---------------------------------------------------------------------------
