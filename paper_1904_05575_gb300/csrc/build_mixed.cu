@@ -305,10 +305,130 @@ __global__ void __launch_bounds__((TS / R) * (TS / R)) k_stage2(Stage2Args a) {
     }
 }
 
+// asynchronous global -> shared copies (zero-filled when pred is false)
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool pred) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc::smem_u32(smem)),
+               "l"(gmem), "r"(pred ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool pred) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(tc::smem_u32(smem)),
+               "l"(gmem), "r"(pred ? 8 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Stage 2 for pair blocks of at most 16 x 16, software-pipelined: the raw
+// complex128 X rows and FP32 T rows of the next 32 plane waves are copied to
+// shared memory asynchronously (cp.async, double-buffered) while the current
+// chunk is converted and contracted.  Same arithmetic as k_stage2<16, 1>.
+__global__ void __launch_bounds__(256) k_stage2_pipe(Stage2Args a) {
+  constexpr int GC = 32;
+  __shared__ __align__(16) uint4 Xr[2][16][GC];      // raw FP64 complex
+  __shared__ __align__(16) float2 Tr[2][GC][16];     // FP32 complex
+  __shared__ float2 Xs[16][GC + 1];                  // converted X of the current chunk
+  const int p = blockIdx.x;
+  const int k = p / a.nk, kp = p % a.nk;
+  const int64_t xp = a.x_transpose_pair ? (int64_t)kp * a.nk + k : (int64_t)p;
+  const uint4* X = reinterpret_cast<const uint4*>(a.x) + xp * a.rows_x * a.ng;
+  const int64_t trow0 = a.t_row0 + (int64_t)a.slot_of_pair[p] * a.rows_t;
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int nchunks = (a.ng + GC - 1) / GC;
+
+  auto prefetch = [&](int c, int buf) {
+    const int g0 = c * GC;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int i = tid + u * 256;            // 16 x 32 X elements
+      const int r = i >> 5, g = i & 31;
+      const bool ok = r < a.rows_x && g0 + g < a.ng;
+      cp_async16(&Xr[buf][r][g], ok ? (const void*)(X + (int64_t)r * a.ng + g0 + g) : (const void*)X, ok);
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int i = tid + u * 256;            // 32 x 16 T elements
+      const int g = i >> 4, r = i & 15;
+      const bool ok = r < a.rows_t && g0 + g < a.ng;
+      const float2* src = a.T + (ok ? (int64_t)(g0 + g) * a.t_ld + trow0 + r : 0);
+      cp_async8(&Tr[buf][g][r], src, ok);
+    }
+    cp_async_commit();
+  };
+
+  float hx = 0.f, hy = 0.f, lx = 0.f, ly = 0.f;
+  const float tsign = a.conj_t ? -1.f : 1.f;
+  const uint32_t xflip = a.conj_x ? 0x80000000u : 0u;
+  prefetch(0, 0);
+  for (int c = 0; c < nchunks; ++c) {
+    const int buf = c & 1;
+    if (c + 1 < nchunks) {
+      prefetch(c + 1, buf ^ 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int i = tid + u * 256;
+      const int r = i >> 5, g = i & 31;
+      const uint4 d = Xr[buf][r][g];
+      Xs[r][g] = make_float2(__uint_as_float(f64w_to_f32_bits(d.x, d.y)),
+                             __uint_as_float(f64w_to_f32_bits(d.z, d.w) ^ xflip));
+    }
+    __syncthreads();
+#pragma unroll
+    for (int g8 = 0; g8 < GC; g8 += 8) {
+      float ax = 0.f, ay = 0.f;
+#pragma unroll
+      for (int g = g8; g < g8 + 8; ++g) {
+        const float2 xv = Xs[ty][g];
+        const float2 tv = Tr[buf][g][tx];
+        const float ty_ = tv.y * tsign;
+        ax = fmaf(xv.x, tv.x, ax);
+        ax = fmaf(-xv.y, ty_, ax);
+        ay = fmaf(xv.x, ty_, ay);
+        ay = fmaf(xv.y, tv.x, ay);
+      }
+      float sv, e;
+      two_sum(hx, ax, sv, e);
+      hx = sv;
+      lx += e;
+      two_sum(hy, ay, sv, e);
+      hy = sv;
+      ly += e;
+    }
+    __syncthreads();   // the next prefetch overwrites this buffer
+  }
+  const int rx = ty, rt = tx;
+  if (rx >= a.rows_x || rt >= a.rows_t) return;
+  const int nv = a.nv, nc = a.nc;
+  int vi, ci, vp, cp;
+  if (a.mode == S2_RR_CC) {
+    vi = rx / nv; vp = rx % nv; ci = rt / nc; cp = rt % nc;
+  } else if (a.mode == S2_RR_VV) {
+    ci = rx / nc; cp = rx % nc; vi = rt / nv; vp = rt % nv;
+  } else {
+    vp = rx / nc; ci = rx % nc; vi = rt / nc; cp = rt % nc;
+  }
+  const int64_t al = ((int64_t)k * nv + vi) * nc + ci;
+  const int64_t ap = ((int64_t)kp * nv + vp) * nc + cp;
+  double2* dst = a.out + al + ap * a.ld;
+  const float sc = (float)a.scale;
+  double2 o = *dst;
+  o.x -= f32_to_f64_bits(sc * hx + sc * lx);
+  o.y -= f32_to_f64_bits(sc * hy + sc * ly);
+  *dst = o;
+}
+
 void launch_stage2(const Stage2Args& a, int npair, cudaStream_t s) {
   if (a.rows_x <= 16 && a.rows_t <= 16) {
-    dim3 grid(npair, 1, 1);
-    k_stage2<16, 1><<<grid, 256, 0, s>>>(a);
+    k_stage2_pipe<<<npair, 256, 0, s>>>(a);
   } else {
     dim3 grid(npair, (a.rows_x + 31) / 32, (a.rows_t + 31) / 32);
     k_stage2<32, 2><<<grid, 256, 0, s>>>(a);
