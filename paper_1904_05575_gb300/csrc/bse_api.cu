@@ -161,11 +161,10 @@ extern "C" int bse_build_kernel(const bse_problem* probs, int32_t nprob, int32_t
     std::vector<Problem> prs;
     prs.reserve(nprob);
     for (int i = 0; i < nprob; ++i) prs.push_back(validate(probs[i], i, s));
-    for (const Problem& pr : prs) {
-      if (precision == BSE_PREC_FP64)
-        build_fp64(pr, s);
-      else
-        build_mixed(pr, precision, s);
+    if (precision == BSE_PREC_FP64) {
+      for (const Problem& pr : prs) build_fp64(pr, s);
+    } else {
+      build_mixed_batch(prs, precision, s);
     }
   });
 }

@@ -103,8 +103,9 @@ constexpr size_t kFp64StaticScratchBytes = (size_t)16 << 20;
 size_t fp64_static_scratch_need(const Problem& pr);
 void build_fp64_static(const Problem& pr, cudaStream_t stream);
 
-// Split-precision tensor-core build (tcgen05).  Writes A (and B) completely.
-void build_mixed(const Problem& pr, int precision, cudaStream_t stream);
+// Split-precision tensor-core build (tcgen05) of several problems through a
+// cached batched plan.  Writes every A (and B) completely.  Syncs.
+void build_mixed_batch(const std::vector<Problem>& probs, int precision, cudaStream_t stream);
 
 // The per-device cuSOLVER / cuBLAS handles; the lock serialises their use.
 struct LibHandles {

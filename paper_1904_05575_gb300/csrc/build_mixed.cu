@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <climits>
 #include <cstdlib>
+#include <cstring>
 #include <memory>
 #include <map>
 #include <mutex>
@@ -550,36 +551,6 @@ void group_pairs(const std::vector<int32_t>& qmap, int nq, std::vector<int>& per
   for (int p = 0; p < npair; ++p) perm[fill[qmap[p]]++] = p;
 }
 
-// ---------------------------------------------------------------------------
-// plan: grouping of the k pairs by q and the tile lists, cached per shape and
-// q-map content (device copies kept until exit)
-// ---------------------------------------------------------------------------
-struct TermPlan {
-  int rows_side = 0;
-  int ntiles = 0;
-  int* perm = nullptr;         // slot -> pair
-  int* slot = nullptr;         // pair -> slot
-  tc::Tile* tiles = nullptr;
-};
-
-struct Plan {
-  int exchange_tiles = 0;
-  tc::Tile* xtiles = nullptr;
-  TermPlan rr, ra;
-};
-
-struct PlanKey {
-  int dev, nk, nv, nc, ng, nq, coupling, direct;
-  uint64_t hash;
-  bool operator<(const PlanKey& o) const {
-    return std::tie(dev, nk, nv, nc, ng, nq, coupling, direct, hash) <
-           std::tie(o.dev, o.nk, o.nv, o.nc, o.ng, o.nq, o.coupling, o.direct, o.hash);
-  }
-};
-
-std::mutex g_plan_mutex;
-std::map<PlanKey, Plan> g_plans;
-
 uint64_t fnv1a(const std::vector<int32_t>& v, uint64_t h = 1469598103934665603ull) {
   for (int32_t x : v) {
     h ^= (uint32_t)x;
@@ -588,216 +559,7 @@ uint64_t fnv1a(const std::vector<int32_t>& v, uint64_t h = 1469598103934665603ul
   return h;
 }
 
-template <class T>
-T* upload_persistent(const std::vector<T>& v) {
-  T* d = nullptr;
-  if (v.empty()) return nullptr;
-  BSE_CUDA(cudaMalloc(&d, v.size() * sizeof(T)));
-  BSE_CUDA(cudaMemcpy(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
-  return d;
-}
-
-TermPlan make_term_plan(const std::vector<int32_t>& qh, int nq, int npair, int rows_side, int ng,
-                        int ng_pad, int nt) {
-  TermPlan tp;
-  tp.rows_side = rows_side;
-  std::vector<int> perm, gstart;
-  group_pairs(qh, nq, perm, gstart);
-  std::vector<int> slot(npair);
-  for (int i = 0; i < npair; ++i) slot[perm[i]] = i;
-  // 128-row tiles inside each q group; the n tiles of one m tile are adjacent in
-  // the list so the second read of the A rows hits L2
-  std::vector<tc::Tile> tiles;
-  for (int q = 0; q < nq; ++q) {
-    const int64_t r0 = (int64_t)gstart[q] * rows_side, r1 = (int64_t)gstart[q + 1] * rows_side;
-    for (int64_t m0 = r0; m0 < r1; m0 += tc::BM)
-      for (int n0 = 0; n0 < ng; n0 += nt)
-        tiles.push_back({(int)m0, (int)std::min<int64_t>(tc::BM, r1 - m0), q * ng_pad + n0, n0,
-                         std::min(nt, ng - n0), (int)m0});
-  }
-  tp.ntiles = (int)tiles.size();
-  tp.perm = upload_persistent(perm);
-  tp.slot = upload_persistent(slot);
-  tp.tiles = upload_persistent(tiles);
-  return tp;
-}
-
-const Plan& get_plan(const Problem& pr, bool direct, int nt_x, int nt_g, int ng_pad) {
-  const bse_problem& p = pr.p;
-  int dev = 0;
-  BSE_CUDA(cudaGetDevice(&dev));
-  uint64_t h = fnv1a(pr.qm_host);
-  h = fnv1a(pr.qp_host, h);
-  PlanKey key{dev, p.nk, p.nv, p.nc, p.ng, p.nq_w, p.coupling, direct ? 1 : 0, h};
-  std::lock_guard<std::mutex> lock(g_plan_mutex);
-  auto it = g_plans.find(key);
-  if (it != g_plans.end()) return it->second;
-  if (g_plans.size() >= 32) {     // bounded: drop everything, plans are cheap to rebuild
-    for (auto& kv : g_plans) {
-      Plan& q = kv.second;
-      cudaFree(q.xtiles);
-      for (TermPlan* t : {&q.rr, &q.ra}) {
-        cudaFree(t->perm);
-        cudaFree(t->slot);
-        cudaFree(t->tiles);
-      }
-    }
-    g_plans.clear();
-  }
-  Plan plan;
-  const int n = (int)pr.n;
-  std::vector<tc::Tile> xt;
-  for (int m0 = 0; m0 < n; m0 += tc::BM)
-    for (int n0 = 0; n0 < n; n0 += nt_x)
-      xt.push_back({m0, std::min(tc::BM, n - m0), n0, n0, std::min(nt_x, n - n0), m0});
-  plan.exchange_tiles = (int)xt.size();
-  plan.xtiles = upload_persistent(xt);
-  if (direct) {
-    const int npair = p.nk * p.nk;
-    const bool cc_side = p.nc * p.nc <= p.nv * p.nv;
-    plan.rr = make_term_plan(pr.qm_host, p.nq_w, npair, cc_side ? p.nc * p.nc : p.nv * p.nv,
-                             p.ng, ng_pad, nt_g);
-    if (p.coupling)
-      plan.ra = make_term_plan(pr.qp_host, p.nq_w, npair, p.nv * p.nc, p.ng, ng_pad, nt_g);
-  }
-  return g_plans.emplace(key, plan).first->second;
-}
-
 }  // namespace
-
-bool mixed_supported(int precision) {
-  return precision == BSE_PREC_BF16X6 || precision == BSE_PREC_BF16X3;
-}
-
-void build_mixed(const Problem& pr, int precision, cudaStream_t s) {
-  const bse_problem& p = pr.p;
-  const int nk = p.nk, nv = p.nv, nc = p.nc, ng = p.ng, nq = p.nq_w;
-  const int n = (int)pr.n, npair = nk * nk;
-  const int pieces = precision == BSE_PREC_BF16X6 ? 3 : 2;
-  const int planes = 2 * pieces;
-  const int Kp = round_up(ng, tc::BK);
-  const int ng_pad = round_up(ng, 32);
-  const int nt_x = tile_cols(round_up(n, 32));
-  const int nt_g = tile_cols(ng_pad);
-  const double kap = pr.kappa;
-  const bool direct = p.gamma_c != 0.0;
-  const Plan plan = get_plan(pr, direct, nt_x, nt_g, ng_pad);   // copy: the cache may evict
-
-  DeviceBuffer err(sizeof(int), s);
-  BSE_CUDA(cudaMemsetAsync(err.ptr, 0, sizeof(int), s));
-
-  // ---- exchange: A = E + 2 gx k V, B = 2 gx k V ----
-  {
-    Phase ph("mixed_exchange", s);
-    DeviceBuffer xa((size_t)planes * n * Kp * 2, s), xb((size_t)planes * n * Kp * 2, s);
-    SplitArgs sa{reinterpret_cast<const double2*>(p.m_x), SPLIT_DENSE, nullptr, 0, 0, ng, Kp, n,
-                 pieces, 1, p.v_bar, xa.as<__nv_bfloat16>()};
-    launch_split(sa, s);
-    SplitArgs sb = sa;
-    sb.conj = 0;
-    sb.kscale = nullptr;
-    sb.out = xb.as<__nv_bfloat16>();
-    launch_split(sb, s);
-    tc::GemmShape sh = make_shape(nt_x, Kp, pieces);
-    CUtensorMap ma = make_plane_map(xa.as<__nv_bfloat16>(), Kp, n, planes, tc::BM);
-    CUtensorMap mb = make_plane_map(xb.as<__nv_bfloat16>(), Kp, n, planes, nt_x);
-    ExchangeEpi epi{reinterpret_cast<double2*>(p.A),
-                    p.coupling ? reinterpret_cast<double2*>(p.B) : nullptr,
-                    p.ld, (float)(2.0 * p.gamma_x * kap), p.e_v, p.e_c, nv, nc};
-    launch_gemm(ma, mb, plan.xtiles, plan.exchange_tiles, sh, epi, err.as<int>(), s);
-  }
-
-  if (direct) {
-    const bool cc_side = nc * nc <= nv * nv;
-    struct Term {
-      const TermPlan* tp;
-      const bse_c128* side;
-      bool w_conj_transpose;
-      Stage2Args s2;
-    };
-    std::vector<Term> terms;
-    {
-      Term t{&plan.rr, cc_side ? p.m_cc : p.m_vv, !cc_side, Stage2Args{}};
-      Stage2Args& a = t.s2;
-      a.mode = cc_side ? S2_RR_CC : S2_RR_VV;
-      a.x = reinterpret_cast<const double2*>(cc_side ? p.m_vv : p.m_cc);
-      a.x_transpose_pair = 0;
-      a.conj_x = cc_side ? 1 : 0;
-      a.conj_t = cc_side ? 0 : 1;
-      a.rows_x = cc_side ? nv * nv : nc * nc;
-      a.rows_t = plan.rr.rows_side;
-      a.out = reinterpret_cast<double2*>(p.A);
-      terms.push_back(t);
-    }
-    if (p.coupling) {
-      Term t{&plan.ra, p.n_vc, false, Stage2Args{}};
-      Stage2Args& a = t.s2;
-      a.mode = S2_RA;
-      a.x = reinterpret_cast<const double2*>(p.n_vc);
-      a.x_transpose_pair = 1;
-      a.conj_x = 1;
-      a.conj_t = 0;
-      a.rows_x = nv * nc;
-      a.rows_t = nv * nc;
-      a.out = reinterpret_cast<double2*>(p.B);
-      terms.push_back(t);
-    }
-    int rows_max = 0;
-    for (const Term& t : terms) rows_max = std::max(rows_max, t.tp->rows_side);
-    const int64_t side_rows_max = (int64_t)npair * rows_max;
-    DeviceBuffer wsplit((size_t)planes * nq * ng_pad * Kp * 2, s);
-    DeviceBuffer asplit((size_t)planes * side_rows_max * Kp * 2, s);
-    DeviceBuffer tbuf((size_t)ng_pad * side_rows_max * sizeof(float2), s);
-    tc::GemmShape sh = make_shape(nt_g, Kp, pieces);
-
-    for (const Term& t : terms) {
-      const int64_t side_rows = (int64_t)npair * t.tp->rows_side;
-      {
-        Phase ph("mixed_split", s);
-        // W planes: row (q, g) = W[q][g][.] (or W^H: conj(W[q][.][g])), zero beyond ng
-        SplitArgs sw{reinterpret_cast<const double2*>(p.w), SPLIT_W, nullptr, ng_pad,
-                     t.w_conj_transpose ? 1 : 0, ng, Kp, nq * ng_pad, pieces,
-                     t.w_conj_transpose ? 1 : 0, nullptr, wsplit.as<__nv_bfloat16>()};
-        launch_split(sw, s);
-        // stage-1 operand rows in slot order (pairs grouped by q)
-        SplitArgs sa{reinterpret_cast<const double2*>(t.side), SPLIT_PAIRS, t.tp->perm,
-                     t.tp->rows_side, 0, ng, Kp, (int)side_rows, pieces, 0, nullptr,
-                     asplit.as<__nv_bfloat16>()};
-        launch_split(sa, s);
-      }
-      {
-        Phase ph("mixed_stage1_gemm", s);
-        CUtensorMap ma = make_plane_map(asplit.as<__nv_bfloat16>(), Kp, (int)side_rows, planes, tc::BM);
-        CUtensorMap mb = make_plane_map(wsplit.as<__nv_bfloat16>(), Kp, nq * ng_pad, planes, nt_g);
-        TEpi epi{tbuf.as<float2>(), side_rows};
-        launch_gemm(ma, mb, t.tp->tiles, t.tp->ntiles, sh, epi, err.as<int>(), s);
-      }
-      {
-        Phase ph("mixed_stage2", s);
-        Stage2Args a = t.s2;
-        a.T = tbuf.as<float2>();
-        a.t_ld = side_rows;
-        a.slot_of_pair = t.tp->slot;
-        a.ng = ng;
-        a.nk = nk;
-        a.nv = nv;
-        a.nc = nc;
-        a.scale = p.gamma_c * kap;
-        a.ld = p.ld;
-        launch_stage2(a, npair, s);
-      }
-    }
-  }
-
-  int herr = 0;
-  BSE_CUDA(cudaMemcpyAsync(&herr, err.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
-  BSE_CUDA(cudaStreamSynchronize(s));
-  if (herr) throw Error(BSE_ERR_TIMEOUT, "tensor-core GEMM: a bounded pipeline wait expired");
-}
-
-}  // namespace bse
-
-namespace bse {
 
 // ===========================================================================
 // Batched plans: many momentum transfers prepared once, then built with
@@ -1169,5 +931,90 @@ int plan_status(BatchPlan* pl, cudaStream_t s) {
 int plan_tile_cols(const BatchPlan* pl) { return pl->nt_g; }
 
 void plan_destroy(BatchPlan* pl) { delete pl; }
+
+
+// ---------------------------------------------------------------------------
+// bse_build_kernel with a tensor-core precision: a plan per set of problem
+// descriptors (pointers, sizes, spin factors and q maps), cached so that
+// repeated builds of the same arrays skip validation-time set-up, then one
+// execute and a status check.  At most kPlanCache plans stay alive (their
+// scratch is device memory held until eviction or exit).
+// ---------------------------------------------------------------------------
+namespace {
+constexpr size_t kPlanCache = 4;
+
+struct CachedPlan {
+  std::vector<uint64_t> key;
+  std::unique_ptr<BatchPlan> plan;
+};
+std::mutex g_cache_mutex;
+std::vector<CachedPlan> g_cache;   // most recent last
+
+std::vector<uint64_t> plan_key(const std::vector<Problem>& probs, int precision) {
+  std::vector<uint64_t> k;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  k.push_back((uint64_t)dev);
+  k.push_back((uint64_t)precision);
+  for (const Problem& pr : probs) {
+    const bse_problem& p = pr.p;
+    const void* ptrs[] = {p.e_v, p.e_c, p.m_x, p.m_vv, p.m_cc, p.n_vc, p.w, p.q_minus, p.q_plus,
+                          p.v_bar, p.A, p.B};
+    for (const void* q : ptrs) k.push_back((uint64_t)(uintptr_t)q);
+    k.push_back(((uint64_t)p.nk << 32) | (uint32_t)p.nv);
+    k.push_back(((uint64_t)p.nc << 32) | (uint32_t)p.ng);
+    k.push_back(((uint64_t)p.nq_w << 32) | (uint32_t)p.coupling);
+    uint64_t bits[4];
+    memcpy(&bits[0], &p.omega_cell, 8);
+    memcpy(&bits[1], &p.gamma_x, 8);
+    memcpy(&bits[2], &p.gamma_c, 8);
+    k.push_back(bits[0]);
+    k.push_back(bits[1]);
+    k.push_back(bits[2]);
+    k.push_back((uint64_t)p.ld);
+    k.push_back(fnv1a(pr.qp_host, fnv1a(pr.qm_host)));
+  }
+  return k;
+}
+}  // namespace
+
+bool mixed_supported(int precision) {
+  return precision == BSE_PREC_BF16X6 || precision == BSE_PREC_BF16X3;
+}
+
+void build_mixed_batch(const std::vector<Problem>& probs, int precision, cudaStream_t s) {
+  // one plan per distinct ng (a tensor-core plan needs one ng)
+  std::vector<int> ngs;
+  for (const Problem& pr : probs)
+    if (std::find(ngs.begin(), ngs.end(), pr.p.ng) == ngs.end()) ngs.push_back(pr.p.ng);
+  for (int ng : ngs) {
+    std::vector<Problem> group;
+    for (const Problem& pr : probs)
+      if (pr.p.ng == ng) group.push_back(pr);
+    const std::vector<uint64_t> key = plan_key(group, precision);
+    BatchPlan* plan = nullptr;
+    {
+      std::lock_guard<std::mutex> lock(g_cache_mutex);
+      for (size_t i = 0; i < g_cache.size(); ++i)
+        if (g_cache[i].key == key) {
+          CachedPlan c = std::move(g_cache[i]);
+          g_cache.erase(g_cache.begin() + i);
+          g_cache.push_back(std::move(c));
+          plan = g_cache.back().plan.get();
+          break;
+        }
+    }
+    if (!plan) {
+      std::unique_ptr<BatchPlan> created(plan_create(group, precision, false, s));
+      std::lock_guard<std::mutex> lock(g_cache_mutex);
+      if (g_cache.size() >= kPlanCache) g_cache.erase(g_cache.begin());
+      g_cache.push_back(CachedPlan{key, std::move(created)});
+      plan = g_cache.back().plan.get();
+    }
+    plan_execute(plan, s);
+    if (plan_status(plan, s) != BSE_OK)
+      throw Error(BSE_ERR_TIMEOUT, "tensor-core GEMM: a bounded pipeline wait expired");
+  }
+}
 
 }  // namespace bse
