@@ -19,6 +19,8 @@
  *   - Energies are in eV; v and W are in Hartree atomic units
  *     (Ha * bohr^3); kappa = Ha / (nk * omega_cell) with Ha = 27.211386245988
  *     eV multiplies the exchange and both direct terms.
+ *   - Device arrays are aligned to their element size: 16 bytes for
+ *     complex128, 8 for double, 4 for int32 (BSE_ERR_ARG otherwise).
  *   - Functions return a bse_status and never throw across the ABI.
  *     Argument errors are detected on the host before any launch and leave
  *     outputs untouched.  bse_last_error() returns a thread-local message
@@ -127,14 +129,25 @@ int bse_build_kernel(const bse_problem* probs, int32_t nprob, int32_t precision,
  * pointers given at creation.  bse_plan_status syncs the stream and returns
  * BSE_ERR_TIMEOUT if a bounded device wait expired in an execute since the
  * previous status call, else BSE_OK.  Errors of create: those of
- * bse_build_kernel, BSE_ERR_UNSUPPORTED (ng differs), BSE_ERR_NOMEM. */
-enum { BSE_PLAN_AUTOTUNE = 1 };
+ * bse_build_kernel, BSE_ERR_UNSUPPORTED (ng differs), BSE_ERR_NOMEM.
+ *
+ * Direct terms (Eqs. wrrm, wrabar) run fused by default when every problem's
+ * pair blocks allow it (rows of the stage-1 side a power of two, rows of the
+ * other side at most min(16, that)): the stage-1 GEMM and the contraction
+ * over G' share one launch and the intermediate T never reaches device
+ * memory.  BSE_PLAN_UNFUSED keeps the two-launch form (T written to plan
+ * scratch, then contracted); both give the same bits.  Autotuning the fused
+ * form times it with its outputs switched off: A and B are not written at
+ * create time. */
+enum { BSE_PLAN_AUTOTUNE = 1, BSE_PLAN_UNFUSED = 2 };
 int bse_plan_create(const bse_problem* probs, int32_t nprob, int32_t precision, int32_t flags,
                     void** plan, void* cuda_stream);
 int bse_plan_execute(void* plan, void* cuda_stream);
 int bse_plan_status(void* plan, void* cuda_stream);
 /* output-column tile width the plan's stage-1 GEMM uses (0 for FP64 plans) */
 int bse_plan_tile_cols(const void* plan);
+/* 1 if the plan's direct terms run as the fused launch, else 0 */
+int bse_plan_fused(const void* plan);
 void bse_plan_destroy(void* plan);
 
 /* FP64 build of one problem that allocates no device memory.

@@ -19,6 +19,7 @@ BSE_OK, BSE_ERR_ARG, BSE_ERR_CUDA, BSE_ERR_NOMEM = 0, -1, -2, -3
 BSE_ERR_NOT_PD, BSE_ERR_NO_CONV, BSE_ERR_TIMEOUT, BSE_ERR_UNSUPPORTED = -4, -5, -6, -7
 BSE_PREC_FP64, BSE_PREC_BF16X6, BSE_PREC_BF16X3 = 0, 2, 3
 BSE_PLAN_AUTOTUNE = 1
+BSE_PLAN_UNFUSED = 2
 HARTREE_EV = 27.211386245988
 
 STATUS_NAMES = {0: "BSE_OK", -1: "BSE_ERR_ARG", -2: "BSE_ERR_CUDA", -3: "BSE_ERR_NOMEM",
@@ -56,7 +57,8 @@ EXPORTED = ("bse_build_kernel", "bse_reduce", "bse_spectrum", "bse_last_error", 
             "bse_mlp_create", "bse_mlp_destroy", "bse_mlp_num_params", "bse_mlp_get_params",
             "bse_mlp_set_params", "bse_mlp_samples", "bse_mlp_loss_grad", "bse_mlp_train",
             "bse_mlp_predict", "bse_xpy", "bse_mlp_trajectory_samples", "bse_plan_create",
-            "bse_plan_execute", "bse_plan_status", "bse_plan_tile_cols", "bse_plan_destroy")
+            "bse_plan_execute", "bse_plan_status", "bse_plan_tile_cols", "bse_plan_destroy",
+            "bse_plan_fused")
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -86,9 +88,11 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.bse_plan_execute.argtypes = [vp, vp]
     lib.bse_plan_status.argtypes = [vp, vp]
     lib.bse_plan_tile_cols.argtypes = [vp]
+    lib.bse_plan_fused.argtypes = [vp]
     lib.bse_plan_destroy.argtypes = [vp]
     lib.bse_plan_destroy.restype = None
-    for name in ("bse_plan_create", "bse_plan_execute", "bse_plan_status", "bse_plan_tile_cols"):
+    for name in ("bse_plan_create", "bse_plan_execute", "bse_plan_status", "bse_plan_tile_cols",
+                 "bse_plan_fused"):
         getattr(lib, name).restype = ctypes.c_int
     f32p = ctypes.POINTER(ctypes.c_float)
     lib.bse_mlp_create.argtypes = [ctypes.POINTER(vp), i32, i32, ctypes.c_uint64]
@@ -417,14 +421,14 @@ class Plan:
     problem structs (and the tensors behind them) must outlive the plan."""
 
     def __init__(self, problems: Sequence[bse_problem], precision: int = BSE_PREC_BF16X6,
-                 autotune: bool = False, stream=None):
+                 autotune: bool = False, fused: bool = True, stream=None):
         lib = load()
         self._problems = list(problems)
         arr = (bse_problem * len(self._problems))(*self._problems)
         h = ctypes.c_void_p()
-        _check(lib.bse_plan_create(arr, len(self._problems), int(precision),
-                                   BSE_PLAN_AUTOTUNE if autotune else 0, ctypes.byref(h),
-                                   _stream(stream)))
+        flags = (BSE_PLAN_AUTOTUNE if autotune else 0) | (0 if fused else BSE_PLAN_UNFUSED)
+        _check(lib.bse_plan_create(arr, len(self._problems), int(precision), flags,
+                                   ctypes.byref(h), _stream(stream)))
         self.handle = h
 
     def execute(self, stream=None) -> None:
@@ -436,6 +440,11 @@ class Plan:
     @property
     def tile_cols(self) -> int:
         return int(load().bse_plan_tile_cols(self.handle))
+
+    @property
+    def fused(self) -> bool:
+        """True if the direct terms run as one fused launch."""
+        return bool(load().bse_plan_fused(self.handle))
 
     def close(self) -> None:
         if self.handle:

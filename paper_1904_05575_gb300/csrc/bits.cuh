@@ -82,6 +82,13 @@ __device__ __forceinline__ double f32_to_f64_bits(float f) {
   return __longlong_as_double((long long)(sign | (be << 52) | ((uint64_t)(u & 0x7FFFFFu) << 29)));
 }
 
+// sc * (hi + lo) for a compensated sum, formed as sc*hi + sc*lo with every
+// rounding explicit (no contraction into an FMA), so that every kernel that
+// finishes such a sum gives the same bits.
+__device__ __forceinline__ float scale_hi_lo(float sc, float hi, float lo) {
+  return __fadd_rn(__fmul_rn(sc, hi), __fmul_rn(sc, lo));
+}
+
 // Error-free sum of two FP32 numbers (Knuth's TwoSum): s + err == a + b exactly.
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& err) {
   s = a + b;

@@ -131,6 +131,15 @@ Problem validate(const bse_problem& p, int index, cudaStream_t s) {
     if (p.coupling) BSE_CHECK_ARG(p.n_vc && p.q_plus, at + "NULL n_vc or q_plus");
   }
   if (p.coupling) BSE_CHECK_ARG(p.B, at + "coupling = 1 needs B");
+  // complex128 arrays are read and written 16 bytes at a time (vector loads,
+  // bulk copies), real arrays 8, q maps 4
+  auto aligned = [](const void* q, uintptr_t a) { return (reinterpret_cast<uintptr_t>(q) & (a - 1)) == 0; };
+  BSE_CHECK_ARG(aligned(p.m_x, 16) && aligned(p.m_vv, 16) && aligned(p.m_cc, 16) &&
+                    aligned(p.n_vc, 16) && aligned(p.w, 16) && aligned(p.A, 16) && aligned(p.B, 16),
+                at + "complex128 arrays must be 16-byte aligned");
+  BSE_CHECK_ARG(aligned(p.e_v, 8) && aligned(p.e_c, 8) && aligned(p.v_bar, 8) &&
+                    aligned(p.q_minus, 4) && aligned(p.q_plus, 4),
+                at + "real arrays must be 8-byte and q maps 4-byte aligned");
   Problem pr;
   if (p.gamma_c != 0.0) {
     pr.qm_host = check_q_map(p.q_minus, p.nk, p.nq_w, "q_minus", s);
@@ -186,12 +195,12 @@ extern "C" int bse_plan_create(const bse_problem* probs, int32_t nprob, int32_t 
     BSE_CHECK_ARG(precision == BSE_PREC_FP64 || precision == BSE_PREC_BF16X6 ||
                       precision == BSE_PREC_BF16X3,
                   "unknown precision " + std::to_string(precision));
-    BSE_CHECK_ARG((flags & ~BSE_PLAN_AUTOTUNE) == 0, "unknown plan flags");
+    BSE_CHECK_ARG((flags & ~(BSE_PLAN_AUTOTUNE | BSE_PLAN_UNFUSED)) == 0, "unknown plan flags");
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     keep_pool_memory();
     std::vector<Problem> prs;
     for (int i = 0; i < nprob; ++i) prs.push_back(validate(probs[i], i, s));
-    *plan = plan_create(std::move(prs), precision, (flags & BSE_PLAN_AUTOTUNE) != 0, s);
+    *plan = plan_create(std::move(prs), precision, flags, s);
   });
 }
 
@@ -214,6 +223,10 @@ extern "C" int bse_plan_status(void* plan, void* cuda_stream) {
 
 extern "C" int bse_plan_tile_cols(const void* plan) {
   return plan ? plan_tile_cols(static_cast<const BatchPlan*>(plan)) : 0;
+}
+
+extern "C" int bse_plan_fused(const void* plan) {
+  return plan ? plan_fused(static_cast<const BatchPlan*>(plan)) : 0;
 }
 
 extern "C" void bse_plan_destroy(void* plan) { plan_destroy(static_cast<BatchPlan*>(plan)); }

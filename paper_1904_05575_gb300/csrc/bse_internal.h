@@ -123,10 +123,11 @@ void davidson_fp64(int n, const bse_c128* A, const bse_c128* B, int64_t ld, int 
 
 // Batched plans (build_mixed.cu).
 struct BatchPlan;
-BatchPlan* plan_create(std::vector<Problem> probs, int precision, bool autotune, cudaStream_t s);
+BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cudaStream_t s);
 void plan_execute(BatchPlan* plan, cudaStream_t s);
 int plan_status(BatchPlan* plan, cudaStream_t s);
 int plan_tile_cols(const BatchPlan* plan);
+int plan_fused(const BatchPlan* plan);
 void plan_destroy(BatchPlan* plan);
 
 // Reduction and spectrum.

@@ -12,6 +12,9 @@
 //   4. stage 2    FP32 CUDA-core contraction of T with the other pair side over
 //                 G, read straight from the complex128 input, subtracted from
 //                 A (W^rr) or B (W^ra) in FP64
+// Where every pair block fits the fused epilogue (rows_t a power of two,
+// rows_x <= min(16, rows_t)), steps 3 and 4 run as one tcgen05 launch whose
+// epilogue performs the contraction on the TMEM tile (tc_direct.cuh).
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -30,6 +33,7 @@
 
 #include "bits.cuh"
 #include "bse_internal.h"
+#include "tc_direct.cuh"
 #include "tc_gemm.cuh"
 
 namespace bse {
@@ -300,8 +304,8 @@ __global__ void __launch_bounds__((TS / R) * (TS / R)) k_stage2(Stage2Args a) {
       double2 o = *dst;
       // contribution formed in FP32 (hi + lo carries the compensated sum), widened exactly
       const float sc = (float)a.scale;
-      o.x -= f32_to_f64_bits(sc * hx[i][j] + sc * lx[i][j]);
-      o.y -= f32_to_f64_bits(sc * hy[i][j] + sc * ly[i][j]);
+      o.x -= f32_to_f64_bits(scale_hi_lo(sc, hx[i][j], lx[i][j]));
+      o.y -= f32_to_f64_bits(scale_hi_lo(sc, hy[i][j], ly[i][j]));
       *dst = o;
     }
 }
@@ -422,8 +426,8 @@ __global__ void __launch_bounds__(256) k_stage2_pipe(Stage2Args a) {
   double2* dst = a.out + al + ap * a.ld;
   const float sc = (float)a.scale;
   double2 o = *dst;
-  o.x -= f32_to_f64_bits(sc * hx + sc * lx);
-  o.y -= f32_to_f64_bits(sc * hy + sc * ly);
+  o.x -= f32_to_f64_bits(scale_hi_lo(sc, hx, lx));
+  o.y -= f32_to_f64_bits(scale_hi_lo(sc, hy, ly));
   *dst = o;
 }
 
@@ -505,6 +509,36 @@ void launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb, const tc::Tile* d
   note_launches(1);
 }
 
+// stage 1 + stage 2 in one launch; a work unit is one 128-row tile with all
+// its output-column tiles (sh.group of them, consecutive in d_tiles)
+void launch_direct(const CUtensorMap& ma, const CUtensorMap& mb, const tc::Tile* d_tiles,
+                   int ntiles, const tc::GemmShape& sh, const tc::S2Term* d_terms, int* d_err,
+                   cudaStream_t s) {
+  if (ntiles == 0) return;
+  if (sh.acc_bufs != 2 || sh.group < 1)
+    throw Error(BSE_ERR_UNSUPPORTED, "fused direct term needs two accumulator sets");
+  const size_t smem = tc::s2_smem_bytes(sh);
+  auto kern = sh.pieces == 3 ? tc::gemm_split_bf16_direct<3> : tc::gemm_split_bf16_direct<2>;
+  static std::once_flag once3, once2;
+  static int max_dyn3 = 0, max_dyn2 = 0;
+  int& max_dyn = sh.pieces == 3 ? max_dyn3 : max_dyn2;
+  std::call_once(sh.pieces == 3 ? once3 : once2, [&] {
+    int dev = 0, optin = 0;
+    BSE_CUDA(cudaGetDevice(&dev));
+    BSE_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa;
+    BSE_CUDA(cudaFuncGetAttributes(&fa, kern));
+    max_dyn = optin - (int)fa.sharedSizeBytes;
+    BSE_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn));
+  });
+  if ((int)smem > max_dyn) throw Error(BSE_ERR_UNSUPPORTED, "tile shape needs too much shared memory");
+  const int units = (ntiles + sh.group - 1) / sh.group;
+  const int grid = std::min<int>(units, num_sms());
+  kern<<<grid, tc::S2_THREADS, smem, s>>>(ma, mb, d_tiles, ntiles, sh, d_terms, d_err);
+  BSE_CUDA(cudaGetLastError());
+  note_launches(1);
+}
+
 tc::GemmShape make_shape(int nt, int Kp, int pieces) {
   tc::GemmShape sh;
   sh.nt = nt;
@@ -517,6 +551,20 @@ tc::GemmShape make_shape(int nt, int Kp, int pieces) {
   const size_t budget = 220 * 1024;
   int st = (int)((budget - 2048) / sb);
   sh.stages = std::max(1, std::min(st, 6));
+  return sh;
+}
+
+// Shape of the fused direct-term launch: nt <= 64 so that two accumulator
+// sets fit TMEM (the contraction of one column tile overlaps the MMAs of the
+// next), and the pipeline depth reduced to leave room for the pair-side ring.
+tc::GemmShape make_shape_direct(int nt, int Kp, int pieces, int group) {
+  tc::GemmShape sh = make_shape(nt, Kp, pieces);
+  sh.acc_bufs = 2;
+  sh.tmem_cols = 8 * nt <= 256 ? 256 : 512;
+  sh.group = group;
+  const uint32_t sb = tc::stage_bytes(sh);
+  const size_t budget = 220 * 1024 - 2048 - tc::s2_extra_bytes(6);
+  sh.stages = std::max(1, std::min((int)(budget / sb), 6));
   return sh;
 }
 
@@ -649,14 +697,23 @@ struct BatchPlan {
   int64_t a_rows = 0, w_rows = 0;
   DevMem wsplit, asplit, tbuf, stiles;
   int n_stiles = 0;
+  // fused direct term (stage 1 + stage 2 in one launch)
+  bool fused = false;
+  std::vector<tc::S2Term> s2host;
+  DevMem s2terms, xmaps;
   DevMem err;
 };
 
 namespace {
 
+// Stage-1 tiles, 128-row tile by 128-row tile with all its column tiles
+// consecutive; Tile::prob is the problem (two-kernel path) or the term
+// (fused path, whose epilogue reads the term's pair side and output).
 std::vector<tc::Tile> stage1_tiles(const BatchPlan& pl, int nt) {
   std::vector<tc::Tile> tiles;
-  for (const BatchPlan::Term& t : pl.terms) {
+  for (size_t ti = 0; ti < pl.terms.size(); ++ti) {
+    const BatchPlan::Term& t = pl.terms[ti];
+    const int id = pl.fused ? (int)ti : t.prob;
     const int nq = pl.probs[t.prob].p.nq_w;
     std::vector<int> perm, gstart;
     group_pairs(t.qh, nq, perm, gstart);
@@ -667,7 +724,7 @@ std::vector<tc::Tile> stage1_tiles(const BatchPlan& pl, int nt) {
         for (int n0 = 0; n0 < pl.ng; n0 += nt)
           tiles.push_back({(int)m0, (int)std::min<int64_t>(tc::BM, r1 - m0),
                            (int)(t.w_row0 + (int64_t)q * pl.ng_pad + n0), n0,
-                           std::min(nt, pl.ng - n0), (int)m0, t.prob});
+                           std::min(nt, pl.ng - n0), (int)m0, id});
     }
   }
   return tiles;
@@ -714,6 +771,12 @@ void plan_execute_mixed(BatchPlan& pl, cudaStream_t s) {
                 ExchangeBatchEpi{pl.exparams.as<ExParams>()}, pl.err.as<int>(), s);
   }
   if (pl.terms.empty()) return;
+  if (pl.fused) {
+    Phase ph("mixed_direct_fused", s);
+    launch_direct(pl.ma_s, pl.mb_s, pl.stiles.as<tc::Tile>(), pl.n_stiles, pl.sh_g,
+                  pl.s2terms.as<tc::S2Term>(), pl.err.as<int>(), s);
+    return;
+  }
   {
     Phase ph("mixed_stage1_gemm", s);
     launch_gemm(pl.ma_s, pl.mb_s, pl.stiles.as<tc::Tile>(), pl.n_stiles, pl.sh_g,
@@ -728,7 +791,8 @@ void plan_execute_mixed(BatchPlan& pl, cudaStream_t s) {
 
 void plan_set_tiles(BatchPlan& pl, int nt) {
   pl.nt_g = nt;
-  pl.sh_g = make_shape(nt, pl.Kp, pl.pieces);
+  pl.sh_g = pl.fused ? make_shape_direct(nt, pl.Kp, pl.pieces, (pl.ng + nt - 1) / nt)
+                     : make_shape(nt, pl.Kp, pl.pieces);
   std::vector<tc::Tile> st = stage1_tiles(pl, nt);
   pl.n_stiles = (int)st.size();
   pl.stiles = upload_mem(st);
@@ -737,18 +801,31 @@ void plan_set_tiles(BatchPlan& pl, int nt) {
 
 // time the stage-1 GEMM at each candidate tile width and keep the fastest
 void plan_autotune(BatchPlan& pl, cudaStream_t s) {
+  const int key = 2 * pl.ng_pad + (pl.fused ? 1 : 0);
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
-    auto it = g_tuned_nt.find(pl.ng_pad);
+    auto it = g_tuned_nt.find(key);
     if (it != g_tuned_nt.end()) {
       plan_set_tiles(pl, it->second);
       return;
     }
   }
   std::vector<int> cands;
-  for (int mx : {64, 128}) {
-    int nt = round_up((pl.ng_pad + ((pl.ng_pad + mx - 1) / mx) - 1) / ((pl.ng_pad + mx - 1) / mx), 32);
-    if (std::find(cands.begin(), cands.end(), nt) == cands.end()) cands.push_back(nt);
+  if (pl.fused) {
+    cands.push_back(32);
+    if (pl.ng_pad >= 64) cands.push_back(64);
+  } else {
+    for (int mx : {64, 128}) {
+      int nt = round_up((pl.ng_pad + ((pl.ng_pad + mx - 1) / mx) - 1) / ((pl.ng_pad + mx - 1) / mx), 32);
+      if (std::find(cands.begin(), cands.end(), nt) == cands.end()) cands.push_back(nt);
+    }
+  }
+  // the fused launch is timed with its outputs switched off (A and B untouched)
+  DevMem timing_terms;
+  if (pl.fused) {
+    std::vector<tc::S2Term> tt = pl.s2host;
+    for (tc::S2Term& x : tt) x.out = nullptr;
+    timing_terms = upload_mem(tt);
   }
   plan_splits(pl, s);
   cudaEvent_t e0, e1;
@@ -761,8 +838,12 @@ void plan_autotune(BatchPlan& pl, cudaStream_t s) {
     float ms = 0.f;
     for (int rep = 0; rep < 3; ++rep) {
       BSE_CUDA(cudaEventRecord(e0, s));
-      launch_gemm(pl.ma_s, pl.mb_s, pl.stiles.as<tc::Tile>(), pl.n_stiles, pl.sh_g,
-                  TEpi{pl.tbuf.as<float2>(), pl.a_rows}, pl.err.as<int>(), s);
+      if (pl.fused)
+        launch_direct(pl.ma_s, pl.mb_s, pl.stiles.as<tc::Tile>(), pl.n_stiles, pl.sh_g,
+                      timing_terms.as<tc::S2Term>(), pl.err.as<int>(), s);
+      else
+        launch_gemm(pl.ma_s, pl.mb_s, pl.stiles.as<tc::Tile>(), pl.n_stiles, pl.sh_g,
+                    TEpi{pl.tbuf.as<float2>(), pl.a_rows}, pl.err.as<int>(), s);
       BSE_CUDA(cudaEventRecord(e1, s));
       BSE_CUDA(cudaEventSynchronize(e1));
       float t = 0.f;
@@ -777,13 +858,24 @@ void plan_autotune(BatchPlan& pl, cudaStream_t s) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   plan_set_tiles(pl, best_nt);
+  BSE_CUDA(cudaMemsetAsync(pl.err.ptr, 0, sizeof(int), s));
   std::lock_guard<std::mutex> lock(g_tune_mutex);
-  g_tuned_nt[pl.ng_pad] = best_nt;
+  g_tuned_nt[key] = best_nt;
 }
 
 }  // namespace
 
-BatchPlan* plan_create(std::vector<Problem> probs, int precision, bool autotune, cudaStream_t s) {
+// True when a term's pair blocks fit the fused epilogue: whole pairs per
+// 128-row tile (rows_t a power of two), 4 or 16 sums per thread, and at most
+// 128 pair-side rows per block of plane waves (rows_x <= rows_t).  With both
+// direct terms this is Nv = Nc in {2, 4}.
+bool fused_fits(const Stage2Args& a) {
+  const int rt = a.rows_t, rx = a.rows_x;
+  return rt >= 1 && rt <= tc::BM && (rt & (rt - 1)) == 0 && (rx == 4 || rx == 16) && rx <= rt;
+}
+
+BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cudaStream_t s) {
+  const bool autotune = (flags & BSE_PLAN_AUTOTUNE) != 0;
   std::unique_ptr<BatchPlan> pl(new BatchPlan);
   BSE_CUDA(cudaGetDevice(&pl->device));
   pl->precision = precision;
@@ -888,19 +980,66 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, bool autotune,
   if (!pl->terms.empty()) {
     if (pl->a_rows > INT32_MAX || pl->w_rows > INT32_MAX)
       throw Error(BSE_ERR_UNSUPPORTED, "batched stage-1 rows exceed 2^31");
+    pl->fused = (flags & BSE_PLAN_UNFUSED) == 0;
+    for (const BatchPlan::Term& t : pl->terms) pl->fused = pl->fused && fused_fits(t.s2);
     pl->wsplit = DevMem((size_t)pl->planes * pl->w_rows * pl->Kp * 2);
     pl->asplit = DevMem((size_t)pl->planes * pl->a_rows * pl->Kp * 2);
-    pl->tbuf = DevMem((size_t)pl->ng_pad * pl->a_rows * sizeof(float2));
-    for (BatchPlan::Term& t : pl->terms) {
-      t.s2.T = pl->tbuf.as<float2>();
-      t.s2.t_ld = pl->a_rows;
+    if (pl->fused) {
+      // the pair side of every term as a 2-D FP64 tensor [pairs * rows_x][2 ng],
+      // boxes of 16 FP64 (8 complex) x rows_x rows, zero-filled past NG
+      std::vector<CUtensorMap> maps;
+      for (const BatchPlan::Term& t : pl->terms) {
+        const Stage2Args& a = t.s2;
+        const bse_problem& p = pl->probs[t.prob].p;
+        CUtensorMap m;
+        cuuint64_t dims[2] = {(cuuint64_t)2 * a.ng, (cuuint64_t)p.nk * p.nk * a.rows_x};
+        cuuint64_t strides[1] = {(cuuint64_t)a.ng * 16};
+        cuuint32_t box[2] = {(cuuint32_t)(2 * tc::S2_GB), (cuuint32_t)a.rows_x};
+        cuuint32_t estr[2] = {1, 1};
+        CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, (void*)a.x, dims, strides,
+                                 box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                 CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS)
+          throw Error(BSE_ERR_CUDA, "cuTensorMapEncodeTiled (pair side) failed with " + std::to_string((int)r));
+        maps.push_back(m);
+      }
+      pl->xmaps = upload_mem(maps);
+      for (size_t ti = 0; ti < pl->terms.size(); ++ti) {
+        const BatchPlan::Term& t = pl->terms[ti];
+        const Stage2Args& a = t.s2;
+        tc::S2Term x;
+        x.xmap = pl->xmaps.as<CUtensorMap>() + ti;
+        x.perm = t.perm.as<int>();
+        x.out = a.out;
+        x.ld = a.ld;
+        x.a_row0 = t.a_row0;
+        x.rows_x = a.rows_x;
+        x.rows_t = a.rows_t;
+        x.nk = a.nk;
+        x.nv = a.nv;
+        x.nc = a.nc;
+        x.ng = a.ng;
+        x.mode = a.mode;
+        x.x_transpose_pair = a.x_transpose_pair;
+        x.conj_x = a.conj_x;
+        x.conj_t = a.conj_t;
+        x.scale = (float)a.scale;
+        pl->s2host.push_back(x);
+      }
+      pl->s2terms = upload_mem(pl->s2host);
+    } else {
+      pl->tbuf = DevMem((size_t)pl->ng_pad * pl->a_rows * sizeof(float2));
+      for (BatchPlan::Term& t : pl->terms) {
+        t.s2.T = pl->tbuf.as<float2>();
+        t.s2.t_ld = pl->a_rows;
+      }
     }
     pl->ma_s = make_plane_map(pl->asplit.as<__nv_bfloat16>(), pl->Kp, (int)pl->a_rows, pl->planes,
                               tc::BM);
     if (autotune)
       plan_autotune(*pl, s);
     else
-      plan_set_tiles(*pl, tile_cols(pl->ng_pad));
+      plan_set_tiles(*pl, pl->fused ? (pl->ng_pad % 64 == 0 ? 64 : 32) : tile_cols(pl->ng_pad));
   }
   BSE_CUDA(cudaStreamSynchronize(s));
   return pl.release();
@@ -929,6 +1068,8 @@ int plan_status(BatchPlan* pl, cudaStream_t s) {
 }
 
 int plan_tile_cols(const BatchPlan* pl) { return pl->nt_g; }
+
+int plan_fused(const BatchPlan* pl) { return pl->fused ? 1 : 0; }
 
 void plan_destroy(BatchPlan* pl) { delete pl; }
 
@@ -1005,7 +1146,7 @@ void build_mixed_batch(const std::vector<Problem>& probs, int precision, cudaStr
         }
     }
     if (!plan) {
-      std::unique_ptr<BatchPlan> created(plan_create(group, precision, false, s));
+      std::unique_ptr<BatchPlan> created(plan_create(group, precision, 0, s));
       std::lock_guard<std::mutex> lock(g_cache_mutex);
       if (g_cache.size() >= kPlanCache) g_cache.erase(g_cache.begin());
       g_cache.push_back(CachedPlan{key, std::move(created)});

@@ -193,6 +193,7 @@ struct GemmShape {    // stages <= 8
   int stages;      // pipeline depth
   int acc_bufs;    // accumulator sets in TMEM (2: epilogue of one tile overlaps the next)
   uint32_t tmem_cols;
+  int group = 1;   // consecutive tiles a CTA takes as one work unit
 };
 
 __host__ __device__ inline uint32_t a_plane_bytes() { return BM * BK * 2; }
@@ -205,6 +206,137 @@ __host__ inline size_t gemm_smem_bytes(const GemmShape& s) {
 }
 
 // ---------------------------------------------------------------------------
+// Work distribution: CTA b takes work units b, b + gridDim.x, ...; unit u is
+// the tiles [u * group, (u + 1) * group) (the last unit may be shorter).
+// Every role walks the same sequence.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int num_units(int ntiles, int group) { return (ntiles + group - 1) / group; }
+
+// Shared-memory pipeline of the operand stages and the TMEM accumulator sets.
+struct Pipe {
+  uint8_t* smem;          // stage 0 (1024-byte aligned)
+  uint64_t* full;         // [stages] operand bytes landed
+  uint64_t* empty;        // [stages] MMAs that read the stage completed
+  uint64_t* tmem_full;    // [2] accumulator set ready for the epilogue
+  uint64_t* tmem_empty;   // [2] epilogue done with the set (4 warp arrivals)
+  uint32_t sbytes, a_bytes;
+};
+
+// TMA producer (one thread): for each tile, each K step, one 3-D box of the A
+// planes and one of the B planes into the next free stage.
+__device__ __forceinline__ void producer_role(const Pipe& pp, const CUtensorMap* tmA,
+                                              const CUtensorMap* tmB, const Tile* tiles, int ntiles,
+                                              const GemmShape& sh, volatile int* abort_flag,
+                                              int* err) {
+  int stage = 0;
+  uint32_t phase = 0;
+  int pending[8];   // parity of the latest arming of each stage, -1 = never armed
+  for (int s = 0; s < 8; ++s) pending[s] = -1;
+  const int units = num_units(ntiles, sh.group);
+  bool ok = true;
+  for (int u = blockIdx.x; u < units && ok && !*abort_flag; u += gridDim.x) {
+    for (int t = u * sh.group; t < min(ntiles, (u + 1) * sh.group) && ok; ++t) {
+      const Tile tl = tiles[t];
+      for (int kc = 0; kc < sh.kchunks; ++kc) {
+        if (!mbar_wait(&pp.empty[stage], phase ^ 1, abort_flag, err)) {
+          ok = false;
+          break;
+        }
+        mbar_expect_tx(&pp.full[stage], pp.sbytes);
+        uint8_t* sa = pp.smem + (size_t)stage * pp.sbytes;
+        tma_load_3d(sa, tmA, kc * BK, tl.a_row0, 0, &pp.full[stage]);
+        tma_load_3d(sa + pp.a_bytes, tmB, kc * BK, tl.b_row0, 0, &pp.full[stage]);
+        pending[stage] = (int)phase;
+        if (++stage == sh.stages) {
+          stage = 0;
+          phase ^= 1;
+        }
+      }
+    }
+  }
+  if (*abort_flag) {
+    // let the copies this thread issued land before shared memory goes away:
+    // the latest arming of each stage completes when its bytes have arrived
+    long long t0 = clock64();
+    for (int s = 0; s < sh.stages; ++s)
+      if (pending[s] >= 0)
+        while (!mbar_try_wait(&pp.full[s], (uint32_t)pending[s]) && clock64() - t0 < WAIT_CYCLES) {
+        }
+  }
+}
+
+// MMA issuer (one thread).  Tile number `local` (counted over this CTA's
+// tiles) accumulates into set local % acc_bufs.
+template <int P>
+__device__ __forceinline__ void mma_role(const Pipe& pp, uint32_t tmem_base, int ntiles,
+                                         const GemmShape& sh, volatile int* abort_flag, int* err) {
+  int stage = 0;
+  uint32_t phase = 0;
+  int local = 0;
+  const int nbuf = sh.acc_bufs;
+  const uint32_t nt = (uint32_t)sh.nt;
+  const uint32_t id_pos = idesc_bf16(sh.nt, false), id_neg = idesc_bf16(sh.nt, true);
+  // descriptors of stage 0, plane 0; the start-address field (bytes >> 4, 14 bits)
+  // is advanced by plain adds for other stages and planes (all below 256 KB)
+  const uint32_t sa0 = smem_u32(pp.smem);
+  const uint64_t da0 = smem_desc_sw32(sa0), db0 = smem_desc_sw32(sa0 + pp.a_bytes);
+  const uint64_t dstage = pp.sbytes >> 4, dpa = a_plane_bytes() >> 4, dpb = b_plane_bytes(sh.nt) >> 4;
+  const int units = num_units(ntiles, sh.group);
+  bool ok = true;
+  for (int u = blockIdx.x; u < units && ok && !*abort_flag; u += gridDim.x) {
+    for (int t = u * sh.group; t < min(ntiles, (u + 1) * sh.group); ++t, ++local) {
+      const int buf = nbuf == 2 ? (local & 1) : 0;
+      const int use = nbuf == 2 ? (local >> 1) : local;    // earlier uses of this buffer
+      if (use > 0 && !mbar_wait(&pp.tmem_empty[buf], (use - 1) & 1, abort_flag, err)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t base = tmem_base + (uint32_t)buf * 4u * nt;
+      const uint32_t m_re = base, m_im = base + nt;               // main
+      const uint32_t c_re = base + 2 * nt, c_im = base + 3 * nt;  // corrections
+      for (int kc = 0; kc < sh.kchunks; ++kc) {
+        if (!mbar_wait(&pp.full[stage], phase, abort_flag, err)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint64_t da = da0 + (uint64_t)stage * dstage, db = db0 + (uint64_t)stage * dstage;
+        const uint32_t first = kc == 0 ? 0u : 1u;
+        // leading products
+        mma_bf16(m_re, da, db, id_pos, first);
+        mma_bf16(m_re, da + P * dpa, db + P * dpb, id_neg, 1);
+        mma_bf16(m_im, da, db + P * dpb, id_pos, first);
+        mma_bf16(m_im, da + P * dpa, db, id_pos, 1);
+        // correction products i + j in [1, P)
+        uint32_t acc_c = first;
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+#pragma unroll
+          for (int j = 0; i + j < P; ++j) {
+            if (i + j == 0) continue;
+            const uint64_t a_re = da + i * dpa, a_im = da + (P + i) * dpa;
+            const uint64_t b_re = db + j * dpb, b_im = db + (P + j) * dpb;
+            mma_bf16(c_re, a_re, b_re, id_pos, acc_c);
+            mma_bf16(c_re, a_im, b_im, id_neg, 1);
+            mma_bf16(c_im, a_re, b_im, id_pos, acc_c);
+            mma_bf16(c_im, a_im, b_re, id_pos, 1);
+            acc_c = 1;
+          }
+        }
+        mma_commit(&pp.empty[stage]);   // frees this stage once its MMAs complete
+        if (++stage == sh.stages) {
+          stage = 0;
+          phase ^= 1;
+        }
+      }
+      if (!ok) break;
+      mma_commit(&pp.tmem_full[buf]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // The kernel.  Epi provides: __device__ void operator()(const Tile&, int row,
 // int col0, const float* re, const float* im) const  for 32 columns at col0.
 // ---------------------------------------------------------------------------
@@ -213,15 +345,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 gemm_split_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 const Tile* __restrict__ tiles, int ntiles, GemmShape sh, Epi epi, int* err) {
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>(
+  Pipe pp;
+  pp.smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  const uint32_t sbytes = stage_bytes(sh);
-  const uint32_t a_bytes = 2u * sh.pieces * a_plane_bytes();
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)sh.stages * sbytes);
-  uint64_t* empty = full + sh.stages;
-  uint64_t* tmem_full = empty + sh.stages;      // [2]: one per accumulator buffer
-  uint64_t* tmem_empty = tmem_full + 2;         // [2]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tmem_empty + 2);
+  pp.sbytes = stage_bytes(sh);
+  pp.a_bytes = 2u * sh.pieces * a_plane_bytes();
+  pp.full = reinterpret_cast<uint64_t*>(pp.smem + (size_t)sh.stages * pp.sbytes);
+  pp.empty = pp.full + sh.stages;
+  pp.tmem_full = pp.empty + sh.stages;
+  pp.tmem_empty = pp.tmem_full + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(pp.tmem_empty + 2);
   __shared__ volatile int abort_flag;
 
   const int warp = threadIdx.x >> 5;
@@ -230,12 +363,12 @@ gemm_split_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < sh.stages; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&pp.full[s], 1);
+      mbar_init(&pp.empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
-      mbar_init(&tmem_full[b], 1);
-      mbar_init(&tmem_empty[b], 4);
+      mbar_init(&pp.tmem_full[b], 1);
+      mbar_init(&pp.tmem_empty[b], 4);
     }
     abort_flag = 0;
     fence_barrier_init();
@@ -247,134 +380,50 @@ gemm_split_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
   const uint32_t tmem_base = *tmem_slot;
 
   if (warp == 0) {
-    // ---------------- TMA producer ----------------
-    if (lane == 0) {
-      int stage = 0;
-      uint32_t phase = 0;
-      int pending[8];   // parity of the latest arming of each stage, -1 = never armed
-      for (int s = 0; s < 8; ++s) pending[s] = -1;
-      for (int t = blockIdx.x; t < ntiles && !abort_flag; t += gridDim.x) {
-        const Tile tl = tiles[t];
-        for (int kc = 0; kc < sh.kchunks; ++kc) {
-          if (!mbar_wait(&empty[stage], phase ^ 1, &abort_flag, err)) break;
-          mbar_expect_tx(&full[stage], sbytes);
-          uint8_t* sa = smem + (size_t)stage * sbytes;
-          tma_load_3d(sa, &tmA, kc * BK, tl.a_row0, 0, &full[stage]);
-          tma_load_3d(sa + a_bytes, &tmB, kc * BK, tl.b_row0, 0, &full[stage]);
-          pending[stage] = (int)phase;
-          if (++stage == sh.stages) {
-            stage = 0;
-            phase ^= 1;
-          }
-        }
-      }
-      if (abort_flag) {
-        // let the copies this thread issued land before shared memory goes away:
-        // the latest arming of each stage completes when its bytes have arrived
-        long long t0 = clock64();
-        for (int s = 0; s < sh.stages; ++s)
-          if (pending[s] >= 0)
-            while (!mbar_try_wait(&full[s], (uint32_t)pending[s]) &&
-                   clock64() - t0 < WAIT_CYCLES) {
-            }
-      }
-    }
+    if (lane == 0) producer_role(pp, &tmA, &tmB, tiles, ntiles, sh, &abort_flag, err);
   } else if (warp == 1) {
-    // ---------------- MMA issuer ----------------
-    if (lane == 0) {
-      int stage = 0;
-      uint32_t phase = 0;
-      int local = 0;
-      const uint32_t nt = (uint32_t)sh.nt;
-      const uint32_t id_pos = idesc_bf16(sh.nt, false), id_neg = idesc_bf16(sh.nt, true);
-      // descriptors of stage 0, plane 0; the start-address field (bytes >> 4, 14 bits)
-      // is advanced by plain adds for other stages and planes (all below 256 KB)
-      const uint32_t sa0 = smem_u32(smem);
-      const uint64_t da0 = smem_desc_sw32(sa0), db0 = smem_desc_sw32(sa0 + a_bytes);
-      const uint64_t dstage = sbytes >> 4, dpa = a_plane_bytes() >> 4,
-                     dpb = b_plane_bytes(sh.nt) >> 4;
-      for (int t = blockIdx.x; t < ntiles && !abort_flag; t += gridDim.x, ++local) {
-        const int buf = nbuf == 2 ? (local & 1) : 0;
-        const int use = nbuf == 2 ? (local >> 1) : local;    // earlier uses of this buffer
-        if (use > 0 && !mbar_wait(&tmem_empty[buf], (use - 1) & 1, &abort_flag, err)) break;
-        tc_fence_after();
-        const uint32_t base = tmem_base + (uint32_t)buf * 4u * nt;
-        const uint32_t m_re = base, m_im = base + nt;               // main
-        const uint32_t c_re = base + 2 * nt, c_im = base + 3 * nt;  // corrections
-        bool ok = true;
-        for (int kc = 0; kc < sh.kchunks; ++kc) {
-          if (!mbar_wait(&full[stage], phase, &abort_flag, err)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          const uint64_t da = da0 + (uint64_t)stage * dstage, db = db0 + (uint64_t)stage * dstage;
-          const uint32_t first = kc == 0 ? 0u : 1u;
-          // leading products
-          mma_bf16(m_re, da, db, id_pos, first);
-          mma_bf16(m_re, da + P * dpa, db + P * dpb, id_neg, 1);
-          mma_bf16(m_im, da, db + P * dpb, id_pos, first);
-          mma_bf16(m_im, da + P * dpa, db, id_pos, 1);
-          // correction products i + j in [1, P)
-          uint32_t acc_c = first;
-#pragma unroll
-          for (int i = 0; i < P; ++i) {
-#pragma unroll
-            for (int j = 0; i + j < P; ++j) {
-              if (i + j == 0) continue;
-              const uint64_t a_re = da + i * dpa, a_im = da + (P + i) * dpa;
-              const uint64_t b_re = db + j * dpb, b_im = db + (P + j) * dpb;
-              mma_bf16(c_re, a_re, b_re, id_pos, acc_c);
-              mma_bf16(c_re, a_im, b_im, id_neg, 1);
-              mma_bf16(c_im, a_re, b_im, id_pos, acc_c);
-              mma_bf16(c_im, a_im, b_re, id_pos, 1);
-              acc_c = 1;
-            }
-          }
-          mma_commit(&empty[stage]);   // frees this stage once its MMAs complete
-          if (++stage == sh.stages) {
-            stage = 0;
-            phase ^= 1;
-          }
-        }
-        if (!ok) break;
-        mma_commit(&tmem_full[buf]);
-      }
-    }
+    if (lane == 0) mma_role<P>(pp, tmem_base, ntiles, sh, &abort_flag, err);
   } else {
     // ---------------- epilogue (warps 2..5) ----------------
     const int quarter = warp & 3;    // TMEM lanes this warp may access
     const int row = quarter * 32 + lane;
     int local = 0;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++local) {
-      // one lane waits, the warp follows (the tcgen05.ld below is warp-collective)
-      const int buf = nbuf == 2 ? (local & 1) : 0;
-      const int use = nbuf == 2 ? (local >> 1) : local;
-      int ok = 0;
-      if (lane == 0) ok = mbar_wait(&tmem_full[buf], use & 1, &abort_flag, err) ? 1 : 0;
-      ok = __shfl_sync(0xffffffffu, ok, 0);
-      if (!ok) break;
-      __syncwarp();
-      tc_fence_after();
-      const Tile tl = tiles[t];
-      float re[32], im[32], cr[32], ci[32];
-      const uint32_t lane_base =
-          tmem_base + (uint32_t)buf * 4u * (uint32_t)sh.nt + ((uint32_t)(quarter * 32) << 16);
-      for (int c0 = 0; c0 < sh.nt; c0 += 32) {
-        tmem_ld32(lane_base + (uint32_t)c0, re);
-        tmem_ld32(lane_base + (uint32_t)(sh.nt + c0), im);
-        tmem_ld32(lane_base + (uint32_t)(2 * sh.nt + c0), cr);
-        tmem_ld32(lane_base + (uint32_t)(3 * sh.nt + c0), ci);
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          re[j] += cr[j];
-          im[j] += ci[j];
+    const int units = num_units(ntiles, sh.group);
+    bool alive = true;
+    for (int u = blockIdx.x; u < units && alive; u += gridDim.x) {
+      for (int t = u * sh.group; t < min(ntiles, (u + 1) * sh.group); ++t, ++local) {
+        // one lane waits, the warp follows (the tcgen05.ld below is warp-collective)
+        const int buf = nbuf == 2 ? (local & 1) : 0;
+        const int use = nbuf == 2 ? (local >> 1) : local;
+        int ok = 0;
+        if (lane == 0) ok = mbar_wait(&pp.tmem_full[buf], use & 1, &abort_flag, err) ? 1 : 0;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) {
+          alive = false;
+          break;
         }
-        if (row < tl.m_valid && c0 < tl.n_valid) epi(tl, row, c0, re, im);
+        __syncwarp();
+        tc_fence_after();
+        const Tile tl = tiles[t];
+        float re[32], im[32], cr[32], ci[32];
+        const uint32_t lane_base =
+            tmem_base + (uint32_t)buf * 4u * (uint32_t)sh.nt + ((uint32_t)(quarter * 32) << 16);
+        for (int c0 = 0; c0 < sh.nt; c0 += 32) {
+          tmem_ld32(lane_base + (uint32_t)c0, re);
+          tmem_ld32(lane_base + (uint32_t)(sh.nt + c0), im);
+          tmem_ld32(lane_base + (uint32_t)(2 * sh.nt + c0), cr);
+          tmem_ld32(lane_base + (uint32_t)(3 * sh.nt + c0), ci);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            re[j] += cr[j];
+            im[j] += ci[j];
+          }
+          if (row < tl.m_valid && c0 < tl.n_valid) epi(tl, row, c0, re, im);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&pp.tmem_empty[buf]);
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&tmem_empty[buf]);
     }
   }
 

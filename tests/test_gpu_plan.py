@@ -1,6 +1,8 @@
 """Batched plans: several momentum transfers with uneven band windows built by
 one plan, against the oracle; the plan's execute captured in a CUDA graph and
-replayed; the tile-width autotuner (GPU)."""
+replayed; the tile-width autotuner; the fused direct term (stage-1 GEMM and
+contraction in one launch) against the oracle and, bit for bit, against the
+two-launch form (GPU)."""
 import numpy as np
 import pytest
 
@@ -32,6 +34,13 @@ def batch():
     probs = [bi.make_problem(MULTI, q_index=q) for q in range(3)]
     refs = [O.build_A_B(p) for p in probs]
     return probs, refs
+
+
+# three Q whose windows all fit the fused direct term (Nv = Nc in {2, 4}):
+# 2x2 windows put 32 pairs in a 128-row tile, and every q group ends in a
+# ragged tile
+SQUARE = bi.BSEConfig("multi-q-square", grid=2, nv=4, nc=4, ng=59, q_abs=(0.1, 0.6, 1.1),
+                      windows=((2, 2), (4, 4), (2, 2)), w_scale=0.1)
 
 
 def _rel(x, ref):
@@ -118,3 +127,87 @@ def test_plan_needs_one_ng(bse, batch):
     fp64 = bse.Plan(structs, precision=bse.BSE_PREC_FP64)   # FP64 plans take any shapes
     fp64.execute()
     fp64.close()
+
+
+def test_plan_with_odd_windows_is_not_fused(bse, batch):
+    probs, _ = batch
+    ds, structs = _upload(bse, probs)
+    plan = bse.Plan(structs, precision=bse.BSE_PREC_BF16X6)
+    assert not plan.fused           # 3x5 and 4x6 windows: pair blocks too tall for the epilogue
+    plan.close()
+
+
+@pytest.fixture(scope="module")
+def square():
+    probs = [bi.make_problem(SQUARE, q_index=q) for q in range(3)]
+    refs = [O.build_A_B(p) for p in probs]
+    return probs, refs
+
+
+def _build(bse, plan, ds):
+    import torch
+    for d in ds:
+        d["A"].fill_(complex(7.0, -7.0))
+        d["B"].fill_(complex(7.0, -7.0))
+    plan.execute()
+    plan.status()
+    torch.cuda.synchronize()
+    return [d["A"].clone() for d in ds] + [d["B"].clone() for d in ds]
+
+
+@pytest.mark.parametrize("prec,tol", [(2, 1e-6), (3, 1e-4)], ids=["bf16x6", "bf16x3"])
+def test_fused_matches_oracle_and_two_launch_form(bse, square, prec, tol):
+    import torch
+    probs, refs = square
+    ds, structs = _upload(bse, probs)
+    fused = bse.Plan(structs, precision=prec)
+    split = bse.Plan(structs, precision=prec, fused=False)
+    assert fused.fused and not split.fused
+    a = _build(bse, fused, ds)
+    _check(bse, probs, refs, ds, tol)
+    b = _build(bse, split, ds)
+    for x, y in zip(a, b):
+        assert torch.equal(x, y), (x - y).abs().max().item()
+    fused.close()
+    split.close()
+
+
+@pytest.mark.parametrize("cfg", ["c1", "c2"])
+def test_fused_one_call_build_is_bitwise_two_launch(bse, cfg):
+    """bse_build_kernel (cached fused plan) against an explicit two-launch plan."""
+    import torch
+    p = bi.make_problem(cfg)
+    d = bse.upload_problem(p)
+    st = bse.make_problem_struct(d)
+    bse.bse_build_kernel([st], bse.BSE_PREC_BF16X6)
+    torch.cuda.synchronize()
+    one = [d["A"].clone(), d["B"].clone()]
+    split = bse.Plan([st], precision=bse.BSE_PREC_BF16X6, fused=False)
+    two = _build(bse, split, [d])
+    for x, y in zip(one, two):
+        assert torch.equal(x, y), (x - y).abs().max().item()
+    split.close()
+
+
+def test_fused_graph_capture_and_autotune_leaves_outputs(bse, square):
+    import torch
+    probs, refs = square
+    ds, structs = _upload(bse, probs)
+    for d in ds:
+        d["A"].fill_(complex(3.0, 1.0))
+        d["B"].fill_(complex(3.0, 1.0))
+    torch.cuda.synchronize()
+    plan = bse.Plan(structs, precision=bse.BSE_PREC_BF16X6, autotune=True)
+    assert plan.fused and plan.tile_cols in (32, 64)
+    for d in ds:                     # autotuning times the fused launch with outputs off
+        assert bool((d["A"] == complex(3.0, 1.0)).all()) and bool((d["B"] == complex(3.0, 1.0)).all())
+    stream = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        with torch.cuda.graph(g, stream=stream):
+            plan.execute(stream)
+    g.replay()
+    torch.cuda.synchronize()
+    plan.status()
+    _check(bse, probs, refs, ds, 1e-6)
+    plan.close()
