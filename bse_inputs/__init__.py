@@ -281,6 +281,122 @@ def make_problem(cfg: BSEConfig | str, q_index: int = 0, seed: int = 20190411,
     )
 
 
+# ----------------------------------------------------------------------------
+# full-size problems drawn on a device (torch)
+# ----------------------------------------------------------------------------
+def _torch_gen(device, *parts):
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(_key(*parts) % (1 << 62))
+    return g
+
+
+def _hermitian_pair_torch(nk, nb, ng, damp, gen, device):
+    """[nk, nk, nb, nb, ng] complex normal x damp with S3 imposed in place:
+    blocks k < k' drawn, blocks k > k' their conjugate transposes (b <-> b'),
+    diagonal blocks Hermitian in (b, b') with a real diagonal."""
+    import torch
+    x = torch.randn((nk, nk, nb, nb, ng), dtype=torch.complex128, device=device, generator=gen)
+    x *= damp
+    iu = torch.triu_indices(nb, nb, 1, device=device)
+    d = torch.arange(nb, device=device)
+    for k in range(nk):
+        if k > 0:
+            x[k, :k] = x[:k, k].transpose(1, 2).conj()
+        blk = x[k, k]
+        blk[iu[1], iu[0]] = blk[iu[0], iu[1]].conj()
+        blk[d, d] = blk[d, d].real.to(torch.complex128)
+    return x
+
+
+def make_problem_torch(cfg: BSEConfig | str, q_index: int = 0, seed: int = 20190411,
+                       device="cuda") -> Dict:
+    """Draw a full-size problem directly on a torch device, for shapes whose
+    inputs are too large to draw on the host (tens of GB).  Same recipe as
+    make_problem (distributions, damping, W(q) construction, symmetries S1-S4,
+    pair maps, v_bar, rho), but the numbers come from torch's generator, so
+    they differ from make_problem's; a check copies the blocks it needs back
+    to the host.  Array entries are torch tensors on `device`."""
+    import torch
+    if isinstance(cfg, str):
+        cfg = CONFIGS[cfg]
+    n, nk = cfg.grid, cfg.nk
+    nv, nc = cfg.window(q_index)
+    ng = cfg.ng
+    gvec = reciprocal_vectors(ng)
+    qvec = np.array([cfg.q_abs[q_index], 0.0, 0.0])
+    g2 = (gvec ** 2).sum(1)
+    damp = torch.as_tensor(1.0 / (1.0 + cfg.m_decay * g2), device=device)
+
+    ge = _torch_gen(device, seed, "energies", q_index, "torch")
+    lo_v, hi_v = cfg.e_v_range
+    lo_c, hi_c = cfg.e_c_range
+    e_v = lo_v + (hi_v - lo_v) * torch.rand((nk, nv), dtype=torch.float64, device=device, generator=ge)
+    e_c = lo_c + (hi_c - lo_c) * torch.rand((nk, nc), dtype=torch.float64, device=device, generator=ge)
+
+    m_x = torch.randn((nk, nv, nc, ng), dtype=torch.complex128, device=device,
+                      generator=_torch_gen(device, seed, "m_x", q_index, "torch"))
+    m_x *= damp
+    m_vv = _hermitian_pair_torch(nk, nv, ng, damp, _torch_gen(device, seed, "m_vv", q_index, "torch"), device)
+    m_cc = _hermitian_pair_torch(nk, nc, ng, damp, _torch_gen(device, seed, "m_cc", q_index, "torch"), device)
+    n_vc = torch.randn((nk, nk, nv, nc, ng), dtype=torch.complex128, device=device,
+                       generator=_torch_gen(device, seed, "n_vc", q_index, "torch"))
+    n_vc *= damp
+
+    q_minus, q_plus, neg = pair_maps(n)
+    gv = torch.as_tensor(gvec, device=device)
+    dg = torch.cdist(gv, gv)
+    gw = _torch_gen(device, seed, "w", q_index, "torch")
+    w = torch.empty((nk, ng, ng), dtype=torch.complex128, device=device)
+    iu = torch.triu_indices(ng, ng, 1, device=device)
+    d = torch.arange(ng, device=device)
+    for q in range(nk):
+        nq = int(neg[q])
+        if nq < q:
+            w[q] = w[nq].conj()
+            continue
+        z = torch.randn((ng, ng), dtype=torch.complex128, device=device, generator=gw)
+        if nq == q:
+            z = z.real.to(torch.complex128)
+        off = z / (1.0 + cfg.w_decay * dg)
+        wq = torch.zeros((ng, ng), dtype=torch.complex128, device=device)
+        wq[iu[0], iu[1]] = off[iu[0], iu[1]]
+        wq[iu[1], iu[0]] = off[iu[0], iu[1]].conj()
+        wq[d, d] = (cfg.w_diag * (1.0 + wq.abs().sum(1))).to(torch.complex128)
+        w[q] = wq
+    w *= cfg.w_scale
+
+    gq2 = ((gvec + qvec[None, :]) ** 2).sum(1)
+    v_bar = np.zeros(ng)
+    v_bar[1:] = 4.0 * np.pi / gq2[1:]          # G = 0 term removed (Eq. vbar_def)
+    qabs = float(np.linalg.norm(qvec))
+    c_q = 4.0 * np.pi if qabs == 0.0 else 4.0 * np.pi / qabs ** 2
+    omega = np.linspace(cfg.omega_range[0], cfg.omega_range[1], cfg.n_omega)
+    return dict(
+        e_v=e_v, e_c=e_c, m_x=m_x, m_vv=m_vv, m_cc=m_cc, n_vc=n_vc, w=w,
+        q_minus=torch.as_tensor(q_minus, device=device), q_plus=torch.as_tensor(q_plus, device=device),
+        v_bar=torch.as_tensor(v_bar, device=device), gvec=gvec, q_vec=qvec,
+        omega_cell=OMEGA_CELL, nk=nk, nv=nv, nc=nc, ng=ng,
+        c_q=c_q, rho=m_x[..., 0].reshape(-1).clone(), omega=omega, delta=cfg.fwhm_ev / 2.0,
+    )
+
+
+def block_inputs(p: Dict, k: int, kp: int, coupling: bool = True) -> Dict:
+    """The inputs of the (k, k') block of A and B as host numpy arrays (from a
+    problem of numpy arrays or torch tensors): what a per-block check needs."""
+    def h(x):
+        return x.detach().cpu().numpy() if hasattr(x, "detach") else np.asarray(x)
+    qm = int(h(p["q_minus"][k, kp]))
+    out = dict(nk=p["nk"], omega_cell=p["omega_cell"], same_k=(k == kp),
+               e_v_k=h(p["e_v"][k]), e_c_k=h(p["e_c"][k]), m_x_k=h(p["m_x"][k]),
+               m_x_kp=h(p["m_x"][kp]), v_bar=h(p["v_bar"]), m_vv=h(p["m_vv"][k, kp]),
+               m_cc=h(p["m_cc"][k, kp]), w_minus=h(p["w"][qm]))
+    if coupling:
+        qp = int(h(p["q_plus"][k, kp]))
+        out.update(n_vc_kkp=h(p["n_vc"][k, kp]), n_vc_kpk=h(p["n_vc"][kp, k]), w_plus=h(p["w"][qp]))
+    return out
+
+
 def scaled(problem: Dict[str, np.ndarray], **factors) -> Dict[str, np.ndarray]:
     """Copy of a problem with some arrays multiplied by scalars, e.g.
     scaled(p, w=0.0, v_bar=0.0) for the independent-particle limit."""

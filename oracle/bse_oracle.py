@@ -25,7 +25,8 @@ Readings of the paper taken here (each listed in the design notes):
 
 Parity status: build_A_B, reduce_sqrt, solve_full, oscillator_strengths and
 eps_M are pinned by the tests in tests/test_oracle_pins.py (closed forms,
-brute force, sum rules, gauge invariance).
+brute force, sum rules, gauge invariance); block_A_B is pinned to build_A_B
+block by block (tests/test_oracle_blocks.py).
 """
 from __future__ import annotations
 
@@ -114,6 +115,41 @@ def build_A_B(p: Dict, gamma_x: float = 1.0, gamma_c: float = 1.0,
         B = 2.0 * gamma_x * V - gamma_c * Wra
     else:
         B = np.zeros_like(A)
+    return A, B
+
+
+def block_A_B(blk: Dict, gamma_x: float = 1.0, gamma_c: float = 1.0,
+              coupling: bool = True) -> Tuple[np.ndarray, np.ndarray]:
+    """The (k, k') block of A and B, rows (v, c) and columns (v', c'), from the
+    inputs of that block alone (for sampled checks of builds too large to
+    form on the CPU).  Same definitions as build_A_B, term by term:
+      V    = kappa sum_G conj(M_x[k,v,c,G]) vbar_G M_x[k',v',c',G]       (Eq. vrrofM)
+      W^rr = kappa sum_GG' conj(M^vv[k,k',v,v',G]) W[q-]_GG' M^cc[k,k',c,c',G']   (Eq. wrrm)
+      W^ra = kappa sum_GG' conj(N^cv[k,k',c,v',G]) W[q+]_GG' N^vc[k,k',v,c',G']   (Eq. wrabar)
+      A = delta_kk' E^ip + 2 gamma_x V - gamma_c W^rr;  B = 2 gamma_x V - gamma_c W^ra
+    blk holds: nk, omega_cell, same_k, e_v_k [nv], e_c_k [nc], m_x_k and
+    m_x_kp [nv, nc, ng], v_bar [ng], m_vv [nv, nv, ng], m_cc [nc, nc, ng],
+    w_minus [ng, ng] and, with coupling, n_vc_kkp = n_vc[k, k'] and
+    n_vc_kpk = n_vc[k', k] [nv, nc, ng] and w_plus [ng, ng]."""
+    kap = kappa(blk["nk"], blk["omega_cell"])
+    mk, mkp = blk["m_x_k"], blk["m_x_kp"]
+    nv, nc, ng = mk.shape
+    n = nv * nc
+    # V[(v,c),(v',c')]: the G sum as a matrix product over G
+    V = kap * ((np.conj(mk.reshape(n, ng)) * blk["v_bar"][None, :]) @ mkp.reshape(n, ng).T)
+    # W^rr: sum over G' first (W M^cc), then over G, as the equation is written
+    inner = np.einsum("gh,cdh->cdg", blk["w_minus"], blk["m_cc"], optimize=True)
+    Wrr = kap * np.einsum("avg,cdg->acvd", np.conj(blk["m_vv"]), inner, optimize=True)
+    A = 2.0 * gamma_x * V - gamma_c * Wrr.reshape(n, n)
+    if blk["same_k"]:
+        e = np.array([blk["e_c_k"][c] - blk["e_v_k"][v] for v in range(nv) for c in range(nc)])
+        A = A + np.diag(e)
+    if not coupling:
+        return A, np.zeros((n, n), np.complex128)
+    # W^ra: N^cv[k,k',c,v'] is n_vc[k',k,v',c] (pair swapped)
+    inner = np.einsum("gh,vyh->vyg", blk["w_plus"], blk["n_vc_kkp"], optimize=True)
+    Wra = kap * np.einsum("xcg,vyg->vcxy", np.conj(blk["n_vc_kpk"]), inner, optimize=True)
+    B = 2.0 * gamma_x * V - gamma_c * Wra.reshape(n, n)
     return A, B
 
 

@@ -285,15 +285,22 @@ def bse_kernel_launches() -> int:
 
 
 def upload_problem(p: Dict, device="cuda", ld: Optional[int] = None, pin: bool = False) -> Dict:
-    """Copy a bse_inputs problem (numpy) to CUDA tensors and allocate A, B [n, ld]."""
+    """Copy a bse_inputs problem (numpy arrays, or torch tensors already on a
+    device) to contiguous CUDA tensors and allocate A, B [n, ld]."""
     import torch
+
+    def dev(x, npt, tt):
+        if isinstance(x, torch.Tensor):
+            return x.to(device=device, dtype=tt).contiguous()
+        return torch.as_tensor(np.ascontiguousarray(x, npt)).to(device)
+
     out = {}
     for k in ("e_v", "e_c", "v_bar"):
-        out[k] = torch.as_tensor(np.ascontiguousarray(p[k], np.float64)).to(device)
+        out[k] = dev(p[k], np.float64, torch.float64)
     for k in ("m_x", "m_vv", "m_cc", "n_vc", "w"):
-        out[k] = torch.as_tensor(np.ascontiguousarray(p[k], np.complex128)).to(device)
+        out[k] = dev(p[k], np.complex128, torch.complex128)
     for k in ("q_minus", "q_plus"):
-        out[k] = torch.as_tensor(np.ascontiguousarray(p[k], np.int32)).to(device)
+        out[k] = dev(p[k], np.int32, torch.int32)
     for k in ("nk", "nv", "nc", "ng"):
         out[k] = int(p[k])
     out["omega_cell"] = float(p["omega_cell"])

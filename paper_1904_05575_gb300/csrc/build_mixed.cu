@@ -487,22 +487,28 @@ void launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb, const tc::Tile* d
                  const tc::GemmShape& sh, const Epi& epi, int* d_err, cudaStream_t s) {
   if (ntiles == 0) return;
   const size_t smem = tc::gemm_smem_bytes(sh);
-  auto kern = sh.pieces == 3 ? tc::gemm_split_bf16<3, Epi> : tc::gemm_split_bf16<2, Epi>;
+  const bool seg = sh.ksegs > 1;
+  if (seg && (sh.nt > 64 || sh.acc_bufs != 2))
+    throw Error(BSE_ERR_UNSUPPORTED, "K-segmented tiles need two accumulator sets of <= 64 columns");
+  const int which = (sh.pieces == 3 ? 2 : 0) + (seg ? 1 : 0);
+  void (*const kerns[4])(CUtensorMap, CUtensorMap, const tc::Tile*, int, tc::GemmShape, Epi, int*) = {
+      tc::gemm_split_bf16<2, Epi, false>, tc::gemm_split_bf16<2, Epi, true>,
+      tc::gemm_split_bf16<3, Epi, false>, tc::gemm_split_bf16<3, Epi, true>};
+  auto kern = kerns[which];
   // the shared-memory opt-in is set once per kernel (not per launch, so that a
   // launch can be captured in a CUDA graph)
-  static std::once_flag once3, once2;
-  static int max_dyn3 = 0, max_dyn2 = 0;
-  int& max_dyn = sh.pieces == 3 ? max_dyn3 : max_dyn2;
-  std::call_once(sh.pieces == 3 ? once3 : once2, [&] {
+  static std::once_flag once[4];
+  static int max_dyn[4] = {0, 0, 0, 0};
+  std::call_once(once[which], [&] {
     int dev = 0, optin = 0;
     BSE_CUDA(cudaGetDevice(&dev));
     BSE_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     cudaFuncAttributes fa;
     BSE_CUDA(cudaFuncGetAttributes(&fa, kern));
-    max_dyn = optin - (int)fa.sharedSizeBytes;
-    BSE_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn));
+    max_dyn[which] = optin - (int)fa.sharedSizeBytes;
+    BSE_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn[which]));
   });
-  if ((int)smem > max_dyn) throw Error(BSE_ERR_UNSUPPORTED, "tile shape needs too much shared memory");
+  if ((int)smem > max_dyn[which]) throw Error(BSE_ERR_UNSUPPORTED, "tile shape needs too much shared memory");
   const int grid = std::min<int>(ntiles, num_sms());
   kern<<<grid, tc::NUM_THREADS, smem, s>>>(ma, mb, d_tiles, ntiles, sh, epi, d_err);
   BSE_CUDA(cudaGetLastError());
@@ -539,11 +545,22 @@ void launch_direct(const CUtensorMap& ma, const CUtensorMap& mb, const tc::Tile*
   note_launches(1);
 }
 
+// K segments of a tile: one segment up to 12 K steps (192 plane waves), else
+// segments of at most 8 steps, summed in the epilogue (bounds the number of
+// accumulate events any TMEM accumulator sees)
+int ksegs_for(int Kp) {
+  const int kchunks = Kp / tc::BK;
+  return kchunks <= 12 ? 1 : (kchunks + 7) / 8;
+}
+
 tc::GemmShape make_shape(int nt, int Kp, int pieces) {
   tc::GemmShape sh;
   sh.nt = nt;
   sh.kchunks = Kp / tc::BK;
   sh.pieces = pieces;
+  sh.ksegs = ksegs_for(Kp);
+  if (sh.ksegs > 1 && nt > 64)
+    throw Error(BSE_ERR_UNSUPPORTED, "K-segmented tiles need at most 64 output columns");
   sh.acc_bufs = 8 * nt <= 512 ? 2 : 1;
   const int cols = 4 * nt * sh.acc_bufs;
   sh.tmem_cols = cols <= 128 ? 128 : cols <= 256 ? 256 : 512;
@@ -559,6 +576,7 @@ tc::GemmShape make_shape(int nt, int Kp, int pieces) {
 // next), and the pipeline depth reduced to leave room for the pair-side ring.
 tc::GemmShape make_shape_direct(int nt, int Kp, int pieces, int group) {
   tc::GemmShape sh = make_shape(nt, Kp, pieces);
+  if (sh.ksegs != 1) throw Error(BSE_ERR_UNSUPPORTED, "the fused direct term takes whole-K tiles");
   sh.acc_bufs = 2;
   sh.tmem_cols = 8 * nt <= 256 ? 256 : 512;
   sh.group = group;
@@ -579,9 +597,10 @@ int nt_max() {
   return v;
 }
 
-// output columns per tile: the padded N split into equal multiples of 32, each <= nt_max()
-int tile_cols(int n_pad) {
-  const int mx = nt_max();
+// output columns per tile: the padded N split into equal multiples of 32, each
+// <= nt_max() (<= 64 when the K range is segmented)
+int tile_cols(int n_pad, int Kp) {
+  const int mx = ksegs_for(Kp) > 1 ? std::min(64, nt_max()) : nt_max();
   int ntiles = (n_pad + mx - 1) / mx;
   return round_up((n_pad + ntiles - 1) / ntiles, 32);
 }
@@ -816,6 +835,7 @@ void plan_autotune(BatchPlan& pl, cudaStream_t s) {
     if (pl.ng_pad >= 64) cands.push_back(64);
   } else {
     for (int mx : {64, 128}) {
+      if (mx > 64 && ksegs_for(pl.Kp) > 1) continue;
       int nt = round_up((pl.ng_pad + ((pl.ng_pad + mx - 1) / mx) - 1) / ((pl.ng_pad + mx - 1) / mx), 32);
       if (std::find(cands.begin(), cands.end(), nt) == cands.end()) cands.push_back(nt);
     }
@@ -897,7 +917,7 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
   std::vector<ExParams> xp;
   int64_t nmax = 0;
   for (const Problem& pr : pl->probs) nmax = std::max<int64_t>(nmax, pr.n);
-  pl->nt_x = tile_cols(round_up((int)nmax, 32));
+  pl->nt_x = tile_cols(round_up((int)nmax, 32), pl->Kp);
   for (size_t i = 0; i < pl->probs.size(); ++i) {
     const bse_problem& p = pl->probs[i].p;
     const int n = (int)pl->probs[i].n;
@@ -980,7 +1000,8 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
   if (!pl->terms.empty()) {
     if (pl->a_rows > INT32_MAX || pl->w_rows > INT32_MAX)
       throw Error(BSE_ERR_UNSUPPORTED, "batched stage-1 rows exceed 2^31");
-    pl->fused = (flags & BSE_PLAN_UNFUSED) == 0;
+    // (the fused epilogue contracts whole-K tiles: no K segments)
+    pl->fused = (flags & BSE_PLAN_UNFUSED) == 0 && ksegs_for(pl->Kp) == 1;
     for (const BatchPlan::Term& t : pl->terms) pl->fused = pl->fused && fused_fits(t.s2);
     pl->wsplit = DevMem((size_t)pl->planes * pl->w_rows * pl->Kp * 2);
     pl->asplit = DevMem((size_t)pl->planes * pl->a_rows * pl->Kp * 2);
@@ -1039,7 +1060,7 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
     if (autotune)
       plan_autotune(*pl, s);
     else
-      plan_set_tiles(*pl, pl->fused ? (pl->ng_pad % 64 == 0 ? 64 : 32) : tile_cols(pl->ng_pad));
+      plan_set_tiles(*pl, pl->fused ? (pl->ng_pad % 64 == 0 ? 64 : 32) : tile_cols(pl->ng_pad, pl->Kp));
   }
   BSE_CUDA(cudaStreamSynchronize(s));
   return pl.release();

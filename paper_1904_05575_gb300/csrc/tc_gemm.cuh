@@ -13,7 +13,10 @@
 // and all correction products (i + j > 0, 2^-8 smaller) to a separate pair:
 // the tensor core's FP32 accumulation loses low bits at every accumulate
 // event, and this keeps the large accumulator at 2 events per K step instead
-// of 2 * (number of products).  The epilogue adds main + correction.
+// of 2 * (number of products).  The epilogue adds main + correction.  For
+// long K (more than 12 steps) the K range is cut into ksegs segments, each
+// accumulated afresh in the next TMEM set, and the epilogue sums the
+// segments in FP32 registers, so no accumulator sees more than 16 events.
 // Conjugation of an operand is applied when it is split (Im stored negated).
 //
 // One CTA per SM, persistent over a list of 128-row tiles:
@@ -194,6 +197,7 @@ struct GemmShape {    // stages <= 8
   int acc_bufs;    // accumulator sets in TMEM (2: epilogue of one tile overlaps the next)
   uint32_t tmem_cols;
   int group = 1;   // consecutive tiles a CTA takes as one work unit
+  int ksegs = 1;   // K segments per tile (> 1 needs nt <= 64 and acc_bufs == 2)
 };
 
 __host__ __device__ inline uint32_t a_plane_bytes() { return BM * BK * 2; }
@@ -282,9 +286,11 @@ __device__ __forceinline__ void mma_role(const Pipe& pp, uint32_t tmem_base, int
   const uint64_t da0 = smem_desc_sw32(sa0), db0 = smem_desc_sw32(sa0 + pp.a_bytes);
   const uint64_t dstage = pp.sbytes >> 4, dpa = a_plane_bytes() >> 4, dpb = b_plane_bytes(sh.nt) >> 4;
   const int units = num_units(ntiles, sh.group);
+  const int seg_len = (sh.kchunks + sh.ksegs - 1) / sh.ksegs;
   bool ok = true;
   for (int u = blockIdx.x; u < units && ok && !*abort_flag; u += gridDim.x) {
-    for (int t = u * sh.group; t < min(ntiles, (u + 1) * sh.group); ++t, ++local) {
+    for (int t = u * sh.group; t < min(ntiles, (u + 1) * sh.group) && ok; ++t) {
+     for (int k0 = 0; k0 < sh.kchunks; k0 += seg_len, ++local) {
       const int buf = nbuf == 2 ? (local & 1) : 0;
       const int use = nbuf == 2 ? (local >> 1) : local;    // earlier uses of this buffer
       if (use > 0 && !mbar_wait(&pp.tmem_empty[buf], (use - 1) & 1, abort_flag, err)) {
@@ -295,14 +301,14 @@ __device__ __forceinline__ void mma_role(const Pipe& pp, uint32_t tmem_base, int
       const uint32_t base = tmem_base + (uint32_t)buf * 4u * nt;
       const uint32_t m_re = base, m_im = base + nt;               // main
       const uint32_t c_re = base + 2 * nt, c_im = base + 3 * nt;  // corrections
-      for (int kc = 0; kc < sh.kchunks; ++kc) {
+      for (int kc = k0; kc < min(sh.kchunks, k0 + seg_len); ++kc) {
         if (!mbar_wait(&pp.full[stage], phase, abort_flag, err)) {
           ok = false;
           break;
         }
         tc_fence_after();
         const uint64_t da = da0 + (uint64_t)stage * dstage, db = db0 + (uint64_t)stage * dstage;
-        const uint32_t first = kc == 0 ? 0u : 1u;
+        const uint32_t first = kc == k0 ? 0u : 1u;
         // leading products
         mma_bf16(m_re, da, db, id_pos, first);
         mma_bf16(m_re, da + P * dpa, db + P * dpb, id_neg, 1);
@@ -332,6 +338,7 @@ __device__ __forceinline__ void mma_role(const Pipe& pp, uint32_t tmem_base, int
       }
       if (!ok) break;
       mma_commit(&pp.tmem_full[buf]);
+     }
     }
   }
 }
@@ -339,8 +346,10 @@ __device__ __forceinline__ void mma_role(const Pipe& pp, uint32_t tmem_base, int
 // ---------------------------------------------------------------------------
 // The kernel.  Epi provides: __device__ void operator()(const Tile&, int row,
 // int col0, const float* re, const float* im) const  for 32 columns at col0.
+// SEG: tiles accumulate K in sh.ksegs segments (compiled only where used, so
+// the register arrays of the segment sums cost nothing elsewhere).
 // ---------------------------------------------------------------------------
-template <int P, class Epi>
+template <int P, class Epi, bool SEG>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
 gemm_split_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 const Tile* __restrict__ tiles, int ntiles, GemmShape sh, Epi epi, int* err) {
@@ -405,6 +414,53 @@ gemm_split_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         __syncwarp();
         tc_fence_after();
         const Tile tl = tiles[t];
+        if constexpr (SEG) {
+          // K segments: sum (main + correction) of each segment in FP32 registers
+          // (nt <= 64: two chunks of 32 columns), then one store
+          float run_re[64], run_im[64], a[32], b[32];
+#pragma unroll
+          for (int j = 0; j < 64; ++j) run_re[j] = run_im[j] = 0.f;
+          for (int sgm = 0; sgm < sh.ksegs; ++sgm) {
+            if (sgm > 0) {   // the next segment's accumulator set
+              ++local;
+              const int bs = local & 1, us = local >> 1;
+              int oks = 0;
+              if (lane == 0) oks = mbar_wait(&pp.tmem_full[bs], us & 1, &abort_flag, err) ? 1 : 0;
+              oks = __shfl_sync(0xffffffffu, oks, 0);
+              if (!oks) {
+                alive = false;
+                break;
+              }
+              __syncwarp();
+              tc_fence_after();
+            }
+            const int bs = local & 1;
+            const uint32_t lb =
+                tmem_base + (uint32_t)bs * 4u * (uint32_t)sh.nt + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll
+            for (int ch = 0; ch < 2; ++ch) {
+              if (ch * 32 < sh.nt) {
+                tmem_ld32(lb + (uint32_t)(ch * 32), a);
+                tmem_ld32(lb + (uint32_t)(2 * sh.nt + ch * 32), b);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) run_re[ch * 32 + j] += a[j] + b[j];
+                tmem_ld32(lb + (uint32_t)(sh.nt + ch * 32), a);
+                tmem_ld32(lb + (uint32_t)(3 * sh.nt + ch * 32), b);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) run_im[ch * 32 + j] += a[j] + b[j];
+              }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&pp.tmem_empty[bs]);
+          }
+          if (!alive) break;
+#pragma unroll
+          for (int ch = 0; ch < 2; ++ch)
+            if (ch * 32 < sh.nt && row < tl.m_valid && ch * 32 < tl.n_valid)
+              epi(tl, row, ch * 32, run_re + ch * 32, run_im + ch * 32);
+          continue;
+        }
         float re[32], im[32], cr[32], ci[32];
         const uint32_t lane_base =
             tmem_base + (uint32_t)buf * 4u * (uint32_t)sh.nt + ((uint32_t)(quarter * 32) << 16);

@@ -33,6 +33,23 @@ def peaks(eps_im, frac=0.1):
     return np.array(idx)
 
 
+# long K (NG > 192): the tensor-core tiles accumulate K in segments of <= 8
+# steps summed in the epilogue; NG = 300 -> 3 segments, NG = 500 -> 4
+LONG_K = [(2, 2, 3, 300), (2, 4, 4, 500)]
+
+
+@pytest.mark.parametrize("name", LONG_K, ids=str)
+def test_build_bf16x6_long_k(bse, name):
+    p = problem(name)
+    A_ref, B_ref = O.build_A_B(p)
+    d = gpu_build(bse, p, precision=bse.BSE_PREC_BF16X6)
+    n = p["nk"] * p["nv"] * p["nc"]
+    ea = rel_fro(bse.matrix_to_numpy(d["A"], n), A_ref)
+    eb = rel_fro(bse.matrix_to_numpy(d["B"], n), B_ref)
+    print(f"\nlong K {name}: A {ea:.2e} B {eb:.2e}")
+    assert ea < 1e-6 and eb < 1e-6, (ea, eb)
+
+
 @pytest.mark.parametrize("name", ["c1", "c2"] + EDGE_SHAPES, ids=str)
 def test_build_bf16x6_parity(bse, name):
     p = problem(name)
