@@ -38,12 +38,12 @@ WORKLOAD = ("optical limit Q=0, full (non-TDA) BSE, Nk=64 (4x4x4), Nv=4, Nc=4, N
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 FP64_PEAK_TFLOPS = 1.25     # GB300 FP64 (CUDA-core and tensor) nominal rate
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, or
-# dram__bytes.sum.per_second x duration) of the c2 workload's kernels, from the
-# ncu captures summarised in profiles/; to be re-taken whenever the kernel changes
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# c2 workload's kernels, from the ncu captures summarised in profiles/; None
+# until re-taken after a kernel changes
 TRAFFIC_BYTES = {
-    "mixed_stage2": None,          # k_stage2_pipe: not captured since it replaced k_stage2<16,1>
-    "mixed_stage1_gemm": None,     # one launch over both terms in a plan: not captured yet
+    "mixed_direct_fused": None,
+    "mixed_split": None,
 }
 
 
@@ -61,6 +61,20 @@ def build_flops(nk, nv, nc, ng, coupling=True):
 
 def stage1_flops(nk, nv, nc, ng):
     return 8.0 * nk * nk * ng * ng * min(nv * nv, nc * nc), 8.0 * nk * nk * ng * ng * nv * nc
+
+
+def split_bytes(nk, nv, nc, ng, pieces=3):
+    """Bytes the operand split must move per build: every complex128 element
+    of M_x (twice: the two exchange operands), W (once per direct term) and the
+    stage-1 side rows of both direct terms read once (16 B), and written as
+    2 x pieces BF16 planes over K padded to 16 (the W rows padded to 32)."""
+    kp = -(-ng // 16) * 16
+    ngp = -(-ng // 32) * 32
+    n = nk * nv * nc
+    rows_side = min(nv * nv, nc * nc) + nv * nc
+    read = 16 * ng * (2 * n + 2 * nk * ng + nk * nk * rows_side)
+    write = 4 * pieces * kp * (2 * n + 2 * nk * ngp + nk * nk * rows_side)
+    return read + write
 
 
 def load_peaks():
@@ -177,6 +191,53 @@ def cpu_cores():
         return os.cpu_count() or 1
 
 
+def build_rooflines(bse, prec, phases, steps, shapes, peaks):
+    """Roofline of the dominant build kernel and of the runner-up, from the
+    library's CUDA-event phase timing over the timed region (one launch of
+    each kernel per build for the tensor-core path)."""
+    def per_build(name):
+        cnt, ms = phases.get(name, (0, float("nan")))
+        return ms / steps
+    s1 = sum(sum(stage1_flops(*sh)) for sh in shapes)
+    if prec == bse.BSE_PREC_FP64:
+        name = "fp64_wra_stage1"
+        ra = sum(stage1_flops(*sh)[1] for sh in shapes)
+        achieved = ra / (per_build(name) * 1e-3) / 1e12
+        return ({"kernel": name, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                 "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak)",
+                 "flops_per_launch": ra}, None)
+    products = 6 if prec == bse.BSE_PREC_BF16X6 else 3
+    pieces = 3 if prec == bse.BSE_PREC_BF16X6 else 2
+    peak_t = peaks["bf16_tflops"] / products
+    tensor_src = f"{peaks['source']} bf16 burst / {products} piece products"
+    if "mixed_direct_fused" in phases:
+        # stage-1 GEMM of both direct terms with the pair contraction in its
+        # epilogue: bound by the tensor cores it drives
+        ms = per_build("mixed_direct_fused")
+        achieved = s1 / (ms * 1e-3) / 1e12
+        dominant = {"kernel": "mixed_direct_fused (gemm_split_bf16_direct, tcgen05, 1 launch per build)",
+                    "bound": "tensor", "achieved": achieved, "peak": peak_t, "unit": "TFLOP/s",
+                    "frac": achieved / peak_t, "traffic": TRAFFIC_BYTES.get("mixed_direct_fused"),
+                    "peak_source": tensor_src, "flops_per_launch": s1, "ms_per_launch": ms}
+    else:
+        ms = per_build("mixed_stage1_gemm")
+        achieved = s1 / (ms * 1e-3) / 1e12
+        dominant = {"kernel": "mixed_stage1_gemm (gemm_split_bf16, tcgen05, 1 launch per build)",
+                    "bound": "tensor", "achieved": achieved, "peak": peak_t, "unit": "TFLOP/s",
+                    "frac": achieved / peak_t, "traffic": None, "peak_source": tensor_src,
+                    "flops_per_launch": s1, "ms_per_launch": ms}
+    ms = per_build("mixed_split")
+    nbytes = sum(split_bytes(*sh, pieces=pieces) for sh in shapes)
+    achieved = nbytes / (ms * 1e-3) / 1e9
+    secondary = {"kernel": "mixed_split (k_split, HBM pass, several launches per build)",
+                 "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                 "frac": achieved / peaks["hbm_gbs"], "traffic": TRAFFIC_BYTES.get("mixed_split"),
+                 "peak_source": f"{peaks['source']} HBM copy bandwidth",
+                 "bytes_per_build": nbytes, "ms_per_build": ms}
+    return dominant, secondary
+
+
 def run_reference(args):
     world, rank, _ = dist_setup(args)
     if rank != 0:
@@ -219,6 +280,12 @@ def main():
     ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "bf16x6", "bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--build-only", action="store_true",
+                    help="time the build alone (no reduction / eigensolve / spectrum)")
+    ap.add_argument("--qs", default="0", help="comma-separated Q indices built by one plan")
+    ap.add_argument("--device-inputs", action="store_true",
+                    help="draw the inputs on the GPU (automatic for c3 and c5)")
+    ap.add_argument("--nev", type=int, default=16, help="lowest excitons for time-to-lowest-excitons")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -248,38 +315,53 @@ def main():
         args.precision = "bf16x6" if bse.mixed_available() else "fp64"
     prec = prec_map[args.precision]
 
-    # each rank: its own momentum transfer (Q replica), resident in HBM
-    p = bi.make_problem(args.config, seed=20190411 + rank)
+    # each rank: its own momentum transfers (Q replicas), resident in HBM
+    if args.config == "c4":
+        raise SystemExit("c4 (560 GB of pair elements) needs a k-row slab build, which this "
+                         "benchmark does not run")
+    qs = [int(x) for x in args.qs.split(",")]
+    device_inputs = args.device_inputs or args.config in ("c3", "c5")
+    if device_inputs or len(qs) > 1:
+        args.build_only = True       # spectra of N up to 25,600 take minutes in cuSOLVER
+    if device_inputs:
+        probs = [bi.make_problem_torch(args.config, q_index=q, seed=20190411 + rank) for q in qs]
+    else:
+        probs = [bi.make_problem(args.config, q_index=q, seed=20190411 + rank) for q in qs]
+    p = probs[0]
     nk, nv, nc, ng = p["nk"], p["nv"], p["nc"], p["ng"]
     n = nk * nv * nc
-    flops = build_flops(nk, nv, nc, ng)
-    d = bse.upload_problem(p)
-    st = bse.make_problem_struct(d)
+    shapes = [(pp["nk"], pp["nv"], pp["nc"], pp["ng"]) for pp in probs]
+    flops = sum(build_flops(*sh) for sh in shapes)
+    ds = [bse.upload_problem(pp) for pp in probs]
+    sts = [bse.make_problem_struct(dd) for dd in ds]
+    d, st = ds[0], sts[0]
     dev = "cuda"
-    S = torch.empty((n, n), dtype=torch.complex128, device=dev)
+    nsq = 0 if args.build_only else n
+    S = torch.empty((nsq, nsq), dtype=torch.complex128, device=dev)
     L = torch.empty_like(S)
     E = torch.empty(n, dtype=torch.float64, device=dev)
     osc = torch.empty_like(E)
     om = torch.as_tensor(p["omega"]).to(dev)
     eps = torch.empty(len(p["omega"]), dtype=torch.complex128, device=dev)
-    rho = torch.as_tensor(p["rho"]).to(dev)
+    rho = p["rho"] if torch.is_tensor(p["rho"]) else torch.as_tensor(p["rho"]).to(dev)
     vc = nk * p["omega_cell"]
     stream = torch.cuda.current_stream()
 
     # a plan per precision (validation, grouping, scratch and tensor maps once,
     # outside the timed region); each step's build is the plan's execute
-    plans = {prec: bse.Plan([st], precision=prec, autotune=True)}
+    plans = {prec: bse.Plan(sts, precision=prec, autotune=True)}
 
     def step(precision, ev=None):
         if ev:
             ev[0].record(stream)
         if precision not in plans:
-            plans[precision] = bse.Plan([st], precision=precision)
+            plans[precision] = bse.Plan(sts, precision=precision)
         plans[precision].execute()
         if ev:
             ev[1].record(stream)
-        bse.bse_reduce(n, d["A"], d["B"], S, L)
-        bse.bse_spectrum(n, S, L, rho, p["c_q"], vc, om, p["delta"], E, osc, eps)
+        if not args.build_only:
+            bse.bse_reduce(n, d["A"], d["B"], S, L)
+            bse.bse_spectrum(n, S, L, rho, p["c_q"], vc, om, p["delta"], E, osc, eps)
         if ev:
             ev[2].record(stream)
 
@@ -318,7 +400,7 @@ def main():
     E_this = E.clone()
     A_this = d["A"].clone()
     extra = {}
-    if prec != bse.BSE_PREC_FP64:
+    if prec != bse.BSE_PREC_FP64 and not args.build_only:
         fp_ms = []
         for i in range(3):
             e0 = torch.cuda.Event(enable_timing=True)
@@ -337,54 +419,53 @@ def main():
                  "fp64_build_tflops": flops / (statistics.mean(fp_ms) * 1e-3) / 1e12,
                  "speedup_vs_fp64_build": statistics.mean(fp_ms) / t_build,
                  "A_rel_fro_vs_fp64": dA, "max_dE_meV_vs_fp64": dE}
+        fp64_t2s = []       # plain FP64 GPU path: build + reduction + eigensolve + spectrum
+        for i in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            bse.bse_build_kernel([st], bse.BSE_PREC_FP64)
+            bse.bse_reduce(n, d["A"], d["B"], S, L)
+            bse.bse_spectrum(n, S, L, rho, p["c_q"], vc, om, p["delta"], E, osc, eps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            fp64_t2s.append(e0.elapsed_time(e1))
+        E_fp64 = E.clone()
+        extra["fp64_time_to_spectrum_ms"] = statistics.mean(fp64_t2s)
+        extra["speedup_time_to_spectrum"] = statistics.mean(fp64_t2s) / t_step
+
+        # ---- time to the lowest excitons: mixed build + block Davidson against
+        # the plain FP64 GPU path (build + dense reduction + eigensolve) ----
+        if args.nev > 0:
+            nev = min(args.nev, n)
+            E_dav = torch.empty(nev, dtype=torch.float64, device=dev)
+            dav_ms, iters = [], 0
+            for i in range(4):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                plans[prec].execute()
+                iters = bse.bse_lowest_excitons(n, d["A"], d["B"], nev, E_dav, None,
+                                                tol_ev=1e-5, max_iter=300)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if i > 0:
+                    dav_ms.append(e0.elapsed_time(e1))
+            t_low = statistics.mean(dav_ms)
+            extra["lowest_excitons"] = {
+                "nev": nev, "davidson_iterations": iters, "preconditioner": "diagonal",
+                "time_to_lowest_excitons_ms": t_low,
+                "fp64_dense_ms": statistics.mean(fp64_t2s),
+                "speedup_vs_fp64_dense": statistics.mean(fp64_t2s) / t_low,
+                "max_dE_meV_vs_fp64_dense": (E_dav - E_fp64[:nev]).abs().max().item() * 1e3}
 
     # ---- roofline of the dominant build kernel (phase timing, live) ----
     peaks = load_peaks()
-    s1_rr, s1_ra = stage1_flops(nk, nv, nc, ng)
-    roofline_tensor = None
-    if prec == bse.BSE_PREC_FP64:
-        name = "fp64_wra_stage1"
-        cnt, ms = phases.get(name, (1, float("nan")))
-        achieved = s1_ra / (ms / cnt * 1e-3) / 1e12
-        roofline = {"kernel": name, "bound": "alu", "achieved": achieved,
-                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                    "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak)",
-                    "flops_per_launch": s1_ra}
-    else:
-        # dominant by time: stage 2 of the direct terms (HBM-bound); algorithmic
-        # bytes per launch = X rows read in FP64 + T read in FP32 + A (or B)
-        # read-modify-write in FP64
-        # a plan's execute: one stage-2 launch per direct term, one stage-1 GEMM
-        # launch covering both terms; per-step algorithmic totals over per-step
-        # phase time give the same ratio as per launch
-        n_pair = nk * nk
-        rows_x, rows_t = (nv * nv, nc * nc) if nc * nc <= nv * nv else (nc * nc, nv * nv)
-        bytes_rr = n_pair * ng * (16 * rows_x + 8 * rows_t) + 32 * n * n
-        bytes_ra = n_pair * ng * (16 + 8) * nv * nc + 32 * n * n
-        _, ms = phases.get("mixed_stage2", (1, float("nan")))
-        ms_step = ms / args.steps
-        achieved = (bytes_rr + bytes_ra) / (ms_step * 1e-3) / 1e9
-        roofline = {"kernel": "mixed_stage2 (k_stage2_pipe, 2 launches per build)", "bound": "hbm",
-                    "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": achieved / peaks["hbm_gbs"],
-                    "traffic": TRAFFIC_BYTES.get("mixed_stage2"),
-                    "peak_source": f"{peaks['source']} HBM copy bandwidth",
-                    "bytes_per_launch": (bytes_rr + bytes_ra) / 2}
-        _, ms = phases.get("mixed_stage1_gemm", (1, float("nan")))
-        products = 6 if prec == bse.BSE_PREC_BF16X6 else 3
-        peak = peaks["bf16_tflops"] / products
-        achieved_t = (s1_rr + s1_ra) / (ms / args.steps * 1e-3) / 1e12
-        roofline_tensor = {"kernel": "mixed_stage1_gemm (gemm_split_bf16, tcgen05, 1 launch per build)",
-                           "bound": "tensor", "achieved": achieved_t, "peak": peak,
-                           "unit": "TFLOP/s", "frac": achieved_t / peak,
-                           "traffic": TRAFFIC_BYTES.get("mixed_stage1_gemm"),
-                           "peak_source": f"{peaks['source']} bf16 burst / {products} piece products",
-                           "flops_per_launch": s1_rr + s1_ra}
+    roofline, roofline_secondary = build_rooflines(bse, prec, phases, args.steps, shapes, peaks)
 
     # ---- end to end through the public API with host buffers ----
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not args.build_only:
         host = {k: d[k].cpu().pin_memory() for k in
                 ("e_v", "e_c", "m_x", "m_vv", "m_cc", "n_vc", "w", "q_minus", "q_plus", "v_bar")}
         h2d = sum(t.numel() * t.element_size() for t in host.values())
@@ -415,12 +496,34 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import bse_oracle as O
-        tb, _ = oracle_step(p, O)
-        cpu = {"value": flops / tb / 1e12, "unit": "TFLOP/s", "cores": cpu_cores(),
-               "kind": "oracle", "sample": "one full build of the same workload (numpy FP64)",
-               "build_s": tb}
+        if device_inputs:
+            # oracle on seeded (k, k') blocks for about 10 s; algorithmic flops
+            # of a block = the build's over Nk^2
+            rng = np.random.default_rng(11)
+            host = dict(p)
+            for key in ("w", "m_x", "v_bar", "e_v", "e_c", "q_minus", "q_plus"):
+                host[key] = p[key].cpu().numpy()
+            nb, t_cpu = 0, 0.0
+            while t_cpu < 10.0 and nb < 4096:
+                k, kp = (int(x) for x in rng.integers(0, nk, 2))
+                blk = bi.block_inputs(host, k, kp)
+                t0 = time.perf_counter()
+                O.block_A_B(blk)
+                t_cpu += time.perf_counter() - t0
+                nb += 1
+            cpu = {"value": nb * build_flops(*shapes[0]) / nk ** 2 / t_cpu / 1e12,
+                   "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle",
+                   "sample": f"{nb} seeded (k,k') blocks of Q {qs[0]} (block_A_B, numpy FP64)",
+                   "build_s": t_cpu}
+        else:
+            tb, _ = oracle_step(p, O)
+            cpu = {"value": flops / tb / 1e12, "unit": "TFLOP/s", "cores": cpu_cores(),
+                   "kind": "oracle", "sample": "one full build of the same workload (numpy FP64)",
+                   "build_s": tb}
 
     if rank == 0:
+        input_gb = sum(t.numel() * t.element_size() for dd in ds for key, t in dd.items()
+                       if key in ("m_x", "m_vv", "m_cc", "n_vc", "w")) / 1e9
         phase_ms = {k: v[1] / args.steps for k, v in phases.items()}
         line = {
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
@@ -428,14 +531,17 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp64": "f64", "bf16x6": "bf16x6(f32 acc)", "bf16x3": "bf16x3(f32 acc)"}[args.precision],
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": args.precision,
-                       "l2": "inputs larger than L2 (0.61 GB resident per step)",
+            "config": {"workload": WORKLOAD if args.config == "c2" else
+                       f"{args.config}: Q {qs}, windows {[(pp['nv'], pp['nc']) for pp in probs]}, "
+                       f"Nk={nk}, NG={ng}" + (" (inputs drawn on the GPU)" if device_inputs else ""),
+                       "precision": args.precision, "build_only": args.build_only,
+                       "l2": f"inputs larger than L2 ({input_gb:.2f} GB resident per step)",
                        "parallelism": f"Q replicas x{world}"},
             "build_ms": t_build, "time_to_spectrum_ms": t_step,
             "build_api": "bse_plan_execute (plan created once, tile width autotuned: "
                          f"{plans[prec].tile_cols} columns)",
             "phase_ms_per_step": phase_ms,
-            "roofline": roofline, "roofline_tensor": roofline_tensor,
+            "roofline": roofline, "roofline_secondary": roofline_secondary,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches, "peaks": peaks,
         }

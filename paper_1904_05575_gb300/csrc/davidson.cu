@@ -12,8 +12,9 @@
 //   X+Y = V u, X-Y = V w                        Ritz vectors, (X+Y)^H (X-Y) = 1
 //   r+ = P u - E V w, r- = M w - E V u          residuals of the two equations
 // Unconverged residuals are preconditioned (diagonal: r / (A_aa - E), or the
-// trained MLP of mlp.cu), orthogonalised against V (two Gram-Schmidt passes)
-// and appended; the basis restarts from the current Ritz vectors when full.
+// trained MLP of mlp.cu), orthogonalised against V as one block (two
+// Gram-Schmidt passes by GEMM, then Cholesky QR twice) and appended; the
+// basis restarts from the current Ritz vectors when full.
 // Small dense steps (projections, m x m factorisations) are cuBLAS / cuSOLVER
 // calls; the host drives the iteration and reads residual norms each step.
 #include <cublas_v2.h>
@@ -109,6 +110,41 @@ __global__ void k_precond_diag(int n, int k, const double* dp, const double* dm,
   }
 }
 
+// out[j] = max(|r1[:, j]|, |r2[:, j]|) (r2 NULL: |r1[:, j]|), one block per
+// column, FP64 sums of squares reduced in shared memory
+__global__ void __launch_bounds__(256) k_col_norms(int n, const double2* r1, const double2* r2,
+                                                   int64_t ld, double* out) {
+  __shared__ double sa[256], sb[256];
+  const int j = blockIdx.x;
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) {
+    const double2 x = r1[i + (int64_t)j * ld];
+    a += x.x * x.x + x.y * x.y;
+    if (r2) {
+      const double2 y = r2[i + (int64_t)j * ld];
+      b += y.x * y.x + y.y * y.y;
+    }
+  }
+  sa[threadIdx.x] = a;
+  sb[threadIdx.x] = b;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      sa[threadIdx.x] += sa[threadIdx.x + w];
+      sb[threadIdx.x] += sb[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[j] = sqrt(fmax(sa[0], sb[0]));
+}
+
+// copy the listed columns of x (ld n) into consecutive columns of y (ld n)
+__global__ void k_gather_cols(int n, int k, const int* idx, const double2* x, double2* y) {
+  const int j = blockIdx.y;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    y[i + (int64_t)j * n] = x[i + (int64_t)idx[j] * n];
+}
+
 struct Solver {
   int n, nev, mmax;
   const bse_c128 *A, *B;
@@ -121,6 +157,10 @@ struct Solver {
   int lwork = 0;
   int m = 0;          // current basis size
   std::vector<double> D;
+  // block orthogonalisation: Gram matrix and triangular factor (b x b, b <=
+  // 4 nev or mmax), column norms and the indices of kept columns
+  int bmax;
+  DeviceBuffer G, Rt, nrm, idx;
 
   Solver(int n_, int nev_, int mmax_, const bse_c128* A_, const bse_c128* B_, int64_t ld_,
          cudaStream_t s_, LibHandles h_)
@@ -134,10 +174,15 @@ struct Solver {
         R2((size_t)n_ * mmax_ * 16, s_), T((size_t)n_ * 2 * std::max(mmax_, nev_) * 16, s_),
         C((size_t)mmax_ * 16, s_), info(sizeof(int), s_), dE((size_t)mmax_ * 8, s_),
         dF((size_t)std::max(mmax_, 2 * nev_) * 8, s_), dD((size_t)n_ * 8, s_),
-        dDp((size_t)n_ * 8, s_), dDm((size_t)n_ * 8, s_), dS((size_t)n_ * 8, s_) {
+        dDp((size_t)n_ * 8, s_), dDm((size_t)n_ * 8, s_), dS((size_t)n_ * 8, s_),
+        bmax(std::max(mmax_, 4 * nev_)), G((size_t)bmax * bmax * 16, s_),
+        Rt((size_t)bmax * bmax * 16, s_), nrm((size_t)bmax * 8, s_),
+        idx((size_t)bmax * 4, s_) {
     int lw1 = 0, lw2 = 0;
     BSE_CUSOLVER(cusolverDnZpotrf_bufferSize(h.solver, CUBLAS_FILL_MODE_LOWER, mmax,
                                              L.as<cuDoubleComplex>(), mmax, &lw1));
+    // (the Jacobi solver cusolverDnZheevj measured 12x slower than zheevd on
+    // these 64-384 sized projected problems)
     BSE_CUSOLVER(cusolverDnZheevd_bufferSize(h.solver, CUSOLVER_EIG_MODE_VECTOR,
                                              CUBLAS_FILL_MODE_LOWER, mmax,
                                              S.as<cuDoubleComplex>(), mmax, dE.as<double>(),
@@ -170,29 +215,97 @@ struct Solver {
     note_launches(1);
   }
 
-  // orthonormalise vector x (device, length n) against V[:, :m] and append it.
-  // Returns false if it is (numerically) inside the span already.
-  bool append(cuDoubleComplex* x) {
+  // Orthonormalise the b columns of X (device, n x b, leading dimension n;
+  // overwritten) against V[:, :m] and among themselves, in column order, and
+  // append the survivors to V (at most mmax - m): two classical Gram-Schmidt passes against V (GEMMs), then a Cholesky QR
+  // of the block whose in-order factorisation drops a column when what
+  // remains of it is below 1e-6 of its norm before the projections, then a
+  // second projection and Cholesky QR pass (CholQR2) for orthogonality to
+  // working precision.  Returns the number appended.
+  int append_block(cuDoubleComplex* X, int b) {
+    if (b <= 0 || m >= mmax) return 0;
     const cuDoubleComplex one = make_cuDoubleComplex(1, 0), zero = make_cuDoubleComplex(0, 0),
                           mone = make_cuDoubleComplex(-1, 0);
-    double n0 = 0.0;
-    BSE_CUBLAS(cublasDznrm2(h.blas, n, x, 1, &n0));
-    if (!(n0 > 0.0)) return false;
-    cuDoubleComplex* c = C.as<cuDoubleComplex>();   // projection coefficients, length m
-    for (int pass = 0; pass < 2 && m > 0; ++pass) {
-      BSE_CUBLAS(cublasZgemv(h.blas, CUBLAS_OP_C, n, m, &one, V.as<cuDoubleComplex>(), n, x, 1,
-                             &zero, c, 1));
-      BSE_CUBLAS(cublasZgemv(h.blas, CUBLAS_OP_N, n, m, &mone, V.as<cuDoubleComplex>(), n, c, 1,
-                             &one, x, 1));
-    }
-    double n1 = 0.0;
-    BSE_CUBLAS(cublasDznrm2(h.blas, n, x, 1, &n1));
-    if (!(n1 > 1e-8 * n0) || m >= mmax) return false;
-    const double inv = 1.0 / n1;
-    BSE_CUBLAS(cublasZdscal(h.blas, n, &inv, x, 1));
-    BSE_CUBLAS(cublasZcopy(h.blas, n, x, 1, col(V, m, n), 1));
-    ++m;
-    return true;
+    std::vector<double> n0(b);
+    k_col_norms<<<b, 256, 0, s>>>(n, reinterpret_cast<const double2*>(X), nullptr, n,
+                                  nrm.as<double>());
+    BSE_CUDA(cudaGetLastError());
+    note_launches(1);
+    BSE_CUDA(cudaMemcpyAsync(n0.data(), nrm.ptr, (size_t)b * 8, cudaMemcpyDeviceToHost, s));
+    auto project = [&](cuDoubleComplex* Y, int k) {
+      if (m == 0) return;
+      BSE_CUBLAS(cublasZgemm(h.blas, CUBLAS_OP_C, CUBLAS_OP_N, m, k, n, &one,
+                             V.as<cuDoubleComplex>(), n, Y, n, &zero, G.as<cuDoubleComplex>(), m));
+      BSE_CUBLAS(cublasZgemm(h.blas, CUBLAS_OP_N, CUBLAS_OP_N, n, k, m, &mone,
+                             V.as<cuDoubleComplex>(), n, G.as<cuDoubleComplex>(), m, &one, Y, n));
+    };
+    // Gram matrix of k columns to the host (column-major k x k)
+    auto gram = [&](const cuDoubleComplex* Y, int k, std::vector<cuDoubleComplex>& g) {
+      BSE_CUBLAS(cublasZgemm(h.blas, CUBLAS_OP_C, CUBLAS_OP_N, k, k, n, &one, Y, n, Y, n, &zero,
+                             G.as<cuDoubleComplex>(), k));
+      g.resize((size_t)k * k);
+      BSE_CUDA(cudaMemcpyAsync(g.data(), G.ptr, (size_t)k * k * 16, cudaMemcpyDeviceToHost, s));
+      BSE_CUDA(cudaStreamSynchronize(s));
+    };
+    // in-order Cholesky g = r^H r over the columns in `cols`, dropping those
+    // whose remaining squared norm is below thr[j]; r is upper triangular over
+    // the kept columns (kk x kk, column-major)
+    auto chol = [&](const std::vector<cuDoubleComplex>& g, int k, const std::vector<double>& thr,
+                    int limit, std::vector<int>& kept, std::vector<cuDoubleComplex>& r) {
+      kept.clear();
+      std::vector<std::vector<cuDoubleComplex>> rows;   // r rows of kept columns, over all k
+      for (int j = 0; j < k && (int)kept.size() < limit; ++j) {
+        double v = cuCreal(g[(size_t)j * k + j]);
+        for (const auto& ri : rows) v -= cuCreal(cuCmul(cuConj(ri[j]), ri[j]));
+        if (!(v > thr[j])) continue;
+        const double rjj = std::sqrt(v);
+        std::vector<cuDoubleComplex> rj(k, zero);
+        rj[j] = make_cuDoubleComplex(rjj, 0.0);
+        for (int l = j + 1; l < k; ++l) {
+          cuDoubleComplex acc = g[(size_t)l * k + j];   // g[j][l]
+          for (const auto& ri : rows) acc = cuCsub(acc, cuCmul(cuConj(ri[j]), ri[l]));
+          rj[l] = make_cuDoubleComplex(cuCreal(acc) / rjj, cuCimag(acc) / rjj);
+        }
+        rows.push_back(std::move(rj));
+        kept.push_back(j);
+      }
+      const int kk = (int)kept.size();
+      r.assign((size_t)kk * kk, zero);
+      for (int a = 0; a < kk; ++a)
+        for (int c = a; c < kk; ++c) r[(size_t)c * kk + a] = rows[a][kept[c]];
+    };
+    // first pass
+    project(X, b);
+    project(X, b);
+    std::vector<cuDoubleComplex> g, r;
+    std::vector<int> kept;
+    gram(X, b, g);
+    std::vector<double> thr(b);
+    for (int j = 0; j < b; ++j) thr[j] = (1e-6 * n0[j]) * (1e-6 * n0[j]);
+    chol(g, b, thr, mmax - m, kept, r);
+    const int kk = (int)kept.size();
+    if (kk == 0) return 0;
+    cuDoubleComplex* Y = col(V, m, n);   // survivors go straight to their place in V
+    BSE_CUDA(cudaMemcpyAsync(idx.ptr, kept.data(), (size_t)kk * 4, cudaMemcpyHostToDevice, s));
+    k_gather_cols<<<dim3((n + 255) / 256, kk), 256, 0, s>>>(
+        n, kk, idx.as<int>(), reinterpret_cast<const double2*>(X), reinterpret_cast<double2*>(Y));
+    BSE_CUDA(cudaGetLastError());
+    note_launches(1);
+    BSE_CUDA(cudaMemcpyAsync(Rt.ptr, r.data(), (size_t)kk * kk * 16, cudaMemcpyHostToDevice, s));
+    BSE_CUBLAS(cublasZtrsm(h.blas, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N,
+                           CUBLAS_DIAG_NON_UNIT, n, kk, &one, Rt.as<cuDoubleComplex>(), kk, Y, n));
+    // second pass: project again, orthonormalise again (nothing expected to drop)
+    project(Y, kk);
+    gram(Y, kk, g);
+    std::vector<double> thr2(kk, 1e-20);
+    chol(g, kk, thr2, kk, kept, r);
+    if ((int)kept.size() != kk)
+      throw Error(BSE_ERR_NO_CONV, "Davidson basis lost orthogonality in the second pass");
+    BSE_CUDA(cudaMemcpyAsync(Rt.ptr, r.data(), (size_t)kk * kk * 16, cudaMemcpyHostToDevice, s));
+    BSE_CUBLAS(cublasZtrsm(h.blas, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N,
+                           CUBLAS_DIAG_NON_UNIT, n, kk, &one, Rt.as<cuDoubleComplex>(), kk, Y, n));
+    m += kk;
+    return kk;
   }
 
   // projected problem on the current basis; fills U (u, m x nev), W (w, m x nev), E (host)
@@ -286,12 +399,11 @@ struct Solver {
                            R2.as<cuDoubleComplex>(), n));
     BSE_CUBLAS(cublasZaxpy(h.blas, n * k, &mone, col(T, k, n), 1, R2.as<cuDoubleComplex>(), 1));
     res.assign(k, 0.0);
-    for (int j = 0; j < k; ++j) {
-      double a = 0, b = 0;
-      BSE_CUBLAS(cublasDznrm2(h.blas, n, col(R1, j, n), 1, &a));
-      BSE_CUBLAS(cublasDznrm2(h.blas, n, col(R2, j, n), 1, &b));
-      res[j] = std::max(a, b);
-    }
+    k_col_norms<<<k, 256, 0, s>>>(n, R1.as<double2>(), R2.as<double2>(), n, nrm.as<double>());
+    BSE_CUDA(cudaGetLastError());
+    note_launches(1);
+    BSE_CUDA(cudaMemcpyAsync(res.data(), nrm.ptr, (size_t)k * 8, cudaMemcpyDeviceToHost, s));
+    BSE_CUDA(cudaStreamSynchronize(s));
   }
 };
 
@@ -405,8 +517,14 @@ void davidson_fp64(int n, const bse_c128* A, const bse_c128* B, int64_t ld, int 
   bool converged = false;
   for (it = 1; it <= max_iter; ++it) {
     const int kr = std::min(sv.m, 2 * k);   // Ritz pairs kept at a restart
-    sv.rayleigh_ritz(kr, E);
-    sv.residuals(k, E, res);
+    {
+      Phase ph("davidson_rayleigh_ritz", s);
+      sv.rayleigh_ritz(kr, E);
+    }
+    {
+      Phase ph("davidson_residuals", s);
+      sv.residuals(k, E, res);
+    }
     std::vector<int> todo;
     for (int j = 0; j < k; ++j)
       if (!(res[j] < tol)) todo.push_back(j);
@@ -443,6 +561,7 @@ void davidson_fp64(int n, const bse_c128* A, const bse_c128* B, int64_t ld, int 
       note_launches(1);
     }
     // restart from the Ritz vectors when the new block would not fit
+    Phase ph_o("davidson_basis", s);
     if (sv.m + 2 * nt > mmax) {
       const cuDoubleComplex one = make_cuDoubleComplex(1, 0), zero = make_cuDoubleComplex(0, 0);
       // X+Y and X-Y of the kr lowest pairs into R1 (n x 2 kr), then rebuild V
@@ -453,11 +572,11 @@ void davidson_fp64(int n, const bse_c128* A, const bse_c128* B, int64_t ld, int 
                              sv.V.as<cuDoubleComplex>(), n, sv.W.as<cuDoubleComplex>(), mmax,
                              &zero, sv.R1.as<cuDoubleComplex>() + (int64_t)kr * n, n));
       sv.m = 0;
-      for (int j = 0; j < 2 * kr; ++j) sv.append(sv.R1.as<cuDoubleComplex>() + (int64_t)j * n);
+      sv.append_block(sv.R1.as<cuDoubleComplex>(), 2 * kr);
       sv.matvec(0, sv.m);
     }
     const int m0 = sv.m;
-    for (int j = 0; j < 2 * nt; ++j) sv.append(sv.T.as<cuDoubleComplex>() + (int64_t)j * n);
+    sv.append_block(sv.T.as<cuDoubleComplex>(), 2 * nt);
     if (sv.m == m0) break;   // no new direction: stagnated
     sv.matvec(m0, sv.m);
   }
