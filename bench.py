@@ -191,14 +191,21 @@ def cpu_cores():
         return os.cpu_count() or 1
 
 
+def term_rows(nv, nc):
+    """(rows_t, rows_x) of the W^rr and W^ra terms: stage 1 runs on the pair side
+    with fewer rows (conduction pairs when nc^2 <= nv^2)."""
+    rr = (nc * nc, nv * nv) if nc * nc <= nv * nv else (nv * nv, nc * nc)
+    return rr, (nv * nc, nv * nc)
+
+
 def build_rooflines(bse, prec, phases, steps, shapes, peaks):
-    """Roofline of the dominant build kernel and of the runner-up, from the
-    library's CUDA-event phase timing over the timed region (one launch of
-    each kernel per build for the tensor-core path)."""
+    """Rooflines of the two longest build kernels (phases), from the
+    library's CUDA-event phase timing over the timed region; each phase is
+    one launch per build except the splits and the CUDA-core stage 2 (one per
+    array / term)."""
     def per_build(name):
         cnt, ms = phases.get(name, (0, float("nan")))
         return ms / steps
-    s1 = sum(sum(stage1_flops(*sh)) for sh in shapes)
     if prec == bse.BSE_PREC_FP64:
         name = "fp64_wra_stage1"
         ra = sum(stage1_flops(*sh)[1] for sh in shapes)
@@ -211,31 +218,44 @@ def build_rooflines(bse, prec, phases, steps, shapes, peaks):
     pieces = 3 if prec == bse.BSE_PREC_BF16X6 else 2
     peak_t = peaks["bf16_tflops"] / products
     tensor_src = f"{peaks['source']} bf16 burst / {products} piece products"
-    if "mixed_direct_fused" in phases:
-        # stage-1 GEMM of both direct terms with the pair contraction in its
-        # epilogue: bound by the tensor cores it drives
-        ms = per_build("mixed_direct_fused")
-        achieved = s1 / (ms * 1e-3) / 1e12
-        dominant = {"kernel": "mixed_direct_fused (gemm_split_bf16_direct, tcgen05, 1 launch per build)",
-                    "bound": "tensor", "achieved": achieved, "peak": peak_t, "unit": "TFLOP/s",
-                    "frac": achieved / peak_t, "traffic": TRAFFIC_BYTES.get("mixed_direct_fused"),
-                    "peak_source": tensor_src, "flops_per_launch": s1, "ms_per_launch": ms}
-    else:
-        ms = per_build("mixed_stage1_gemm")
-        achieved = s1 / (ms * 1e-3) / 1e12
-        dominant = {"kernel": "mixed_stage1_gemm (gemm_split_bf16, tcgen05, 1 launch per build)",
-                    "bound": "tensor", "achieved": achieved, "peak": peak_t, "unit": "TFLOP/s",
-                    "frac": achieved / peak_t, "traffic": None, "peak_source": tensor_src,
-                    "flops_per_launch": s1, "ms_per_launch": ms}
-    ms = per_build("mixed_split")
-    nbytes = sum(split_bytes(*sh, pieces=pieces) for sh in shapes)
-    achieved = nbytes / (ms * 1e-3) / 1e9
-    secondary = {"kernel": "mixed_split (k_split, HBM pass, several launches per build)",
-                 "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                 "frac": achieved / peaks["hbm_gbs"], "traffic": TRAFFIC_BYTES.get("mixed_split"),
-                 "peak_source": f"{peaks['source']} HBM copy bandwidth",
-                 "bytes_per_build": nbytes, "ms_per_build": ms}
-    return dominant, secondary
+    hbm_src = f"{peaks['source']} HBM copy bandwidth"
+    s1 = sum(sum(stage1_flops(*sh)) for sh in shapes)
+    ex = sum(8.0 * (sh[0] * sh[1] * sh[2]) ** 2 * sh[3] for sh in shapes)
+    s2 = sum(2 * 8.0 * sh[3] * (sh[0] * sh[1] * sh[2]) ** 2 for sh in shapes)
+    s2_bytes = 0.0
+    for nk, nv, nc, ng in shapes:
+        n = nk * nv * nc
+        for rt, rx in term_rows(nv, nc):
+            s2_bytes += nk * nk * ng * (16 * rx + 8 * rt) + 32 * n * n
+    kinds = {
+        "mixed_direct_fused": ("gemm_split_bf16_direct: stage-1 GEMM + pair contraction, tcgen05",
+                               "tensor", s1),
+        "mixed_stage1_gemm": ("gemm_split_bf16: stage-1 GEMM, tcgen05", "tensor", s1),
+        "mixed_stage2_tc": ("gemm_split_bf16: stage-2 pair-block GEMM, tcgen05", "tensor", s2),
+        "mixed_exchange": ("gemm_split_bf16: exchange GEMM, tcgen05", "tensor", ex),
+        "mixed_stage2": ("k_stage2_pipe: stage-2 contraction, CUDA cores", "hbm", s2_bytes),
+        "mixed_split": ("k_split: operand split, HBM pass", "hbm",
+                        sum(split_bytes(*sh, pieces=pieces) for sh in shapes)),
+    }
+    found = sorted(((per_build(k), k) for k in kinds if k in phases), reverse=True)
+    out = []
+    for ms, name in found[:2]:
+        what, bound, work = kinds[name]
+        if bound == "tensor":
+            achieved = work / (ms * 1e-3) / 1e12
+            out.append({"kernel": f"{name} ({what})", "bound": "tensor", "achieved": achieved,
+                        "peak": peak_t, "unit": "TFLOP/s", "frac": achieved / peak_t,
+                        "traffic": TRAFFIC_BYTES.get(name), "peak_source": tensor_src,
+                        "flops_per_build": work, "ms_per_build": ms})
+        else:
+            achieved = work / (ms * 1e-3) / 1e9
+            out.append({"kernel": f"{name} ({what})", "bound": "hbm", "achieved": achieved,
+                        "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                        "traffic": TRAFFIC_BYTES.get(name), "peak_source": hbm_src,
+                        "bytes_per_build": work, "ms_per_build": ms})
+    while len(out) < 2:
+        out.append(None)
+    return out[0], out[1]
 
 
 def run_reference(args):

@@ -138,8 +138,14 @@ int bse_build_kernel(const bse_problem* probs, int32_t nprob, int32_t precision,
  * memory.  BSE_PLAN_UNFUSED keeps the two-launch form (T written to plan
  * scratch, then contracted); both give the same bits.  Autotuning the fused
  * form times it with its outputs switched off: A and B are not written at
- * create time. */
-enum { BSE_PLAN_AUTOTUNE = 1, BSE_PLAN_UNFUSED = 2 };
+ * create time.
+ *
+ * Where both pair sides of a direct term have at least 64 rows (e.g. 20
+ * valence x 20 conduction bands), its second contraction (over G') also runs
+ * on the tensor cores: stage 1 writes T as split BF16 planes and one
+ * persistent launch multiplies each pair block; BSE_PLAN_CUDA_CORE_STAGE2
+ * keeps the FP32 CUDA-core contraction instead. */
+enum { BSE_PLAN_AUTOTUNE = 1, BSE_PLAN_UNFUSED = 2, BSE_PLAN_CUDA_CORE_STAGE2 = 4 };
 int bse_plan_create(const bse_problem* probs, int32_t nprob, int32_t precision, int32_t flags,
                     void** plan, void* cuda_stream);
 int bse_plan_execute(void* plan, void* cuda_stream);

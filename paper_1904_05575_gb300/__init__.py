@@ -20,6 +20,7 @@ BSE_ERR_NOT_PD, BSE_ERR_NO_CONV, BSE_ERR_TIMEOUT, BSE_ERR_UNSUPPORTED = -4, -5, 
 BSE_PREC_FP64, BSE_PREC_BF16X6, BSE_PREC_BF16X3 = 0, 2, 3
 BSE_PLAN_AUTOTUNE = 1
 BSE_PLAN_UNFUSED = 2
+BSE_PLAN_CUDA_CORE_STAGE2 = 4
 HARTREE_EV = 27.211386245988
 
 STATUS_NAMES = {0: "BSE_OK", -1: "BSE_ERR_ARG", -2: "BSE_ERR_CUDA", -3: "BSE_ERR_NOMEM",
@@ -428,12 +429,14 @@ class Plan:
     problem structs (and the tensors behind them) must outlive the plan."""
 
     def __init__(self, problems: Sequence[bse_problem], precision: int = BSE_PREC_BF16X6,
-                 autotune: bool = False, fused: bool = True, stream=None):
+                 autotune: bool = False, fused: bool = True, tc_stage2: bool = True,
+                 stream=None):
         lib = load()
         self._problems = list(problems)
         arr = (bse_problem * len(self._problems))(*self._problems)
         h = ctypes.c_void_p()
-        flags = (BSE_PLAN_AUTOTUNE if autotune else 0) | (0 if fused else BSE_PLAN_UNFUSED)
+        flags = ((BSE_PLAN_AUTOTUNE if autotune else 0) | (0 if fused else BSE_PLAN_UNFUSED)
+                 | (0 if tc_stage2 else BSE_PLAN_CUDA_CORE_STAGE2))
         _check(lib.bse_plan_create(arr, len(self._problems), int(precision), flags,
                                    ctypes.byref(h), _stream(stream)))
         self.handle = h

@@ -195,7 +195,8 @@ extern "C" int bse_plan_create(const bse_problem* probs, int32_t nprob, int32_t 
     BSE_CHECK_ARG(precision == BSE_PREC_FP64 || precision == BSE_PREC_BF16X6 ||
                       precision == BSE_PREC_BF16X3,
                   "unknown precision " + std::to_string(precision));
-    BSE_CHECK_ARG((flags & ~(BSE_PLAN_AUTOTUNE | BSE_PLAN_UNFUSED)) == 0, "unknown plan flags");
+    BSE_CHECK_ARG((flags & ~(BSE_PLAN_AUTOTUNE | BSE_PLAN_UNFUSED | BSE_PLAN_CUDA_CORE_STAGE2)) == 0,
+                  "unknown plan flags");
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     keep_pool_memory();
     std::vector<Problem> prs;

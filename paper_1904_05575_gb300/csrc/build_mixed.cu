@@ -168,15 +168,118 @@ struct ExchangeEpi {   // V[alpha][alpha'] -> A, B (column-major FP64)
   }
 };
 
-struct TEpi {          // T[G][row] (FP32 complex), G-major so a warp's stores coalesce
-  float2* T;
-  int64_t t_ld;        // rows in T
+// Stage-1 output per direct term (Tile::prob = term): FP32 T[G][row] for the
+// CUDA-core stage 2, or, for a term whose stage 2 runs on the tensor cores,
+// T split at once into BF16 planes [2P][plane_rows][Kp] (K = G', row-major,
+// the operand layout of the GEMM), conjugated when opT conjugates.
+struct TOut {
+  float2* T;                  // FP32 path (NULL: planes)
+  int64_t t_ld;
+  __nv_bfloat16* planes;      // split path
+  int64_t plane_rows;
+  int Kp, pieces, conj;
+};
+
+struct TEpiMulti {
+  const TOut* outs;
   __device__ __forceinline__ void operator()(const tc::Tile& t, int row, int c0, const float* re,
                                              const float* im) const {
+    const TOut o = outs[t.prob];
     const int64_t r = t.out_row0 + row;
+    if (o.T) {
 #pragma unroll
-    for (int j = 0; j < 32; ++j)
-      if (c0 + j < t.n_valid) T[(int64_t)(t.n0 + c0 + j) * t_ld + r] = make_float2(re[j], im[j]);
+      for (int j = 0; j < 32; ++j)
+        if (c0 + j < t.n_valid) o.T[(int64_t)(t.n0 + c0 + j) * o.t_ld + r] = make_float2(re[j], im[j]);
+      return;
+    }
+    // 8 columns per 16-byte store and plane; a group starting at or past the
+    // padded K is not written (columns past NG hold zeros from set-up)
+    const int64_t plane = o.plane_rows * o.Kp;
+    const uint32_t flip = o.conj ? 0x80000000u : 0u;
+#pragma unroll
+    for (int g8 = 0; g8 < 4; ++g8) {
+      const int col = t.n0 + c0 + 8 * g8;
+      if (col >= o.Kp) continue;
+      uint32_t hr[3][8], hi[3][8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int j = 8 * g8 + e;
+        const bool ok = c0 + j < t.n_valid;
+        const uint32_t ur = ok ? __float_as_uint(re[j]) : 0u;
+        const uint32_t ui = ok ? (__float_as_uint(im[j]) ^ flip) : 0u;
+        uint32_t a3[3], b3[3];
+        if (o.pieces == 3) {
+          split_f32_bf16<3>(ur, a3);
+          split_f32_bf16<3>(ui, b3);
+        } else {
+          split_f32_bf16<2>(ur, a3);
+          split_f32_bf16<2>(ui, b3);
+          a3[2] = b3[2] = 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          hr[q][e] = a3[q];
+          hi[q][e] = b3[q];
+        }
+      }
+      const int64_t off = r * o.Kp + col;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        if (q < o.pieces) {
+          uint4 vr, vi;
+          vr.x = hr[q][0] | (hr[q][1] << 16); vr.y = hr[q][2] | (hr[q][3] << 16);
+          vr.z = hr[q][4] | (hr[q][5] << 16); vr.w = hr[q][6] | (hr[q][7] << 16);
+          vi.x = hi[q][0] | (hi[q][1] << 16); vi.y = hi[q][2] | (hi[q][3] << 16);
+          vi.z = hi[q][4] | (hi[q][5] << 16); vi.w = hi[q][6] | (hi[q][7] << 16);
+          *reinterpret_cast<uint4*>(o.planes + (int64_t)q * plane + off) = vr;
+          *reinterpret_cast<uint4*>(o.planes + (int64_t)(o.pieces + q) * plane + off) = vi;
+        }
+      }
+    }
+  }
+};
+
+// Stage 2 on the tensor cores (large pair blocks): tile rows are one pair's
+// rx (Tile::out_row0 = pair * rows_x + first rx), columns its rt; the
+// epilogue subtracts gamma_c kappa P (formed in FP32, widened exactly) from
+// A (W^rr) or B (W^ra) in FP64, one owner per element.
+struct S2TcParams {
+  double2* out;
+  int64_t ld;
+  int rows_x, nk, nv, nc, mode;
+  float scale;
+};
+
+struct S2TcEpi {
+  const S2TcParams* params;
+  __device__ __forceinline__ void operator()(const tc::Tile& t, int row, int c0, const float* re,
+                                             const float* im) const {
+    const S2TcParams q = params[t.prob];
+    const int rxg = t.out_row0 + row;
+    const int pair = rxg / q.rows_x, rx = rxg - pair * q.rows_x;
+    const int k = pair / q.nk, kp = pair - k * q.nk;
+    const int nv = q.nv, nc = q.nc;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      if (c0 + j < t.n_valid) {
+        const int rt = t.n0 + c0 + j;
+        int vi, ci, vp, cp;
+        if (q.mode == 0) {          // rx = (v, v'), rt = (c, c')
+          vi = rx / nv; vp = rx % nv; ci = rt / nc; cp = rt % nc;
+        } else if (q.mode == 1) {   // rx = (c, c'), rt = (v, v')
+          ci = rx / nc; cp = rx % nc; vi = rt / nv; vp = rt % nv;
+        } else {                    // rx = (v', c), rt = (v, c')
+          vp = rx / nc; ci = rx % nc; vi = rt / nc; cp = rt % nc;
+        }
+        const int64_t al = ((int64_t)k * nv + vi) * nc + ci;
+        const int64_t ap = ((int64_t)kp * nv + vp) * nc + cp;
+        double2* dst = q.out + al + ap * q.ld;
+        double2 o = *dst;
+        o.x -= f32_to_f64_bits(q.scale * re[j]);
+        o.y -= f32_to_f64_bits(q.scale * im[j]);
+        *dst = o;
+      }
+    }
   }
 };
 
@@ -545,20 +648,21 @@ void launch_direct(const CUtensorMap& ma, const CUtensorMap& mb, const tc::Tile*
   note_launches(1);
 }
 
-// K segments of a tile: one segment up to 12 K steps (192 plane waves), else
-// segments of at most 8 steps, summed in the epilogue (bounds the number of
-// accumulate events any TMEM accumulator sees)
-int ksegs_for(int Kp) {
+// K segments of a tile: one segment up to `whole` K steps, else segments of at
+// most `seg` steps, summed in the epilogue (bounds the number of accumulate
+// events any TMEM accumulator sees).  Default: whole up to 12 steps (192 plane
+// waves), segments of 8.
+int ksegs_for(int Kp, int seg = 8, int whole = 12) {
   const int kchunks = Kp / tc::BK;
-  return kchunks <= 12 ? 1 : (kchunks + 7) / 8;
+  return kchunks <= whole ? 1 : (kchunks + seg - 1) / seg;
 }
 
-tc::GemmShape make_shape(int nt, int Kp, int pieces) {
+tc::GemmShape make_shape(int nt, int Kp, int pieces, int seg = 8, int whole = 12) {
   tc::GemmShape sh;
   sh.nt = nt;
   sh.kchunks = Kp / tc::BK;
   sh.pieces = pieces;
-  sh.ksegs = ksegs_for(Kp);
+  sh.ksegs = ksegs_for(Kp, seg, whole);
   if (sh.ksegs > 1 && nt > 64)
     throw Error(BSE_ERR_UNSUPPORTED, "K-segmented tiles need at most 64 output columns");
   sh.acc_bufs = 8 * nt <= 512 ? 2 : 1;
@@ -599,8 +703,8 @@ int nt_max() {
 
 // output columns per tile: the padded N split into equal multiples of 32, each
 // <= nt_max() (<= 64 when the K range is segmented)
-int tile_cols(int n_pad, int Kp) {
-  const int mx = ksegs_for(Kp) > 1 ? std::min(64, nt_max()) : nt_max();
+int tile_cols(int n_pad, int Kp, int seg = 8, int whole = 12) {
+  const int mx = ksegs_for(Kp, seg, whole) > 1 ? std::min(64, nt_max()) : nt_max();
   int ntiles = (n_pad + mx - 1) / mx;
   return round_up((n_pad + ntiles - 1) / ntiles, 32);
 }
@@ -711,11 +815,21 @@ struct BatchPlan {
     DevMem perm, slot;
     Stage2Args s2{};
     std::vector<int32_t> qh;
+    // stage 2 on the tensor cores (large pair blocks)
+    bool tc2 = false;
+    int64_t x2_row0 = 0;     // first row of this term's pair side in the x2 planes
+    DevMem x2perm;           // pair -> pair whose side rows are read (identity, or (k', k))
   };
   std::vector<Term> terms;
   int64_t a_rows = 0, w_rows = 0;
   DevMem wsplit, asplit, tbuf, stiles;
   int n_stiles = 0;
+  // stage 2 on the tensor cores for terms with large pair blocks
+  int64_t x2_rows = 0;
+  DevMem x2split, tplanes, touts, s2tiles, s2params;
+  int n_s2tiles = 0, nt2 = 0;
+  tc::GemmShape sh_2{};
+  CUtensorMap ma_2{}, mb_2{};
   // fused direct term (stage 1 + stage 2 in one launch)
   bool fused = false;
   std::vector<tc::S2Term> s2host;
@@ -726,13 +840,13 @@ struct BatchPlan {
 namespace {
 
 // Stage-1 tiles, 128-row tile by 128-row tile with all its column tiles
-// consecutive; Tile::prob is the problem (two-kernel path) or the term
-// (fused path, whose epilogue reads the term's pair side and output).
+// consecutive; Tile::prob is the direct term (whose output the epilogue
+// writes: FP32 T, T split planes, or the fused contraction).
 std::vector<tc::Tile> stage1_tiles(const BatchPlan& pl, int nt) {
   std::vector<tc::Tile> tiles;
   for (size_t ti = 0; ti < pl.terms.size(); ++ti) {
     const BatchPlan::Term& t = pl.terms[ti];
-    const int id = pl.fused ? (int)ti : t.prob;
+    const int id = (int)ti;
     const int nq = pl.probs[t.prob].p.nq_w;
     std::vector<int> perm, gstart;
     group_pairs(t.qh, nq, perm, gstart);
@@ -775,6 +889,12 @@ void plan_splits(BatchPlan& pl, cudaStream_t s) {
                  t.rows_side, 0, pl.ng, pl.Kp, npair * t.rows_side, pl.pieces, 0, nullptr,
                  pl.asplit.as<__nv_bfloat16>(), pl.a_rows, t.a_row0};
     launch_split(sa, s);
+    if (t.tc2) {   // the other pair side, in pair order, conjugated as opX
+      SplitArgs sx{t.s2.x, SPLIT_PAIRS, t.x2perm.as<int>(), t.s2.rows_x, 0, pl.ng, pl.Kp,
+                   npair * t.s2.rows_x, pl.pieces, t.s2.conj_x, nullptr,
+                   pl.x2split.as<__nv_bfloat16>(), pl.x2_rows, t.x2_row0};
+      launch_split(sx, s);
+    }
   }
 }
 
@@ -799,12 +919,22 @@ void plan_execute_mixed(BatchPlan& pl, cudaStream_t s) {
   {
     Phase ph("mixed_stage1_gemm", s);
     launch_gemm(pl.ma_s, pl.mb_s, pl.stiles.as<tc::Tile>(), pl.n_stiles, pl.sh_g,
-                TEpi{pl.tbuf.as<float2>(), pl.a_rows}, pl.err.as<int>(), s);
+                TEpiMulti{pl.touts.as<TOut>()}, pl.err.as<int>(), s);
   }
-  Phase ph("mixed_stage2", s);
-  for (BatchPlan::Term& t : pl.terms) {
-    const bse_problem& p = pl.probs[t.prob].p;
-    launch_stage2(t.s2, p.nk * p.nk, s);
+  bool any_cuda_core = false;
+  for (const BatchPlan::Term& t : pl.terms) any_cuda_core = any_cuda_core || !t.tc2;
+  if (any_cuda_core) {
+    Phase ph("mixed_stage2", s);
+    for (BatchPlan::Term& t : pl.terms) {
+      if (t.tc2) continue;
+      const bse_problem& p = pl.probs[t.prob].p;
+      launch_stage2(t.s2, p.nk * p.nk, s);
+    }
+  }
+  if (pl.n_s2tiles) {
+    Phase ph("mixed_stage2_tc", s);
+    launch_gemm(pl.ma_2, pl.mb_2, pl.s2tiles.as<tc::Tile>(), pl.n_s2tiles, pl.sh_2,
+                S2TcEpi{pl.s2params.as<S2TcParams>()}, pl.err.as<int>(), s);
   }
 }
 
@@ -863,7 +993,7 @@ void plan_autotune(BatchPlan& pl, cudaStream_t s) {
                       timing_terms.as<tc::S2Term>(), pl.err.as<int>(), s);
       else
         launch_gemm(pl.ma_s, pl.mb_s, pl.stiles.as<tc::Tile>(), pl.n_stiles, pl.sh_g,
-                    TEpi{pl.tbuf.as<float2>(), pl.a_rows}, pl.err.as<int>(), s);
+                    TEpiMulti{pl.touts.as<TOut>()}, pl.err.as<int>(), s);
       BSE_CUDA(cudaEventRecord(e1, s));
       BSE_CUDA(cudaEventSynchronize(e1));
       float t = 0.f;
@@ -1049,11 +1179,72 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
       }
       pl->s2terms = upload_mem(pl->s2host);
     } else {
-      pl->tbuf = DevMem((size_t)pl->ng_pad * pl->a_rows * sizeof(float2));
+      // large pair blocks: stage 2 on the tensor cores, T straight into split planes
+      bool any_fp32 = false, any_tc2 = false;
+      for (BatchPlan::Term& t : pl->terms) {
+        t.tc2 = (flags & BSE_PLAN_CUDA_CORE_STAGE2) == 0 && t.s2.rows_x >= 64 && t.s2.rows_t >= 64;
+        any_tc2 = any_tc2 || t.tc2;
+        any_fp32 = any_fp32 || !t.tc2;
+      }
+      if (any_fp32) pl->tbuf = DevMem((size_t)pl->ng_pad * pl->a_rows * sizeof(float2));
+      std::vector<TOut> outs;
       for (BatchPlan::Term& t : pl->terms) {
         t.s2.T = pl->tbuf.as<float2>();
         t.s2.t_ld = pl->a_rows;
+        outs.push_back(TOut{t.tc2 ? nullptr : pl->tbuf.as<float2>(), pl->a_rows, nullptr,
+                            pl->a_rows, pl->Kp, pl->pieces, t.s2.conj_t});
       }
+      if (any_tc2) {
+        // columns of T past NG are never written: zero once
+        const size_t tp_bytes = (size_t)pl->planes * pl->a_rows * pl->Kp * 2;
+        pl->tplanes = DevMem(tp_bytes);
+        BSE_CUDA(cudaMemsetAsync(pl->tplanes.ptr, 0, tp_bytes, s));
+        for (size_t ti = 0; ti < pl->terms.size(); ++ti)
+          if (pl->terms[ti].tc2) outs[ti].planes = pl->tplanes.as<__nv_bfloat16>();
+        // pair sides in pair order, and the tiles of every pair block
+        std::vector<S2TcParams> prm;
+        std::vector<tc::Tile> tiles;
+        pl->nt2 = 0;
+        int max_rt = 0;
+        for (const BatchPlan::Term& t : pl->terms)
+          if (t.tc2) max_rt = std::max(max_rt, t.s2.rows_t);
+        // stage 2 products feed A and B directly: K segments of at most 4 steps
+        pl->nt2 = tile_cols(round_up(max_rt, 32), pl->Kp, 4, 4);
+        for (size_t ti = 0; ti < pl->terms.size(); ++ti) {
+          BatchPlan::Term& t = pl->terms[ti];
+          const Stage2Args& a = t.s2;
+          prm.push_back(S2TcParams{a.out, a.ld, a.rows_x, a.nk, a.nv, a.nc, a.mode, (float)a.scale});
+          if (!t.tc2) continue;
+          const int npair = a.nk * a.nk;
+          std::vector<int> xp(npair);
+          for (int pr = 0; pr < npair; ++pr)
+            xp[pr] = a.x_transpose_pair ? (pr % a.nk) * a.nk + pr / a.nk : pr;
+          t.x2perm = upload_mem(xp);
+          t.x2_row0 = pl->x2_rows;
+          pl->x2_rows += (int64_t)npair * a.rows_x;
+          std::vector<int> slot(npair);
+          BSE_CUDA(cudaMemcpy(slot.data(), a.slot_of_pair, npair * sizeof(int), cudaMemcpyDeviceToHost));
+          for (int pr = 0; pr < npair; ++pr)
+            for (int m0 = 0; m0 < a.rows_x; m0 += tc::BM)
+              for (int n0 = 0; n0 < a.rows_t; n0 += pl->nt2)
+                tiles.push_back({(int)(t.x2_row0 + (int64_t)pr * a.rows_x + m0),
+                                 std::min(tc::BM, a.rows_x - m0),
+                                 (int)(t.a_row0 + (int64_t)slot[pr] * a.rows_t + n0), n0,
+                                 std::min(pl->nt2, a.rows_t - n0), pr * a.rows_x + m0, (int)ti});
+        }
+        if (pl->x2_rows > INT32_MAX)
+          throw Error(BSE_ERR_UNSUPPORTED, "tensor-core stage-2 rows exceed 2^31");
+        pl->x2split = DevMem((size_t)pl->planes * pl->x2_rows * pl->Kp * 2);
+        pl->n_s2tiles = (int)tiles.size();
+        pl->s2tiles = upload_mem(tiles);
+        pl->s2params = upload_mem(prm);
+        pl->sh_2 = make_shape(pl->nt2, pl->Kp, pl->pieces, 4, 4);
+        pl->ma_2 = make_plane_map(pl->x2split.as<__nv_bfloat16>(), pl->Kp, (int)pl->x2_rows,
+                                  pl->planes, tc::BM);
+        pl->mb_2 = make_plane_map(pl->tplanes.as<__nv_bfloat16>(), pl->Kp, (int)pl->a_rows,
+                                  pl->planes, pl->nt2);
+      }
+      pl->touts = upload_mem(outs);
     }
     pl->ma_s = make_plane_map(pl->asplit.as<__nv_bfloat16>(), pl->Kp, (int)pl->a_rows, pl->planes,
                               tc::BM);

@@ -211,3 +211,27 @@ def test_fused_graph_capture_and_autotune_leaves_outputs(bse, square):
     plan.status()
     _check(bse, probs, refs, ds, 1e-6)
     plan.close()
+
+
+# pair blocks of 64 x 64 rows (Nv = Nc = 8): the second contraction runs on the
+# tensor cores; NG = 300 also cuts K into segments
+@pytest.mark.parametrize("ng", [59, 300])
+def test_tensor_core_stage2_matches_oracle_and_cuda_cores(bse, ng):
+    import torch
+    cfg = bi.BSEConfig(f"big-blocks-{ng}", grid=2, nv=8, nc=8, ng=ng, w_scale=0.05)
+    p = bi.make_problem(cfg)
+    A_ref, B_ref = O.build_A_B(p)
+    ds, structs = _upload(bse, [p])
+    tc = bse.Plan(structs, precision=bse.BSE_PREC_BF16X6)
+    cc = bse.Plan(structs, precision=bse.BSE_PREC_BF16X6, tc_stage2=False)
+    a = _build(bse, tc, ds)
+    _check(bse, [p], [(A_ref, B_ref)], ds, 1e-6)
+    b = _build(bse, cc, ds)
+    _check(bse, [p], [(A_ref, B_ref)], ds, 1e-6)
+    n = p["nk"] * p["nv"] * p["nc"]
+    for x, y in zip(a, b):
+        x = bse.matrix_to_numpy(x, n)
+        y = bse.matrix_to_numpy(y, n)
+        assert _rel(x, y) < 1e-6
+    tc.close()
+    cc.close()
