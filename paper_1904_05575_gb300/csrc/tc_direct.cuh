@@ -295,25 +295,38 @@ __device__ __forceinline__ bool direct_unit(const EpiCtx& cx, EpiState& st, int 
   const int nk = tm.nk, nv = tm.nv, nc = tm.nc;
   const int k = pair / nk, kp = pair - k * nk;
   const float sc = tm.scale;
+  // groups of 4 outputs: all loads first, then the stores (the loads of a
+  // group are independent, so their latencies overlap)
 #pragma unroll
-  for (int rx = 0; rx < RX; ++rx) {
-    int vi, ci, vp, cp;
-    if (tm.mode == 0) {
-      vi = rx / nv; vp = rx % nv; ci = rt / nc; cp = rt % nc;
-    } else if (tm.mode == 1) {
-      ci = rx / nc; cp = rx % nc; vi = rt / nv; vp = rt % nv;
-    } else {
-      vp = rx / nc; ci = rx % nc; vi = rt / nc; cp = rt % nc;
+  for (int r0 = 0; r0 < RX; r0 += 4) {
+    double2* dst[4];
+    double2 o[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int rx = r0 + u;
+      int vi, ci, vp, cp;
+      if (tm.mode == 0) {
+        vi = rx / nv; vp = rx % nv; ci = rt / nc; cp = rt % nc;
+      } else if (tm.mode == 1) {
+        ci = rx / nc; cp = rx % nc; vi = rt / nv; vp = rt % nv;
+      } else {
+        vp = rx / nc; ci = rx % nc; vi = rt / nc; cp = rt % nc;
+      }
+      const int64_t al = ((int64_t)k * nv + vi) * nc + ci;
+      const int64_t ap = ((int64_t)kp * nv + vp) * nc + cp;
+      dst[u] = tm.out + al + ap * tm.ld;
     }
-    const int64_t al = ((int64_t)k * nv + vi) * nc + ci;
-    const int64_t ap = ((int64_t)kp * nv + vp) * nc + cp;
-    double2* dst = tm.out + al + ap * tm.ld;
-    const uint64_t hx = HX[rx / 2], lx = LX[rx / 2], hy = HY[rx / 2], ly = LY[rx / 2];
-    const bool odd = rx & 1;
-    double2 o = *dst;
-    o.x -= f32_to_f64_bits(scale_hi_lo(sc, odd ? hi_of(hx) : lo_of(hx), odd ? hi_of(lx) : lo_of(lx)));
-    o.y -= f32_to_f64_bits(scale_hi_lo(sc, odd ? hi_of(hy) : lo_of(hy), odd ? hi_of(ly) : lo_of(ly)));
-    *dst = o;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) o[u] = dst[u][0];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int rx = r0 + u;
+      const uint64_t hx = HX[rx / 2], lx = LX[rx / 2], hy = HY[rx / 2], ly = LY[rx / 2];
+      const bool odd = rx & 1;
+      o[u].x -= f32_to_f64_bits(scale_hi_lo(sc, odd ? hi_of(hx) : lo_of(hx), odd ? hi_of(lx) : lo_of(lx)));
+      o[u].y -= f32_to_f64_bits(scale_hi_lo(sc, odd ? hi_of(hy) : lo_of(hy), odd ? hi_of(ly) : lo_of(ly)));
+      dst[u][0] = o[u];
+    }
   }
   return true;
 }
