@@ -42,8 +42,8 @@ FP64_PEAK_TFLOPS = 1.25     # GB300 FP64 (CUDA-core and tensor) nominal rate
 # c2 workload's kernels, from the ncu captures summarised in profiles/; None
 # until re-taken after a kernel changes
 TRAFFIC_BYTES = {
-    "mixed_direct_fused": None,
-    "mixed_split": None,
+    "mixed_direct_fused": 832.9e6,     # one launch = one build (profiles/mixed_build_c2_kernels.md)
+    "mixed_split": 671e6,              # the 6 launches of one build
 }
 
 
@@ -237,6 +237,8 @@ def build_rooflines(bse, prec, phases, steps, shapes, peaks):
         "mixed_split": ("k_split: operand split, HBM pass", "hbm",
                         sum(split_bytes(*sh, pieces=pieces) for sh in shapes)),
     }
+    # the captured DRAM bytes describe the c2 workload alone
+    traffic = TRAFFIC_BYTES if shapes == [(64, 4, 4, 181)] and products == 6 else {}
     found = sorted(((per_build(k), k) for k in kinds if k in phases), reverse=True)
     out = []
     for ms, name in found[:2]:
@@ -245,13 +247,13 @@ def build_rooflines(bse, prec, phases, steps, shapes, peaks):
             achieved = work / (ms * 1e-3) / 1e12
             out.append({"kernel": f"{name} ({what})", "bound": "tensor", "achieved": achieved,
                         "peak": peak_t, "unit": "TFLOP/s", "frac": achieved / peak_t,
-                        "traffic": TRAFFIC_BYTES.get(name), "peak_source": tensor_src,
+                        "traffic": traffic.get(name), "peak_source": tensor_src,
                         "flops_per_build": work, "ms_per_build": ms})
         else:
             achieved = work / (ms * 1e-3) / 1e9
             out.append({"kernel": f"{name} ({what})", "bound": "hbm", "achieved": achieved,
                         "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                        "traffic": TRAFFIC_BYTES.get(name), "peak_source": hbm_src,
+                        "traffic": traffic.get(name), "peak_source": hbm_src,
                         "bytes_per_build": work, "ms_per_build": ms})
     while len(out) < 2:
         out.append(None)
