@@ -473,13 +473,21 @@ def main():
                 torch.cuda.synchronize()
                 if i > 0:
                     dav_ms.append(e0.elapsed_time(e1))
-            t_low = statistics.mean(dav_ms)
+            t_dav = statistics.mean(dav_ms)
+            # the other route: mixed build + dense reduction / eigensolve (the
+            # timed step, which yields every exciton)
+            best = min(t_dav, t_step)
             extra["lowest_excitons"] = {
-                "nev": nev, "davidson_iterations": iters, "preconditioner": "diagonal",
-                "time_to_lowest_excitons_ms": t_low,
+                "nev": nev, "time_to_lowest_excitons_ms": best,
+                "method": "mixed build + block Davidson" if t_dav <= t_step else
+                          "mixed build + dense reduction and eigensolve",
+                "davidson_ms": t_dav, "davidson_iterations": iters,
+                "davidson_preconditioner": "diagonal", "dense_mixed_ms": t_step,
                 "fp64_dense_ms": statistics.mean(fp64_t2s),
-                "speedup_vs_fp64_dense": statistics.mean(fp64_t2s) / t_low,
-                "max_dE_meV_vs_fp64_dense": (E_dav - E_fp64[:nev]).abs().max().item() * 1e3}
+                "speedup_vs_fp64_dense": statistics.mean(fp64_t2s) / best,
+                "max_dE_meV_davidson_vs_fp64_dense":
+                    (E_dav - E_fp64[:nev]).abs().max().item() * 1e3,
+                "max_dE_meV_dense_mixed_vs_fp64_dense": dE}
 
     # ---- roofline of the dominant build kernel (phase timing, live) ----
     peaks = load_peaks()
