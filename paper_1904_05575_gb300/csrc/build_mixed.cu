@@ -140,22 +140,36 @@ void launch_split(const SplitArgs& a, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // epilogues of the tensor-core GEMM
 // ---------------------------------------------------------------------------
-struct ExchangeEpi {   // V[alpha][alpha'] -> A, B (column-major FP64)
+// V[alpha][alpha'] -> A, B (column-major FP64).  V is Hermitian (Eq. vrrofM);
+// with `tri`, only tiles touching the lower triangle are computed: the
+// epilogue writes (alpha, alpha') for alpha' <= alpha and its conjugate at
+// (alpha', alpha) for alpha' < alpha, and skips the tile's upper-triangle
+// elements (their mirror is written from the lower tile).  Every element is
+// written once; the diagonal of V is stored real.
+struct ExchangeEpi {
   double2 *A, *B;
   int64_t ld;
   float scale;         // 2 gamma_x kappa (the product is formed in FP32, then widened exactly)
   const double *e_v, *e_c;
   int nv, nc;
+  int tri;
   __device__ __forceinline__ void operator()(const tc::Tile& t, int row, int c0, const float* re,
                                              const float* im) const {
     const int64_t al = t.out_row0 + row;
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
       const int col = c0 + j;
-      if (col < t.n_valid) {
-        const int64_t ap = t.n0 + col;
+      const int64_t ap = t.n0 + col;
+      if (col < t.n_valid && (!tri || ap <= al)) {
         double2 val = make_double2(f32_to_f64_bits(scale * re[j]), f32_to_f64_bits(scale * im[j]));
         const int64_t off = al + ap * ld;
+        if (tri && ap < al) {
+          const double2 mir = make_double2(val.x, -val.y);
+          const int64_t moff = ap + al * ld;
+          if (B) B[moff] = mir;
+          A[moff] = mir;
+        }
+        if (al == ap) val.y = 0.0;   // the diagonal of a Hermitian V is real
         if (B) B[off] = val;
         if (al == ap) {
           const int64_t kk = al / (nv * nc);
@@ -776,6 +790,7 @@ struct ExParams {
   float scale;
   const double *e_v, *e_c;
   int nv, nc;
+  int tri;        // lower-triangle tiles only (see ExchangeEpi)
 };
 
 struct ExchangeBatchEpi {   // ExchangeEpi with per-problem outputs
@@ -783,7 +798,7 @@ struct ExchangeBatchEpi {   // ExchangeEpi with per-problem outputs
   __device__ __forceinline__ void operator()(const tc::Tile& t, int row, int c0, const float* re,
                                              const float* im) const {
     const ExParams q = params[t.prob];
-    ExchangeEpi e{q.A, q.B, q.ld, q.scale, q.e_v, q.e_c, q.nv, q.nc};
+    ExchangeEpi e{q.A, q.B, q.ld, q.scale, q.e_v, q.e_c, q.nv, q.nc, q.tri};
     e(t, row, c0, re, im);
   }
 };
@@ -1047,17 +1062,30 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
   std::vector<ExParams> xp;
   int64_t nmax = 0;
   for (const Problem& pr : pl->probs) nmax = std::max<int64_t>(nmax, pr.n);
-  pl->nt_x = tile_cols(round_up((int)nmax, 32), pl->Kp);
+  // exchange tiles: the widest column tile that still gives every SM a tile;
+  // the lower triangle only (Hermitian V) when the full square has at least
+  // two tiles per SM (below that the half-empty GPU would not gain)
+  const int sms = num_sms();
+  int64_t full = 0;
+  for (int cand : {128, 96, 64, 32}) {
+    if (cand > tile_cols(round_up((int)nmax, 32), pl->Kp)) continue;
+    pl->nt_x = cand;
+    full = 0;
+    for (const Problem& pr : pl->probs)
+      full += (int64_t)((pr.n + tc::BM - 1) / tc::BM) * ((pr.n + cand - 1) / cand);
+    if (full >= sms) break;
+  }
+  const int tri = full >= 2 * sms ? 1 : 0;
   for (size_t i = 0; i < pl->probs.size(); ++i) {
     const bse_problem& p = pl->probs[i].p;
     const int n = (int)pl->probs[i].n;
     pl->x_row0.push_back(pl->x_rows);
     for (int m0 = 0; m0 < n; m0 += tc::BM)
-      for (int n0 = 0; n0 < n; n0 += pl->nt_x)
+      for (int n0 = 0; n0 < n && (!tri || n0 < m0 + tc::BM); n0 += pl->nt_x)
         xt.push_back({(int)(pl->x_rows + m0), std::min(tc::BM, n - m0), (int)(pl->x_rows + n0), n0,
                       std::min(pl->nt_x, n - n0), m0, (int)i});
     xp.push_back({reinterpret_cast<double2*>(p.A), p.coupling ? reinterpret_cast<double2*>(p.B) : nullptr,
-                  p.ld, (float)(2.0 * p.gamma_x * pl->probs[i].kappa), p.e_v, p.e_c, p.nv, p.nc});
+                  p.ld, (float)(2.0 * p.gamma_x * pl->probs[i].kappa), p.e_v, p.e_c, p.nv, p.nc, tri});
     pl->x_rows += n;
   }
   pl->xa = DevMem((size_t)pl->planes * pl->x_rows * pl->Kp * 2);
