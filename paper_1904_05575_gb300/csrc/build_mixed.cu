@@ -66,6 +66,7 @@ struct SplitArgs {
   __nv_bfloat16* out;       // [2 * pieces][plane_rows][Kp]
   int64_t plane_rows = 0;   // rows of each destination plane (0: rows)
   int64_t row0 = 0;         // first destination row
+  int pair_nb = 0;          // SPLIT_PAIRS: rows_per = nb^2 rows (b, b') stored as (b', b)
 };
 
 // One thread per (output row, 8 consecutive k): every element is read as two
@@ -82,7 +83,9 @@ __global__ void __launch_bounds__(256) k_split(SplitArgs a) {
     const int row = (int)(i / kg), k0 = (int)(i % kg) * 8;
     int64_t off = (int64_t)row * a.K, kstride = 1;
     if (a.mode == SPLIT_PAIRS) {
-      const int slot = row / a.rows_per, j = row % a.rows_per;
+      const int slot = row / a.rows_per;
+      int j = row % a.rows_per;
+      if (a.pair_nb) j = (j % a.pair_nb) * a.pair_nb + j / a.pair_nb;
       off = ((int64_t)a.perm[slot] * a.rows_per + j) * a.K;
     } else if (a.mode == SPLIT_W) {
       const int q = row / a.rows_per, g = row % a.rows_per;
@@ -253,15 +256,24 @@ struct TEpiMulti {
   }
 };
 
-// Stage 2 on the tensor cores (large pair blocks): tile rows are one pair's
-// rx (Tile::out_row0 = pair * rows_x + first rx), columns its rt; the
-// epilogue subtracts gamma_c kappa P (formed in FP32, widened exactly) from
-// A (W^rr) or B (W^ra) in FP64, one owner per element.
+// Stage 2 on the tensor cores (large pair blocks): one pair block per tile
+// row range (Tile::out_row0 = pair * rows_r + first row); the epilogue
+// subtracts gamma_c kappa P (formed in FP32, widened exactly) from A (W^rr)
+// or B (W^ra) in FP64, one owner per element.  The operands are oriented so
+// that the tile rows (the TMEM lanes, one per thread) run over the
+// conduction index c fastest: consecutive lanes then update consecutive rows
+// of one column of A or B (runs of Nc) instead of Nc-strided columns.
 struct S2TcParams {
   double2* out;
   int64_t ld;
-  int rows_x, nk, nv, nc, mode;
+  int nk, nvnc;     // k points; Nv * Nc
   float scale;
+  int rows_r;       // rows per pair of the side that forms the tile rows
+  int row_nb;       // tile rows stored (b', b) for a side indexed (b, b') (0: as stored)
+  // each side's pair index is (a, b) with b < nb; it moves the element
+  // (row al, column ap) of A or B by a * sa + b * sb in al + ap * ld
+  int nb_r, nb_c;   // row side, column side
+  int64_t ra, rb, ca, cb;
 };
 
 struct S2TcEpi {
@@ -269,29 +281,42 @@ struct S2TcEpi {
   __device__ __forceinline__ void operator()(const tc::Tile& t, int row, int c0, const float* re,
                                              const float* im) const {
     const S2TcParams q = params[t.prob];
-    const int rxg = t.out_row0 + row;
-    const int pair = rxg / q.rows_x, rx = rxg - pair * q.rows_x;
+    const int rg = t.out_row0 + row;
+    const int pair = rg / q.rows_r;
+    int ir = rg - pair * q.rows_r;
+    if (q.row_nb) ir = (ir % q.row_nb) * q.row_nb + ir / q.row_nb;
     const int k = pair / q.nk, kp = pair - k * q.nk;
-    const int nv = q.nv, nc = q.nc;
+    const int ar = ir / q.nb_r, br = ir - ar * q.nb_r;
+    double2* base = q.out + (int64_t)k * q.nvnc + (int64_t)kp * q.nvnc * q.ld + ar * q.ra + br * q.rb;
+    const int jc0 = t.n0 + c0;
+    int bc = jc0 % q.nb_c;
+    double2* dst = base + (int64_t)(jc0 / q.nb_c) * q.ca + bc * q.cb;
+    const int64_t wrap = q.ca - (int64_t)q.nb_c * q.cb;
+    // groups of 8: the addresses and loads first, then the stores, so the
+    // loads of a group are in flight together
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      if (c0 + j < t.n_valid) {
-        const int rt = t.n0 + c0 + j;
-        int vi, ci, vp, cp;
-        if (q.mode == 0) {          // rx = (v, v'), rt = (c, c')
-          vi = rx / nv; vp = rx % nv; ci = rt / nc; cp = rt % nc;
-        } else if (q.mode == 1) {   // rx = (c, c'), rt = (v, v')
-          ci = rx / nc; cp = rx % nc; vi = rt / nv; vp = rt % nv;
-        } else {                    // rx = (v', c), rt = (v, c')
-          vp = rx / nc; ci = rx % nc; vi = rt / nc; cp = rt % nc;
+    for (int j0 = 0; j0 < 32; j0 += 8) {
+      double2* p[8];
+      double2 o[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        p[u] = dst;
+        dst += q.cb;
+        if (++bc == q.nb_c) {
+          bc = 0;
+          dst += wrap;
         }
-        const int64_t al = ((int64_t)k * nv + vi) * nc + ci;
-        const int64_t ap = ((int64_t)kp * nv + vp) * nc + cp;
-        double2* dst = q.out + al + ap * q.ld;
-        double2 o = *dst;
-        o.x -= f32_to_f64_bits(q.scale * re[j]);
-        o.y -= f32_to_f64_bits(q.scale * im[j]);
-        *dst = o;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (c0 + j0 + u < t.n_valid) o[u] = *p[u];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (c0 + j0 + u < t.n_valid) {
+          o[u].x -= f32_to_f64_bits(q.scale * re[j0 + u]);
+          o[u].y -= f32_to_f64_bits(q.scale * im[j0 + u]);
+          *p[u] = o[u];
+        }
       }
     }
   }
@@ -832,6 +857,8 @@ struct BatchPlan {
     std::vector<int32_t> qh;
     // stage 2 on the tensor cores (large pair blocks)
     bool tc2 = false;
+    bool rows_t_side = false;   // stage-2 tile rows are the T side (W^rr with T on (c, c'))
+    int side_nb = 0, x_nb = 0;  // (b, b') rows stored (b', b) in the stage-1 side / x2 planes
     int64_t x2_row0 = 0;     // first row of this term's pair side in the x2 planes
     DevMem x2perm;           // pair -> pair whose side rows are read (identity, or (k', k))
   };
@@ -841,10 +868,10 @@ struct BatchPlan {
   int n_stiles = 0;
   // stage 2 on the tensor cores for terms with large pair blocks
   int64_t x2_rows = 0;
-  DevMem x2split, tplanes, touts, s2tiles, s2params;
-  int n_s2tiles = 0, nt2 = 0;
+  DevMem x2split, tplanes, touts, s2tiles, s2tiles_t, s2params;
+  int n_s2tiles = 0, n_s2tiles_t = 0, nt2 = 0;
   tc::GemmShape sh_2{};
-  CUtensorMap ma_2{}, mb_2{};
+  CUtensorMap ma_2{}, mb_2{}, ma_2t{}, mb_2t{};   // rows = X side / rows = T side
   // fused direct term (stage 1 + stage 2 in one launch)
   bool fused = false;
   std::vector<tc::S2Term> s2host;
@@ -903,11 +930,13 @@ void plan_splits(BatchPlan& pl, cudaStream_t s) {
     SplitArgs sa{reinterpret_cast<const double2*>(t.side), SPLIT_PAIRS, t.perm.as<int>(),
                  t.rows_side, 0, pl.ng, pl.Kp, npair * t.rows_side, pl.pieces, 0, nullptr,
                  pl.asplit.as<__nv_bfloat16>(), pl.a_rows, t.a_row0};
+    sa.pair_nb = t.side_nb;
     launch_split(sa, s);
     if (t.tc2) {   // the other pair side, in pair order, conjugated as opX
       SplitArgs sx{t.s2.x, SPLIT_PAIRS, t.x2perm.as<int>(), t.s2.rows_x, 0, pl.ng, pl.Kp,
                    npair * t.s2.rows_x, pl.pieces, t.s2.conj_x, nullptr,
                    pl.x2split.as<__nv_bfloat16>(), pl.x2_rows, t.x2_row0};
+      sx.pair_nb = t.x_nb;
       launch_split(sx, s);
     }
   }
@@ -946,10 +975,14 @@ void plan_execute_mixed(BatchPlan& pl, cudaStream_t s) {
       launch_stage2(t.s2, p.nk * p.nk, s);
     }
   }
-  if (pl.n_s2tiles) {
+  if (pl.n_s2tiles || pl.n_s2tiles_t) {
     Phase ph("mixed_stage2_tc", s);
-    launch_gemm(pl.ma_2, pl.mb_2, pl.s2tiles.as<tc::Tile>(), pl.n_s2tiles, pl.sh_2,
-                S2TcEpi{pl.s2params.as<S2TcParams>()}, pl.err.as<int>(), s);
+    if (pl.n_s2tiles)
+      launch_gemm(pl.ma_2, pl.mb_2, pl.s2tiles.as<tc::Tile>(), pl.n_s2tiles, pl.sh_2,
+                  S2TcEpi{pl.s2params.as<S2TcParams>()}, pl.err.as<int>(), s);
+    if (pl.n_s2tiles_t)
+      launch_gemm(pl.ma_2t, pl.mb_2t, pl.s2tiles_t.as<tc::Tile>(), pl.n_s2tiles_t, pl.sh_2,
+                  S2TcEpi{pl.s2params.as<S2TcParams>()}, pl.err.as<int>(), s);
   }
 }
 
@@ -1229,19 +1262,47 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
         BSE_CUDA(cudaMemsetAsync(pl->tplanes.ptr, 0, tp_bytes, s));
         for (size_t ti = 0; ti < pl->terms.size(); ++ti)
           if (pl->terms[ti].tc2) outs[ti].planes = pl->tplanes.as<__nv_bfloat16>();
-        // pair sides in pair order, and the tiles of every pair block
+        // pair sides in pair order, and the tiles of every pair block, oriented
+        // so that the tile rows run over c fastest (see S2TcEpi)
         std::vector<S2TcParams> prm;
-        std::vector<tc::Tile> tiles;
-        pl->nt2 = 0;
-        int max_rt = 0;
-        for (const BatchPlan::Term& t : pl->terms)
-          if (t.tc2) max_rt = std::max(max_rt, t.s2.rows_t);
+        std::vector<tc::Tile> tiles, tiles_t;
+        int max_cols = 0;
+        for (BatchPlan::Term& t : pl->terms) {
+          if (!t.tc2) continue;
+          const Stage2Args& a = t.s2;
+          t.rows_t_side = a.mode == S2_RR_CC;            // T rows (c, c') -> (c', c)
+          t.side_nb = a.mode == S2_RR_CC ? a.nc : 0;
+          t.x_nb = a.mode == S2_RR_VV ? a.nc : 0;        // X rows (c, c') -> (c', c)
+          max_cols = std::max(max_cols, t.rows_t_side ? a.rows_x : a.rows_t);
+        }
         // stage 2 products feed A and B directly: K segments of at most 4 steps
-        pl->nt2 = tile_cols(round_up(max_rt, 32), pl->Kp, 4, 4);
+        pl->nt2 = tile_cols(round_up(max_cols, 32), pl->Kp, 4, 4);
         for (size_t ti = 0; ti < pl->terms.size(); ++ti) {
           BatchPlan::Term& t = pl->terms[ti];
           const Stage2Args& a = t.s2;
-          prm.push_back(S2TcParams{a.out, a.ld, a.rows_x, a.nk, a.nv, a.nc, a.mode, (float)a.scale});
+          // (a, b) of each side and its strides in al + ap * ld:
+          //   W^rr, T on (c, c'):  X (v, v'): (nc, nc ld)   T (c, c'): (1, ld)
+          //   W^rr, T on (v, v'):  X (c, c'): (1, ld)       T (v, v'): (nc, nc ld)
+          //   W^ra:                X (v', c): (nc ld, 1)    T (v, c'): (nc, ld)
+          const int64_t ld = a.ld, nc = a.nc;
+          int nb_x, nb_t;
+          int64_t xa, xb, ta, tb;
+          if (a.mode == S2_RR_CC) {
+            nb_x = a.nv; xa = nc; xb = nc * ld; nb_t = a.nc; ta = 1; tb = ld;
+          } else if (a.mode == S2_RR_VV) {
+            nb_x = a.nc; xa = 1; xb = ld; nb_t = a.nv; ta = nc; tb = nc * ld;
+          } else {
+            nb_x = a.nc; xa = nc * ld; xb = 1; nb_t = a.nc; ta = nc; tb = ld;
+          }
+          S2TcParams q{a.out, a.ld, a.nk, a.nv * a.nc, (float)a.scale, 0, 0, 0, 0, 0, 0, 0, 0};
+          if (t.rows_t_side) {
+            q.rows_r = a.rows_t; q.row_nb = t.side_nb;
+            q.nb_r = nb_t; q.ra = ta; q.rb = tb; q.nb_c = nb_x; q.ca = xa; q.cb = xb;
+          } else {
+            q.rows_r = a.rows_x; q.row_nb = t.x_nb;
+            q.nb_r = nb_x; q.ra = xa; q.rb = xb; q.nb_c = nb_t; q.ca = ta; q.cb = tb;
+          }
+          prm.push_back(q);
           if (!t.tc2) continue;
           const int npair = a.nk * a.nk;
           std::vector<int> xp(npair);
@@ -1252,25 +1313,41 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
           pl->x2_rows += (int64_t)npair * a.rows_x;
           std::vector<int> slot(npair);
           BSE_CUDA(cudaMemcpy(slot.data(), a.slot_of_pair, npair * sizeof(int), cudaMemcpyDeviceToHost));
-          for (int pr = 0; pr < npair; ++pr)
-            for (int m0 = 0; m0 < a.rows_x; m0 += tc::BM)
-              for (int n0 = 0; n0 < a.rows_t; n0 += pl->nt2)
-                tiles.push_back({(int)(t.x2_row0 + (int64_t)pr * a.rows_x + m0),
-                                 std::min(tc::BM, a.rows_x - m0),
-                                 (int)(t.a_row0 + (int64_t)slot[pr] * a.rows_t + n0), n0,
-                                 std::min(pl->nt2, a.rows_t - n0), pr * a.rows_x + m0, (int)ti});
+          for (int pr = 0; pr < npair; ++pr) {
+            const int64_t xr = t.x2_row0 + (int64_t)pr * a.rows_x;      // X rows of the pair
+            const int64_t tr = t.a_row0 + (int64_t)slot[pr] * a.rows_t;  // T rows of the pair
+            if (t.rows_t_side) {
+              for (int m0 = 0; m0 < a.rows_t; m0 += tc::BM)
+                for (int n0 = 0; n0 < a.rows_x; n0 += pl->nt2)
+                  tiles_t.push_back({(int)(tr + m0), std::min(tc::BM, a.rows_t - m0), (int)(xr + n0),
+                                     n0, std::min(pl->nt2, a.rows_x - n0), pr * a.rows_t + m0,
+                                     (int)ti});
+            } else {
+              for (int m0 = 0; m0 < a.rows_x; m0 += tc::BM)
+                for (int n0 = 0; n0 < a.rows_t; n0 += pl->nt2)
+                  tiles.push_back({(int)(xr + m0), std::min(tc::BM, a.rows_x - m0), (int)(tr + n0),
+                                   n0, std::min(pl->nt2, a.rows_t - n0), pr * a.rows_x + m0,
+                                   (int)ti});
+            }
+          }
         }
         if (pl->x2_rows > INT32_MAX)
           throw Error(BSE_ERR_UNSUPPORTED, "tensor-core stage-2 rows exceed 2^31");
         pl->x2split = DevMem((size_t)pl->planes * pl->x2_rows * pl->Kp * 2);
         pl->n_s2tiles = (int)tiles.size();
         pl->s2tiles = upload_mem(tiles);
+        pl->n_s2tiles_t = (int)tiles_t.size();
+        pl->s2tiles_t = upload_mem(tiles_t);
         pl->s2params = upload_mem(prm);
         pl->sh_2 = make_shape(pl->nt2, pl->Kp, pl->pieces, 4, 4);
         pl->ma_2 = make_plane_map(pl->x2split.as<__nv_bfloat16>(), pl->Kp, (int)pl->x2_rows,
                                   pl->planes, tc::BM);
         pl->mb_2 = make_plane_map(pl->tplanes.as<__nv_bfloat16>(), pl->Kp, (int)pl->a_rows,
                                   pl->planes, pl->nt2);
+        pl->ma_2t = make_plane_map(pl->tplanes.as<__nv_bfloat16>(), pl->Kp, (int)pl->a_rows,
+                                   pl->planes, tc::BM);
+        pl->mb_2t = make_plane_map(pl->x2split.as<__nv_bfloat16>(), pl->Kp, (int)pl->x2_rows,
+                                   pl->planes, pl->nt2);
       }
       pl->touts = upload_mem(outs);
     }

@@ -213,12 +213,14 @@ def test_fused_graph_capture_and_autotune_leaves_outputs(bse, square):
     plan.close()
 
 
-# pair blocks of 64 x 64 rows (Nv = Nc = 8): the second contraction runs on the
-# tensor cores; NG = 300 also cuts K into segments
-@pytest.mark.parametrize("ng", [59, 300])
-def test_tensor_core_stage2_matches_oracle_and_cuda_cores(bse, ng):
+# pair blocks of at least 64 x 64 rows: the second contraction runs on the
+# tensor cores.  Nv = Nc = 8 puts the W^rr stage-1 side on (c, c') (tile rows
+# from T), Nv = 8, Nc = 9 on (v, v') (tile rows from the other side, stored
+# (c', c)); NG = 300 also cuts K into segments
+@pytest.mark.parametrize("nv,nc,ng", [(8, 8, 59), (8, 8, 300), (8, 9, 59)], ids=str)
+def test_tensor_core_stage2_matches_oracle_and_cuda_cores(bse, nv, nc, ng):
     import torch
-    cfg = bi.BSEConfig(f"big-blocks-{ng}", grid=2, nv=8, nc=8, ng=ng, w_scale=0.05)
+    cfg = bi.BSEConfig(f"big-blocks-{nv}-{nc}-{ng}", grid=2, nv=nv, nc=nc, ng=ng, w_scale=0.05)
     p = bi.make_problem(cfg)
     A_ref, B_ref = O.build_A_B(p)
     ds, structs = _upload(bse, [p])
