@@ -308,6 +308,10 @@ def main():
     ap.add_argument("--device-inputs", action="store_true",
                     help="draw the inputs on the GPU (automatic for c3 and c5)")
     ap.add_argument("--nev", type=int, default=16, help="lowest excitons for time-to-lowest-excitons")
+    ap.add_argument("--lowest", action="store_true",
+                    help="build-only configs: also time mixed build + Davidson (tensor-core matvecs)")
+    ap.add_argument("--fp64-dense", action="store_true",
+                    help="with --lowest: also time the plain FP64 path (FP64 build + dense solve)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -488,6 +492,41 @@ def main():
                 "max_dE_meV_davidson_vs_fp64_dense":
                     (E_dav - E_fp64[:nev]).abs().max().item() * 1e3,
                 "max_dE_meV_dense_mixed_vs_fp64_dense": dE}
+
+    # ---- large N: time to the lowest excitons by mixed build + Davidson with
+    # tensor-core matvecs, against the plain FP64 path (FP64 build + dense
+    # reduction and eigensolve) when asked ----
+    if args.build_only and args.lowest and len(probs) == 1:
+        nev = min(args.nev, n)
+        E_dav = torch.empty(nev, dtype=torch.float64, device=dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plans[prec].execute()
+        iters = bse.bse_lowest_excitons(n, d["A"], d["B"], nev, E_dav, None, tol_ev=1e-5,
+                                        max_iter=300, matvec_precision=prec)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        low = {"nev": nev, "method": "mixed build + block Davidson (tensor-core matvecs)",
+               "time_to_lowest_excitons_ms": e0.elapsed_time(e1), "davidson_iterations": iters}
+        if args.fp64_dense:
+            S2 = torch.empty((n, n), dtype=torch.complex128, device=dev)
+            L2 = torch.empty_like(S2)
+            E_all = torch.empty(n, dtype=torch.float64, device=dev)
+            osc_all = torch.empty_like(E_all)
+            e0.record(stream)
+            bse.bse_build_kernel([st], bse.BSE_PREC_FP64)
+            e1.record(stream)
+            bse.bse_reduce(n, d["A"], d["B"], S2, L2)
+            bse.bse_spectrum(n, S2, L2, rho, p["c_q"], vc, om, p["delta"], E_all, osc_all, eps)
+            e2 = torch.cuda.Event(enable_timing=True)
+            e2.record(stream)
+            torch.cuda.synchronize()
+            low.update({"fp64_build_ms": e0.elapsed_time(e1), "fp64_dense_ms": e0.elapsed_time(e2),
+                        "speedup_vs_fp64_dense": e0.elapsed_time(e2) / low["time_to_lowest_excitons_ms"],
+                        "max_dE_meV_vs_fp64_dense": (E_dav - E_all[:nev]).abs().max().item() * 1e3})
+            del S2, L2
+        extra["lowest_excitons"] = low
 
     # ---- roofline of the dominant build kernel (phase timing, live) ----
     peaks = load_peaks()

@@ -102,9 +102,11 @@ CONFIGS: Dict[str, BSEConfig] = {
                     e_v_range=(-400.5, -399.5), e_c_range=(1.0, 4.0),
                     m_decay=0.05, w_scale=0.25, omega_range=(395.0, 410.0)),
     # molecular-crystal-like: 4x4x4 grid, 20x20 bands, NG = 500, strong off-diagonal W
+    # (strong off-diagonal W with 500 plane waves: scale 0.002 keeps |W^rr| near
+    # 0.7 eV, below the 1.1 eV smallest transition, as 0.25 does at c2)
     "c5": BSEConfig("c5", grid=4, nv=20, nc=20, ng=500,
                     q_abs=tuple(0.1 * i for i in range(8)),
-                    w_decay=0.2, w_diag=1.05, w_scale=0.25),
+                    w_decay=0.2, w_diag=1.05, w_scale=0.002),
 }
 
 

@@ -244,6 +244,11 @@ int bse_xpy(int32_t n, int32_t k, const bse_c128* Z, const bse_c128* L, int64_t 
  *              (eV; 1e-4 gives energies far inside 1 meV)
  *   max_iter   iteration limit
  *   precond    0 = diagonal (r_a / (A_aa - E)), 1 = the trained MLP given in mlp
+ *   matvec_precision  BSE_PREC_FP64: matvecs (A+B)V, (A-B)V by the FP64 GEMM;
+ *              BSE_PREC_BF16X6 / BF16X3: A and B split once into BF16 pieces
+ *              and the matvecs run on the tensor cores (FP32 accumulation in
+ *              K segments, FP64 results); workspace 2 x 12 N^2 bytes (BF16X6).
+ *              The residual floor is then ~1e-7 of |A|: keep tol_ev above it.
  *   E_out      [nev] device, ascending exciton energies (eV)
  *   XpY_out    [n x nev] device column-major, X+Y with (X+Y)^H (X-Y) = 1, or NULL
  *   iters_out  host, iterations used (may be NULL)
@@ -251,7 +256,8 @@ int bse_xpy(int32_t n, int32_t k, const bse_c128* Z, const bse_c128* L, int64_t 
  * (E_out then holds the last estimates), BSE_ERR_UNSUPPORTED, BSE_ERR_CUDA. */
 int bse_lowest_excitons(int32_t n, const bse_c128* A, const bse_c128* B, int64_t ld, int32_t nev,
                         double tol_ev, int32_t max_iter, int32_t precond, const void* mlp,
-                        double* E_out, bse_c128* XpY_out, int32_t* iters_out, void* cuda_stream);
+                        int32_t matvec_precision, double* E_out, bse_c128* XpY_out,
+                        int32_t* iters_out, void* cuda_stream);
 
 /* ---- learned preconditioner for bse_lowest_excitons -------------------------
  * Not in the paper: a per-transition network (4 features -> 128 -> 128 -> 1,

@@ -79,7 +79,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.bse_kernel_launches.restype = ctypes.c_int64
     lib.bse_build_kernel_fp64_static.argtypes = [ctypes.POINTER(bse_problem), vp]
     lib.bse_build_kernel_fp64_static.restype = ctypes.c_int
-    lib.bse_lowest_excitons.argtypes = [i32, vp, vp, i64, i32, dbl, i32, i32, vp, vp, vp,
+    lib.bse_lowest_excitons.argtypes = [i32, vp, vp, i64, i32, dbl, i32, i32, vp, i32, vp, vp,
                                         ctypes.POINTER(i32), vp]
     lib.bse_lowest_excitons.restype = ctypes.c_int
     lib.bse_xpy.argtypes = [i32, i32, vp, vp, i64, vp, vp, vp]
@@ -229,7 +229,8 @@ def bse_spectrum(n: int, S, L, rho, c_q: float, vc: float, omega, delta: float,
 
 
 def bse_lowest_excitons(n: int, A, B, nev: int, E_out, XpY_out=None, tol_ev: float = 1e-4,
-                        max_iter: int = 100, precond: int = 0, mlp=None, stream=None) -> int:
+                        max_iter: int = 100, precond: int = 0, mlp=None, stream=None,
+                        matvec_precision: int = BSE_PREC_FP64) -> int:
     """Lowest nev excitons by block Davidson; returns the iterations used.  On
     BSE_ERR_NO_CONV the raised error carries .iters."""
     import torch
@@ -244,8 +245,8 @@ def bse_lowest_excitons(n: int, A, B, nev: int, E_out, XpY_out=None, tol_ev: flo
     iters = ctypes.c_int32(0)
     handle = mlp.handle if mlp is not None else None
     st = lib.bse_lowest_excitons(n, a, b, ld, nev, float(tol_ev), int(max_iter), int(precond),
-                                 handle, _ptr(E_out, torch.float64, "E_out"), x,
-                                 ctypes.byref(iters), _stream(stream))
+                                 handle, int(matvec_precision), _ptr(E_out, torch.float64, "E_out"),
+                                 x, ctypes.byref(iters), _stream(stream))
     if st != BSE_OK:
         err = BSEError(st, lib.bse_last_error().decode(errors="replace"))
         err.iters = iters.value

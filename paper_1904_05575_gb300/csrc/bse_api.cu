@@ -328,8 +328,8 @@ extern "C" int bse_xpy(int32_t n, int32_t k, const bse_c128* Z, const bse_c128* 
 
 extern "C" int bse_lowest_excitons(int32_t n, const bse_c128* A, const bse_c128* B, int64_t ld,
                                    int32_t nev, double tol_ev, int32_t max_iter, int32_t precond,
-                                   const void* mlp, double* E_out, bse_c128* XpY_out,
-                                   int32_t* iters_out, void* cuda_stream) {
+                                   const void* mlp, int32_t matvec_precision, double* E_out,
+                                   bse_c128* XpY_out, int32_t* iters_out, void* cuda_stream) {
   return guarded([&] {
     if (iters_out) *iters_out = 0;
     BSE_CHECK_ARG(n >= 1, "n must be >= 1");
@@ -340,10 +340,17 @@ extern "C" int bse_lowest_excitons(int32_t n, const bse_c128* A, const bse_c128*
     BSE_CHECK_ARG(A && E_out, "NULL A or E_out");
     BSE_CHECK_ARG(precond == 0 || precond == 1, "precond must be 0 (diagonal) or 1 (MLP)");
     BSE_CHECK_ARG(precond == 0 || mlp != nullptr, "precond = 1 needs an MLP handle");
+    BSE_CHECK_ARG(matvec_precision == BSE_PREC_FP64 || matvec_precision == BSE_PREC_BF16X6 ||
+                      matvec_precision == BSE_PREC_BF16X3,
+                  "unknown matvec precision " + std::to_string(matvec_precision));
+    BSE_CHECK_ARG(matvec_precision == BSE_PREC_FP64 || mixed_supported(matvec_precision),
+                  "this build has no tensor-core path");
+    BSE_CHECK_ARG(((uintptr_t)A & 15) == 0 && ((uintptr_t)B & 15) == 0,
+                  "A and B must be 16-byte aligned");
     keep_pool_memory();
     davidson_fp64(n, A, B, ld, nev, tol_ev, max_iter, precond,
                   static_cast<const MlpNet*>(mlp), E_out, XpY_out, iters_out,
-                  static_cast<cudaStream_t>(cuda_stream));
+                  static_cast<cudaStream_t>(cuda_stream), nullptr, matvec_precision);
   });
 }
 

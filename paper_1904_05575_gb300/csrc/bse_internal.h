@@ -119,7 +119,17 @@ struct MlpNet;
 struct TrajectorySink;
 void davidson_fp64(int n, const bse_c128* A, const bse_c128* B, int64_t ld, int nev, double tol,
                    int max_iter, int precond, const MlpNet* mlp, double* E_out, bse_c128* XpY_out,
-                   int32_t* iters_out, cudaStream_t stream, TrajectorySink* sink = nullptr);
+                   int32_t* iters_out, cudaStream_t stream, TrajectorySink* sink = nullptr,
+                   int matvec_precision = BSE_PREC_FP64);
+
+// Hermitian matrix-vector blocks on the tensor cores (build_mixed.cu): A and
+// B split once; apply writes AV = A V and BV = B V (n x k, column-major, ld n).
+struct TcMatvec;
+TcMatvec* tc_matvec_create(int n, const bse_c128* A, const bse_c128* B, int64_t ld, int precision,
+                           int kmax, cudaStream_t stream);
+void tc_matvec_apply(TcMatvec* m, const bse_c128* V, int k, bse_c128* AV, bse_c128* BV,
+                     cudaStream_t stream);
+void tc_matvec_destroy(TcMatvec* m);
 
 // Batched plans (build_mixed.cu).
 struct BatchPlan;

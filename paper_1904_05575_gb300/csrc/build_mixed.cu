@@ -67,6 +67,7 @@ struct SplitArgs {
   int64_t plane_rows = 0;   // rows of each destination plane (0: rows)
   int64_t row0 = 0;         // first destination row
   int pair_nb = 0;          // SPLIT_PAIRS: rows_per = nb^2 rows (b, b') stored as (b', b)
+  int64_t src_ld = 0;       // SPLIT_DENSE: source row stride (0: K)
 };
 
 // One thread per (output row, 8 consecutive k): every element is read as two
@@ -81,7 +82,7 @@ __global__ void __launch_bounds__(256) k_split(SplitArgs a) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int row = (int)(i / kg), k0 = (int)(i % kg) * 8;
-    int64_t off = (int64_t)row * a.K, kstride = 1;
+    int64_t off = (int64_t)row * (a.src_ld ? a.src_ld : a.K), kstride = 1;
     if (a.mode == SPLIT_PAIRS) {
       const int slot = row / a.rows_per;
       int j = row % a.rows_per;
@@ -1474,5 +1475,98 @@ void build_mixed_batch(const std::vector<Problem>& probs, int precision, cudaStr
       throw Error(BSE_ERR_TIMEOUT, "tensor-core GEMM: a bounded pipeline wait expired");
   }
 }
+
+
+// ---------------------------------------------------------------------------
+// Matrix-vector blocks of a Hermitian N x N matrix on the tensor cores, for the
+// Davidson solve: AV = A V and BV = B V with V an N x k block.  Row m of a
+// Hermitian matrix is the conjugate of its column m, which is contiguous in
+// the column-major input, so A and B are split once (conjugated columns as
+// GEMM rows, K = N); each call splits V's columns and runs one GEMM per
+// matrix (K segments of 8 steps), writing FP64 results column-major.
+// ---------------------------------------------------------------------------
+namespace {
+struct MatvecEpi {
+  double2* out;
+  int64_t ld;
+  __device__ __forceinline__ void operator()(const tc::Tile& t, int row, int c0, const float* re,
+                                             const float* im) const {
+    const int64_t r = t.out_row0 + row;
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (c0 + j < t.n_valid)
+        out[r + (int64_t)(t.n0 + c0 + j) * ld] =
+            make_double2(f32_to_f64_bits(re[j]), f32_to_f64_bits(im[j]));
+  }
+};
+}  // namespace
+
+struct TcMatvec {
+  int n = 0, Kp = 0, pieces = 3, planes = 6, kmax = 0, kmax_rows = 0, nt = 0, max_tiles = 0;
+  bool has_b = false;
+  DevMem ap, bp, vp, tiles, err;
+  CUtensorMap ma_a{}, ma_b{}, mb_v{};
+  tc::GemmShape sh{};
+};
+
+TcMatvec* tc_matvec_create(int n, const bse_c128* A, const bse_c128* B, int64_t ld, int precision,
+                           int kmax, cudaStream_t s) {
+  std::unique_ptr<TcMatvec> m(new TcMatvec);
+  m->n = n;
+  m->pieces = precision == BSE_PREC_BF16X6 ? 3 : 2;
+  m->planes = 2 * m->pieces;
+  m->Kp = round_up(n, tc::BK);
+  m->kmax = kmax;
+  m->kmax_rows = round_up(kmax, 32);
+  m->nt = tile_cols(m->kmax_rows, m->Kp);
+  m->sh = make_shape(m->nt, m->Kp, m->pieces);
+  m->has_b = B != nullptr;
+  m->max_tiles = ((n + tc::BM - 1) / tc::BM) * ((kmax + m->nt - 1) / m->nt);
+  const size_t mat_bytes = (size_t)m->planes * n * m->Kp * 2;
+  m->ap = DevMem(mat_bytes);
+  if (B) m->bp = DevMem(mat_bytes);
+  m->vp = DevMem((size_t)m->planes * m->kmax_rows * m->Kp * 2);
+  BSE_CUDA(cudaMemsetAsync(m->vp.ptr, 0, (size_t)m->planes * m->kmax_rows * m->Kp * 2, s));
+  m->tiles = DevMem((size_t)m->max_tiles * sizeof(tc::Tile));
+  m->err = DevMem(sizeof(int));
+  BSE_CUDA(cudaMemsetAsync(m->err.ptr, 0, sizeof(int), s));
+  for (int which = 0; which < (B ? 2 : 1); ++which) {
+    SplitArgs sa{reinterpret_cast<const double2*>(which ? B : A), SPLIT_DENSE, nullptr, 0, 0, n,
+                 m->Kp, n, m->pieces, 1, nullptr,
+                 (which ? m->bp : m->ap).as<__nv_bfloat16>(), n, 0};
+    sa.src_ld = ld;
+    launch_split(sa, s);
+  }
+  m->ma_a = make_plane_map(m->ap.as<__nv_bfloat16>(), m->Kp, n, m->planes, tc::BM);
+  if (B) m->ma_b = make_plane_map(m->bp.as<__nv_bfloat16>(), m->Kp, n, m->planes, tc::BM);
+  m->mb_v = make_plane_map(m->vp.as<__nv_bfloat16>(), m->Kp, m->kmax_rows, m->planes, m->nt);
+  return m.release();
+}
+
+void tc_matvec_apply(TcMatvec* m, const bse_c128* V, int k, bse_c128* AV, bse_c128* BV,
+                     cudaStream_t s) {
+  if (k <= 0) return;
+  if (k > m->kmax) throw Error(BSE_ERR_UNSUPPORTED, "tensor-core matvec block wider than planned");
+  SplitArgs sv{reinterpret_cast<const double2*>(V), SPLIT_DENSE, nullptr, 0, 0, m->n, m->Kp, k,
+               m->pieces, 0, nullptr, m->vp.as<__nv_bfloat16>(), m->kmax_rows, 0};
+  launch_split(sv, s);
+  std::vector<tc::Tile> tl;
+  for (int m0 = 0; m0 < m->n; m0 += tc::BM)
+    for (int n0 = 0; n0 < k; n0 += m->nt)
+      tl.push_back({m0, std::min(tc::BM, m->n - m0), n0, n0, std::min(m->nt, k - n0), m0, 0});
+  BSE_CUDA(cudaMemcpyAsync(m->tiles.ptr, tl.data(), tl.size() * sizeof(tc::Tile),
+                           cudaMemcpyHostToDevice, s));
+  launch_gemm(m->ma_a, m->mb_v, m->tiles.as<tc::Tile>(), (int)tl.size(), m->sh,
+              MatvecEpi{reinterpret_cast<double2*>(AV), m->n}, m->err.as<int>(), s);
+  if (m->has_b && BV)
+    launch_gemm(m->ma_b, m->mb_v, m->tiles.as<tc::Tile>(), (int)tl.size(), m->sh,
+                MatvecEpi{reinterpret_cast<double2*>(BV), m->n}, m->err.as<int>(), s);
+  int herr = 0;
+  BSE_CUDA(cudaMemcpyAsync(&herr, m->err.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+  BSE_CUDA(cudaStreamSynchronize(s));   // also keeps the host tile list alive until used
+  if (herr) throw Error(BSE_ERR_TIMEOUT, "tensor-core matvec: a bounded pipeline wait expired");
+}
+
+void tc_matvec_destroy(TcMatvec* m) { delete m; }
 
 }  // namespace bse

@@ -5,7 +5,8 @@
 // (A-B)(A+B)(X+Y) = E^2 (X+Y): the half-size form behind Eq. auxevp.  The
 // solver keeps one orthonormal basis V for both X+Y and X-Y (the scheme of
 // Stratmann, Scuseria and Frisch, J. Chem. Phys. 109, 8218 (1998)):
-//   P = (A+B) V, M = (A-B) V                   matvecs: FP64 GEMM kernels here
+//   P = (A+B) V, M = (A-B) V                   matvecs: FP64 GEMM kernel, or the
+//                                               split-precision tensor-core GEMM
 //   a+ = V^H P, a- = V^H M                      projected (m x m) matrices
 //   a- = l l^H, s = l^H a+ l, s z = E^2 z       the projected problem, in the
 //   u = l z E^-1/2, w = a+ u / E                Cholesky form used by bse_reduce
@@ -195,17 +196,25 @@ struct Solver {
     return b.as<cuDoubleComplex>() + (int64_t)j * ldb;
   }
 
+  // tensor-core matvecs (split-precision A, B), or NULL for the FP64 kernel
+  TcMatvec* tcm = nullptr;
+
   // P, M for basis columns [j0, j1)
   void matvec(int j0, int j1) {
     const int k = j1 - j0;
     if (k <= 0) return;
-    MatvecProb pa{n, k, n, A, ld, V.as<bse_c128>() + (int64_t)j0 * n, n,
-                  AV.as<bse_c128>(), n};
-    launch_zgemm(pa, 1, s);
-    if (B) {
-      MatvecProb pb{n, k, n, B, ld, V.as<bse_c128>() + (int64_t)j0 * n, n,
-                    BV.as<bse_c128>(), n};
-      launch_zgemm(pb, 1, s);
+    if (tcm) {
+      tc_matvec_apply(tcm, V.as<bse_c128>() + (int64_t)j0 * n, k, AV.as<bse_c128>(),
+                      B ? BV.as<bse_c128>() : nullptr, s);
+    } else {
+      MatvecProb pa{n, k, n, A, ld, V.as<bse_c128>() + (int64_t)j0 * n, n,
+                    AV.as<bse_c128>(), n};
+      launch_zgemm(pa, 1, s);
+      if (B) {
+        MatvecProb pb{n, k, n, B, ld, V.as<bse_c128>() + (int64_t)j0 * n, n,
+                      BV.as<bse_c128>(), n};
+        launch_zgemm(pb, 1, s);
+      }
     }
     const int64_t total = (int64_t)n * k;
     k_plus_minus_cols<<<(int)std::min<int64_t>((total + 255) / 256, 152 * 16), 256, 0, s>>>(
@@ -458,7 +467,8 @@ __global__ void k_xmy(int64_t total, int n, const double2* ax, const double2* bx
 
 void davidson_fp64(int n, const bse_c128* A, const bse_c128* B, int64_t ld, int nev, double tol,
                    int max_iter, int precond, const MlpNet* mlp, double* E_out,
-                   bse_c128* XpY_out, int32_t* iters_out, cudaStream_t s, TrajectorySink* sink) {
+                   bse_c128* XpY_out, int32_t* iters_out, cudaStream_t s, TrajectorySink* sink,
+                   int matvec_precision) {
   std::unique_lock<std::mutex> lock;
   LibHandles h = acquire_handles(lock);
   BSE_CUSOLVER(cusolverDnSetStream(h.solver, s));
@@ -469,6 +479,11 @@ void davidson_fp64(int n, const bse_c128* A, const bse_c128* B, int64_t ld, int 
   // lowest Ritz pairs (thick restart)
   const int mmax = std::min(n, std::max(24 * nev, nev + 96));
   Solver sv(n, nev, mmax, A, B, ld, s, h);
+  std::unique_ptr<TcMatvec, void (*)(TcMatvec*)> tcm(nullptr, tc_matvec_destroy);
+  if (matvec_precision != BSE_PREC_FP64) {
+    tcm.reset(tc_matvec_create(n, A, B, ld, matvec_precision, mmax, s));
+    sv.tcm = tcm.get();
+  }
 
   // diagonal of A: initial guess (unit vectors at the smallest A_aa); diagonals
   // of A+B and A-B and off-diagonal row norms for the preconditioners

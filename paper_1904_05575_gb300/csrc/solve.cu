@@ -10,6 +10,7 @@
 #include <cusolverDn.h>
 
 #include <mutex>
+#include <memory>
 #include <vector>
 
 #include "bse_internal.h"
@@ -268,19 +269,26 @@ void spectrum_fp64(int n, bse_c128* S, const bse_c128* L, int64_t ld, const bse_
   Handles& h = handles_for_current_device();
   BSE_CUSOLVER(cusolverDnSetStream(h.solver, s));
 
-  int lwork = 0;
-  BSE_CUSOLVER(cusolverDnZheevd_bufferSize(h.solver, CUSOLVER_EIG_MODE_VECTOR,
-                                           CUBLAS_FILL_MODE_LOWER, n,
-                                           reinterpret_cast<cuDoubleComplex*>(S), (int)ld,
-                                           E_out, &lwork));
-  DeviceBuffer work((size_t)(lwork > 0 ? lwork : 1) * sizeof(cuDoubleComplex), s);
+  // 64-bit generic interface: the 32-bit zheevd rejects N of tens of thousands
+  cusolverDnParams_t params = nullptr;
+  BSE_CUSOLVER(cusolverDnCreateParams(&params));
+  std::unique_ptr<cusolverDnParams, cusolverStatus_t (*)(cusolverDnParams_t)> params_guard(
+      params, cusolverDnDestroyParams);
+  size_t dev_bytes = 0, host_bytes = 0;
+  BSE_CUSOLVER(cusolverDnXsyevd_bufferSize(h.solver, params, CUSOLVER_EIG_MODE_VECTOR,
+                                           CUBLAS_FILL_MODE_LOWER, n, CUDA_C_64F, S, ld,
+                                           CUDA_R_64F, E_out, CUDA_C_64F, &dev_bytes,
+                                           &host_bytes));
+  DeviceBuffer work(dev_bytes > 0 ? dev_bytes : 16, s);
+  std::vector<char> host_work(host_bytes > 0 ? host_bytes : 16);
   DeviceBuffer flags(2 * sizeof(int), s);
   BSE_CUDA(cudaMemsetAsync(flags.ptr, 0, 2 * sizeof(int), s));
   {
     Phase ph("eig_heevd", s);
-    BSE_CUSOLVER(cusolverDnZheevd(h.solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER,
-                                  n, reinterpret_cast<cuDoubleComplex*>(S), (int)ld, E_out,
-                                  work.as<cuDoubleComplex>(), lwork, flags.as<int>()));
+    BSE_CUSOLVER(cusolverDnXsyevd(h.solver, params, CUSOLVER_EIG_MODE_VECTOR,
+                                  CUBLAS_FILL_MODE_LOWER, n, CUDA_C_64F, S, ld, CUDA_R_64F, E_out,
+                                  CUDA_C_64F, work.ptr, dev_bytes, host_work.data(), host_bytes,
+                                  flags.as<int>()));
   }
   Phase ph("spectrum_kernels", s);
   k_sqrt_energies<<<(n + 255) / 256, 256, 0, s>>>(n, E_out, flags.as<int>() + 1);
