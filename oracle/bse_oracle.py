@@ -26,7 +26,10 @@ Readings of the paper taken here (each listed in the design notes):
 Parity status: build_A_B, reduce_sqrt, solve_full, oscillator_strengths and
 eps_M are pinned by the tests in tests/test_oracle_pins.py (closed forms,
 brute force, sum rules, gauge invariance); block_A_B is pinned to build_A_B
-block by block (tests/test_oracle_blocks.py).
+block by block (tests/test_oracle_blocks.py); transition_coefficients,
+eps_tensor, loss_function and structure_factor by tests/test_oracle_spectra.py
+(contraction to the pinned scalar spectrum, a one-transition case worked by
+hand, rotation covariance, the loss identities).
 """
 from __future__ import annotations
 
@@ -227,6 +230,46 @@ def eps_M(e: np.ndarray, osc: np.ndarray, omega: np.ndarray, delta: float,
         res = 1.0 / (w - e + 1j * delta) + 1.0 / (-w - e - 1j * delta)
         out[i] = 1.0 - c_q * HARTREE_EV * np.sum(osc * res)
     return out
+
+
+def transition_coefficients(xpy: np.ndarray, D: np.ndarray, vc: float) -> np.ndarray:
+    """t_{lambda,i} = -i V_c^{-1/2} sum_alpha conj((X+Y)_{alpha lambda}) conj(D_{alpha,i})
+    for each Cartesian direction i (Eq. tlambdai, with the 1/V_c of Eq. osci);
+    D [n, 3], returns [n_lambda, 3]."""
+    nl, nd = xpy.shape[1], D.shape[1]
+    t = np.empty((nl, nd), np.complex128)
+    for lam in range(nl):
+        for i in range(nd):
+            t[lam, i] = -1j * np.sum(np.conj(xpy[:, lam]) * np.conj(D[:, i])) / np.sqrt(vc)
+    return t
+
+
+def eps_tensor(e: np.ndarray, t: np.ndarray, omega: np.ndarray, delta: float,
+               c_q: float) -> np.ndarray:
+    """eps^{ij}(w) = delta_ij - c_Q Ha sum_lambda t*_{lambda i} t_{lambda j}
+    [1/(w - E + i d) + 1/(-w - E - i d)]   (Eq. epsmij; its second denominator
+    read as -w - E - i delta, as in Eq. epsmtensor).  Returns [n_omega, 3, 3]."""
+    nd = t.shape[1]
+    out = np.empty((len(omega), nd, nd), np.complex128)
+    for iw, w in enumerate(omega):
+        res = 1.0 / (w - e + 1j * delta) + 1.0 / (-w - e - 1j * delta)
+        for i in range(nd):
+            for j in range(nd):
+                out[iw, i, j] = (1.0 if i == j else 0.0) - c_q * HARTREE_EV * np.sum(
+                    np.conj(t[:, i]) * t[:, j] * res)
+    return out
+
+
+def loss_function(eps: np.ndarray) -> np.ndarray:
+    """Electron energy-loss function L = -Im 1/eps_M (Eq. Lofeps)."""
+    return -np.imag(1.0 / eps)
+
+
+def structure_factor(eps: np.ndarray, v_inv: float) -> np.ndarray:
+    """Dynamical structure factor S(Q, w) = -(1/pi) v_G(q)^{-1} Im 1/eps_M(q, w)
+    (the definition after the double-differential cross-section, Sec. on
+    scattering spectra); v_inv = |G+q|^2 / (4 pi), the inverse Coulomb potential."""
+    return -(1.0 / np.pi) * v_inv * np.imag(1.0 / eps)
 
 
 def spectrum(A: np.ndarray, B: np.ndarray, p: Dict, coupling: bool = True):
