@@ -214,6 +214,32 @@ int bse_spectrum(int32_t n, bse_c128* S_inout, const bse_c128* L, int64_t ld,
                  const double* omega, double delta, double* E_out, double* osc_out,
                  bse_c128* eps_out, void* cuda_stream);
 
+/* Cartesian dielectric tensor (Eq. epsmij) from the eigenpairs that
+ * bse_spectrum leaves: Z (its S_inout on return, N x N, ld), L from
+ * bse_reduce, E [n] its energies.  D: N x 3 column-major (leading dimension
+ * ldd >= n), the momentum matrix elements D_{alpha,i} of Eq. tlambdai for the
+ * three Cartesian directions (the scalar spectrum uses rho = q.D).
+ *   t*_{lambda i} t_{lambda j} from Eq. tlambdai (with the 1/vc of Eq. osci)
+ *   eps_out[w][i][j] = delta_ij - c_q Ha sum_lambda t*_{lambda i} t_{lambda j}
+ *                      [1/(w - E + i delta) - 1/(w + E + i delta)]
+ * eps_out: [n_omega][3][3] complex, row-major in (i, j).  Contracting it with a
+ * real unit vector q gives the scalar eps_M of bse_spectrum for rho = D q.
+ * All arrays device pointers.  Syncs.  Errors: BSE_ERR_ARG, BSE_ERR_NOMEM,
+ * BSE_ERR_CUDA. */
+int bse_spectrum_tensor(int32_t n, const bse_c128* Z, const bse_c128* L, int64_t ld,
+                        const bse_c128* D, int64_t ldd, double c_q, double vc, int32_t n_omega,
+                        const double* omega, double delta, const double* E, bse_c128* eps_out,
+                        void* cuda_stream);
+
+/* Electron energy-loss function L(w) = -Im 1/eps_M(w) (Eq. Lofeps) and the
+ * dynamical structure factor S(Q, w) = -(1/pi) v_G(q)^{-1} Im 1/eps_M(q, w)
+ * from eps [n_omega] (complex, e.g. bse_spectrum's eps_out).  v_inv =
+ * |G+q|^2 / (4 pi), the inverse Coulomb potential of the momentum loss.
+ * loss_out, sqw_out: [n_omega] doubles, either may be NULL (not both).
+ * Device pointers; asynchronous.  Errors: BSE_ERR_ARG, BSE_ERR_CUDA. */
+int bse_loss_function(int32_t n_omega, const bse_c128* eps, double v_inv, double* loss_out,
+                      double* sqw_out, void* cuda_stream);
+
 /* Per-phase timing for measurement.  bse_phase_timing(1) makes the library
  * record a CUDA event pair on the launching stream around each of its
  * phases (one or more kernels, or one cuSOLVER / cuBLAS call);

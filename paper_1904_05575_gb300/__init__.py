@@ -59,7 +59,7 @@ EXPORTED = ("bse_build_kernel", "bse_reduce", "bse_spectrum", "bse_last_error", 
             "bse_mlp_set_params", "bse_mlp_samples", "bse_mlp_loss_grad", "bse_mlp_train",
             "bse_mlp_predict", "bse_xpy", "bse_mlp_trajectory_samples", "bse_plan_create",
             "bse_plan_execute", "bse_plan_status", "bse_plan_tile_cols", "bse_plan_destroy",
-            "bse_plan_fused")
+            "bse_plan_fused", "bse_spectrum_tensor", "bse_loss_function")
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -75,6 +75,11 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.bse_build_kernel.argtypes = [ctypes.POINTER(bse_problem), i32, i32, vp]
     lib.bse_reduce.argtypes = [i32, vp, vp, i64, vp, vp, ctypes.POINTER(i32), vp]
     lib.bse_spectrum.argtypes = [i32, vp, vp, i64, vp, dbl, dbl, i32, vp, dbl, vp, vp, vp, vp]
+    lib.bse_spectrum_tensor.argtypes = [i32, vp, vp, i64, vp, i64, dbl, dbl, i32, vp, dbl, vp, vp,
+                                        vp]
+    lib.bse_spectrum_tensor.restype = ctypes.c_int
+    lib.bse_loss_function.argtypes = [i32, vp, dbl, vp, vp, vp]
+    lib.bse_loss_function.restype = ctypes.c_int
     lib.bse_last_error.restype = ctypes.c_char_p
     lib.bse_kernel_launches.restype = ctypes.c_int64
     lib.bse_build_kernel_fp64_static.argtypes = [ctypes.POINTER(bse_problem), vp]
@@ -226,6 +231,34 @@ def bse_spectrum(n: int, S, L, rho, c_q: float, vc: float, omega, delta: float,
                             float(delta), _ptr(E_out, torch.float64, "E_out"),
                             _ptr(osc_out, torch.float64, "osc_out"),
                             _ptr(eps_out, torch.complex128, "eps_out"), _stream(stream)))
+
+
+def bse_spectrum_tensor(n: int, Z, L, D, c_q: float, vc: float, omega, delta: float, E,
+                        eps_out, stream=None) -> None:
+    """Cartesian dielectric tensor eps_out [n_omega, 3, 3] from bse_spectrum's
+    eigenvectors Z (its S after the call), L and energies E; D [3, n] holds the
+    three directions' matrix elements (row i = direction i)."""
+    import torch
+    lib = load()
+    z, ld = _matrix_ptr(Z, n, "Z")
+    l, _ = _matrix_ptr(L, n, "L")
+    if tuple(D.shape) != (3, n) or not D.is_contiguous():
+        raise ValueError("D must be a contiguous [3, n] tensor")
+    n_omega = omega.numel()
+    if tuple(eps_out.shape) != (n_omega, 3, 3) or not eps_out.is_contiguous():
+        raise ValueError("eps_out must be a contiguous [n_omega, 3, 3] tensor")
+    _check(lib.bse_spectrum_tensor(n, z, l, ld, _ptr(D, torch.complex128, "D"), n, float(c_q),
+                                   float(vc), n_omega, _ptr(omega, torch.float64, "omega"),
+                                   float(delta), _ptr(E, torch.float64, "E"),
+                                   _ptr(eps_out, torch.complex128, "eps_out"), _stream(stream)))
+
+
+def bse_loss_function(eps, v_inv: float, loss_out=None, sqw_out=None, stream=None) -> None:
+    """Loss function -Im 1/eps and S(Q, w) = v_inv L / pi for eps [n_omega]."""
+    import torch
+    _check(load().bse_loss_function(eps.numel(), _ptr(eps, torch.complex128, "eps"), float(v_inv),
+                                    _ptr(loss_out, torch.float64, "loss_out"),
+                                    _ptr(sqw_out, torch.float64, "sqw_out"), _stream(stream)))
 
 
 def bse_lowest_excitons(n: int, A, B, nev: int, E_out, XpY_out=None, tol_ev: float = 1e-4,

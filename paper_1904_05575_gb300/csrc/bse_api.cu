@@ -246,6 +246,33 @@ extern "C" int bse_reduce(int32_t n, const bse_c128* A, const bse_c128* B, int64
   });
 }
 
+extern "C" int bse_spectrum_tensor(int32_t n, const bse_c128* Z, const bse_c128* L, int64_t ld,
+                                   const bse_c128* D, int64_t ldd, double c_q, double vc,
+                                   int32_t n_omega, const double* omega, double delta,
+                                   const double* E, bse_c128* eps_out, void* cuda_stream) {
+  return guarded([&] {
+    BSE_CHECK_ARG(n >= 1 && ld >= n && ldd >= n, "need n >= 1, ld >= n and ldd >= n");
+    BSE_CHECK_ARG(Z && L && D && E, "NULL Z, L, D or E");
+    BSE_CHECK_ARG(n_omega >= 0 && (n_omega == 0 || (omega && eps_out)), "need omega and eps_out");
+    BSE_CHECK_ARG(std::isfinite(delta) && delta > 0.0, "delta must be > 0");
+    BSE_CHECK_ARG(std::isfinite(vc) && vc > 0.0, "vc must be > 0");
+    keep_pool_memory();
+    spectrum_tensor_fp64(n, Z, L, ld, D, ldd, c_q, vc, n_omega, omega, delta, E, eps_out,
+                         static_cast<cudaStream_t>(cuda_stream));
+  });
+}
+
+extern "C" int bse_loss_function(int32_t n_omega, const bse_c128* eps, double v_inv,
+                                 double* loss_out, double* sqw_out, void* cuda_stream) {
+  return guarded([&] {
+    BSE_CHECK_ARG(n_omega >= 0, "n_omega must be >= 0");
+    BSE_CHECK_ARG(n_omega == 0 || eps, "NULL eps");
+    BSE_CHECK_ARG(loss_out || sqw_out, "need loss_out or sqw_out");
+    BSE_CHECK_ARG(std::isfinite(v_inv), "v_inv must be finite");
+    loss_fp64(n_omega, eps, v_inv, loss_out, sqw_out, static_cast<cudaStream_t>(cuda_stream));
+  });
+}
+
 extern "C" int bse_spectrum(int32_t n, bse_c128* S_inout, const bse_c128* L, int64_t ld,
                             const bse_c128* rho, double c_q, double vc, int32_t n_omega,
                             const double* omega, double delta, double* E_out, double* osc_out,

@@ -145,6 +145,12 @@ void reduce_fp64(int n, const bse_c128* A, const bse_c128* B, int64_t ld, bse_c1
                  bse_c128* L, int32_t* failed_minor, cudaStream_t stream);
 void xpy_fp64(int n, int k, const bse_c128* Z, const bse_c128* L, int64_t ld, const double* E,
               bse_c128* XpY, int64_t ldx, cudaStream_t stream);
+void spectrum_tensor_fp64(int n, const bse_c128* Z, const bse_c128* L, int64_t ld,
+                          const bse_c128* D, int64_t ldd, double c_q, double vc, int n_omega,
+                          const double* omega, double delta, const double* E, bse_c128* eps_out,
+                          cudaStream_t s);
+void loss_fp64(int n_omega, const bse_c128* eps, double v_inv, double* loss_out, double* sqw_out,
+               cudaStream_t s);
 void spectrum_fp64(int n, bse_c128* S, const bse_c128* L, int64_t ld, const bse_c128* rho,
                    double c_q, double vc, int n_omega, const double* omega, double delta,
                    double* E_out, double* osc_out, bse_c128* eps_out, cudaStream_t stream);

@@ -317,4 +317,132 @@ void spectrum_fp64(int n, bse_c128* S, const bse_c128* L, int64_t ld, const bse_
     throw Error(BSE_ERR_NOT_PD, "an eigenvalue E^2 <= 0: A+B is not positive definite");
 }
 
+
+// ---------------------------------------------------------------------------
+// Cartesian dielectric tensor (Eq. epsmij) and loss function (Eq. Lofeps)
+// ---------------------------------------------------------------------------
+namespace {
+
+// u[lambda][i] = sum_j Z_{j lambda} r_i[j] for the three directions (r_i =
+// L^T D_i), one warp per lambda; with X+Y = L Z E^{-1/2} this is
+// E^{1/2} sum_alpha (X+Y)_{alpha lambda} D_{alpha i}, so that the coefficient
+// t*_{lambda i} t_{lambda j} of Eq. tlambdai is u_i conj(u_j) / (E vc)
+__global__ void k_tensor_u(int n, const double2* Z, int64_t ld, const double2* r, double2* u) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const double2* col = Z + (int64_t)warp * ld;
+  double sx[3] = {0, 0, 0}, sy[3] = {0, 0, 0};
+  for (int j = lane; j < n; j += 32) {
+    const double2 z = col[j];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const double2 q = r[(int64_t)i * n + j];
+      sx[i] = fma(z.x, q.x, fma(-z.y, q.y, sx[i]));
+      sy[i] = fma(z.x, q.y, fma(z.y, q.x, sy[i]));
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    sx[i] = warp_sum(sx[i]);
+    sy[i] = warp_sum(sy[i]);
+    if (lane == 0) u[(int64_t)warp * 3 + i] = make_double2(sx[i], sy[i]);
+  }
+}
+
+// eps^{ij}(w) = delta_ij - pref sum_l u_i conj(u_j) / (E_l vc) [1/(w - E_l + i d)
+// - 1/(w + E_l + i d)], one block per w; 9 complex sums reduced per block
+__global__ void __launch_bounds__(256) k_eps_tensor(int n, const double* e, const double2* u,
+                                                    double vc, int n_omega, const double* omega,
+                                                    double delta, double pref, double2* eps) {
+  __shared__ double red[18][8];
+  const int iw = blockIdx.x;
+  if (iw >= n_omega) return;
+  const double w = omega[iw], d2 = delta * delta;
+  double acc[18];
+#pragma unroll
+  for (int q = 0; q < 18; ++q) acc[q] = 0.0;
+  for (int l = threadIdx.x; l < n; l += blockDim.x) {
+    const double el = e[l];
+    const double a = w - el, b = w + el;
+    const double ia = 1.0 / (a * a + d2), ib = 1.0 / (b * b + d2);
+    const double fx = (a * ia - b * ib) / (el * vc), fy = (-delta * ia + delta * ib) / (el * vc);
+    double2 ui[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) ui[i] = u[(int64_t)l * 3 + i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        // c = u_i conj(u_j); c * f
+        const double cx = ui[i].x * ui[j].x + ui[i].y * ui[j].y;
+        const double cy = ui[i].y * ui[j].x - ui[i].x * ui[j].y;
+        acc[2 * (3 * i + j)] += cx * fx - cy * fy;
+        acc[2 * (3 * i + j) + 1] += cx * fy + cy * fx;
+      }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < 18; ++q) {
+    const double v = warp_sum(acc[q]);
+    if (lane == 0) red[q][wid] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 18) {
+    double v = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) v += red[threadIdx.x][k];
+    red[threadIdx.x][0] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 9) {
+    const int i = threadIdx.x / 3, j = threadIdx.x % 3;
+    eps[(int64_t)iw * 9 + threadIdx.x] =
+        make_double2((i == j ? 1.0 : 0.0) - pref * red[2 * threadIdx.x][0],
+                     -pref * red[2 * threadIdx.x + 1][0]);
+  }
+}
+
+// L = -Im 1/eps = Im eps / |eps|^2; S = v_inv L / pi
+__global__ void k_loss(int n_omega, const double2* eps, double v_inv, double* loss, double* sqw) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_omega) return;
+  const double2 e = eps[i];
+  const double l = e.y / (e.x * e.x + e.y * e.y);
+  if (loss) loss[i] = l;
+  if (sqw) sqw[i] = v_inv * l / 3.14159265358979323846;
+}
+
+}  // namespace
+
+void spectrum_tensor_fp64(int n, const bse_c128* Z, const bse_c128* L, int64_t ld,
+                          const bse_c128* D, int64_t ldd, double c_q, double vc, int n_omega,
+                          const double* omega, double delta, const double* E, bse_c128* eps_out,
+                          cudaStream_t s) {
+  DeviceBuffer r((size_t)3 * n * sizeof(bse_c128), s);
+  DeviceBuffer u((size_t)3 * n * sizeof(bse_c128), s);
+  const int warps_per_block = 8;
+  const int blocks = (n + warps_per_block - 1) / warps_per_block;
+  for (int i = 0; i < 3; ++i)
+    k_lt_rho<<<blocks, 32 * warps_per_block, 0, s>>>(
+        n, reinterpret_cast<const double2*>(L), ld,
+        reinterpret_cast<const double2*>(D) + (int64_t)i * ldd, r.as<double2>() + (int64_t)i * n);
+  k_tensor_u<<<blocks, 32 * warps_per_block, 0, s>>>(n, reinterpret_cast<const double2*>(Z), ld,
+                                                     r.as<double2>(), u.as<double2>());
+  if (n_omega > 0)
+    k_eps_tensor<<<n_omega, 256, 0, s>>>(n, E, u.as<double2>(), vc, n_omega, omega, delta,
+                                         c_q * kHartreeEv, reinterpret_cast<double2*>(eps_out));
+  BSE_CUDA(cudaGetLastError());
+  note_launches(n_omega > 0 ? 5 : 4);
+  BSE_CUDA(cudaStreamSynchronize(s));   // r, u are stream-ordered workspace
+}
+
+void loss_fp64(int n_omega, const bse_c128* eps, double v_inv, double* loss_out, double* sqw_out,
+               cudaStream_t s) {
+  if (n_omega <= 0) return;
+  k_loss<<<(n_omega + 255) / 256, 256, 0, s>>>(n_omega, reinterpret_cast<const double2*>(eps),
+                                               v_inv, loss_out, sqw_out);
+  BSE_CUDA(cudaGetLastError());
+  note_launches(1);
+}
+
 }  // namespace bse
