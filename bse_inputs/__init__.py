@@ -311,14 +311,59 @@ def _hermitian_pair_torch(nk, nb, ng, damp, gen, device):
     return x
 
 
+def pair_slab_torch(cfg: BSEConfig | str, k_begin: int, k_count: int, q_index: int = 0,
+                    seed: int = 20190411, device="cuda"):
+    """m_vv and m_cc for the k rows [k_begin, k_begin + k_count) only, drawn on
+    a torch device: ([k_count, nk, nv, nv, ng], [k_count, nk, nc, nc, ng]).
+
+    For problems whose pair arrays exceed the device memory (hundreds of GB),
+    built a slab of k rows at a time.  Each block (k, k') with k <= k' is drawn
+    from its own stream keyed by (seed, array, Q, k, k'); a block with k > k'
+    is the conjugate transpose (b <-> b') of block (k', k), and a diagonal block
+    is Hermitian in (b, b') with a real diagonal.  So S3 holds across slabs and
+    any slab is reproducible on its own (the numbers differ from those of
+    make_problem_torch's whole arrays)."""
+    import torch
+    if isinstance(cfg, str):
+        cfg = CONFIGS[cfg]
+    nk, ng = cfg.nk, cfg.ng
+    nv, nc = cfg.window(q_index)
+    gvec = reciprocal_vectors(ng)
+    damp = torch.as_tensor(1.0 / (1.0 + cfg.m_decay * (gvec ** 2).sum(1)), device=device)
+    gen = torch.Generator(device=device)
+    out = []
+    for name, nb in (("m_vv", nv), ("m_cc", nc)):
+        x = torch.empty((k_count, nk, nb, nb, ng), dtype=torch.complex128, device=device)
+        iu = torch.triu_indices(nb, nb, 1, device=device)
+        d = torch.arange(nb, device=device)
+        for r in range(k_count):
+            k = k_begin + r
+            for kp in range(nk):
+                lo, hi = (k, kp) if k <= kp else (kp, k)
+                gen.manual_seed(_key(seed, name, q_index, lo, hi, "slab") % (1 << 62))
+                blk = torch.randn((nb, nb, ng), dtype=torch.complex128, device=device, generator=gen)
+                blk *= damp
+                if k == kp:
+                    blk[iu[1], iu[0]] = blk[iu[0], iu[1]].conj()
+                    blk[d, d] = blk[d, d].real.to(torch.complex128)
+                elif k > kp:
+                    blk = blk.transpose(0, 1).conj()
+                x[r, kp] = blk
+        out.append(x)
+    return tuple(out)
+
+
 def make_problem_torch(cfg: BSEConfig | str, q_index: int = 0, seed: int = 20190411,
-                       device="cuda") -> Dict:
+                       device="cuda", k_slab: Optional[Tuple[int, int]] = None) -> Dict:
     """Draw a full-size problem directly on a torch device, for shapes whose
     inputs are too large to draw on the host (tens of GB).  Same recipe as
     make_problem (distributions, damping, W(q) construction, symmetries S1-S4,
     pair maps, v_bar, rho), but the numbers come from torch's generator, so
     they differ from make_problem's; a check copies the blocks it needs back
-    to the host.  Array entries are torch tensors on `device`."""
+    to the host.  Array entries are torch tensors on `device`.
+
+    k_slab = (k_begin, k_count) draws m_vv and m_cc for those k rows only
+    (pair_slab_torch); every other array is whole."""
     import torch
     if isinstance(cfg, str):
         cfg = CONFIGS[cfg]
@@ -339,8 +384,11 @@ def make_problem_torch(cfg: BSEConfig | str, q_index: int = 0, seed: int = 20190
     m_x = torch.randn((nk, nv, nc, ng), dtype=torch.complex128, device=device,
                       generator=_torch_gen(device, seed, "m_x", q_index, "torch"))
     m_x *= damp
-    m_vv = _hermitian_pair_torch(nk, nv, ng, damp, _torch_gen(device, seed, "m_vv", q_index, "torch"), device)
-    m_cc = _hermitian_pair_torch(nk, nc, ng, damp, _torch_gen(device, seed, "m_cc", q_index, "torch"), device)
+    if k_slab is None:
+        m_vv = _hermitian_pair_torch(nk, nv, ng, damp, _torch_gen(device, seed, "m_vv", q_index, "torch"), device)
+        m_cc = _hermitian_pair_torch(nk, nc, ng, damp, _torch_gen(device, seed, "m_cc", q_index, "torch"), device)
+    else:
+        m_vv, m_cc = pair_slab_torch(cfg, k_slab[0], k_slab[1], q_index, seed, device)
     n_vc = torch.randn((nk, nk, nv, nc, ng), dtype=torch.complex128, device=device,
                        generator=_torch_gen(device, seed, "n_vc", q_index, "torch"))
     n_vc *= damp

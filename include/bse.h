@@ -89,7 +89,17 @@ typedef enum {
  *                             w[q_minus[k][k']][G][G'] m_cc[k][k'][c][c'][G']   (Eq. wrrm)
  *      W^ra_{(kvc)(k'v'c')} = kappa sum_GG' conj(n_vc[k'][k][v'][c][G])
  *                             w[q_plus[k][k']][G][G'] n_vc[k][k'][v][c'][G']    (Eq. wrabar)
- * B is not touched when coupling == 0 (Tamm-Dancoff, Eq. tdaevp) and may be NULL. */
+ * B is not touched when coupling == 0 (Tamm-Dancoff, Eq. tdaevp) and may be NULL.
+ *
+ * k-row slabs (k_begin, k_count; both 0 = the whole problem).  With k_count > 0
+ * only the rows (k v c) of A and B with k_begin <= k < k_begin + k_count are
+ * written (every column); all other rows are left as they are.  m_vv and m_cc
+ * then hold only those k rows, [k_count][nk][..][..][ng] with row 0 = k_begin,
+ * so a problem whose pair arrays exceed the device memory is built slab by slab
+ * (the terms of Eqs. vrrofM, wrrm, wrabar are sums over independent (k, k')
+ * blocks).  n_vc stays whole: W^ra of row k reads n_vc[k'][k] for every k'.
+ * e_v, e_c, m_x, w, q_minus, q_plus, v_bar, A and B keep their full shapes.
+ * Requires 0 <= k_begin, k_begin + k_count <= nk; else BSE_ERR_ARG. */
 typedef struct {
   int32_t nk, nv, nc, ng, nq_w;
   double omega_cell;                  /* Omega in bohr^3; V_c = nk * Omega */
@@ -101,6 +111,7 @@ typedef struct {
   const double *v_bar;
   bse_c128 *A, *B;
   int64_t ld;
+  int32_t k_begin, k_count;           /* k-row slab; 0, 0 = all rows */
 } bse_problem;
 
 /* Build A and B for nprob independent momentum transfers (each Q is its own

@@ -47,6 +47,7 @@ class bse_problem(ctypes.Structure):
         ("q_minus", ctypes.c_void_p), ("q_plus", ctypes.c_void_p),
         ("v_bar", ctypes.c_void_p),
         ("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("ld", ctypes.c_int64),
+        ("k_begin", ctypes.c_int32), ("k_count", ctypes.c_int32),
     ]
 
 
@@ -164,11 +165,24 @@ def _matrix_ptr(t, n, name):
 
 
 def make_problem_struct(d: Dict, gamma_x: float = 1.0, gamma_c: float = 1.0,
-                        coupling: bool = True) -> bse_problem:
-    """bse_problem from a dict of CUDA tensors (see upload_problem) and outputs A, B."""
+                        coupling: bool = True, k_begin: int = 0,
+                        k_count: int = 0) -> bse_problem:
+    """bse_problem from a dict of CUDA tensors (see upload_problem) and outputs A, B.
+
+    k_count > 0 builds only the rows k_begin <= k < k_begin + k_count of A and
+    B; m_vv and m_cc then hold only those k rows ([k_count, nk, ...]) while
+    n_vc stays whole ([nk, nk, ...])."""
     import torch
     c128, f64, i32 = torch.complex128, torch.float64, torch.int32
     n = d["nk"] * d["nv"] * d["nc"]
+    nk = d["nk"]
+    kn = k_count if k_count > 0 else nk
+    if not (0 <= k_begin and k_count >= 0 and k_begin + k_count <= nk and (k_count > 0 or k_begin == 0)):
+        raise ValueError(f"k-row slab [{k_begin}, {k_begin + k_count}) outside [0, {nk})")
+    for name, rows in (("m_vv", kn), ("m_cc", kn), ("n_vc", nk)):
+        t = d.get(name)
+        if t is not None and (name != "n_vc" or coupling) and tuple(t.shape[:2]) != (rows, nk):
+            raise ValueError(f"{name} must have leading shape ({rows}, {nk}), got {tuple(t.shape[:2])}")
     a_ptr, ld = _matrix_ptr(d["A"], n, "A")
     b_ptr = None
     if coupling:
@@ -185,7 +199,8 @@ def make_problem_struct(d: Dict, gamma_x: float = 1.0, gamma_c: float = 1.0,
         n_vc=_ptr(d["n_vc"], c128, "n_vc") if coupling else None,
         w=_ptr(d["w"], c128, "w"), q_minus=_ptr(d["q_minus"], i32, "q_minus"),
         q_plus=_ptr(d["q_plus"], i32, "q_plus") if coupling else None,
-        v_bar=_ptr(d["v_bar"], f64, "v_bar"), A=a_ptr, B=b_ptr, ld=ld)
+        v_bar=_ptr(d["v_bar"], f64, "v_bar"), A=a_ptr, B=b_ptr, ld=ld,
+        k_begin=int(k_begin), k_count=int(k_count))
 
 
 def bse_build_kernel(problems: Sequence[bse_problem], precision: int = BSE_PREC_FP64,

@@ -125,6 +125,10 @@ Problem validate(const bse_problem& p, int index, cudaStream_t s) {
   BSE_CHECK_ARG(std::isfinite(p.gamma_x) && std::isfinite(p.gamma_c),
                 at + "gamma_x and gamma_c must be finite");
   BSE_CHECK_ARG(p.coupling == 0 || p.coupling == 1, at + "coupling must be 0 or 1");
+  BSE_CHECK_ARG(p.k_begin >= 0 && p.k_count >= 0 && (int64_t)p.k_begin + p.k_count <= p.nk &&
+                    (p.k_count > 0 || p.k_begin == 0),
+                at + "k-row slab [k_begin, k_begin + k_count) must lie in [0, nk) "
+                     "(k_begin = k_count = 0: the whole problem)");
   BSE_CHECK_ARG(p.e_v && p.e_c && p.m_x && p.v_bar && p.A, at + "NULL e_v, e_c, m_x, v_bar or A");
   if (p.gamma_c != 0.0) {
     BSE_CHECK_ARG(p.m_vv && p.m_cc && p.w && p.q_minus, at + "NULL m_vv, m_cc, w or q_minus");
@@ -148,6 +152,8 @@ Problem validate(const bse_problem& p, int index, cudaStream_t s) {
   pr.p = p;
   pr.n = n;
   pr.kappa = kHartreeEv / ((double)p.nk * p.omega_cell);
+  pr.kb = p.k_begin;
+  pr.kn = p.k_count > 0 ? p.k_count : p.nk;
   return pr;
 }
 

@@ -88,7 +88,11 @@ struct Problem {
   bse_problem p;
   int64_t n;          // nk * nv * nc
   double kappa;       // Ha / (nk * omega_cell)
-  std::vector<int32_t> qm_host, qp_host;   // host copies of q_minus / q_plus (checked)
+  std::vector<int32_t> qm_host, qp_host;   // host copies of q_minus / q_plus (checked, whole)
+  int kb = 0, kn = 0; // k-row slab [kb, kb + kn) (kn = nk for the whole problem)
+  int64_t rows() const { return (int64_t)kn * p.nv * p.nc; }        // rows of A, B written
+  int64_t row0() const { return (int64_t)kb * p.nv * p.nc; }        // first of them
+  int64_t slab_pairs() const { return (int64_t)kn * p.nk; }         // (k, k') with k in the slab
 };
 
 // FP64 build (CUDA cores).  Writes A (and B when coupling) completely.

@@ -268,6 +268,7 @@ struct S2TcParams {
   double2* out;
   int64_t ld;
   int nk, nvnc;     // k points; Nv * Nc
+  int k_begin;      // first k row of the slab (pair = (k - k_begin) nk + k')
   float scale;
   int rows_r;       // rows per pair of the side that forms the tile rows
   int row_nb;       // tile rows stored (b', b) for a side indexed (b, b') (0: as stored)
@@ -286,7 +287,7 @@ struct S2TcEpi {
     const int pair = rg / q.rows_r;
     int ir = rg - pair * q.rows_r;
     if (q.row_nb) ir = (ir % q.row_nb) * q.row_nb + ir / q.row_nb;
-    const int k = pair / q.nk, kp = pair - k * q.nk;
+    const int kl = pair / q.nk, kp = pair - kl * q.nk, k = q.k_begin + kl;
     const int ar = ir / q.nb_r, br = ir - ar * q.nb_r;
     double2* base = q.out + (int64_t)k * q.nvnc + (int64_t)kp * q.nvnc * q.ld + ar * q.ra + br * q.rb;
     const int jc0 = t.n0 + c0;
@@ -330,14 +331,15 @@ enum Stage2Mode { S2_RR_CC = 0, S2_RR_VV = 1, S2_RA = 2 };
 
 struct Stage2Args {
   int mode;
-  const double2* x;      // complex128 pair array, [nk][nk][rows_x][ng]
-  int x_transpose_pair;  // read X of pair (k', k) (W^ra)
+  const double2* x;      // complex128 pair array, [slab pairs][rows_x][ng] ([nk][nk].. when transposed)
+  int x_transpose_pair;  // read X of pair (k', k) (W^ra) from the whole array
   int conj_x, conj_t;
   const float2* T;
   int64_t t_ld;
   const int* slot_of_pair;
   int rows_x, rows_t, ng, nk, nv, nc;
   int64_t t_row0 = 0;    // first T row of this term (batched plans)
+  int k_begin = 0;       // first k row of the slab: pair p = (k - k_begin) nk + k'
   double scale;          // gamma_c kappa
   double2* out;          // A or B
   int64_t ld;
@@ -350,7 +352,7 @@ __global__ void __launch_bounds__((TS / R) * (TS / R)) k_stage2(Stage2Args a) {
   __shared__ float2 Xs[TS][GC + 1];
   __shared__ float2 Ts[GC][TS + 1];
   const int p = blockIdx.x;
-  const int k = p / a.nk, kp = p % a.nk;
+  const int k = a.k_begin + p / a.nk, kp = p % a.nk;
   const int rx0 = blockIdx.y * TS, rt0 = blockIdx.z * TS;
   const int64_t xp = a.x_transpose_pair ? (int64_t)kp * a.nk + k : (int64_t)p;
   const double2* X = a.x + xp * a.rows_x * a.ng;
@@ -480,7 +482,7 @@ __global__ void __launch_bounds__(256) k_stage2_pipe(Stage2Args a) {
   __shared__ __align__(16) float2 Tr[2][GC][16];     // FP32 complex
   __shared__ float2 Xs[16][GC + 1];                  // converted X of the current chunk
   const int p = blockIdx.x;
-  const int k = p / a.nk, kp = p % a.nk;
+  const int k = a.k_begin + p / a.nk, kp = p % a.nk;
   const int64_t xp = a.x_transpose_pair ? (int64_t)kp * a.nk + k : (int64_t)p;
   const uint4* X = reinterpret_cast<const uint4*>(a.x) + xp * a.rows_x * a.ng;
   const int64_t trow0 = a.t_row0 + (int64_t)a.slot_of_pair[p] * a.rows_t;
@@ -922,7 +924,7 @@ void plan_splits(BatchPlan& pl, cudaStream_t s) {
   }
   for (BatchPlan::Term& t : pl.terms) {
     const bse_problem& p = pl.probs[t.prob].p;
-    const int npair = p.nk * p.nk;
+    const int npair = (int)pl.probs[t.prob].slab_pairs();
     SplitArgs sw{reinterpret_cast<const double2*>(p.w), SPLIT_W, nullptr, pl.ng_pad,
                  t.w_conj_transpose ? 1 : 0, pl.ng, pl.Kp, p.nq_w * pl.ng_pad, pl.pieces,
                  t.w_conj_transpose ? 1 : 0, nullptr, pl.wsplit.as<__nv_bfloat16>(), pl.w_rows,
@@ -972,8 +974,7 @@ void plan_execute_mixed(BatchPlan& pl, cudaStream_t s) {
     Phase ph("mixed_stage2", s);
     for (BatchPlan::Term& t : pl.terms) {
       if (t.tc2) continue;
-      const bse_problem& p = pl.probs[t.prob].p;
-      launch_stage2(t.s2, p.nk * p.nk, s);
+      launch_stage2(t.s2, (int)pl.probs[t.prob].slab_pairs(), s);
     }
   }
   if (pl.n_s2tiles || pl.n_s2tiles_t) {
@@ -1106,20 +1107,24 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
     pl->nt_x = cand;
     full = 0;
     for (const Problem& pr : pl->probs)
-      full += (int64_t)((pr.n + tc::BM - 1) / tc::BM) * ((pr.n + cand - 1) / cand);
+      full += (int64_t)((pr.rows() + tc::BM - 1) / tc::BM) * ((pr.n + cand - 1) / cand);
     if (full >= sms) break;
   }
-  const int tri = full >= 2 * sms ? 1 : 0;
+  const int tri_all = full >= 2 * sms ? 1 : 0;
   for (size_t i = 0; i < pl->probs.size(); ++i) {
-    const bse_problem& p = pl->probs[i].p;
-    const int n = (int)pl->probs[i].n;
+    const Problem& pr = pl->probs[i];
+    const bse_problem& p = pr.p;
+    const int n = (int)pr.n;
+    // a k-row slab computes its own rows of V for every column (no mirror)
+    const int tri = tri_all && pr.kn == p.nk;
+    const int r0 = (int)pr.row0(), r1 = (int)(pr.row0() + pr.rows());
     pl->x_row0.push_back(pl->x_rows);
-    for (int m0 = 0; m0 < n; m0 += tc::BM)
+    for (int m0 = r0; m0 < r1; m0 += tc::BM)
       for (int n0 = 0; n0 < n && (!tri || n0 < m0 + tc::BM); n0 += pl->nt_x)
-        xt.push_back({(int)(pl->x_rows + m0), std::min(tc::BM, n - m0), (int)(pl->x_rows + n0), n0,
+        xt.push_back({(int)(pl->x_rows + m0), std::min(tc::BM, r1 - m0), (int)(pl->x_rows + n0), n0,
                       std::min(pl->nt_x, n - n0), m0, (int)i});
     xp.push_back({reinterpret_cast<double2*>(p.A), p.coupling ? reinterpret_cast<double2*>(p.B) : nullptr,
-                  p.ld, (float)(2.0 * p.gamma_x * pl->probs[i].kappa), p.e_v, p.e_c, p.nv, p.nc, tri});
+                  p.ld, (float)(2.0 * p.gamma_x * pr.kappa), p.e_v, p.e_c, p.nv, p.nc, tri});
     pl->x_rows += n;
   }
   pl->xa = DevMem((size_t)pl->planes * pl->x_rows * pl->Kp * 2);
@@ -1136,7 +1141,9 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
     const Problem& pr = pl->probs[i];
     const bse_problem& p = pr.p;
     if (p.gamma_c == 0.0) continue;
-    const int nv = p.nv, nc = p.nc, npair = p.nk * p.nk;
+    // pairs (k, k') of the slab's rows, p = (k - kb) nk + k'
+    const int nv = p.nv, nc = p.nc, npair = (int)pr.slab_pairs();
+    const int64_t pair_off = (int64_t)pr.kb * p.nk;   // first slab pair in the whole arrays
     const bool cc_side = nc * nc <= nv * nv;
     for (int term = 0; term < (p.coupling ? 2 : 1); ++term) {
       BatchPlan::Term t;
@@ -1146,7 +1153,7 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
         t.rows_side = cc_side ? nc * nc : nv * nv;
         t.side = cc_side ? p.m_cc : p.m_vv;
         t.w_conj_transpose = !cc_side;
-        t.qh = pr.qm_host;
+        t.qh.assign(pr.qm_host.begin() + pair_off, pr.qm_host.begin() + pair_off + npair);
         a.mode = cc_side ? S2_RR_CC : S2_RR_VV;
         a.x = reinterpret_cast<const double2*>(cc_side ? p.m_vv : p.m_cc);
         a.x_transpose_pair = 0;
@@ -1156,9 +1163,9 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
         a.out = reinterpret_cast<double2*>(p.A);
       } else {
         t.rows_side = nv * nc;
-        t.side = p.n_vc;
+        t.side = p.n_vc + pair_off * nv * nc * p.ng;   // the slab's rows of the whole n_vc
         t.w_conj_transpose = false;
-        t.qh = pr.qp_host;
+        t.qh.assign(pr.qp_host.begin() + pair_off, pr.qp_host.begin() + pair_off + npair);
         a.mode = S2_RA;
         a.x = reinterpret_cast<const double2*>(p.n_vc);
         a.x_transpose_pair = 1;
@@ -1181,6 +1188,7 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
       a.slot_of_pair = t.slot.as<int>();
       a.ng = ng;
       a.nk = p.nk;
+      a.k_begin = pr.kb;
       a.nv = nv;
       a.nc = nc;
       a.scale = p.gamma_c * pr.kappa;
@@ -1203,9 +1211,10 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
       std::vector<CUtensorMap> maps;
       for (const BatchPlan::Term& t : pl->terms) {
         const Stage2Args& a = t.s2;
-        const bse_problem& p = pl->probs[t.prob].p;
+        const Problem& pr = pl->probs[t.prob];
+        const int64_t x_pairs = a.x_transpose_pair ? (int64_t)pr.p.nk * pr.p.nk : pr.slab_pairs();
         CUtensorMap m;
-        cuuint64_t dims[2] = {(cuuint64_t)2 * a.ng, (cuuint64_t)p.nk * p.nk * a.rows_x};
+        cuuint64_t dims[2] = {(cuuint64_t)2 * a.ng, (cuuint64_t)(x_pairs * a.rows_x)};
         cuuint64_t strides[1] = {(cuuint64_t)a.ng * 16};
         cuuint32_t box[2] = {(cuuint32_t)(2 * tc::S2_GB), (cuuint32_t)a.rows_x};
         cuuint32_t estr[2] = {1, 1};
@@ -1229,6 +1238,7 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
         x.rows_x = a.rows_x;
         x.rows_t = a.rows_t;
         x.nk = a.nk;
+        x.k_begin = a.k_begin;
         x.nv = a.nv;
         x.nc = a.nc;
         x.ng = a.ng;
@@ -1295,7 +1305,7 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
           } else {
             nb_x = a.nc; xa = nc * ld; xb = 1; nb_t = a.nc; ta = nc; tb = ld;
           }
-          S2TcParams q{a.out, a.ld, a.nk, a.nv * a.nc, (float)a.scale, 0, 0, 0, 0, 0, 0, 0, 0};
+          S2TcParams q{a.out, a.ld, a.nk, a.nv * a.nc, a.k_begin, (float)a.scale, 0, 0, 0, 0, 0, 0, 0, 0};
           if (t.rows_t_side) {
             q.rows_r = a.rows_t; q.row_nb = t.side_nb;
             q.nb_r = nb_t; q.ra = ta; q.rb = tb; q.nb_c = nb_x; q.ca = xa; q.cb = xb;
@@ -1305,10 +1315,10 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
           }
           prm.push_back(q);
           if (!t.tc2) continue;
-          const int npair = a.nk * a.nk;
+          const int npair = (int)pl->probs[t.prob].slab_pairs();
           std::vector<int> xp(npair);
-          for (int pr = 0; pr < npair; ++pr)
-            xp[pr] = a.x_transpose_pair ? (pr % a.nk) * a.nk + pr / a.nk : pr;
+          for (int pr = 0; pr < npair; ++pr)   // (k', k) of the whole array, k = k_begin + pr / nk
+            xp[pr] = a.x_transpose_pair ? (pr % a.nk) * a.nk + a.k_begin + pr / a.nk : pr;
           t.x2perm = upload_mem(xp);
           t.x2_row0 = pl->x2_rows;
           pl->x2_rows += (int64_t)npair * a.rows_x;
@@ -1431,6 +1441,7 @@ std::vector<uint64_t> plan_key(const std::vector<Problem>& probs, int precision)
     k.push_back(bits[1]);
     k.push_back(bits[2]);
     k.push_back((uint64_t)p.ld);
+    k.push_back(((uint64_t)(uint32_t)p.k_begin << 32) | (uint32_t)p.k_count);
     k.push_back(fnv1a(pr.qp_host, fnv1a(pr.qm_host)));
   }
   return k;

@@ -45,13 +45,15 @@ __host__ __device__ constexpr uint32_t s2_pstride(int rx) { return S2_GB * s2_gs
 constexpr uint32_t S2_XF_BYTES = (BM / 4) * s2_pstride(4);
 
 struct S2Term {
-  const CUtensorMap* xmap;   // other pair side, complex128 [nk * nk][rows_x][ng] seen as FP64
-                             // [nk * nk * rows_x][2 ng], box {16, rows_x} (device memory)
-  const int* perm;        // slot -> pair (pairs sorted by q; -1: padding slot, zero rows)
+  const CUtensorMap* xmap;   // other pair side, complex128 [pairs][rows_x][ng] seen as FP64
+                             // [pairs * rows_x][2 ng], box {16, rows_x} (device memory);
+                             // pairs = the slab's (k, k'), or all nk^2 when transposed
+  const int* perm;        // slot -> pair (k - k_begin) nk + k' (sorted by q; -1: padding slot)
   double2* out;           // A (W^rr) or B (W^ra), column-major; NULL: contraction only (timing)
   int64_t ld;
   int64_t a_row0;         // first stage-1 row of this term
   int rows_x, rows_t, nk, nv, nc, ng;
+  int k_begin;            // first k row of the slab
   int mode;               // 0: rx = (v,v'), rt = (c,c'); 1: rx = (c,c'), rt = (v,v'); 2: W^ra
   int x_transpose_pair;   // read the side of pair (k', k)
   int conj_x, conj_t;
@@ -293,7 +295,7 @@ __device__ __forceinline__ bool direct_unit(const EpiCtx& cx, EpiState& st, int 
   const int pair = tm.perm[((int64_t)tg.out_row0 - tm.a_row0) / rows_t + j];
   if (pair < 0) return true;   // padding slot
   const int nk = tm.nk, nv = tm.nv, nc = tm.nc;
-  const int k = pair / nk, kp = pair - k * nk;
+  const int kl = pair / nk, kp = pair - kl * nk, k = tm.k_begin + kl;
   const float sc = tm.scale;
   // groups of 4 outputs: all loads first, then the stores (the loads of a
   // group are independent, so their latencies overlap)
@@ -408,8 +410,8 @@ gemm_split_bf16_direct(const __grid_constant__ CUtensorMap tmA,
         if (j < npairs) {
           const int pair = tm.perm[slot0 + j];
           if (pair >= 0) {   // a padding slot reads pair 0's rows (its T rows are zero)
-            const int k = pair / nk, kp = pair - k * nk;
-            y[i] = (tm.x_transpose_pair ? kp * nk + k : pair) * rows_x;
+            const int kl = pair / nk, kp = pair - kl * nk;
+            y[i] = (tm.x_transpose_pair ? kp * nk + tm.k_begin + kl : pair) * rows_x;
           }
         }
       }

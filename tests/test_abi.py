@@ -64,6 +64,11 @@ def test_host_side_argument_errors(lib):
     arr = (bse.bse_problem * 1)(q)
     assert lib2.bse_build_kernel(arr, 1, 0, None) == bse.BSE_ERR_ARG
     assert b"16-byte" in lib2.bse_last_error()
+    # a k-row slab past nk is refused before any launch
+    r = bse.bse_problem(nk=2, nv=1, nc=1, ng=1, nq_w=1, omega_cell=1.0, ld=2, k_begin=1, k_count=2)
+    arr = (bse.bse_problem * 1)(r)
+    assert lib2.bse_build_kernel(arr, 1, 0, None) == bse.BSE_ERR_ARG
+    assert b"slab" in lib2.bse_last_error()
     assert lib2.bse_reduce(0, None, None, 1, None, None, None, None) == bse.BSE_ERR_ARG
     assert lib2.bse_spectrum(4, None, None, 2, None, 1.0, 1.0, 0, None, 0.1,
                              None, None, None, None) == bse.BSE_ERR_ARG

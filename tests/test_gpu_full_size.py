@@ -11,6 +11,10 @@ interaction terms) are also checked on their own.
   c5  Nk = 64, Nv = Nc = 20, N = 25,600, NG = 500 (strong off-diagonal W), Q = 0
   c3  Nk = 512, NG = 113, two of the 16 Q in one plan: the smallest window
       (2, 2), N = 2,048, and the largest (4, 6), N = 12,288, at |Q| = 0.1 and 1.5
+  c4  Nk = 512, Nv = 2 core levels, Nc = 20, NG = 300, N = 20,480: m_cc alone
+      is 503 GB, so A and B are built in k-row slabs of 64 rows (two slabs
+      built: the first and a middle one) and sampled blocks of their rows
+      are checked
 """
 import numpy as np
 import pytest
@@ -122,3 +126,61 @@ def test_c3_full_size_uneven_windows_one_plan(bse, prec, tol):
         _free(d)
     for p in probs:
         _free(p)
+
+
+class _SlabRows:
+    """A slab's m_vv or m_cc indexed with whole-problem k (for block_inputs)."""
+
+    def __init__(self, t, k_begin):
+        self.t, self.k_begin = t, k_begin
+
+    def __getitem__(self, idx):
+        k, kp = idx
+        return self.t[k - self.k_begin, kp]
+
+
+def _sample_slab_blocks(nk, s, kb, kn, seed, entries=50_000):
+    """3 diagonal blocks of the slab's rows and seeded off-diagonal blocks (k, k')
+    with k in the slab, about `entries` sampled entries."""
+    rng = np.random.default_rng(seed)
+    out = [(k, k) for k in sorted({kb, kb + kn // 2, kb + kn - 1})]
+    n_off = int(min(2000, max(9, entries // (s * s))))
+    while len(out) < 3 + n_off:
+        k, kp = kb + int(rng.integers(0, kn)), int(rng.integers(0, nk))
+        if k != kp and (k, kp) not in out:
+            out.append((k, kp))
+    return out
+
+
+def test_c4_full_size_bf16x6_slabs(bse):
+    import time
+    import torch
+    kn = 64
+    p = bi.make_problem_torch("c4", q_index=0, k_slab=(0, kn))
+    nk, s = p["nk"], p["nv"] * p["nc"]
+    d = bse.upload_problem(p)
+    for kb in (0, 320):
+        if kb:
+            for x in (p, d):
+                x["m_vv"] = x["m_cc"] = None
+            torch.cuda.empty_cache()
+            m_vv, m_cc = bi.pair_slab_torch("c4", kb, kn, q_index=0)
+            p["m_vv"], p["m_cc"] = d["m_vv"], d["m_cc"] = m_vv, m_cc
+        plan = bse.Plan([bse.make_problem_struct(d, k_begin=kb, k_count=kn)],
+                        precision=bse.BSE_PREC_BF16X6, autotune=True)
+        plan.execute()
+        plan.status()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan.execute()
+        torch.cuda.synchronize()
+        ms = 1e3 * (time.perf_counter() - t0)
+        plan.status()
+        plan.close()
+        view = dict(p)
+        view["m_vv"], view["m_cc"] = _SlabRows(p["m_vv"], kb), _SlabRows(p["m_cc"], kb)
+        blocks = _sample_slab_blocks(nk, s, kb, kn, seed=kb)
+        err = _errors(view, d, blocks)
+        print(f"\nc4 slab [{kb}, {kb + kn}) build {ms:.1f} ms, {len(blocks)} sampled blocks: {err}")
+        assert err["A"] < 1e-6 and err["B"] < 1e-6 and err["A_off"] < 1e-6, err
+    _free(d, p)
