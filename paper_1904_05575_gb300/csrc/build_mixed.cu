@@ -345,30 +345,31 @@ struct Stage2Args {
   int64_t ld;
 };
 
-template <int TS, int R>   // TS x TS output tile per block, R x R outputs per thread
-__global__ void __launch_bounds__((TS / R) * (TS / R)) k_stage2(Stage2Args a) {
-  constexpr int NTH = (TS / R) * (TS / R);
+// TX x TT output tile per block (X rows x T rows), RX x RT outputs per thread
+template <int TX, int TT, int RX, int RT>
+__global__ void __launch_bounds__((TX / RX) * (TT / RT)) k_stage2(Stage2Args a) {
+  constexpr int NTH = (TX / RX) * (TT / RT), CT = TT / RT, CX = TX / RX;
   constexpr int GC = 32;
-  __shared__ float2 Xs[TS][GC + 1];
-  __shared__ float2 Ts[GC][TS + 1];
+  __shared__ float2 Xs[TX][GC + 1];
+  __shared__ float2 Ts[GC][TT + 1];
   const int p = blockIdx.x;
   const int k = a.k_begin + p / a.nk, kp = p % a.nk;
-  const int rx0 = blockIdx.y * TS, rt0 = blockIdx.z * TS;
+  const int rx0 = blockIdx.y * TX, rt0 = blockIdx.z * TT;
   const int64_t xp = a.x_transpose_pair ? (int64_t)kp * a.nk + k : (int64_t)p;
   const double2* X = a.x + xp * a.rows_x * a.ng;
   const int64_t trow0 = a.t_row0 + (int64_t)a.slot_of_pair[p] * a.rows_t;
   const int tid = threadIdx.x;
-  const int tx = tid % (TS / R), ty = tid / (TS / R);
+  const int tx = tid % CT, ty = tid / CT;
   // compensated FP32: sums over 8 plane waves in FMA, folded into (hi, lo) pairs
   // with TwoSum, so no FP64 instruction runs inside the loop
-  float hx[R][R], hy[R][R], lx[R][R], ly[R][R];
+  float hx[RX][RT], hy[RX][RT], lx[RX][RT], ly[RX][RT];
 #pragma unroll
-  for (int i = 0; i < R; ++i)
+  for (int i = 0; i < RX; ++i)
 #pragma unroll
-    for (int j = 0; j < R; ++j) hx[i][j] = hy[i][j] = lx[i][j] = ly[i][j] = 0.f;
+    for (int j = 0; j < RT; ++j) hx[i][j] = hy[i][j] = lx[i][j] = ly[i][j] = 0.f;
 
   for (int g0 = 0; g0 < a.ng; g0 += GC) {
-    for (int i = tid; i < TS * GC; i += NTH) {
+    for (int i = tid; i < TX * GC; i += NTH) {
       const int r = i / GC, g = i % GC;
       float2 v = make_float2(0.f, 0.f);
       if (rx0 + r < a.rows_x && g0 + g < a.ng) {
@@ -378,8 +379,8 @@ __global__ void __launch_bounds__((TS / R) * (TS / R)) k_stage2(Stage2Args a) {
       }
       Xs[r][g] = v;
     }
-    for (int i = tid; i < TS * GC; i += NTH) {
-      const int g = i / TS, r = i % TS;
+    for (int i = tid; i < TT * GC; i += NTH) {
+      const int g = i / TT, r = i % TT;
       float2 v = make_float2(0.f, 0.f);
       if (rt0 + r < a.rows_t && g0 + g < a.ng) {
         v = a.T[(int64_t)(g0 + g) * a.t_ld + trow0 + rt0 + r];
@@ -390,22 +391,22 @@ __global__ void __launch_bounds__((TS / R) * (TS / R)) k_stage2(Stage2Args a) {
     __syncthreads();
 #pragma unroll
     for (int g8 = 0; g8 < GC; g8 += 8) {
-      float accx[R][R], accy[R][R];
+      float accx[RX][RT], accy[RX][RT];
 #pragma unroll
-      for (int i = 0; i < R; ++i)
+      for (int i = 0; i < RX; ++i)
 #pragma unroll
-        for (int j = 0; j < R; ++j) accx[i][j] = accy[i][j] = 0.f;
+        for (int j = 0; j < RT; ++j) accx[i][j] = accy[i][j] = 0.f;
 #pragma unroll
       for (int g = g8; g < g8 + 8; ++g) {
-        float2 xv[R], tv[R];
+        float2 xv[RX], tv[RT];
 #pragma unroll
-        for (int i = 0; i < R; ++i) xv[i] = Xs[ty + i * (TS / R)][g];
+        for (int i = 0; i < RX; ++i) xv[i] = Xs[ty + i * CX][g];
 #pragma unroll
-        for (int j = 0; j < R; ++j) tv[j] = Ts[g][tx + j * (TS / R)];
+        for (int j = 0; j < RT; ++j) tv[j] = Ts[g][tx + j * CT];
 #pragma unroll
-        for (int i = 0; i < R; ++i)
+        for (int i = 0; i < RX; ++i)
 #pragma unroll
-          for (int j = 0; j < R; ++j) {
+          for (int j = 0; j < RT; ++j) {
             accx[i][j] = fmaf(xv[i].x, tv[j].x, accx[i][j]);
             accx[i][j] = fmaf(-xv[i].y, tv[j].y, accx[i][j]);
             accy[i][j] = fmaf(xv[i].x, tv[j].y, accy[i][j]);
@@ -413,9 +414,9 @@ __global__ void __launch_bounds__((TS / R) * (TS / R)) k_stage2(Stage2Args a) {
           }
       }
 #pragma unroll
-      for (int i = 0; i < R; ++i)
+      for (int i = 0; i < RX; ++i)
 #pragma unroll
-        for (int j = 0; j < R; ++j) {
+        for (int j = 0; j < RT; ++j) {
           float s, e;
           two_sum(hx[i][j], accx[i][j], s, e);
           hx[i][j] = s;
@@ -430,10 +431,10 @@ __global__ void __launch_bounds__((TS / R) * (TS / R)) k_stage2(Stage2Args a) {
 
   const int nv = a.nv, nc = a.nc;
 #pragma unroll
-  for (int i = 0; i < R; ++i)
+  for (int i = 0; i < RX; ++i)
 #pragma unroll
-    for (int j = 0; j < R; ++j) {
-      const int rx = rx0 + ty + i * (TS / R), rt = rt0 + tx + j * (TS / R);
+    for (int j = 0; j < RT; ++j) {
+      const int rx = rx0 + ty + i * CX, rt = rt0 + tx + j * CT;
       if (rx >= a.rows_x || rt >= a.rows_t) continue;
       int vi, ci, vp, cp;
       if (a.mode == S2_RR_CC) {          // rx = (v, v'), rt = (c, c')
@@ -576,12 +577,162 @@ __global__ void __launch_bounds__(256) k_stage2_pipe(Stage2Args a) {
   *dst = o;
 }
 
+// Stage 2 for skinny pair blocks: at most RT rows of T against long X rows
+// (W^rr with 2 core levels: 4 (v, v') rows of T, 400 (c, c') rows of X).  One
+// thread per X row, SK_ROWS consecutive rows of the term (running across pair
+// blocks, at most SK_PAIRS of them) per block.  The raw complex128 X rows
+// stream through shared memory in chunks of SK_GC plane waves (cp.async,
+// double-buffered, 128-byte runs per row), each thread converts its own row
+// once and contracts it against the T rows of its pair, which every thread of
+// the pair reads at the same address.  The work is bound by reading X once.
+// Same compensated FP32 arithmetic, in the same order, as k_stage2.
+constexpr int SK_ROWS = 128, SK_GC = 8, SK_PAIRS = 3;
+
+template <int RT>
+__global__ void __launch_bounds__(SK_ROWS) k_stage2_skinny(Stage2Args a, int64_t total_rows) {
+  __shared__ __align__(16) uint4 Xr[2][SK_ROWS][SK_GC + 1];   // +16 B per row: no bank conflicts
+  static_assert(SK_GC == 8, "one compensation group of 8 plane waves per chunk");
+  __shared__ __align__(16) float2 Tr[2][SK_GC][SK_PAIRS][RT];
+  __shared__ int64_t xoff[SK_ROWS];      // first complex of each row in X (-1: past the end)
+  __shared__ int64_t toff[SK_PAIRS];     // first T row of each pair of the block
+  const int tid = threadIdx.x;
+  const int64_t row0 = (int64_t)blockIdx.x * SK_ROWS;
+  const int rows_x = a.rows_x, nk = a.nk;
+  const int p_first = (int)(row0 / rows_x);
+  {
+    const int64_t R = row0 + tid;
+    int64_t off = -1;
+    if (R < total_rows) {
+      const int p = (int)(R / rows_x), r = (int)(R - (int64_t)p * rows_x);
+      const int k = a.k_begin + p / nk, kp = p % nk;
+      const int64_t xp = a.x_transpose_pair ? (int64_t)kp * nk + k : (int64_t)p;
+      off = (xp * rows_x + r) * a.ng;
+    }
+    xoff[tid] = off;
+    if (tid < SK_PAIRS) {
+      const int64_t p = p_first + tid;
+      toff[tid] = p * rows_x < total_rows ? a.t_row0 + (int64_t)a.slot_of_pair[p] * a.rows_t : -1;
+    }
+  }
+  __syncthreads();
+  const uint4* X = reinterpret_cast<const uint4*>(a.x);
+  const int nchunks = (a.ng + SK_GC - 1) / SK_GC;
+  auto prefetch = [&](int c, int buf) {
+    const int g0 = c * SK_GC;
+#pragma unroll
+    for (int u = 0; u < SK_GC; ++u) {   // SK_GC threads per row, 16 B each
+      const int i = tid + u * SK_ROWS;
+      const int r = i / SK_GC, g = i % SK_GC;
+      const int64_t off = xoff[r];
+      const bool ok = off >= 0 && g0 + g < a.ng;
+      cp_async16(&Xr[buf][r][g], ok ? (const void*)(X + off + g0 + g) : (const void*)X, ok);
+    }
+    for (int i = tid; i < SK_GC * SK_PAIRS * RT; i += SK_ROWS) {
+      const int g = i / (SK_PAIRS * RT), q = (i / RT) % SK_PAIRS, rt = i % RT;
+      const bool ok = toff[q] >= 0 && rt < a.rows_t && g0 + g < a.ng;
+      const float2* src = a.T + (ok ? (int64_t)(g0 + g) * a.t_ld + toff[q] + rt : 0);
+      cp_async8(&Tr[buf][g][q][rt], src, ok);
+    }
+    cp_async_commit();
+  };
+
+  const int64_t R = row0 + tid;
+  const int q = (int)(R / rows_x) - p_first;   // this thread's pair within the block
+  const uint32_t xflip = a.conj_x ? 0x80000000u : 0u;
+  const float tsign = a.conj_t ? -1.f : 1.f;
+  float hx[RT], hy[RT], lx[RT], ly[RT];
+#pragma unroll
+  for (int j = 0; j < RT; ++j) hx[j] = hy[j] = lx[j] = ly[j] = 0.f;
+  prefetch(0, 0);
+  for (int c = 0; c < nchunks; ++c) {
+    const int buf = c & 1;
+    if (c + 1 < nchunks) {
+      prefetch(c + 1, buf ^ 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+#pragma unroll
+    for (int g8 = 0; g8 < SK_GC; g8 += 8) {
+      float accx[RT], accy[RT];
+#pragma unroll
+      for (int j = 0; j < RT; ++j) accx[j] = accy[j] = 0.f;
+#pragma unroll
+      for (int g = g8; g < g8 + 8; ++g) {
+        const uint4 d = Xr[buf][tid][g];
+        const float2 xv = make_float2(__uint_as_float(f64w_to_f32_bits(d.x, d.y)),
+                                      __uint_as_float(f64w_to_f32_bits(d.z, d.w) ^ xflip));
+#pragma unroll
+        for (int j = 0; j < RT; ++j) {
+          const float2 tv = Tr[buf][g][q < 0 ? 0 : q][j];
+          const float ty_ = tv.y * tsign;
+          accx[j] = fmaf(xv.x, tv.x, accx[j]);
+          accx[j] = fmaf(-xv.y, ty_, accx[j]);
+          accy[j] = fmaf(xv.x, ty_, accy[j]);
+          accy[j] = fmaf(xv.y, tv.x, accy[j]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < RT; ++j) {
+        float sv, e;
+        two_sum(hx[j], accx[j], sv, e);
+        hx[j] = sv;
+        lx[j] += e;
+        two_sum(hy[j], accy[j], sv, e);
+        hy[j] = sv;
+        ly[j] += e;
+      }
+    }
+    __syncthreads();   // the next prefetch overwrites this buffer
+  }
+  if (R >= total_rows) return;
+  const int p = (int)(R / rows_x), rx = (int)(R - (int64_t)p * rows_x);
+  const int k = a.k_begin + p / nk, kp = p % nk;
+  const int nv = a.nv, nc = a.nc;
+  const float sc = (float)a.scale;
+#pragma unroll
+  for (int j = 0; j < RT; ++j) {
+    const int rt = j;
+    if (rt >= a.rows_t) break;
+    int vi, ci, vp, cp;
+    if (a.mode == S2_RR_CC) {
+      vi = rx / nv; vp = rx % nv; ci = rt / nc; cp = rt % nc;
+    } else if (a.mode == S2_RR_VV) {
+      ci = rx / nc; cp = rx % nc; vi = rt / nv; vp = rt % nv;
+    } else {
+      vp = rx / nc; ci = rx % nc; vi = rt / nc; cp = rt % nc;
+    }
+    const int64_t al = ((int64_t)k * nv + vi) * nc + ci;
+    const int64_t ap = ((int64_t)kp * nv + vp) * nc + cp;
+    double2* dst = a.out + al + ap * a.ld;
+    double2 o = *dst;
+    o.x -= f32_to_f64_bits(scale_hi_lo(sc, hx[j], lx[j]));
+    o.y -= f32_to_f64_bits(scale_hi_lo(sc, hy[j], ly[j]));
+    *dst = o;
+  }
+}
+
+// true when k_stage2_skinny serves the term: T rows fit the register tile and
+// a block's SK_ROWS rows touch at most SK_PAIRS pair blocks
+// (rows_t is Nv^2 or Nc^2 there, so at most 4 when skinny)
+bool stage2_skinny(const Stage2Args& a) {
+  return a.rows_t <= 4 && (SK_ROWS - 1 + a.rows_x - 1) / a.rows_x + 1 <= SK_PAIRS;
+}
+
 void launch_stage2(const Stage2Args& a, int npair, cudaStream_t s) {
-  if (a.rows_x <= 16 && a.rows_t <= 16) {
+  if (stage2_skinny(a)) {
+    const int64_t total = (int64_t)npair * a.rows_x;
+    const int64_t blocks = (total + SK_ROWS - 1) / SK_ROWS;
+    k_stage2_skinny<4><<<(unsigned)blocks, SK_ROWS, 0, s>>>(a, total);
+  } else if (a.rows_x <= 16 && a.rows_t <= 16) {
     k_stage2_pipe<<<npair, 256, 0, s>>>(a);
+  } else if (a.rows_x <= 40 && a.rows_t <= 40 && (a.rows_x > 32 || a.rows_t > 32)) {
+    // one 40 x 40 tile per pair block (e.g. W^ra with Nv * Nc = 40)
+    k_stage2<40, 40, 2, 5><<<npair, 160, 0, s>>>(a);
   } else {
     dim3 grid(npair, (a.rows_x + 31) / 32, (a.rows_t + 31) / 32);
-    k_stage2<32, 2><<<grid, 256, 0, s>>>(a);
+    k_stage2<32, 32, 2, 2><<<grid, 256, 0, s>>>(a);
   }
   BSE_CUDA(cudaGetLastError());
   note_launches(1);
@@ -974,6 +1125,7 @@ void plan_execute_mixed(BatchPlan& pl, cudaStream_t s) {
     Phase ph("mixed_stage2", s);
     for (BatchPlan::Term& t : pl.terms) {
       if (t.tc2) continue;
+      Phase pt(t.s2.mode == S2_RA ? "mixed_stage2_wra" : "mixed_stage2_wrr", s);
       launch_stage2(t.s2, (int)pl.probs[t.prob].slab_pairs(), s);
     }
   }

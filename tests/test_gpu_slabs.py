@@ -8,7 +8,8 @@ A and B (slab arrays are row slices of the whole device arrays) and compares
 the union with the oracle's whole A and B; a single slab must leave every
 other row untouched.  Paths: FP64, the fused tensor-core direct term
 (Nv = Nc = 2), the two-launch form with CUDA-core stage 2 (an uneven window,
-W applied to the valence side), and the tensor-core stage 2 (8 x 8 bands).
+W applied to the valence side; the core-level window with its skinny W^rr
+and 40 x 40 W^ra blocks), and the tensor-core stage 2 (8 x 8 bands).
 """
 import numpy as np
 import pytest
@@ -40,6 +41,12 @@ SHAPES = {
     "v2c3": bi.BSEConfig("slab-v2c3", grid=2, nv=2, nc=3, ng=59, w_scale=0.1),
     # 8 x 8 bands: 64-row pair blocks, stage 2 on the tensor cores
     "v8c8": bi.BSEConfig("slab-v8c8", grid=2, nv=8, nc=8, ng=59, w_scale=0.05),
+    # the core-level window (2 x 20 bands): 4 T rows against 400 X rows (one
+    # thread per X row) and 40 x 40 W^ra blocks (one 40 x 40 tile per pair)
+    "v2c20": bi.BSEConfig("slab-v2c20", grid=2, nv=2, nc=20, ng=59, w_scale=0.05,
+                          e_v_range=(-400.5, -399.5), m_decay=0.05),
+    # 4 T rows against 64 X rows: a block of 128 X rows spans three pair blocks
+    "v2c8": bi.BSEConfig("slab-v2c8", grid=2, nv=2, nc=8, ng=59, w_scale=0.1),
 }
 
 
@@ -54,6 +61,13 @@ def cases():
 
 def _rel(x, ref):
     return np.linalg.norm(x - ref) / np.linalg.norm(ref)
+
+
+def _rel_interaction(p, A, A_ref):
+    """Error of A without its E^ip diagonal (which dominates A's norm when the
+    transition energies are hundreds of eV, as for core levels)."""
+    D = np.diag(O.transition_energies(p["e_v"], p["e_c"]).astype(np.complex128))
+    return _rel(A - D, A_ref - D)
 
 
 def _slab_view(d, kb, kn):
@@ -84,7 +98,8 @@ def _build_slabs(bse, d, slabs, prec, fused=True, one_call=False):
 
 
 PATHS = [("c1", 0, True), ("c1", 2, True), ("c1", 2, False), ("v2c3", 0, True),
-         ("v2c3", 2, True), ("v8c8", 0, True), ("v8c8", 2, True)]
+         ("v2c3", 2, True), ("v8c8", 0, True), ("v8c8", 2, True), ("v2c20", 0, True),
+         ("v2c20", 2, True), ("v2c8", 2, True)]
 
 
 @pytest.mark.parametrize("shape,prec,fused", PATHS,
@@ -99,9 +114,10 @@ def test_slabs_cover_the_whole_problem(bse, cases, shape, prec, fused):
     slabs = [(0, 3), (3, 1), (4, nk - 4)]
     _build_slabs(bse, d, slabs, prec, fused)
     tol = FP64_TOL if prec == 0 else MIXED_TOL
-    ea = _rel(bse.matrix_to_numpy(d["A"], n), A_ref)
+    A = bse.matrix_to_numpy(d["A"], n)
+    ea, ei = _rel(A, A_ref), _rel_interaction(p, A, A_ref)
     eb = _rel(bse.matrix_to_numpy(d["B"], n), B_ref)
-    assert ea < tol and eb < tol, (ea, eb)
+    assert ea < tol and ei < tol and eb < tol, (ea, ei, eb)
 
 
 @pytest.mark.parametrize("prec", [0, 2], ids=["fp64", "bf16x6"])
