@@ -266,6 +266,10 @@ def run_reference(args):
         return 0
     import bse_inputs as bi
     from oracle import bse_oracle as O
+    if args.config not in ("c1", "c2"):
+        raise SystemExit(f"--impl reference times the oracle on whole problems (c1, c2); the "
+                         f"{args.config} workload is sampled block by block by the cpu_baseline "
+                         f"leg of the GPU arm instead")
     p = bi.make_problem(args.config)
     flops = build_flops(p["nk"], p["nv"], p["nc"], p["ng"])
     for _ in range(args.warmup):
@@ -281,7 +285,8 @@ def run_reference(args):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * statistics.mean(tt), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": "fp64 (numpy, host)"},
+        "config": {"workload": WORKLOAD if args.config == "c2" else args.config,
+                   "precision": "fp64 (numpy, host)"},
         "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cpu_cores(),
                          "kind": "oracle",
                          "sample": f"full workload, {args.steps} steps of build+reduce+spectrum"},
@@ -289,6 +294,177 @@ def run_reference(args):
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+    return 0
+
+
+C4_SLAB = 64   # k rows per slab of the core-level workload (63 GB of m_cc per slab)
+
+
+def run_c4(args, bse, bi, prec, world, rank, local):
+    """Core-level workload (Nk=512, Nv=2 core levels, Nc=20, NG=300, N=20,480,
+    full BSE): its pair arrays (m_cc alone 503 GB) exceed the device memory,
+    so A and B are built in k-row slabs of C4_SLAB rows.  Before each slab's
+    build its m_vv and m_cc are drawn on the device (untimed, S3 kept across
+    slabs); n_vc, W, M_x and A, B stay resident.  Each slab's plan execute is
+    timed `steps` times after `warmup` untimed runs; a step is the whole build,
+    so ms_per_step is the sum over slabs of the mean slab time.  --lowest then
+    runs block Davidson (tensor-core matvecs) on the complete A, B; with
+    --fp64-dense the plain FP64 path (FP64 slab builds + dense reduction and
+    eigensolve) is timed beside it and the exciton energies compared."""
+    import numpy as np
+    import torch
+    dev = "cuda"
+    stream = torch.cuda.current_stream()
+    seed = 20190411 + rank
+    kn = C4_SLAB
+    p = bi.make_problem_torch("c4", q_index=0, seed=seed, k_slab=(0, kn))
+    nk, nv, nc, ng = p["nk"], p["nv"], p["nc"], p["ng"]
+    n = nk * nv * nc
+    flops = build_flops(nk, nv, nc, ng)
+    d = bse.upload_problem(p)
+    fp64_dense = args.lowest and args.fp64_dense
+    if fp64_dense:
+        A64, B64 = torch.zeros_like(d["A"]), torch.zeros_like(d["B"])
+    slab_ms, fp64_slab_ms, tile_cols = [], [], None
+    launches = 0
+    sampler = ClockSampler(local)
+    sampler.start()
+    for kb in range(0, nk, kn):
+        if kb:
+            for x in (p, d):
+                x["m_vv"] = x["m_cc"] = None
+            torch.cuda.empty_cache()
+            p["m_vv"], p["m_cc"] = d["m_vv"], d["m_cc"] = bi.pair_slab_torch("c4", kb, kn, 0, seed)
+        plan = bse.Plan([bse.make_problem_struct(d, k_begin=kb, k_count=kn)], precision=prec,
+                        autotune=True)
+        tile_cols = plan.tile_cols
+        for _ in range(args.warmup):
+            plan.execute()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        l0 = bse.bse_kernel_launches()
+        bse.bse_phase_timing(True)
+        for e0, e1 in evs:
+            e0.record(stream)
+            plan.execute()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        bse.bse_phase_timing(False)
+        launches += bse.bse_kernel_launches() - l0
+        plan.status()
+        plan.close()
+        slab_ms.append(statistics.mean(e0.elapsed_time(e1) for e0, e1 in evs))
+        if fp64_dense:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            st64 = bse.make_problem_struct(dict(d, A=A64, B=B64), k_begin=kb, k_count=kn)
+            e0.record(stream)
+            bse.bse_build_kernel([st64], bse.BSE_PREC_FP64)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            fp64_slab_ms.append(e0.elapsed_time(e1))
+    clocks = sampler.stop()
+    phases = bse.bse_phase_report()
+    t_build = max_over_ranks([sum(slab_ms)], dev, world)[0]
+    value = weak_scaling_value(world, flops, t_build)
+
+    # CPU oracle on seeded (k, k') blocks of the last slab's rows, about 10 s
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import bse_oracle as O
+        host = dict(p)
+        for key in ("w", "m_x", "v_bar", "e_v", "e_c", "q_minus", "q_plus"):
+            host[key] = p[key].cpu().numpy()
+        kb_last = nk - kn
+        rng = np.random.default_rng(11)
+        nb, t_cpu = 0, 0.0
+        while t_cpu < 10.0 and nb < 4096:
+            k, kp = kb_last + int(rng.integers(0, kn)), int(rng.integers(0, nk))
+            blk_host = dict(host, m_vv={(k, kp): p["m_vv"][k - kb_last, kp]},
+                            m_cc={(k, kp): p["m_cc"][k - kb_last, kp]})
+            blk = bi.block_inputs(blk_host, k, kp)
+            t0 = time.perf_counter()
+            O.block_A_B(blk)
+            t_cpu += time.perf_counter() - t0
+            nb += 1
+        cpu = {"value": nb * flops / nk ** 2 / t_cpu / 1e12, "unit": "TFLOP/s",
+               "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"{nb} seeded (k,k') blocks of the last slab (block_A_B, numpy FP64)",
+               "build_s": t_cpu}
+
+    extra = {}
+    if args.lowest:
+        for x in (p, d):
+            for key in ("m_vv", "m_cc", "n_vc", "w"):
+                x[key] = None
+        torch.cuda.empty_cache()
+        nev = min(args.nev, n)
+        E_dav = torch.empty(nev, dtype=torch.float64, device=dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tol = args.dav_tol or 1e-4
+        converged = True
+        e0.record(stream)
+        try:
+            iters = bse.bse_lowest_excitons(n, d["A"], d["B"], nev, E_dav, None, tol_ev=tol,
+                                            max_iter=args.dav_max_iter, matvec_precision=prec)
+        except bse.BSEError as err:     # E_dav still holds the last Ritz values
+            if err.status != bse.BSE_ERR_NO_CONV:
+                raise
+            converged, iters = False, args.dav_max_iter
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dav = e0.elapsed_time(e1)
+        low = {"nev": nev, "method": "mixed slab builds + block Davidson (tensor-core matvecs, "
+                                     "diagonal preconditioner)",
+               "time_to_lowest_excitons_ms": t_build + dav, "davidson_ms": dav,
+               "davidson_iterations": iters, "residual_tol_ev": tol, "converged": converged,
+               "lowest_E_eV": [round(x, 6) for x in E_dav[:4].tolist()]}
+        if fp64_dense:
+            del d["A"], d["B"]
+            torch.cuda.empty_cache()
+            S2 = torch.empty((n, n), dtype=torch.complex128, device=dev)
+            L2 = torch.empty_like(S2)
+            E_all = torch.empty(n, dtype=torch.float64, device=dev)
+            osc_all = torch.empty_like(E_all)
+            om = torch.as_tensor(p["omega"]).to(dev)
+            eps = torch.empty(len(p["omega"]), dtype=torch.complex128, device=dev)
+            e0.record(stream)
+            bse.bse_reduce(n, A64, B64, S2, L2)
+            bse.bse_spectrum(n, S2, L2, p["rho"], p["c_q"], nk * p["omega_cell"], om, p["delta"],
+                             E_all, osc_all, eps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            fp64_total = sum(fp64_slab_ms) + e0.elapsed_time(e1)
+            low.update({"fp64_build_ms": sum(fp64_slab_ms), "fp64_dense_ms": fp64_total,
+                        "speedup_vs_fp64_dense": fp64_total / low["time_to_lowest_excitons_ms"],
+                        "max_dE_meV_vs_fp64_dense": (E_dav - E_all[:nev]).abs().max().item() * 1e3})
+        extra["lowest_excitons"] = low
+
+    peaks = load_peaks()
+    roofline, roofline_secondary = build_rooflines(bse, prec, phases, args.steps,
+                                                   [(nk, nv, nc, ng)], peaks)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_build,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "bf16x6": "bf16x6(f32 acc)", "bf16x3": "bf16x3(f32 acc)"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": f"c4 core-level case: Q 0, Nk={nk} (8x8x8), Nv={nv} core levels, "
+                                   f"Nc={nc}, N={n}, NG={ng}, full BSE, built in {nk // kn} k-row "
+                                   f"slabs of {kn} (pair arrays drawn on the GPU per slab)",
+                       "precision": args.precision, "build_only": True,
+                       "l2": "inputs larger than L2 (63 GB of m_cc per slab)",
+                       "parallelism": f"Q replicas x{world}"},
+            "build_ms": t_build, "slab_build_ms": slab_ms,
+            "build_api": f"bse_plan_execute per slab (tile width autotuned: {tile_cols} columns)",
+            "phase_ms_per_step": {k: v[1] / args.steps for k, v in phases.items()},
+            "roofline": roofline, "roofline_secondary": roofline_secondary,
+            "cpu_baseline": cpu, "e2e": None, "clocks": clocks,
+            "gpu_launches": launches, "peaks": peaks,
+        }
+        line.update(extra)
+        print(json.dumps(line), flush=True)
     return 0
 
 
@@ -307,12 +483,19 @@ def main():
     ap.add_argument("--qs", default="0", help="comma-separated Q indices built by one plan")
     ap.add_argument("--device-inputs", action="store_true",
                     help="draw the inputs on the GPU (automatic for c3 and c5)")
-    ap.add_argument("--nev", type=int, default=16, help="lowest excitons for time-to-lowest-excitons")
+    ap.add_argument("--nev", type=int, default=None,
+                    help="lowest excitons for time-to-lowest-excitons (16; 50 for c4)")
     ap.add_argument("--lowest", action="store_true",
                     help="build-only configs: also time mixed build + Davidson (tensor-core matvecs)")
+    ap.add_argument("--dav-tol", type=float, default=None,
+                    help="Davidson residual tolerance in eV (1e-5; 1e-4 for c4, whose "
+                         "interaction terms reach 100 eV)")
+    ap.add_argument("--dav-max-iter", type=int, default=300)
     ap.add_argument("--fp64-dense", action="store_true",
                     help="with --lowest: also time the plain FP64 path (FP64 build + dense solve)")
     args = ap.parse_args()
+    if args.nev is None:
+        args.nev = 50 if args.config == "c4" else 16
     if args.impl == "reference":
         return run_reference(args)
     args.warmup = max(args.warmup, 3)
@@ -343,8 +526,10 @@ def main():
 
     # each rank: its own momentum transfers (Q replicas), resident in HBM
     if args.config == "c4":
-        raise SystemExit("c4 (560 GB of pair elements) needs a k-row slab build, which this "
-                         "benchmark does not run")
+        rc = run_c4(args, bse, bi, prec, world, rank, local)
+        if world > 1:
+            dist.destroy_process_group()
+        return rc
     qs = [int(x) for x in args.qs.split(",")]
     device_inputs = args.device_inputs or args.config in ("c3", "c5")
     if device_inputs or len(qs) > 1:

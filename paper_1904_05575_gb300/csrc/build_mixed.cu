@@ -68,6 +68,7 @@ struct SplitArgs {
   int64_t row0 = 0;         // first destination row
   int pair_nb = 0;          // SPLIT_PAIRS: rows_per = nb^2 rows (b, b') stored as (b', b)
   int64_t src_ld = 0;       // SPLIT_DENSE: source row stride (0: K)
+  int zero_diag = 0;        // SPLIT_DENSE: element k == row stored as zero
 };
 
 // One thread per (output row, 8 consecutive k): every element is read as two
@@ -98,7 +99,7 @@ __global__ void __launch_bounds__(256) k_split(SplitArgs a) {
     for (int e = 0; e < 8; ++e) {
       const int k = k0 + e;
       uint4 x = make_uint4(0u, 0u, 0u, 0u);
-      if (k < a.K && off >= 0) x = __ldg(src + off + (int64_t)k * kstride);
+      if (k < a.K && off >= 0 && !(a.zero_diag && k == row)) x = __ldg(src + off + (int64_t)k * kstride);
       uint32_t fr = f64w_to_f32_bits(x.x, x.y), fi = f64w_to_f32_bits(x.z, x.w);
       if (a.kscale && k < a.K) {   // exchange operand only: scale in FP32
         const float sc = (float)a.kscale[k];
@@ -1646,20 +1647,35 @@ void build_mixed_batch(const std::vector<Problem>& probs, int precision, cudaStr
 // Hermitian matrix is the conjugate of its column m, which is contiguous in
 // the column-major input, so A and B are split once (conjugated columns as
 // GEMM rows, K = N); each call splits V's columns and runs one GEMM per
-// matrix (K segments of 8 steps), writing FP64 results column-major.
+// matrix (K segments of 8 steps), writing FP64 results column-major.  A's
+// diagonal (the transition energies, hundreds of eV for core levels) is left
+// out of the split and applied in FP64 in the epilogue, so the split error
+// scales with the interaction, not with the energies.
 // ---------------------------------------------------------------------------
 namespace {
 struct MatvecEpi {
   double2* out;
   int64_t ld;
+  const double2* diag = nullptr;   // the matrix (its diagonal is added in FP64), or NULL
+  int64_t diag_ld = 0;
+  const double2* v = nullptr;      // the FP64 block V, column-major with leading dimension ld
   __device__ __forceinline__ void operator()(const tc::Tile& t, int row, int c0, const float* re,
                                              const float* im) const {
     const int64_t r = t.out_row0 + row;
+    double2 d = make_double2(0.0, 0.0);
+    if (diag) d = diag[r * (diag_ld + 1)];
 #pragma unroll
     for (int j = 0; j < 32; ++j)
-      if (c0 + j < t.n_valid)
-        out[r + (int64_t)(t.n0 + c0 + j) * ld] =
-            make_double2(f32_to_f64_bits(re[j]), f32_to_f64_bits(im[j]));
+      if (c0 + j < t.n_valid) {
+        const int64_t o = r + (int64_t)(t.n0 + c0 + j) * ld;
+        double2 y = make_double2(f32_to_f64_bits(re[j]), f32_to_f64_bits(im[j]));
+        if (diag) {
+          const double2 x = v[o];
+          y.x += d.x * x.x - d.y * x.y;
+          y.y += d.x * x.y + d.y * x.x;
+        }
+        out[o] = y;
+      }
   }
 };
 }  // namespace
@@ -1667,6 +1683,8 @@ struct MatvecEpi {
 struct TcMatvec {
   int n = 0, Kp = 0, pieces = 3, planes = 6, kmax = 0, kmax_rows = 0, nt = 0, max_tiles = 0;
   bool has_b = false;
+  const bse_c128* A = nullptr;   // caller's A (its diagonal, in FP64)
+  int64_t ld = 0;
   DevMem ap, bp, vp, tiles, err;
   CUtensorMap ma_a{}, ma_b{}, mb_v{};
   tc::GemmShape sh{};
@@ -1684,6 +1702,8 @@ TcMatvec* tc_matvec_create(int n, const bse_c128* A, const bse_c128* B, int64_t 
   m->nt = tile_cols(m->kmax_rows, m->Kp);
   m->sh = make_shape(m->nt, m->Kp, m->pieces);
   m->has_b = B != nullptr;
+  m->A = A;
+  m->ld = ld;
   m->max_tiles = ((n + tc::BM - 1) / tc::BM) * ((kmax + m->nt - 1) / m->nt);
   const size_t mat_bytes = (size_t)m->planes * n * m->Kp * 2;
   m->ap = DevMem(mat_bytes);
@@ -1698,6 +1718,7 @@ TcMatvec* tc_matvec_create(int n, const bse_c128* A, const bse_c128* B, int64_t 
                  m->Kp, n, m->pieces, 1, nullptr,
                  (which ? m->bp : m->ap).as<__nv_bfloat16>(), n, 0};
     sa.src_ld = ld;
+    sa.zero_diag = which == 0;
     launch_split(sa, s);
   }
   m->ma_a = make_plane_map(m->ap.as<__nv_bfloat16>(), m->Kp, n, m->planes, tc::BM);
@@ -1720,7 +1741,9 @@ void tc_matvec_apply(TcMatvec* m, const bse_c128* V, int k, bse_c128* AV, bse_c1
   BSE_CUDA(cudaMemcpyAsync(m->tiles.ptr, tl.data(), tl.size() * sizeof(tc::Tile),
                            cudaMemcpyHostToDevice, s));
   launch_gemm(m->ma_a, m->mb_v, m->tiles.as<tc::Tile>(), (int)tl.size(), m->sh,
-              MatvecEpi{reinterpret_cast<double2*>(AV), m->n}, m->err.as<int>(), s);
+              MatvecEpi{reinterpret_cast<double2*>(AV), m->n, reinterpret_cast<const double2*>(m->A),
+                        m->ld, reinterpret_cast<const double2*>(V)},
+              m->err.as<int>(), s);
   if (m->has_b && BV)
     launch_gemm(m->ma_b, m->mb_v, m->tiles.as<tc::Tile>(), (int)tl.size(), m->sh,
                 MatvecEpi{reinterpret_cast<double2*>(BV), m->n}, m->err.as<int>(), s);

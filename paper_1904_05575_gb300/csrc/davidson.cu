@@ -67,17 +67,24 @@ __global__ void k_diag_real(int n, const double2* A, int64_t ld, double* d) {
   if (i < n) d[i] = A[i + (int64_t)i * ld].x;
 }
 
-// s <- (s + s^H) / 2 on an m x m block with leading dimension lds
-__global__ void k_hermitize(int m, double2* s, int lds) {
+// After columns m0..m-1 of s were computed (rows 0..m-1): rows m0..m-1 of
+// the old columns become the conjugates of what was computed, and the new
+// square block is hermitized as k_hermitize does.
+__global__ void k_hermitize_new(int m0, int m, double2* s, int lds) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i < m && j < m && i < j) {
+  int j = m0 + blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= m || j >= m) return;
+  if (i < m0) {
+    const double2 a = s[i + (int64_t)j * lds];
+    s[j + (int64_t)i * lds] = make_double2(a.x, -a.y);
+  } else if (i < j) {
     double2 a = s[i + (int64_t)j * lds], b = s[j + (int64_t)i * lds];
     double2 h = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
     s[i + (int64_t)j * lds] = h;
     s[j + (int64_t)i * lds] = make_double2(h.x, -h.y);
+  } else if (i == j) {
+    s[i + (int64_t)i * lds].y = 0.0;
   }
-  if (i < m && j < m && i == j) s[i + (int64_t)i * lds].y = 0.0;
 }
 
 __global__ void k_zero_strict_upper(int m, double2* l, int ldl) {
@@ -157,6 +164,7 @@ struct Solver {
   std::unique_ptr<DeviceBuffer> work_;
   int lwork = 0;
   int m = 0;          // current basis size
+  int m_proj = 0;     // columns of the projected a+ and a- already computed
   std::vector<double> D;
   // block orthogonalisation: Gram matrix and triangular factor (b x b, b <=
   // 4 nev or mmax), column norms and the indices of kept columns
@@ -320,15 +328,21 @@ struct Solver {
   // projected problem on the current basis; fills U (u, m x nev), W (w, m x nev), E (host)
   void rayleigh_ritz(int k, std::vector<double>& E) {
     const cuDoubleComplex one = make_cuDoubleComplex(1, 0), zero = make_cuDoubleComplex(0, 0);
-    BSE_CUBLAS(cublasZgemm(h.blas, CUBLAS_OP_C, CUBLAS_OP_N, m, m, n, &one,
-                           V.as<cuDoubleComplex>(), n, P.as<cuDoubleComplex>(), n, &zero,
-                           ap.as<cuDoubleComplex>(), mmax));
-    BSE_CUBLAS(cublasZgemm(h.blas, CUBLAS_OP_C, CUBLAS_OP_N, m, m, n, &one,
-                           V.as<cuDoubleComplex>(), n, M.as<cuDoubleComplex>(), n, &zero,
-                           am.as<cuDoubleComplex>(), mmax));
+    // a+ = V^H P, a- = V^H M: only the columns of the vectors added since the
+    // last step (the basis only grows between restarts); the rows of the new
+    // vectors in the old columns follow from Hermiticity
+    const int m0 = m_proj < m ? m_proj : 0, nw = m - m0;
+    BSE_CUBLAS(cublasZgemm(h.blas, CUBLAS_OP_C, CUBLAS_OP_N, m, nw, n, &one,
+                           V.as<cuDoubleComplex>(), n, P.as<cuDoubleComplex>() + (int64_t)m0 * n, n,
+                           &zero, ap.as<cuDoubleComplex>() + (int64_t)m0 * mmax, mmax));
+    BSE_CUBLAS(cublasZgemm(h.blas, CUBLAS_OP_C, CUBLAS_OP_N, m, nw, n, &one,
+                           V.as<cuDoubleComplex>(), n, M.as<cuDoubleComplex>() + (int64_t)m0 * n, n,
+                           &zero, am.as<cuDoubleComplex>() + (int64_t)m0 * mmax, mmax));
+    m_proj = m;
     dim3 tb(16, 16), gb((m + 15) / 16, (m + 15) / 16);
-    k_hermitize<<<gb, tb, 0, s>>>(m, ap.as<double2>(), mmax);
-    k_hermitize<<<gb, tb, 0, s>>>(m, am.as<double2>(), mmax);
+    dim3 gn((m + 15) / 16, (nw + 15) / 16);
+    k_hermitize_new<<<gn, tb, 0, s>>>(m0, m, ap.as<double2>(), mmax);
+    k_hermitize_new<<<gn, tb, 0, s>>>(m0, m, am.as<double2>(), mmax);
     note_launches(2);
     // a- = l l^H
     BSE_CUDA(cudaMemcpy2DAsync(L.ptr, (size_t)mmax * 16, am.ptr, (size_t)mmax * 16, (size_t)m * 16,
@@ -587,6 +601,7 @@ void davidson_fp64(int n, const bse_c128* A, const bse_c128* B, int64_t ld, int 
                              sv.V.as<cuDoubleComplex>(), n, sv.W.as<cuDoubleComplex>(), mmax,
                              &zero, sv.R1.as<cuDoubleComplex>() + (int64_t)kr * n, n));
       sv.m = 0;
+      sv.m_proj = 0;
       sv.append_block(sv.R1.as<cuDoubleComplex>(), 2 * kr);
       sv.matvec(0, sv.m);
     }

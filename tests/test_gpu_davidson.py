@@ -96,3 +96,23 @@ def test_davidson_tensor_core_matvecs(bse, name, nev, coupling):
     assert np.abs(e - np.sort(e_ref)[:nev]).max() < 1e-5
     assert 1 <= it < 200
     print(f" [{name} nev={nev} {'full' if coupling else 'tda'} TC matvecs: {it} iterations]", end="")
+
+
+def test_davidson_core_levels_tensor_core_matvecs(bse):
+    """Core-level window (2 levels near -400 eV x 20 conduction bands): the
+    transition energies on A's diagonal are 400 eV while the interaction is
+    about 100 eV.  The tensor-core matvecs apply the diagonal in FP64, so the
+    energies still agree with the dense FP64 solve far inside 1 meV."""
+    cfg = bi.BSEConfig("core", grid=2, nv=2, nc=20, ng=59, w_scale=0.05,
+                       e_v_range=(-400.5, -399.5), m_decay=0.05)
+    p = bi.make_problem(cfg)
+    n = p["nk"] * p["nv"] * p["nc"]
+    A, B = O.build_A_B(p)
+    e_ref = np.sort(O.solve_full(A, B)[0])
+    d = gpu_build(bse, p)
+    nev = 12
+    e, xpy, it = _run(bse, d, n, nev, tol=1e-5, matvec_precision=bse.BSE_PREC_BF16X6)
+    assert e_ref[0] > 399.0
+    assert np.abs(e - e_ref[:nev]).max() < 1e-5
+    assert 1 <= it < 200
+    print(f" [core levels nev={nev} TC matvecs: {it} iterations]", end="")
