@@ -233,7 +233,7 @@ def build_rooflines(bse, prec, phases, steps, shapes, peaks):
         "mixed_stage1_gemm": ("gemm_split_bf16: stage-1 GEMM, tcgen05", "tensor", s1),
         "mixed_stage2_tc": ("gemm_split_bf16: stage-2 pair-block GEMM, tcgen05", "tensor", s2),
         "mixed_exchange": ("gemm_split_bf16: exchange GEMM, tcgen05", "tensor", ex),
-        "mixed_stage2": ("k_stage2_pipe: stage-2 contraction, CUDA cores", "hbm", s2_bytes),
+        "mixed_stage2": ("k_stage2 family: stage-2 contraction, CUDA cores", "hbm", s2_bytes),
         "mixed_split": ("k_split: operand split, HBM pass", "hbm",
                         sum(split_bytes(*sh, pieces=pieces) for sh in shapes)),
     }

@@ -346,21 +346,61 @@ struct Stage2Args {
   int64_t ld;
 };
 
-// TX x TT output tile per block (X rows x T rows), RX x RT outputs per thread
+// asynchronous global -> shared copies (zero-filled when pred is false)
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool pred) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc::smem_u32(smem)),
+               "l"(gmem), "r"(pred ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool pred) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(tc::smem_u32(smem)),
+               "l"(gmem), "r"(pred ? 8 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// TX x TT output tile per block (X rows x T rows), RX x RT outputs per thread.
+// Software-pipelined: the raw complex128 X rows and FP32 T rows of the next 16
+// plane waves are copied to shared memory asynchronously (cp.async, double
+// buffered) while the current chunk is converted and contracted.
 template <int TX, int TT, int RX, int RT>
 __global__ void __launch_bounds__((TX / RX) * (TT / RT)) k_stage2(Stage2Args a) {
   constexpr int NTH = (TX / RX) * (TT / RT), CT = TT / RT, CX = TX / RX;
-  constexpr int GC = 32;
-  __shared__ float2 Xs[TX][GC + 1];
-  __shared__ float2 Ts[GC][TT + 1];
+  constexpr int GC = 16;
+  __shared__ __align__(16) uint4 Xr[2][TX][GC];      // raw FP64 complex
+  __shared__ __align__(16) float2 Tr[2][GC][TT];     // FP32 complex
+  __shared__ float2 Xs[TX][GC + 1];                  // converted X of the current chunk
   const int p = blockIdx.x;
   const int k = a.k_begin + p / a.nk, kp = p % a.nk;
   const int rx0 = blockIdx.y * TX, rt0 = blockIdx.z * TT;
   const int64_t xp = a.x_transpose_pair ? (int64_t)kp * a.nk + k : (int64_t)p;
-  const double2* X = a.x + xp * a.rows_x * a.ng;
+  const uint4* X = reinterpret_cast<const uint4*>(a.x) + xp * a.rows_x * a.ng;
   const int64_t trow0 = a.t_row0 + (int64_t)a.slot_of_pair[p] * a.rows_t;
   const int tid = threadIdx.x;
   const int tx = tid % CT, ty = tid / CT;
+  const int nchunks = (a.ng + GC - 1) / GC;
+
+  auto prefetch = [&](int c, int buf) {
+    const int g0 = c * GC;
+    for (int i = tid; i < TX * GC; i += NTH) {
+      const int r = i / GC, g = i % GC;
+      const bool ok = rx0 + r < a.rows_x && g0 + g < a.ng;
+      cp_async16(&Xr[buf][r][g], ok ? (const void*)(X + (int64_t)(rx0 + r) * a.ng + g0 + g)
+                                    : (const void*)X, ok);
+    }
+    for (int i = tid; i < GC * TT; i += NTH) {
+      const int g = i / TT, r = i % TT;
+      const bool ok = rt0 + r < a.rows_t && g0 + g < a.ng;
+      const float2* src = a.T + (ok ? (int64_t)(g0 + g) * a.t_ld + trow0 + rt0 + r : 0);
+      cp_async8(&Tr[buf][g][r], src, ok);
+    }
+    cp_async_commit();
+  };
+
   // compensated FP32: sums over 8 plane waves in FMA, folded into (hi, lo) pairs
   // with TwoSum, so no FP64 instruction runs inside the loop
   float hx[RX][RT], hy[RX][RT], lx[RX][RT], ly[RX][RT];
@@ -368,26 +408,24 @@ __global__ void __launch_bounds__((TX / RX) * (TT / RT)) k_stage2(Stage2Args a) 
   for (int i = 0; i < RX; ++i)
 #pragma unroll
     for (int j = 0; j < RT; ++j) hx[i][j] = hy[i][j] = lx[i][j] = ly[i][j] = 0.f;
+  const uint32_t xflip = a.conj_x ? 0x80000000u : 0u;
+  const float tsign = a.conj_t ? -1.f : 1.f;
 
-  for (int g0 = 0; g0 < a.ng; g0 += GC) {
+  prefetch(0, 0);
+  for (int c = 0; c < nchunks; ++c) {
+    const int buf = c & 1;
+    if (c + 1 < nchunks) {
+      prefetch(c + 1, buf ^ 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
     for (int i = tid; i < TX * GC; i += NTH) {
       const int r = i / GC, g = i % GC;
-      float2 v = make_float2(0.f, 0.f);
-      if (rx0 + r < a.rows_x && g0 + g < a.ng) {
-        const uint4 d = __ldg(reinterpret_cast<const uint4*>(X) + (int64_t)(rx0 + r) * a.ng + g0 + g);
-        const uint32_t dy = f64w_to_f32_bits(d.z, d.w) ^ (a.conj_x ? 0x80000000u : 0u);
-        v = make_float2(__uint_as_float(f64w_to_f32_bits(d.x, d.y)), __uint_as_float(dy));
-      }
-      Xs[r][g] = v;
-    }
-    for (int i = tid; i < TT * GC; i += NTH) {
-      const int g = i / TT, r = i % TT;
-      float2 v = make_float2(0.f, 0.f);
-      if (rt0 + r < a.rows_t && g0 + g < a.ng) {
-        v = a.T[(int64_t)(g0 + g) * a.t_ld + trow0 + rt0 + r];
-        if (a.conj_t) v.y = -v.y;
-      }
-      Ts[g][r] = v;
+      const uint4 d = Xr[buf][r][g];
+      Xs[r][g] = make_float2(__uint_as_float(f64w_to_f32_bits(d.x, d.y)),
+                             __uint_as_float(f64w_to_f32_bits(d.z, d.w) ^ xflip));
     }
     __syncthreads();
 #pragma unroll
@@ -403,7 +441,10 @@ __global__ void __launch_bounds__((TX / RX) * (TT / RT)) k_stage2(Stage2Args a) 
 #pragma unroll
         for (int i = 0; i < RX; ++i) xv[i] = Xs[ty + i * CX][g];
 #pragma unroll
-        for (int j = 0; j < RT; ++j) tv[j] = Ts[g][tx + j * CT];
+        for (int j = 0; j < RT; ++j) {
+          tv[j] = Tr[buf][g][tx + j * CT];
+          tv[j].y *= tsign;
+        }
 #pragma unroll
         for (int i = 0; i < RX; ++i)
 #pragma unroll
@@ -427,7 +468,7 @@ __global__ void __launch_bounds__((TX / RX) * (TT / RT)) k_stage2(Stage2Args a) 
           ly[i][j] += e;
         }
     }
-    __syncthreads();
+    __syncthreads();   // the next prefetch overwrites this buffer
   }
 
   const int nv = a.nv, nc = a.nc;
@@ -455,23 +496,6 @@ __global__ void __launch_bounds__((TX / RX) * (TT / RT)) k_stage2(Stage2Args a) 
       o.y -= f32_to_f64_bits(scale_hi_lo(sc, hy[i][j], ly[i][j]));
       *dst = o;
     }
-}
-
-// asynchronous global -> shared copies (zero-filled when pred is false)
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool pred) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc::smem_u32(smem)),
-               "l"(gmem), "r"(pred ? 16 : 0)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool pred) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(tc::smem_u32(smem)),
-               "l"(gmem), "r"(pred ? 8 : 0)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 // Stage 2 for pair blocks of at most 16 x 16, software-pipelined: the raw
@@ -578,8 +602,9 @@ __global__ void __launch_bounds__(256) k_stage2_pipe(Stage2Args a) {
   *dst = o;
 }
 
-// Stage 2 for skinny pair blocks: at most RT rows of T against long X rows
-// (W^rr with 2 core levels: 4 (v, v') rows of T, 400 (c, c') rows of X).  One
+// Stage 2 for skinny pair blocks: at most RT rows of T against X rows of 16
+// or more (W^rr with 2 core levels: 4 (v, v') rows of T, 400 (c, c') rows of
+// X; or 2 conduction bands against 4 to 6 valence bands).  One
 // thread per X row, SK_ROWS consecutive rows of the term (running across pair
 // blocks, at most SK_PAIRS of them) per block.  The raw complex128 X rows
 // stream through shared memory in chunks of SK_GC plane waves (cp.async,
@@ -587,7 +612,7 @@ __global__ void __launch_bounds__(256) k_stage2_pipe(Stage2Args a) {
 // once and contracts it against the T rows of its pair, which every thread of
 // the pair reads at the same address.  The work is bound by reading X once.
 // Same compensated FP32 arithmetic, in the same order, as k_stage2.
-constexpr int SK_ROWS = 128, SK_GC = 8, SK_PAIRS = 3;
+constexpr int SK_ROWS = 128, SK_GC = 8, SK_PAIRS = 9;
 
 template <int RT>
 __global__ void __launch_bounds__(SK_ROWS) k_stage2_skinny(Stage2Args a, int64_t total_rows) {
@@ -618,6 +643,9 @@ __global__ void __launch_bounds__(SK_ROWS) k_stage2_skinny(Stage2Args a, int64_t
   __syncthreads();
   const uint4* X = reinterpret_cast<const uint4*>(a.x);
   const int nchunks = (a.ng + SK_GC - 1) / SK_GC;
+  // pair blocks this block's rows touch (at most SK_PAIRS)
+  const int64_t row_last = (row0 + SK_ROWS < total_rows ? row0 + SK_ROWS : total_rows) - 1;
+  const int npp = (int)(row_last / rows_x) - p_first + 1;
   auto prefetch = [&](int c, int buf) {
     const int g0 = c * SK_GC;
 #pragma unroll
@@ -628,8 +656,8 @@ __global__ void __launch_bounds__(SK_ROWS) k_stage2_skinny(Stage2Args a, int64_t
       const bool ok = off >= 0 && g0 + g < a.ng;
       cp_async16(&Xr[buf][r][g], ok ? (const void*)(X + off + g0 + g) : (const void*)X, ok);
     }
-    for (int i = tid; i < SK_GC * SK_PAIRS * RT; i += SK_ROWS) {
-      const int g = i / (SK_PAIRS * RT), q = (i / RT) % SK_PAIRS, rt = i % RT;
+    for (int i = tid; i < SK_GC * npp * RT; i += SK_ROWS) {
+      const int g = i / (npp * RT), q = (i / RT) % npp, rt = i % RT;
       const bool ok = toff[q] >= 0 && rt < a.rows_t && g0 + g < a.ng;
       const float2* src = a.T + (ok ? (int64_t)(g0 + g) * a.t_ld + toff[q] + rt : 0);
       cp_async8(&Tr[buf][g][q][rt], src, ok);
@@ -716,11 +744,20 @@ __global__ void __launch_bounds__(SK_ROWS) k_stage2_skinny(Stage2Args a, int64_t
 
 // true when k_stage2_skinny serves the term: T rows fit the register tile and
 // a block's SK_ROWS rows touch at most SK_PAIRS pair blocks
-// (rows_t is Nv^2 or Nc^2 there, so at most 4 when skinny)
+// (rows_t is Nv^2 or Nc^2 there, so at most 4 when skinny; X rows >= 16)
 bool stage2_skinny(const Stage2Args& a) {
   return a.rows_t <= 4 && (SK_ROWS - 1 + a.rows_x - 1) / a.rows_x + 1 <= SK_PAIRS;
 }
 
+// one pair block per grid.x, tiles of TX x TT outputs over grid.y / grid.z
+template <int TX, int TT, int RX, int RT>
+void launch_stage2_tiles(const Stage2Args& a, int npair, cudaStream_t s) {
+  dim3 grid(npair, (a.rows_x + TX - 1) / TX, (a.rows_t + TT - 1) / TT);
+  k_stage2<TX, TT, RX, RT><<<grid, (TX / RX) * (TT / RT), 0, s>>>(a);
+}
+
+// The kernel whose tile fits the pair block best (every variant adds in the
+// same order: the results do not depend on the choice).
 void launch_stage2(const Stage2Args& a, int npair, cudaStream_t s) {
   if (stage2_skinny(a)) {
     const int64_t total = (int64_t)npair * a.rows_x;
@@ -728,12 +765,16 @@ void launch_stage2(const Stage2Args& a, int npair, cudaStream_t s) {
     k_stage2_skinny<4><<<(unsigned)blocks, SK_ROWS, 0, s>>>(a, total);
   } else if (a.rows_x <= 16 && a.rows_t <= 16) {
     k_stage2_pipe<<<npair, 256, 0, s>>>(a);
-  } else if (a.rows_x <= 40 && a.rows_t <= 40 && (a.rows_x > 32 || a.rows_t > 32)) {
-    // one 40 x 40 tile per pair block (e.g. W^ra with Nv * Nc = 40)
-    k_stage2<40, 40, 2, 5><<<npair, 160, 0, s>>>(a);
+  } else if (a.rows_x <= 24 && a.rows_t <= 24) {           // e.g. W^ra, 4 x 6 bands
+    launch_stage2_tiles<24, 24, 2, 3>(a, npair, s);
+  } else if (a.rows_x <= 32 && a.rows_t <= 16) {           // e.g. W^rr, 3 x 5 bands (25 x 9)
+    launch_stage2_tiles<32, 16, 2, 2>(a, npair, s);
+  } else if (a.rows_x <= 40 && a.rows_t <= 16) {           // e.g. W^rr, 4 x 6 bands (36 x 16)
+    launch_stage2_tiles<40, 16, 2, 2>(a, npair, s);
+  } else if (a.rows_x <= 40 && a.rows_t <= 40) {           // e.g. W^ra, 2 x 20 bands (40 x 40)
+    launch_stage2_tiles<40, 40, 2, 5>(a, npair, s);
   } else {
-    dim3 grid(npair, (a.rows_x + 31) / 32, (a.rows_t + 31) / 32);
-    k_stage2<32, 32, 2, 2><<<grid, 256, 0, s>>>(a);
+    launch_stage2_tiles<32, 32, 2, 2>(a, npair, s);
   }
   BSE_CUDA(cudaGetLastError());
   note_launches(1);

@@ -47,6 +47,11 @@ SHAPES = {
                           e_v_range=(-400.5, -399.5), m_decay=0.05),
     # 4 T rows against 64 X rows: a block of 128 X rows spans three pair blocks
     "v2c8": bi.BSEConfig("slab-v2c8", grid=2, nv=2, nc=8, ng=59, w_scale=0.1),
+    # 4 T rows against 36 (c, c') rows, and 4 (c, c') T rows against 16 (v, v')
+    # X rows (W applied to the conduction side): up to nine pair blocks per
+    # block of 128 X rows
+    "v2c6": bi.BSEConfig("slab-v2c6", grid=2, nv=2, nc=6, ng=59, w_scale=0.1),
+    "v4c2": bi.BSEConfig("slab-v4c2", grid=2, nv=4, nc=2, ng=59, w_scale=0.1),
 }
 
 
@@ -99,7 +104,7 @@ def _build_slabs(bse, d, slabs, prec, fused=True, one_call=False):
 
 PATHS = [("c1", 0, True), ("c1", 2, True), ("c1", 2, False), ("v2c3", 0, True),
          ("v2c3", 2, True), ("v8c8", 0, True), ("v8c8", 2, True), ("v2c20", 0, True),
-         ("v2c20", 2, True), ("v2c8", 2, True)]
+         ("v2c20", 2, True), ("v2c8", 2, True), ("v2c6", 2, True), ("v4c2", 2, True)]
 
 
 @pytest.mark.parametrize("shape,prec,fused", PATHS,
