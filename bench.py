@@ -42,8 +42,8 @@ FP64_PEAK_TFLOPS = 1.25     # GB300 FP64 (CUDA-core and tensor) nominal rate
 # c2 workload's kernels, from the ncu captures summarised in profiles/; None
 # until re-taken after a kernel changes
 TRAFFIC_BYTES = {
-    "mixed_direct_fused": 832.9e6,     # one launch = one build (profiles/mixed_build_c2_kernels.md)
-    "mixed_split": 671e6,              # the 6 launches of one build
+    "mixed_direct_fused": 832.4e6,     # one launch = one build (profiles/mixed_build_c2_kernels.md)
+    "mixed_split": 663.9e6,            # the 6 launches of one build
 }
 
 
@@ -222,11 +222,14 @@ def build_rooflines(bse, prec, phases, steps, shapes, peaks):
     s1 = sum(sum(stage1_flops(*sh)) for sh in shapes)
     ex = sum(8.0 * (sh[0] * sh[1] * sh[2]) ** 2 * sh[3] for sh in shapes)
     s2 = sum(2 * 8.0 * sh[3] * (sh[0] * sh[1] * sh[2]) ** 2 for sh in shapes)
-    s2_bytes = 0.0
+    # CUDA-core stage 2 per term: X read as complex128, T as FP32 complex, the
+    # A or B entries read and written once
+    s2_term = [0.0, 0.0]
     for nk, nv, nc, ng in shapes:
         n = nk * nv * nc
-        for rt, rx in term_rows(nv, nc):
-            s2_bytes += nk * nk * ng * (16 * rx + 8 * rt) + 32 * n * n
+        for i, (rt, rx) in enumerate(term_rows(nv, nc)):
+            s2_term[i] += nk * nk * ng * (16 * rx + 8 * rt) + 32 * n * n
+    s2_bytes = sum(s2_term)
     kinds = {
         "mixed_direct_fused": ("gemm_split_bf16_direct: stage-1 GEMM + pair contraction, tcgen05",
                                "tensor", s1),
@@ -234,12 +237,19 @@ def build_rooflines(bse, prec, phases, steps, shapes, peaks):
         "mixed_stage2_tc": ("gemm_split_bf16: stage-2 pair-block GEMM, tcgen05", "tensor", s2),
         "mixed_exchange": ("gemm_split_bf16: exchange GEMM, tcgen05", "tensor", ex),
         "mixed_stage2": ("k_stage2 family: stage-2 contraction, CUDA cores", "hbm", s2_bytes),
+        "mixed_stage2_wrr": ("k_stage2 family: W^rr stage-2 contraction, CUDA cores", "hbm",
+                             s2_term[0]),
+        "mixed_stage2_wra": ("k_stage2 family: W^ra stage-2 contraction, CUDA cores", "hbm",
+                             s2_term[1]),
         "mixed_split": ("k_split: operand split, HBM pass", "hbm",
                         sum(split_bytes(*sh, pieces=pieces) for sh in shapes)),
     }
     # the captured DRAM bytes describe the c2 workload alone
     traffic = TRAFFIC_BYTES if shapes == [(64, 4, 4, 181)] and products == 6 else {}
-    found = sorted(((per_build(k), k) for k in kinds if k in phases), reverse=True)
+    # the per-term stage-2 phases, where timed, replace their sum
+    per_term = "mixed_stage2_wrr" in phases or "mixed_stage2_wra" in phases
+    found = sorted(((per_build(k), k) for k in kinds
+                    if k in phases and not (per_term and k == "mixed_stage2")), reverse=True)
     out = []
     for ms, name in found[:2]:
         what, bound, work = kinds[name]
@@ -297,13 +307,11 @@ def run_reference(args):
     return 0
 
 
-C4_SLAB = 64   # k rows per slab of the core-level workload (63 GB of m_cc per slab)
-
-
 def run_c4(args, bse, bi, prec, world, rank, local):
-    """Core-level workload (Nk=512, Nv=2 core levels, Nc=20, NG=300, N=20,480,
-    full BSE): its pair arrays (m_cc alone 503 GB) exceed the device memory,
-    so A and B are built in k-row slabs of C4_SLAB rows.  Before each slab's
+    """Core-level workload (c4: Nk=512, Nv=2 core levels, Nc=20, NG=300,
+    N=20,480, full BSE; c4s: the same recipe on a 4x4x4 grid): c4's pair
+    arrays (m_cc alone 503 GB) exceed the device memory, so A and B are built
+    in k-row slabs of --slab-rows rows.  Before each slab's
     build its m_vv and m_cc are drawn on the device (untimed, S3 kept across
     slabs); n_vc, W, M_x and A, B stay resident.  Each slab's plan execute is
     timed `steps` times after `warmup` untimed runs; a step is the whole build,
@@ -316,8 +324,8 @@ def run_c4(args, bse, bi, prec, world, rank, local):
     dev = "cuda"
     stream = torch.cuda.current_stream()
     seed = 20190411 + rank
-    kn = C4_SLAB
-    p = bi.make_problem_torch("c4", q_index=0, seed=seed, k_slab=(0, kn))
+    kn = args.slab_rows
+    p = bi.make_problem_torch(args.config, q_index=0, seed=seed, k_slab=(0, kn))
     nk, nv, nc, ng = p["nk"], p["nv"], p["nc"], p["ng"]
     n = nk * nv * nc
     flops = build_flops(nk, nv, nc, ng)
@@ -329,12 +337,15 @@ def run_c4(args, bse, bi, prec, world, rank, local):
     launches = 0
     sampler = ClockSampler(local)
     sampler.start()
+    if nk % kn:
+        raise SystemExit(f"--slab-rows {kn} must divide Nk = {nk}")
     for kb in range(0, nk, kn):
         if kb:
             for x in (p, d):
                 x["m_vv"] = x["m_cc"] = None
             torch.cuda.empty_cache()
-            p["m_vv"], p["m_cc"] = d["m_vv"], d["m_cc"] = bi.pair_slab_torch("c4", kb, kn, 0, seed)
+            p["m_vv"], p["m_cc"] = d["m_vv"], d["m_cc"] = bi.pair_slab_torch(args.config, kb, kn, 0,
+                                                                               seed)
         plan = bse.Plan([bse.make_problem_struct(d, k_begin=kb, k_count=kn)], precision=prec,
                         autotune=True)
         tile_cols = plan.tile_cols
@@ -365,6 +376,7 @@ def run_c4(args, bse, bi, prec, world, rank, local):
             fp64_slab_ms.append(e0.elapsed_time(e1))
     clocks = sampler.stop()
     phases = bse.bse_phase_report()
+    m_cc_gb = kn * nk * nc * nc * ng * 16 / 1e9
     t_build = max_over_ranks([sum(slab_ms)], dev, world)[0]
     value = weak_scaling_value(world, flops, t_build)
 
@@ -450,11 +462,11 @@ def run_c4(args, bse, bi, prec, world, rank, local):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp64": "f64", "bf16x6": "bf16x6(f32 acc)", "bf16x3": "bf16x3(f32 acc)"}[args.precision],
             "data": "synthetic",
-            "config": {"workload": f"c4 core-level case: Q 0, Nk={nk} (8x8x8), Nv={nv} core levels, "
+            "config": {"workload": f"{args.config} core-level case: Q 0, Nk={nk}, Nv={nv} core levels, "
                                    f"Nc={nc}, N={n}, NG={ng}, full BSE, built in {nk // kn} k-row "
                                    f"slabs of {kn} (pair arrays drawn on the GPU per slab)",
                        "precision": args.precision, "build_only": True,
-                       "l2": "inputs larger than L2 (63 GB of m_cc per slab)",
+                       "l2": f"inputs larger than L2 ({m_cc_gb:.1f} GB of m_cc per slab)",
                        "parallelism": f"Q replicas x{world}"},
             "build_ms": t_build, "slab_build_ms": slab_ms,
             "build_api": f"bse_plan_execute per slab (tile width autotuned: {tile_cols} columns)",
@@ -491,11 +503,13 @@ def main():
                     help="Davidson residual tolerance in eV (1e-5; 1e-4 for c4, whose "
                          "interaction terms reach 100 eV)")
     ap.add_argument("--dav-max-iter", type=int, default=300)
+    ap.add_argument("--slab-rows", type=int, default=64,
+                    help="c4 / c4s: k rows per slab of the pair arrays")
     ap.add_argument("--fp64-dense", action="store_true",
                     help="with --lowest: also time the plain FP64 path (FP64 build + dense solve)")
     args = ap.parse_args()
     if args.nev is None:
-        args.nev = 50 if args.config == "c4" else 16
+        args.nev = 50 if args.config in ("c4", "c4s") else 16
     if args.impl == "reference":
         return run_reference(args)
     args.warmup = max(args.warmup, 3)
@@ -525,7 +539,7 @@ def main():
     prec = prec_map[args.precision]
 
     # each rank: its own momentum transfers (Q replicas), resident in HBM
-    if args.config == "c4":
+    if args.config in ("c4", "c4s"):
         rc = run_c4(args, bse, bi, prec, world, rank, local)
         if world > 1:
             dist.destroy_process_group()

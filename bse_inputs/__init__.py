@@ -101,6 +101,12 @@ CONFIGS: Dict[str, BSEConfig] = {
                     q_abs=(0.2, 0.3, 0.4, 0.5, 0.6),
                     e_v_range=(-400.5, -399.5), e_c_range=(1.0, 4.0),
                     m_decay=0.05, w_scale=0.25, omega_range=(395.0, 410.0)),
+    # the core-like recipe on a 4x4x4 grid (N = 2,560): small enough for
+    # profiling captures and quick Davidson checks, same pair-block shapes
+    "c4s": BSEConfig("c4s", grid=4, nv=2, nc=20, ng=300,
+                     q_abs=(0.2, 0.3, 0.4, 0.5, 0.6),
+                     e_v_range=(-400.5, -399.5), e_c_range=(1.0, 4.0),
+                     m_decay=0.05, w_scale=0.25, omega_range=(395.0, 410.0)),
     # molecular-crystal-like: 4x4x4 grid, 20x20 bands, NG = 500, strong off-diagonal W
     # (strong off-diagonal W with 500 plane waves: scale 0.002 keeps |W^rr| near
     # 0.7 eV, below the 1.1 eV smallest transition, as 0.25 does at c2)
