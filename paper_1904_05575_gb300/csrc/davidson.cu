@@ -481,15 +481,16 @@ __global__ void k_xmy(int64_t total, int n, const double2* ax, const double2* bx
 }  // namespace
 
 // Largest basis per wanted exciton (vectors of V per nev).  The projected
-// m x m eigensolve dominates an iteration and grows as m^3, so a smaller basis
-// trades more restarts for cheaper iterations: for the lowest 50 of N = 8,640
-// core-level excitons 24 per exciton took 70 iterations in 8.4 s, 12 took 97
-// in 6.3 s, 8 took 178 in 10.4 s.  The environment variable
-// BSE_DAVIDSON_BASIS_PER_EV (6 to 48) overrides the default for tuning.
+// m x m eigensolve grows as m^3, so a smaller basis trades more restarts for
+// cheaper iterations; which wins depends on the problem.  Lowest 50 core-level
+// excitons: at N = 8,640, 24 per exciton took 70 iterations in 8.4 s and 12
+// took 97 in 6.3 s; at N = 20,480, 24 took 84 in 16.6 s and 12 took 161 in
+// 26.5 s.  The environment variable BSE_DAVIDSON_BASIS_PER_EV (6 to 48)
+// overrides the default for tuning.
 static int basis_per_ev() {
   const char* e = getenv("BSE_DAVIDSON_BASIS_PER_EV");
-  const int v = e ? atoi(e) : 12;
-  return v >= 6 && v <= 48 ? v : 12;
+  const int v = e ? atoi(e) : 24;
+  return v >= 6 && v <= 48 ? v : 24;
 }
 
 void davidson_fp64(int n, const bse_c128* A, const bse_c128* B, int64_t ld, int nev, double tol,
