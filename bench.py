@@ -45,6 +45,14 @@ TRAFFIC_BYTES = {
     "mixed_direct_fused": 832.4e6,     # one launch = one build (profiles/mixed_build_c2_kernels.md)
     "mixed_split": 663.9e6,            # the 6 launches of one build
 }
+# the c4 core-level build's stage-2 kernels, per build (8 slab launches each):
+# the capture of one 16-row slab of the same recipe on a 4x4x4 grid (1,024
+# pair blocks) scaled by the 262,144 pair blocks of c4
+# (profiles/mixed_build_c4_slab_kernels.md)
+TRAFFIC_BYTES_C4 = {
+    "mixed_stage2_wrr": 2072.9e6 * 256,
+    "mixed_stage2_wra": 338.6e6 * 256,
+}
 
 
 def build_flops(nk, nv, nc, ng, coupling=True):
@@ -244,8 +252,12 @@ def build_rooflines(bse, prec, phases, steps, shapes, peaks):
         "mixed_split": ("k_split: operand split, HBM pass", "hbm",
                         sum(split_bytes(*sh, pieces=pieces) for sh in shapes)),
     }
-    # the captured DRAM bytes describe the c2 workload alone
-    traffic = TRAFFIC_BYTES if shapes == [(64, 4, 4, 181)] and products == 6 else {}
+    # the captured DRAM bytes describe the c2 and c4 workloads alone
+    traffic = {}
+    if shapes == [(64, 4, 4, 181)] and products == 6:
+        traffic = TRAFFIC_BYTES
+    elif shapes == [(512, 2, 20, 300)] and products == 6:
+        traffic = TRAFFIC_BYTES_C4
     # the per-term stage-2 phases, where timed, replace their sum
     per_term = "mixed_stage2_wrr" in phases or "mixed_stage2_wra" in phases
     found = sorted(((per_build(k), k) for k in kinds
