@@ -223,17 +223,23 @@ def _w_matrix(rng, gvec, w_decay, w_diag, real):
 
 
 def make_problem(cfg: BSEConfig | str, q_index: int = 0, seed: int = 20190411,
-                 k_rows: Optional[Sequence[int]] = None) -> Dict[str, np.ndarray]:
+                 k_rows: Optional[Sequence[int]] = None,
+                 draws_of: Optional[int] = None) -> Dict[str, np.ndarray]:
     """Draw one BSE problem (one momentum transfer Q) of configuration cfg.
 
     k_rows restricts the pair arrays (m_vv, m_cc, n_vc) to a slab of k rows;
-    every other array is always complete.  Returns plain numpy arrays plus
-    scalars: omega_cell (bohr^3), nk, nv, nc, ng, q_vec, c_q, rho, omega,
-    delta (half width at half maximum, eV)."""
+    every other array is always complete.  draws_of = j takes every random
+    array (energies, M, N, W) from the streams of Q index j while Q itself is
+    cfg.q_abs[q_index]: the problems of one j then form a family that changes
+    smoothly along Q (through v(G+Q) and c_Q only), as an exciton dispersion
+    needs.  Returns plain numpy arrays plus scalars: omega_cell (bohr^3), nk,
+    nv, nc, ng, q_vec, c_q, rho, omega, delta (half width at half maximum,
+    eV)."""
     if isinstance(cfg, str):
         cfg = CONFIGS[cfg]
     n, nk = cfg.grid, cfg.nk
     nv, nc = cfg.window(q_index)
+    qd = q_index if draws_of is None else draws_of
     ng = cfg.ng
     if k_rows is None:
         k_rows = range(nk)
@@ -244,20 +250,20 @@ def make_problem(cfg: BSEConfig | str, q_index: int = 0, seed: int = 20190411,
     g2 = (gvec ** 2).sum(1)
     damp = 1.0 / (1.0 + cfg.m_decay * g2)
 
-    r_e = _rng(seed, "energies", q_index)
+    r_e = _rng(seed, "energies", qd)
     e_v = r_e.uniform(*cfg.e_v_range, size=(nk, nv))
     e_c = r_e.uniform(*cfg.e_c_range, size=(nk, nc))
 
     m_x = np.empty((nk, nv, nc, ng), np.complex128)
     for k in range(nk):
-        m_x[k] = _cnormal(_rng(seed, "m_x", q_index, k), (nv, nc, ng)) * damp
+        m_x[k] = _cnormal(_rng(seed, "m_x", qd, k), (nv, nc, ng)) * damp
 
-    m_vv = _hermitian_pair_array(nk, nv, ng, damp, seed, "m_vv", q_index, k_rows)
-    m_cc = _hermitian_pair_array(nk, nc, ng, damp, seed, "m_cc", q_index, k_rows)
+    m_vv = _hermitian_pair_array(nk, nv, ng, damp, seed, "m_vv", qd, k_rows)
+    m_cc = _hermitian_pair_array(nk, nc, ng, damp, seed, "m_cc", qd, k_rows)
     n_vc = np.empty((len(k_rows), nk, nv, nc, ng), np.complex128)
     for r, k in enumerate(k_rows):
         for kp in range(nk):
-            n_vc[r, kp] = _cnormal(_rng(seed, "n_vc", q_index, k, kp), (nv, nc, ng)) * damp
+            n_vc[r, kp] = _cnormal(_rng(seed, "n_vc", qd, k, kp), (nv, nc, ng)) * damp
 
     q_minus, q_plus, neg = pair_maps(n)
     w = np.empty((nk, ng, ng), np.complex128)
@@ -266,7 +272,7 @@ def make_problem(cfg: BSEConfig | str, q_index: int = 0, seed: int = 20190411,
         if nq < q:
             w[q] = np.conj(w[nq])
         else:
-            w[q] = _w_matrix(_rng(seed, "w", q_index, q), gvec, cfg.w_decay, cfg.w_diag,
+            w[q] = _w_matrix(_rng(seed, "w", qd, q), gvec, cfg.w_decay, cfg.w_diag,
                              real=(nq == q))
     w *= cfg.w_scale
 

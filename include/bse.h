@@ -285,7 +285,8 @@ int bse_xpy(int32_t n, int32_t k, const bse_c128* Z, const bse_c128* L, int64_t 
  *              BSE_PREC_BF16X6 / BF16X3: A and B split once into BF16 pieces
  *              and the matvecs run on the tensor cores (FP32 accumulation in
  *              K segments, FP64 results); workspace 2 x 12 N^2 bytes (BF16X6).
- *              The residual floor is then ~1e-7 of |A|: keep tol_ev above it.
+ *              The residual floor then scales with ~1e-7 of the off-diagonal
+ *              part of A (A's diagonal is applied in FP64): keep tol_ev above it.
  *   E_out      [nev] device, ascending exciton energies (eV)
  *   XpY_out    [n x nev] device column-major, X+Y with (X+Y)^H (X-Y) = 1, or NULL
  *   iters_out  host, iterations used (may be NULL)
@@ -295,6 +296,21 @@ int bse_lowest_excitons(int32_t n, const bse_c128* A, const bse_c128* B, int64_t
                         double tol_ev, int32_t max_iter, int32_t precond, const void* mlp,
                         int32_t matvec_precision, double* E_out, bse_c128* XpY_out,
                         int32_t* iters_out, void* cuda_stream);
+
+/* bse_lowest_excitons started from a given subspace instead of unit vectors:
+ * the k0 columns of V0 ([n x k0] device column-major, read only), typically
+ * the X+Y of the same excitons at a neighbouring momentum transfer when the
+ * exciton dispersion E_lambda(Q) is traced over a line of Q (the warm start
+ * of an exciton band structure; the problems must share n and the transition
+ * order).  The columns are orthonormalised (dependent ones dropped) and unit
+ * vectors at the smallest A_aa are added until the basis holds
+ * nev + max(4, nev/4) vectors.  1 <= k0 <= min(4 nev, n); V0 16-byte aligned.
+ * Other arguments, outputs and errors as for bse_lowest_excitons. */
+int bse_lowest_excitons_from(int32_t n, const bse_c128* A, const bse_c128* B, int64_t ld,
+                             int32_t nev, double tol_ev, int32_t max_iter, int32_t precond,
+                             const void* mlp, int32_t matvec_precision, const bse_c128* V0,
+                             int32_t k0, double* E_out, bse_c128* XpY_out, int32_t* iters_out,
+                             void* cuda_stream);
 
 /* ---- learned preconditioner for bse_lowest_excitons -------------------------
  * Not in the paper: a per-transition network (4 features -> 128 -> 128 -> 1,

@@ -60,7 +60,8 @@ EXPORTED = ("bse_build_kernel", "bse_reduce", "bse_spectrum", "bse_last_error", 
             "bse_mlp_set_params", "bse_mlp_samples", "bse_mlp_loss_grad", "bse_mlp_train",
             "bse_mlp_predict", "bse_xpy", "bse_mlp_trajectory_samples", "bse_plan_create",
             "bse_plan_execute", "bse_plan_status", "bse_plan_tile_cols", "bse_plan_destroy",
-            "bse_plan_fused", "bse_spectrum_tensor", "bse_loss_function")
+            "bse_plan_fused", "bse_spectrum_tensor", "bse_loss_function",
+            "bse_lowest_excitons_from")
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -88,6 +89,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.bse_lowest_excitons.argtypes = [i32, vp, vp, i64, i32, dbl, i32, i32, vp, i32, vp, vp,
                                         ctypes.POINTER(i32), vp]
     lib.bse_lowest_excitons.restype = ctypes.c_int
+    lib.bse_lowest_excitons_from.argtypes = [i32, vp, vp, i64, i32, dbl, i32, i32, vp, i32, vp,
+                                             i32, vp, vp, ctypes.POINTER(i32), vp]
+    lib.bse_lowest_excitons_from.restype = ctypes.c_int
     lib.bse_xpy.argtypes = [i32, i32, vp, vp, i64, vp, vp, vp]
     lib.bse_xpy.restype = ctypes.c_int
     lib.bse_plan_create.argtypes = [ctypes.POINTER(bse_problem), i32, i32, i32,
@@ -278,9 +282,11 @@ def bse_loss_function(eps, v_inv: float, loss_out=None, sqw_out=None, stream=Non
 
 def bse_lowest_excitons(n: int, A, B, nev: int, E_out, XpY_out=None, tol_ev: float = 1e-4,
                         max_iter: int = 100, precond: int = 0, mlp=None, stream=None,
-                        matvec_precision: int = BSE_PREC_FP64) -> int:
+                        matvec_precision: int = BSE_PREC_FP64, start=None) -> int:
     """Lowest nev excitons by block Davidson; returns the iterations used.  On
-    BSE_ERR_NO_CONV the raised error carries .iters."""
+    BSE_ERR_NO_CONV the raised error carries .iters.  start: optional [k0, n]
+    complex128 CUDA tensor (column-major n x k0, e.g. the X+Y found at a
+    neighbouring Q) that seeds the basis (bse_lowest_excitons_from)."""
     import torch
     lib = load()
     a, ld = _matrix_ptr(A, n, "A")
@@ -292,14 +298,45 @@ def bse_lowest_excitons(n: int, A, B, nev: int, E_out, XpY_out=None, tol_ev: flo
         x = _ptr(XpY_out, torch.complex128, "XpY_out")
     iters = ctypes.c_int32(0)
     handle = mlp.handle if mlp is not None else None
-    st = lib.bse_lowest_excitons(n, a, b, ld, nev, float(tol_ev), int(max_iter), int(precond),
-                                 handle, int(matvec_precision), _ptr(E_out, torch.float64, "E_out"),
-                                 x, ctypes.byref(iters), _stream(stream))
+    if start is None:
+        st = lib.bse_lowest_excitons(n, a, b, ld, nev, float(tol_ev), int(max_iter), int(precond),
+                                     handle, int(matvec_precision),
+                                     _ptr(E_out, torch.float64, "E_out"), x, ctypes.byref(iters),
+                                     _stream(stream))
+    else:
+        if start.dim() != 2 or start.shape[1] != n:
+            raise ValueError("start must have shape [k0, n] (column-major n x k0)")
+        st = lib.bse_lowest_excitons_from(n, a, b, ld, nev, float(tol_ev), int(max_iter),
+                                          int(precond), handle, int(matvec_precision),
+                                          _ptr(start, torch.complex128, "start"), start.shape[0],
+                                          _ptr(E_out, torch.float64, "E_out"), x,
+                                          ctypes.byref(iters), _stream(stream))
     if st != BSE_OK:
         err = BSEError(st, lib.bse_last_error().decode(errors="replace"))
         err.iters = iters.value
         raise err
     return iters.value
+
+
+def exciton_bands(problems: Sequence[tuple], nev: int, tol_ev: float = 1e-4, max_iter: int = 200,
+                  matvec_precision: int = BSE_PREC_FP64, warm: bool = True, stream=None):
+    """Lowest nev exciton energies along a line of momentum transfers: problems
+    is a sequence of (n, A, B) built for consecutive Q (same n and transition
+    order).  Each Q after the first starts Davidson from the X+Y found at the
+    previous one (warm=False: from unit vectors).  Returns (E [nQ, nev] host
+    numpy array, iterations per Q)."""
+    import torch
+    out, iters, prev = [], [], None
+    for n, A, B in problems:
+        E = torch.empty(nev, dtype=torch.float64, device=A.device)
+        X = torch.empty((nev, n), dtype=torch.complex128, device=A.device)
+        it = bse_lowest_excitons(n, A, B, nev, E, X, tol_ev=tol_ev, max_iter=max_iter,
+                                 matvec_precision=matvec_precision, stream=stream,
+                                 start=prev if warm else None)
+        out.append(E.cpu().numpy())
+        iters.append(it)
+        prev = X
+    return np.stack(out), iters
 
 
 def bse_phase_timing(enable: bool) -> None:

@@ -359,10 +359,11 @@ extern "C" int bse_xpy(int32_t n, int32_t k, const bse_c128* Z, const bse_c128* 
   });
 }
 
-extern "C" int bse_lowest_excitons(int32_t n, const bse_c128* A, const bse_c128* B, int64_t ld,
-                                   int32_t nev, double tol_ev, int32_t max_iter, int32_t precond,
-                                   const void* mlp, int32_t matvec_precision, double* E_out,
-                                   bse_c128* XpY_out, int32_t* iters_out, void* cuda_stream) {
+namespace {
+int lowest_excitons(int32_t n, const bse_c128* A, const bse_c128* B, int64_t ld, int32_t nev,
+                    double tol_ev, int32_t max_iter, int32_t precond, const void* mlp,
+                    int32_t matvec_precision, const bse_c128* V0, int32_t k0, double* E_out,
+                    bse_c128* XpY_out, int32_t* iters_out, void* cuda_stream) {
   return guarded([&] {
     if (iters_out) *iters_out = 0;
     BSE_CHECK_ARG(n >= 1, "n must be >= 1");
@@ -380,11 +381,34 @@ extern "C" int bse_lowest_excitons(int32_t n, const bse_c128* A, const bse_c128*
                   "this build has no tensor-core path");
     BSE_CHECK_ARG(((uintptr_t)A & 15) == 0 && ((uintptr_t)B & 15) == 0,
                   "A and B must be 16-byte aligned");
+    if (V0 || k0) {
+      BSE_CHECK_ARG(V0 && k0 >= 1 && k0 <= 4 * nev && k0 <= n,
+                    "a starting block needs V0 and 1 <= k0 <= min(4 nev, n)");
+      BSE_CHECK_ARG(((uintptr_t)V0 & 15) == 0, "V0 must be 16-byte aligned");
+    }
     keep_pool_memory();
     davidson_fp64(n, A, B, ld, nev, tol_ev, max_iter, precond,
                   static_cast<const MlpNet*>(mlp), E_out, XpY_out, iters_out,
-                  static_cast<cudaStream_t>(cuda_stream), nullptr, matvec_precision);
+                  static_cast<cudaStream_t>(cuda_stream), nullptr, matvec_precision, V0, k0);
   });
+}
+}  // namespace
+
+extern "C" int bse_lowest_excitons(int32_t n, const bse_c128* A, const bse_c128* B, int64_t ld,
+                                   int32_t nev, double tol_ev, int32_t max_iter, int32_t precond,
+                                   const void* mlp, int32_t matvec_precision, double* E_out,
+                                   bse_c128* XpY_out, int32_t* iters_out, void* cuda_stream) {
+  return lowest_excitons(n, A, B, ld, nev, tol_ev, max_iter, precond, mlp, matvec_precision,
+                         nullptr, 0, E_out, XpY_out, iters_out, cuda_stream);
+}
+
+extern "C" int bse_lowest_excitons_from(int32_t n, const bse_c128* A, const bse_c128* B,
+                                        int64_t ld, int32_t nev, double tol_ev, int32_t max_iter,
+                                        int32_t precond, const void* mlp, int32_t matvec_precision,
+                                        const bse_c128* V0, int32_t k0, double* E_out,
+                                        bse_c128* XpY_out, int32_t* iters_out, void* cuda_stream) {
+  return lowest_excitons(n, A, B, ld, nev, tol_ev, max_iter, precond, mlp, matvec_precision, V0,
+                         k0, E_out, XpY_out, iters_out, cuda_stream);
 }
 
 extern "C" int bse_mlp_create(void** mlp, int32_t n_features, int32_t hidden, uint64_t seed) {

@@ -124,7 +124,8 @@ struct TrajectorySink;
 void davidson_fp64(int n, const bse_c128* A, const bse_c128* B, int64_t ld, int nev, double tol,
                    int max_iter, int precond, const MlpNet* mlp, double* E_out, bse_c128* XpY_out,
                    int32_t* iters_out, cudaStream_t stream, TrajectorySink* sink = nullptr,
-                   int matvec_precision = BSE_PREC_FP64);
+                   int matvec_precision = BSE_PREC_FP64, const bse_c128* V0 = nullptr,
+                   int k0 = 0);
 
 // Hermitian matrix-vector blocks on the tensor cores (build_mixed.cu): A and
 // B split once; apply writes AV = A V and BV = B V (n x k, column-major, ld n).

@@ -501,7 +501,7 @@ __global__ void __launch_bounds__((TX / RX) * (TT / RT)) k_stage2(Stage2Args a) 
 // Stage 2 for pair blocks of at most 16 x 16, software-pipelined: the raw
 // complex128 X rows and FP32 T rows of the next 32 plane waves are copied to
 // shared memory asynchronously (cp.async, double-buffered) while the current
-// chunk is converted and contracted.  Same arithmetic as k_stage2<16, 1>.
+// chunk is converted and contracted.  Same arithmetic as k_stage2<16, 16, 1, 1>.
 __global__ void __launch_bounds__(256) k_stage2_pipe(Stage2Args a) {
   constexpr int GC = 32;
   __shared__ __align__(16) uint4 Xr[2][16][GC];      // raw FP64 complex

@@ -496,7 +496,7 @@ static int basis_per_ev() {
 void davidson_fp64(int n, const bse_c128* A, const bse_c128* B, int64_t ld, int nev, double tol,
                    int max_iter, int precond, const MlpNet* mlp, double* E_out,
                    bse_c128* XpY_out, int32_t* iters_out, cudaStream_t s, TrajectorySink* sink,
-                   int matvec_precision) {
+                   int matvec_precision, const bse_c128* V0, int k0) {
   std::unique_lock<std::mutex> lock;
   LibHandles h = acquire_handles(lock);
   BSE_CUSOLVER(cusolverDnSetStream(h.solver, s));
@@ -526,14 +526,34 @@ void davidson_fp64(int n, const bse_c128* A, const bse_c128* B, int64_t ld, int 
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return sv.D[a] < sv.D[b]; });
   const int b0 = std::min(n, std::min(mmax, nev + std::max(4, nev / 4)));
-  BSE_CUDA(cudaMemsetAsync(sv.V.ptr, 0, (size_t)n * b0 * 16, s));
-  for (int j = 0; j < b0; ++j) {
-    const double2 one = make_double2(1.0, 0.0);
-    BSE_CUDA(cudaMemcpyAsync(sv.V.as<double2>() + (int64_t)j * n + order[j], &one, 16,
-                             cudaMemcpyHostToDevice, s));
+  if (V0 && k0 > 0) {
+    // warm start: the given vectors, orthonormalised, then unit vectors at
+    // the smallest A_aa until the basis holds b0 vectors (dependent ones drop)
+    BSE_CUDA(cudaMemcpyAsync(sv.T.ptr, V0, (size_t)n * k0 * 16, cudaMemcpyDeviceToDevice, s));
+    sv.m = 0;
+    sv.append_block(sv.T.as<cuDoubleComplex>(), k0);
+    int next = 0;
+    while (sv.m < b0 && next < n) {
+      const int b = std::min(b0 - sv.m, n - next);
+      BSE_CUDA(cudaMemsetAsync(sv.T.ptr, 0, (size_t)n * b * 16, s));
+      for (int j = 0; j < b; ++j) {
+        const double2 one = make_double2(1.0, 0.0);
+        BSE_CUDA(cudaMemcpyAsync(sv.T.as<double2>() + (int64_t)j * n + order[next + j], &one, 16,
+                                 cudaMemcpyHostToDevice, s));
+      }
+      next += b;
+      sv.append_block(sv.T.as<cuDoubleComplex>(), b);
+    }
+  } else {
+    BSE_CUDA(cudaMemsetAsync(sv.V.ptr, 0, (size_t)n * b0 * 16, s));
+    for (int j = 0; j < b0; ++j) {
+      const double2 one = make_double2(1.0, 0.0);
+      BSE_CUDA(cudaMemcpyAsync(sv.V.as<double2>() + (int64_t)j * n + order[j], &one, 16,
+                               cudaMemcpyHostToDevice, s));
+    }
+    sv.m = b0;
   }
-  sv.m = b0;
-  sv.matvec(0, b0);
+  sv.matvec(0, sv.m);
 
   // exact X-Y of the recorded problem (trajectory samples only)
   std::unique_ptr<DeviceBuffer> xm_exact;

@@ -116,3 +116,28 @@ def test_davidson_core_levels_tensor_core_matvecs(bse):
     assert np.abs(e - e_ref[:nev]).max() < 1e-5
     assert 1 <= it < 200
     print(f" [core levels nev={nev} TC matvecs: {it} iterations]", end="")
+
+
+def test_exciton_bands_warm_start(bse):
+    """Exciton dispersion over a line of Q (a smooth family: only v(G+Q)
+    changes): every Q's lowest energies match the oracle's dense solve from a
+    cold or a warm start (bse_lowest_excitons_from, seeded with the previous
+    Q's X+Y), and the warm starts need fewer iterations."""
+    cfg = bi.BSEConfig("band", grid=4, nv=4, nc=4, ng=59, q_abs=(0.10, 0.12, 0.14, 0.16),
+                       w_scale=0.25)
+    nev = 12
+    probs = [bi.make_problem(cfg, q_index=q, draws_of=0) for q in range(4)]
+    refs = [np.sort(O.solve_full(*O.build_A_B(p))[0])[:nev] for p in probs]
+    ds = [gpu_build(bse, p) for p in probs]
+    n = probs[0]["nk"] * probs[0]["nv"] * probs[0]["nc"]
+    items = [(n, d["A"], d["B"]) for d in ds]
+    e_cold, it_cold = bse.exciton_bands(items, nev, tol_ev=1e-6, warm=False)
+    e_warm, it_warm = bse.exciton_bands(items, nev, tol_ev=1e-6, warm=True)
+    for q in range(4):
+        assert np.abs(e_cold[q] - refs[q]).max() < 1e-8
+        assert np.abs(e_warm[q] - refs[q]).max() < 1e-8
+    assert it_warm[0] == it_cold[0]
+    assert all(w < c for w, c in zip(it_warm[1:], it_cold[1:])), (it_warm, it_cold)
+    # the dispersion itself: the lowest exciton moves with Q
+    assert np.abs(refs[3][0] - refs[0][0]) > 1e-6
+    print(f" [iterations cold {it_cold}, warm {it_warm}]", end="")
