@@ -302,9 +302,9 @@ int bse_lowest_excitons(int32_t n, const bse_c128* A, const bse_c128* B, int64_t
  * the X+Y of the same excitons at a neighbouring momentum transfer when the
  * exciton dispersion E_lambda(Q) is traced over a line of Q (the warm start
  * of an exciton band structure; the problems must share n and the transition
- * order).  The columns are orthonormalised (dependent ones dropped) and unit
- * vectors at the smallest A_aa are added until the basis holds
- * nev + max(4, nev/4) vectors.  1 <= k0 <= min(4 nev, n); V0 16-byte aligned.
+ * order).  The columns and their images under A+B (which carry the matching
+ * X-Y) are orthonormalised (dependent ones dropped) and unit vectors at the
+ * smallest A_aa are added until the basis holds nev + max(4, nev/4) vectors.  1 <= k0 <= min(4 nev, n); V0 16-byte aligned.
  * Other arguments, outputs and errors as for bse_lowest_excitons. */
 int bse_lowest_excitons_from(int32_t n, const bse_c128* A, const bse_c128* B, int64_t ld,
                              int32_t nev, double tol_ev, int32_t max_iter, int32_t precond,

@@ -526,12 +526,22 @@ void davidson_fp64(int n, const bse_c128* A, const bse_c128* B, int64_t ld, int 
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return sv.D[a] < sv.D[b]; });
   const int b0 = std::min(n, std::min(mmax, nev + std::max(4, nev / 4)));
+  int m_done = 0;   // basis columns whose P and M are computed
   if (V0 && k0 > 0) {
-    // warm start: the given vectors, orthonormalised, then unit vectors at
-    // the smallest A_aa until the basis holds b0 vectors (dependent ones drop)
+    // warm start: the given vectors (X+Y of nearby excitons) and their images
+    // under A+B (proportional to the matching X-Y, which the one basis must
+    // also hold), orthonormalised, then unit vectors at the smallest A_aa
+    // until the basis holds b0 vectors (dependent ones drop)
     BSE_CUDA(cudaMemcpyAsync(sv.T.ptr, V0, (size_t)n * k0 * 16, cudaMemcpyDeviceToDevice, s));
     sv.m = 0;
     sv.append_block(sv.T.as<cuDoubleComplex>(), k0);
+    sv.matvec(0, sv.m);
+    m_done = sv.m;
+    BSE_CUDA(cudaMemcpyAsync(sv.T.ptr, sv.P.ptr, (size_t)n * m_done * 16, cudaMemcpyDeviceToDevice,
+                             s));
+    sv.append_block(sv.T.as<cuDoubleComplex>(), m_done);
+    sv.matvec(m_done, sv.m);
+    m_done = sv.m;
     int next = 0;
     while (sv.m < b0 && next < n) {
       const int b = std::min(b0 - sv.m, n - next);
@@ -553,7 +563,7 @@ void davidson_fp64(int n, const bse_c128* A, const bse_c128* B, int64_t ld, int 
     }
     sv.m = b0;
   }
-  sv.matvec(0, sv.m);
+  sv.matvec(m_done, sv.m);
 
   // exact X-Y of the recorded problem (trajectory samples only)
   std::unique_ptr<DeviceBuffer> xm_exact;
