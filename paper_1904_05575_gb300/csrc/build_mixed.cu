@@ -756,6 +756,136 @@ void launch_stage2_tiles(const Stage2Args& a, int npair, cudaStream_t s) {
   k_stage2<TX, TT, RX, RT><<<grid, (TX / RX) * (TT / RT), 0, s>>>(a);
 }
 
+// Stage 2 for several small pair blocks per thread block (e.g. 4 x 4 for
+// 2 x 2 band windows, 6 x 6, 9 x 4): PB pair blocks of rows_x x rows_t
+// outputs, one output per thread, so that the 256 threads stay busy where the
+// one-pair kernel would leave most of them idle.  The raw complex128 X rows
+// and FP32 T rows of the next 8 plane waves of all PB pairs are copied by
+// cp.async (double buffered) while the current chunk is contracted.  Same
+// compensated FP32 arithmetic, in the same order, as k_stage2.
+constexpr int MP_ROWS = 64, MP_GC = 8, MP_MAXPB = 16;
+
+// pair blocks per thread block for the multi-pair kernel (1: not worth it)
+int stage2_multi_pairs(const Stage2Args& a) {
+  const int rx = a.rows_x, rt = a.rows_t;
+  if (rx > 16 || rt > 16) return 1;
+  int pb = std::min(MP_MAXPB, 256 / (rx * rt));
+  pb = std::min(pb, std::min(MP_ROWS / rx, MP_ROWS / rt));
+  return std::max(pb, 1);
+}
+
+__global__ void __launch_bounds__(256) k_stage2_multi(Stage2Args a, int npair, int pb) {
+  __shared__ __align__(16) uint4 Xr[2][MP_ROWS][MP_GC];     // raw FP64 complex
+  __shared__ __align__(16) float2 Tr[2][MP_GC][MP_ROWS];    // FP32 complex
+  __shared__ float2 Xs[MP_ROWS][MP_GC + 1];                 // converted X of the chunk
+  __shared__ int64_t xbase[MP_MAXPB], tbase[MP_MAXPB];      // -1: no such pair
+  const int tid = threadIdx.x;
+  const int rx_n = a.rows_x, rt_n = a.rows_t, per = rx_n * rt_n;
+  const int p0 = blockIdx.x * pb;
+  if (tid < pb) {
+    const int p = p0 + tid;
+    int64_t xb = -1, tb = -1;
+    if (p < npair) {
+      const int k = a.k_begin + p / a.nk, kp = p % a.nk;
+      const int64_t xp = a.x_transpose_pair ? (int64_t)kp * a.nk + k : (int64_t)p;
+      xb = xp * rx_n * a.ng;
+      tb = a.t_row0 + (int64_t)a.slot_of_pair[p] * rt_n;
+    }
+    xbase[tid] = xb;
+    tbase[tid] = tb;
+  }
+  __syncthreads();
+  const uint4* X = reinterpret_cast<const uint4*>(a.x);
+  const int xrows = pb * rx_n, trows = pb * rt_n;
+  const int nchunks = (a.ng + MP_GC - 1) / MP_GC;
+  auto prefetch = [&](int c, int buf) {
+    const int g0 = c * MP_GC;
+    for (int i = tid; i < xrows * MP_GC; i += 256) {
+      const int r = i / MP_GC, g = i % MP_GC;
+      const int q = r / rx_n;
+      const int64_t xb = xbase[q];
+      const bool ok = xb >= 0 && g0 + g < a.ng;
+      cp_async16(&Xr[buf][r][g],
+                 ok ? (const void*)(X + xb + (int64_t)(r - q * rx_n) * a.ng + g0 + g) : (const void*)X,
+                 ok);
+    }
+    for (int i = tid; i < MP_GC * trows; i += 256) {
+      const int g = i / trows, r = i % trows;
+      const int q = r / rt_n;
+      const int64_t tb = tbase[q];
+      const bool ok = tb >= 0 && g0 + g < a.ng;
+      const float2* src = a.T + (ok ? (int64_t)(g0 + g) * a.t_ld + tb + (r - q * rt_n) : 0);
+      cp_async8(&Tr[buf][g][r], src, ok);
+    }
+    cp_async_commit();
+  };
+
+  const int q = tid / per, o = tid - q * per;
+  const int ri = o / rt_n, rj = o - ri * rt_n;
+  const bool active = q < pb;
+  const int xrow = active ? q * rx_n + ri : 0, trow = active ? q * rt_n + rj : 0;
+  const uint32_t xflip = a.conj_x ? 0x80000000u : 0u;
+  const float tsign = a.conj_t ? -1.f : 1.f;
+  float hx = 0.f, hy = 0.f, lx = 0.f, ly = 0.f;
+  prefetch(0, 0);
+  for (int c = 0; c < nchunks; ++c) {
+    const int buf = c & 1;
+    if (c + 1 < nchunks) {
+      prefetch(c + 1, buf ^ 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    for (int i = tid; i < xrows * MP_GC; i += 256) {
+      const int r = i / MP_GC, g = i % MP_GC;
+      const uint4 d = Xr[buf][r][g];
+      Xs[r][g] = make_float2(__uint_as_float(f64w_to_f32_bits(d.x, d.y)),
+                             __uint_as_float(f64w_to_f32_bits(d.z, d.w) ^ xflip));
+    }
+    __syncthreads();
+    float ax = 0.f, ay = 0.f;
+#pragma unroll
+    for (int g = 0; g < MP_GC; ++g) {
+      const float2 xv = Xs[xrow][g];
+      const float2 tv = Tr[buf][g][trow];
+      const float ty_ = tv.y * tsign;
+      ax = fmaf(xv.x, tv.x, ax);
+      ax = fmaf(-xv.y, ty_, ax);
+      ay = fmaf(xv.x, ty_, ay);
+      ay = fmaf(xv.y, tv.x, ay);
+    }
+    float sv, e;
+    two_sum(hx, ax, sv, e);
+    hx = sv;
+    lx += e;
+    two_sum(hy, ay, sv, e);
+    hy = sv;
+    ly += e;
+    __syncthreads();   // the next prefetch overwrites this buffer
+  }
+  if (!active || xbase[q] < 0) return;
+  const int p = p0 + q;
+  const int k = a.k_begin + p / a.nk, kp = p % a.nk;
+  const int nv = a.nv, nc = a.nc, rx = ri, rt = rj;
+  int vi, ci, vp, cp;
+  if (a.mode == S2_RR_CC) {
+    vi = rx / nv; vp = rx % nv; ci = rt / nc; cp = rt % nc;
+  } else if (a.mode == S2_RR_VV) {
+    ci = rx / nc; cp = rx % nc; vi = rt / nv; vp = rt % nv;
+  } else {
+    vp = rx / nc; ci = rx % nc; vi = rt / nc; cp = rt % nc;
+  }
+  const int64_t al = ((int64_t)k * nv + vi) * nc + ci;
+  const int64_t ap = ((int64_t)kp * nv + vp) * nc + cp;
+  double2* dst = a.out + al + ap * a.ld;
+  const float sc = (float)a.scale;
+  double2 o2 = *dst;
+  o2.x -= f32_to_f64_bits(scale_hi_lo(sc, hx, lx));
+  o2.y -= f32_to_f64_bits(scale_hi_lo(sc, hy, ly));
+  *dst = o2;
+}
+
 // The kernel whose tile fits the pair block best (every variant adds in the
 // same order: the results do not depend on the choice).
 void launch_stage2(const Stage2Args& a, int npair, cudaStream_t s) {
@@ -764,7 +894,11 @@ void launch_stage2(const Stage2Args& a, int npair, cudaStream_t s) {
     const int64_t blocks = (total + SK_ROWS - 1) / SK_ROWS;
     k_stage2_skinny<4><<<(unsigned)blocks, SK_ROWS, 0, s>>>(a, total);
   } else if (a.rows_x <= 16 && a.rows_t <= 16) {
-    k_stage2_pipe<<<npair, 256, 0, s>>>(a);
+    const int pb = stage2_multi_pairs(a);
+    if (pb >= 2)
+      k_stage2_multi<<<(npair + pb - 1) / pb, 256, 0, s>>>(a, npair, pb);
+    else
+      k_stage2_pipe<<<npair, 256, 0, s>>>(a);
   } else if (a.rows_x <= 24 && a.rows_t <= 24) {           // e.g. W^ra, 4 x 6 bands
     launch_stage2_tiles<24, 24, 2, 3>(a, npair, s);
   } else if (a.rows_x <= 32 && a.rows_t <= 16) {           // e.g. W^rr, 3 x 5 bands (25 x 9)
