@@ -43,7 +43,7 @@ FP64_PEAK_TFLOPS = 1.25     # GB300 FP64 (CUDA-core and tensor) nominal rate
 # until re-taken after a kernel changes
 TRAFFIC_BYTES = {
     "mixed_direct_fused": 832.4e6,     # one launch = one build (profiles/mixed_build_c2_kernels.md)
-    "mixed_split": 663.9e6,            # the 6 launches of one build
+    "mixed_split": 630.3e6,            # the 5 launches of one build (one W split serves both terms)
 }
 # the c4 core-level build's stage-2 kernels, per build (8 slab launches each):
 # the capture of one 16-row slab of the same recipe on a 4x4x4 grid (1,024
@@ -73,15 +73,17 @@ def stage1_flops(nk, nv, nc, ng):
 
 def split_bytes(nk, nv, nc, ng, pieces=3):
     """Bytes the operand split must move per build: every complex128 element
-    of M_x (twice: the two exchange operands), W (once per direct term) and the
-    stage-1 side rows of both direct terms read once (16 B), and written as
-    2 x pieces BF16 planes over K padded to 16 (the W rows padded to 32)."""
+    of M_x (twice: the two exchange operands), W (once, or twice when W^rr
+    applies it conjugate-transposed to the valence side) and the stage-1 side
+    rows of both direct terms read once (16 B), and written as 2 x pieces BF16
+    planes over K padded to 16 (the W rows padded to 32)."""
     kp = -(-ng // 16) * 16
     ngp = -(-ng // 32) * 32
     n = nk * nv * nc
     rows_side = min(nv * nv, nc * nc) + nv * nc
-    read = 16 * ng * (2 * n + 2 * nk * ng + nk * nk * rows_side)
-    write = 4 * pieces * kp * (2 * n + 2 * nk * ngp + nk * nk * rows_side)
+    w_splits = 1 if nc * nc <= nv * nv else 2
+    read = 16 * ng * (2 * n + w_splits * nk * ng + nk * nk * rows_side)
+    write = 4 * pieces * kp * (2 * n + w_splits * nk * ngp + nk * nk * rows_side)
     return read + write
 
 

@@ -1179,6 +1179,7 @@ struct BatchPlan {
   struct Term {
     int prob = 0;
     int64_t a_row0 = 0, w_row0 = 0;
+    bool w_owner = true;     // this term splits its W planes (false: shares the other term's)
     int rows_side = 0;
     const bse_c128* side = nullptr;
     bool w_conj_transpose = false;
@@ -1256,7 +1257,7 @@ void plan_splits(BatchPlan& pl, cudaStream_t s) {
                  t.w_conj_transpose ? 1 : 0, pl.ng, pl.Kp, p.nq_w * pl.ng_pad, pl.pieces,
                  t.w_conj_transpose ? 1 : 0, nullptr, pl.wsplit.as<__nv_bfloat16>(), pl.w_rows,
                  t.w_row0};
-    launch_split(sw, s);
+    if (t.w_owner) launch_split(sw, s);
     SplitArgs sa{reinterpret_cast<const double2*>(t.side), SPLIT_PAIRS, t.perm.as<int>(),
                  t.rows_side, 0, pl.ng, pl.Kp, npair * t.rows_side, pl.pieces, 0, nullptr,
                  pl.asplit.as<__nv_bfloat16>(), pl.a_rows, t.a_row0};
@@ -1510,9 +1511,17 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
       t.perm = upload_mem(perm);
       t.slot = upload_mem(slot);
       t.a_row0 = pl->a_rows;
-      t.w_row0 = pl->w_rows;
       pl->a_rows += (int64_t)npair * t.rows_side;
-      pl->w_rows += (int64_t)p.nq_w * pl->ng_pad;
+      if (term == 1 && !pl->terms.empty() && pl->terms.back().prob == (int)i &&
+          !pl->terms.back().w_conj_transpose) {
+        // W^ra uses W(q) as stored, like a W^rr term that applies it to the
+        // conduction side: one set of split planes serves both
+        t.w_row0 = pl->terms.back().w_row0;
+        t.w_owner = false;
+      } else {
+        t.w_row0 = pl->w_rows;
+        pl->w_rows += (int64_t)p.nq_w * pl->ng_pad;
+      }
       a.slot_of_pair = t.slot.as<int>();
       a.ng = ng;
       a.nk = p.nk;
