@@ -72,3 +72,31 @@ def test_host_side_argument_errors(lib):
     assert lib2.bse_reduce(0, None, None, 1, None, None, None, None) == bse.BSE_ERR_ARG
     assert lib2.bse_spectrum(4, None, None, 2, None, 1.0, 1.0, 0, None, 0.1,
                              None, None, None, None) == bse.BSE_ERR_ARG
+
+
+def test_header_is_c99_and_matches_the_binding(tmp_path):
+    """include/bse.h compiles as strict C99, and bse_problem has the same size
+    and field offsets in C as in the ctypes binding."""
+    import shutil
+    import subprocess
+    import paper_1904_05575_gb300 as bse
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    inc = os.path.join(ROOT, "include")
+    fields = [f for f, _ in bse.bse_problem._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text(
+        "#include <stdio.h>\n#include <stddef.h>\n#include \"bse.h\"\n"
+        "int main(void) {\n  printf(\"%zu\\n\", sizeof(bse_problem));\n"
+        + "".join(f"  printf(\"%zu\\n\", offsetof(bse_problem, {f}));\n" for f in fields)
+        + "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", inc,
+                        str(src), "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(bse.bse_problem)
+    for f, off in zip(fields, out[1:]):
+        assert getattr(bse.bse_problem, f).offset == off, f
