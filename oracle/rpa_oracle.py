@@ -23,7 +23,9 @@ Readings taken here (listed in the design notes):
 Parity status: pinned in tests/test_oracle_rpa.py by the no-transition limit,
 a one-transition / one-plane-wave case and a two-plane-wave case worked by
 hand, the Sherman-Morrison closed form for one transition, and the identity
-w = (v^-1 + 2 kappa X)^-1 that makes w Hermitian with 0 < w <= v.
+w = (v^-1 + 2 kappa X)^-1 that makes w Hermitian with 0 < w <= v; seven
+planted mistakes (factor, sign, conjugate and index placement, kappa) are
+each caught by one of them.
 """
 from __future__ import annotations
 
