@@ -9,12 +9,18 @@
 //   2. exchange   tensor-core GEMM conj(M_x) diag(v_bar) M_x^T; the epilogue
 //                 writes A = E + 2 gx k V and B = 2 gx k V (FP64)
 //   3. stage 1    tensor-core GEMM T = X_side W(q)^T per q group -> FP32 T[G][row]
-//   4. stage 2    FP32 CUDA-core contraction of T with the other pair side over
-//                 G, read straight from the complex128 input, subtracted from
-//                 A (W^rr) or B (W^ra) in FP64
+//                 (or T split at once into BF16 planes for a tensor-core stage 2)
+//   4. stage 2    contraction of T with the other pair side over G, subtracted
+//                 from A (W^rr) or B (W^ra) in FP64: a tensor-core GEMM per pair
+//                 block where both sides have >= 64 rows, else FP32 on CUDA
+//                 cores reading the complex128 input directly (k_stage2_skinny,
+//                 k_stage2_multi, k_stage2_pipe, k_stage2<TX, TT, RX, RT>)
 // Where every pair block fits the fused epilogue (rows_t a power of two,
 // rows_x <= min(16, rows_t)), steps 3 and 4 run as one tcgen05 launch whose
 // epilogue performs the contraction on the TMEM tile (tc_direct.cuh).
+// A problem given as a k-row slab (bse_problem.k_begin / k_count) builds only
+// the rows (k v c) of its slab: exchange tiles over those rows, direct terms
+// over the slab's pairs (k, k'), pair decodes offset by k_begin.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
