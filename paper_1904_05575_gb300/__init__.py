@@ -168,6 +168,22 @@ def _matrix_ptr(t, n, name):
     return _ptr(t, torch.complex128, name), t.shape[1]
 
 
+def _check_shapes(d: Dict, kn: int, coupling: bool) -> None:
+    """The array shapes include/bse.h states (the library reads them through
+    bare pointers and cannot check them): raises ValueError on a mismatch."""
+    nk, nv, nc, ng = d["nk"], d["nv"], d["nc"], d["ng"]
+    nq = d["w"].shape[0] if d.get("w") is not None else 0
+    want = {"e_v": (nk, nv), "e_c": (nk, nc), "m_x": (nk, nv, nc, ng), "v_bar": (ng,),
+            "w": (nq, ng, ng), "q_minus": (nk, nk), "m_vv": (kn, nk, nv, nv, ng),
+            "m_cc": (kn, nk, nc, nc, ng)}
+    if coupling:
+        want.update(n_vc=(nk, nk, nv, nc, ng), q_plus=(nk, nk))
+    for name, shape in want.items():
+        t = d.get(name)
+        if t is not None and tuple(t.shape) != shape:
+            raise ValueError(f"{name} must have shape {shape}, got {tuple(t.shape)}")
+
+
 def make_problem_struct(d: Dict, gamma_x: float = 1.0, gamma_c: float = 1.0,
                         coupling: bool = True, k_begin: int = 0,
                         k_count: int = 0) -> bse_problem:
@@ -187,6 +203,7 @@ def make_problem_struct(d: Dict, gamma_x: float = 1.0, gamma_c: float = 1.0,
         t = d.get(name)
         if t is not None and (name != "n_vc" or coupling) and tuple(t.shape[:2]) != (rows, nk):
             raise ValueError(f"{name} must have leading shape ({rows}, {nk}), got {tuple(t.shape[:2])}")
+    _check_shapes(d, kn, coupling)
     a_ptr, ld = _matrix_ptr(d["A"], n, "A")
     b_ptr = None
     if coupling:

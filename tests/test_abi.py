@@ -100,3 +100,27 @@ def test_header_is_c99_and_matches_the_binding(tmp_path):
     assert out[0] == ctypes.sizeof(bse.bse_problem)
     for f, off in zip(fields, out[1:]):
         assert getattr(bse.bse_problem, f).offset == off, f
+
+
+def test_problem_struct_shape_checks():
+    """make_problem_struct checks every array's shape before taking pointers:
+    problems as upload_problem lays them out (whole, k-row slab views, padded
+    ld, TDA) pass the checks and only then meet the CUDA-tensor requirement
+    (TypeError on the CPU); a mis-shaped array is a ValueError."""
+    import bse_inputs as bi
+    import paper_1904_05575_gb300 as bse
+    torch = pytest.importorskip("torch")
+    cfg = bi.BSEConfig("shapes", grid=2, nv=2, nc=3, ng=15, w_scale=0.1)
+    d = bse.upload_problem(bi.make_problem(cfg), device="cpu", ld=50)
+    slab = dict(d, m_vv=d["m_vv"][2:5], m_cc=d["m_cc"][2:5])
+    for kw, dd in ((dict(), d), (dict(coupling=False), d), (dict(k_begin=2, k_count=3), slab)):
+        with pytest.raises(TypeError):
+            bse.make_problem_struct(dd, **kw)
+    for name, bad in (("w", d["w"][:, :-1]), ("m_x", d["m_x"][..., :-1]), ("e_c", d["e_c"][:, :2]),
+                      ("q_minus", d["q_minus"][:4]), ("v_bar", d["v_bar"][:-1]),
+                      ("n_vc", d["n_vc"][..., :-1])):
+        with pytest.raises(ValueError):
+            bse.make_problem_struct(dict(d, **{name: bad}))
+    # TDA does not read n_vc or q_plus
+    with pytest.raises(TypeError):
+        bse.make_problem_struct(dict(d, n_vc=d["n_vc"][..., :-1]), coupling=False)
