@@ -242,6 +242,24 @@ int bse_spectrum_tensor(int32_t n, const bse_c128* Z, const bse_c128* L, int64_t
                         const double* omega, double delta, const double* E, bse_c128* eps_out,
                         void* cuda_stream);
 
+/* Static screened interaction of an insulator in the random-phase
+ * approximation (Sec. 2: Eq. wggq, w = v eps^-1, with the RPA dielectric
+ * matrix at omega = 0), FP64, for one momentum q:
+ *   X_GG'   = sum_{k v c} conj(m[k][v][c][G]) m[k][v][c][G'] / (e_c_kq[k][c] - e_v[k][v])
+ *   eps_GG' = delta_GG' + 2 kappa v_G' X_GG'     (kappa = Ha / (nk omega_cell);
+ *             the factor 2: the reversed (c, v) pairs, equal at omega = 0)
+ *   w_out[G][G'] = v_G (eps^-1)_GG'
+ * e_v [nk][nv] valence energies at k, e_c_kq [nk][nc] conduction energies at
+ * k + q (eV; every e_c_kq - e_v > 0), m [nk][nv][nc][ng] the pair elements
+ * M_vc(k, q)(G), v [ng] = 4 pi / |G+q|^2 (>= 0, Hartree atomic units), w_out
+ * [ng][ng] row-major, the layout of one q of bse_problem.w.  Device pointers;
+ * m and w_out 16-byte aligned.  X on cuBLAS (ZGEMM), eps^-1 by cuSOLVER LU.
+ * Syncs.  Errors: BSE_ERR_ARG (sizes, NULL, a non-positive gap), BSE_ERR_NOMEM,
+ * BSE_ERR_CUDA (also a singular eps). */
+int bse_rpa_screening(int32_t nk, int32_t nv, int32_t nc, int32_t ng, double omega_cell,
+                      const double* e_v, const double* e_c_kq, const bse_c128* m, const double* v,
+                      bse_c128* w_out, void* cuda_stream);
+
 /* Electron energy-loss function L(w) = -Im 1/eps_M(w) (Eq. Lofeps) and the
  * dynamical structure factor S(Q, w) = -(1/pi) v_G(q)^{-1} Im 1/eps_M(q, w)
  * from eps [n_omega] (complex, e.g. bse_spectrum's eps_out).  v_inv =

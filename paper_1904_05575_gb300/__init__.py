@@ -61,7 +61,7 @@ EXPORTED = ("bse_build_kernel", "bse_reduce", "bse_spectrum", "bse_last_error", 
             "bse_mlp_predict", "bse_xpy", "bse_mlp_trajectory_samples", "bse_plan_create",
             "bse_plan_execute", "bse_plan_status", "bse_plan_tile_cols", "bse_plan_destroy",
             "bse_plan_fused", "bse_spectrum_tensor", "bse_loss_function",
-            "bse_lowest_excitons_from")
+            "bse_lowest_excitons_from", "bse_rpa_screening")
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -92,6 +92,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.bse_lowest_excitons_from.argtypes = [i32, vp, vp, i64, i32, dbl, i32, i32, vp, i32, vp,
                                              i32, vp, vp, ctypes.POINTER(i32), vp]
     lib.bse_lowest_excitons_from.restype = ctypes.c_int
+    lib.bse_rpa_screening.argtypes = [i32, i32, i32, i32, dbl, vp, vp, vp, vp, vp, vp]
+    lib.bse_rpa_screening.restype = ctypes.c_int
     lib.bse_xpy.argtypes = [i32, i32, vp, vp, i64, vp, vp, vp]
     lib.bse_xpy.restype = ctypes.c_int
     lib.bse_plan_create.argtypes = [ctypes.POINTER(bse_problem), i32, i32, i32,
@@ -354,6 +356,22 @@ def exciton_bands(problems: Sequence[tuple], nev: int, tol_ev: float = 1e-4, max
         iters.append(it)
         prev = X
     return np.stack(out), iters
+
+
+def bse_rpa_screening(e_v, e_c_kq, m, v, omega_cell: float, w_out, stream=None) -> None:
+    """Static RPA screened interaction w = v eps^-1 for one q (include/bse.h):
+    e_v [nk, nv], e_c_kq [nk, nc] float64, m [nk, nv, nc, ng] complex128,
+    v [ng] float64, w_out [ng, ng] complex128 (row-major), CUDA tensors."""
+    import torch
+    nk, nv, nc, ng = m.shape
+    if tuple(e_v.shape) != (nk, nv) or tuple(e_c_kq.shape) != (nk, nc) or tuple(v.shape) != (ng,):
+        raise ValueError("e_v [nk, nv], e_c_kq [nk, nc] and v [ng] must match m [nk, nv, nc, ng]")
+    if tuple(w_out.shape) != (ng, ng):
+        raise ValueError("w_out must have shape [ng, ng]")
+    f64, c128 = torch.float64, torch.complex128
+    _check(load().bse_rpa_screening(nk, nv, nc, ng, float(omega_cell), _ptr(e_v, f64, "e_v"),
+                                    _ptr(e_c_kq, f64, "e_c_kq"), _ptr(m, c128, "m"),
+                                    _ptr(v, f64, "v"), _ptr(w_out, c128, "w_out"), _stream(stream)))
 
 
 def bse_phase_timing(enable: bool) -> None:

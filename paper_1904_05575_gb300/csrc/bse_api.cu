@@ -279,6 +279,34 @@ extern "C" int bse_loss_function(int32_t n_omega, const bse_c128* eps, double v_
   });
 }
 
+extern "C" int bse_rpa_screening(int32_t nk, int32_t nv, int32_t nc, int32_t ng,
+                                 double omega_cell, const double* e_v, const double* e_c_kq,
+                                 const bse_c128* m, const double* v, bse_c128* w_out,
+                                 void* cuda_stream) {
+  return guarded([&] {
+    BSE_CHECK_ARG(nk >= 1 && nv >= 1 && nc >= 1 && ng >= 1, "nk, nv, nc and ng must be >= 1");
+    BSE_CHECK_ARG((int64_t)nk * nv * nc <= 2147483647LL, "nk*nv*nc is too large");
+    BSE_CHECK_ARG(std::isfinite(omega_cell) && omega_cell > 0.0, "omega_cell must be > 0");
+    BSE_CHECK_ARG(e_v && e_c_kq && m && v && w_out, "NULL e_v, e_c_kq, m, v or w_out");
+    BSE_CHECK_ARG(((uintptr_t)m & 15) == 0 && ((uintptr_t)w_out & 15) == 0,
+                  "m and w_out must be 16-byte aligned");
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    // every transition energy must be positive (an insulator's gaps)
+    std::vector<double> ev((size_t)nk * nv), ec((size_t)nk * nc);
+    BSE_CUDA(cudaMemcpyAsync(ev.data(), e_v, ev.size() * 8, cudaMemcpyDeviceToHost, s));
+    BSE_CUDA(cudaMemcpyAsync(ec.data(), e_c_kq, ec.size() * 8, cudaMemcpyDeviceToHost, s));
+    BSE_CUDA(cudaStreamSynchronize(s));
+    for (int k = 0; k < nk; ++k)
+      for (int a = 0; a < nv; ++a)
+        for (int b = 0; b < nc; ++b)
+          BSE_CHECK_ARG(ec[(size_t)k * nc + b] - ev[(size_t)k * nv + a] > 0.0,
+                        "e_c_kq - e_v must be > 0 for every transition (k " + std::to_string(k) +
+                            ", v " + std::to_string(a) + ", c " + std::to_string(b) + ")");
+    keep_pool_memory();
+    rpa_screening_fp64(nk, nv, nc, ng, omega_cell, e_v, e_c_kq, m, v, w_out, s);
+  });
+}
+
 extern "C" int bse_spectrum(int32_t n, bse_c128* S_inout, const bse_c128* L, int64_t ld,
                             const bse_c128* rho, double c_q, double vc, int32_t n_omega,
                             const double* omega, double delta, double* E_out, double* osc_out,

@@ -156,6 +156,9 @@ void spectrum_tensor_fp64(int n, const bse_c128* Z, const bse_c128* L, int64_t l
                           cudaStream_t s);
 void loss_fp64(int n_omega, const bse_c128* eps, double v_inv, double* loss_out, double* sqw_out,
                cudaStream_t s);
+void rpa_screening_fp64(int nk, int nv, int nc, int ng, double omega_cell, const double* e_v,
+                        const double* e_c_kq, const bse_c128* m, const double* v, bse_c128* w_out,
+                        cudaStream_t s);
 void spectrum_fp64(int n, bse_c128* S, const bse_c128* L, int64_t ld, const bse_c128* rho,
                    double c_q, double vc, int n_omega, const double* omega, double delta,
                    double* E_out, double* osc_out, bse_c128* eps_out, cudaStream_t stream);

@@ -445,4 +445,102 @@ void loss_fp64(int n_omega, const bse_c128* eps, double v_inv, double* loss_out,
   note_launches(1);
 }
 
+// ---------------------------------------------------------------------------
+// Static RPA screening (Sec. 2: Eq. wggq with the RPA dielectric matrix), FP64
+// ---------------------------------------------------------------------------
+namespace {
+
+// mt[a][G] = m[a][G] / sqrt(e_c_kq[k][c] - e_v[k][v]), a = (k v c)
+__global__ void k_rpa_scale(int64_t total, int nv, int nc, int ng, const double* e_v,
+                            const double* e_c_kq, const double2* m, double2* mt) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = i / ng;
+    const int c = (int)(a % nc), v = (int)((a / nc) % nv);
+    const int64_t k = a / ((int64_t)nv * nc);
+    const double f = 1.0 / sqrt(e_c_kq[k * nc + c] - e_v[k * nv + v]);
+    const double2 x = m[i];
+    mt[i] = make_double2(x.x * f, x.y * f);
+  }
+}
+
+// eps[G][G'] = delta + 2 kappa X[G][G'] v[G'] in place (row-major), and the
+// identity into rhs (column-major, the right-hand side of the solve)
+__global__ void k_rpa_eps(int ng, double two_kappa, const double* v, double2* x, double2* rhs) {
+  const int64_t total = (int64_t)ng * ng;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int g = (int)(i / ng), gp = (int)(i % ng);
+    double2 e = x[i];
+    e.x *= two_kappa * v[gp];
+    e.y *= two_kappa * v[gp];
+    if (g == gp) e.x += 1.0;
+    x[i] = e;
+    rhs[i] = make_double2(g == gp ? 1.0 : 0.0, 0.0);
+  }
+}
+
+// w[G][G'] = v[G] inv[G][G'] (row-major)
+__global__ void k_rpa_w(int ng, const double* v, const double2* inv, double2* w) {
+  const int64_t total = (int64_t)ng * ng;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double f = v[i / ng];
+    const double2 y = inv[i];
+    w[i] = make_double2(f * y.x, f * y.y);
+  }
+}
+
+}  // namespace
+
+void rpa_screening_fp64(int nk, int nv, int nc, int ng, double omega_cell, const double* e_v,
+                        const double* e_c_kq, const bse_c128* m, const double* v, bse_c128* w_out,
+                        cudaStream_t s) {
+  std::lock_guard<std::mutex> lock(g_handle_mutex);
+  Handles& h = handles_for_current_device();
+  BSE_CUSOLVER(cusolverDnSetStream(h.solver, s));
+  BSE_CUBLAS(cublasSetStream(h.blas, s));
+  const int64_t ntr = (int64_t)nk * nv * nc;
+  DeviceBuffer mt((size_t)ntr * ng * sizeof(bse_c128), s);
+  k_rpa_scale<<<grid_for(ntr * ng, 256), 256, 0, s>>>(ntr * ng, nv, nc, ng, e_v, e_c_kq,
+                                                     reinterpret_cast<const double2*>(m),
+                                                     mt.as<double2>());
+  BSE_CUDA(cudaGetLastError());
+  // Mt row-major [ntr][ng] is, column-major, the ng x ntr matrix C; C C^H in
+  // column-major storage is X in row-major storage:
+  // (C C^H)[G'][G] = sum_a Mt[a][G'] conj(Mt[a][G]) = X[G][G'] at G' + G ng
+  DeviceBuffer eps((size_t)ng * ng * sizeof(bse_c128), s);
+  const cuDoubleComplex one = make_cuDoubleComplex(1.0, 0.0), zero = make_cuDoubleComplex(0.0, 0.0);
+  BSE_CUBLAS(cublasZgemm(h.blas, CUBLAS_OP_N, CUBLAS_OP_C, ng, ng, (int)ntr, &one,
+                         mt.as<cuDoubleComplex>(), ng, mt.as<cuDoubleComplex>(), ng, &zero,
+                         eps.as<cuDoubleComplex>(), ng));
+  DeviceBuffer rhs((size_t)ng * ng * sizeof(bse_c128), s);
+  const double two_kappa = 2.0 * kHartreeEv / ((double)nk * omega_cell);
+  k_rpa_eps<<<grid_for((int64_t)ng * ng, 256), 256, 0, s>>>(ng, two_kappa, v, eps.as<double2>(),
+                                                           rhs.as<double2>());
+  BSE_CUDA(cudaGetLastError());
+  // the row-major eps is, column-major, eps^T; its inverse (eps^T)^-1 =
+  // (eps^-1)^T in column-major storage is eps^-1 in row-major storage
+  int lwork = 0;
+  BSE_CUSOLVER(cusolverDnZgetrf_bufferSize(h.solver, ng, ng, eps.as<cuDoubleComplex>(), ng, &lwork));
+  DeviceBuffer work((size_t)(lwork > 0 ? lwork : 1) * sizeof(cuDoubleComplex), s);
+  DeviceBuffer ipiv((size_t)ng * sizeof(int), s);
+  DeviceBuffer info(sizeof(int), s);
+  BSE_CUSOLVER(cusolverDnZgetrf(h.solver, ng, ng, eps.as<cuDoubleComplex>(), ng,
+                                work.as<cuDoubleComplex>(), ipiv.as<int>(), info.as<int>()));
+  int hinfo = 0;
+  BSE_CUDA(cudaMemcpyAsync(&hinfo, info.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+  BSE_CUDA(cudaStreamSynchronize(s));
+  if (hinfo != 0)
+    throw Error(BSE_ERR_CUDA, "zgetrf of the dielectric matrix failed (info " +
+                                  std::to_string(hinfo) + ")");
+  BSE_CUSOLVER(cusolverDnZgetrs(h.solver, CUBLAS_OP_N, ng, ng, eps.as<cuDoubleComplex>(), ng,
+                                ipiv.as<int>(), rhs.as<cuDoubleComplex>(), ng, info.as<int>()));
+  k_rpa_w<<<grid_for((int64_t)ng * ng, 256), 256, 0, s>>>(ng, v, rhs.as<double2>(),
+                                                         reinterpret_cast<double2*>(w_out));
+  BSE_CUDA(cudaGetLastError());
+  note_launches(3);
+  BSE_CUDA(cudaStreamSynchronize(s));   // the workspace is stream-ordered
+}
+
 }  // namespace bse
