@@ -53,7 +53,7 @@ typedef enum {
   BSE_ERR_NOT_PD = -4,       /* A-B or A+B not positive definite */
   BSE_ERR_NO_CONV = -5,      /* iterative solver did not converge */
   BSE_ERR_TIMEOUT = -6,      /* a bounded device-side wait gave up */
-  BSE_ERR_UNSUPPORTED = -7   /* valid request this build cannot serve */
+  BSE_ERR_UNSUPPORTED = -7   /* valid request this library cannot serve */
 } bse_status;
 
 /* Arithmetic of the M / W / v contractions of bse_build_kernel.  The
@@ -392,7 +392,7 @@ int bse_mlp_train(void* mlp, const float* feat, const float* target, const float
 int bse_mlp_predict(const void* mlp, const float* feat, int64_t nsamp, float* factor_out,
                     void* cuda_stream);
 
-/* 1 if this build serves the given bse_precision in bse_build_kernel, else 0.
+/* 1 if this library serves the given bse_precision in bse_build_kernel, else 0.
  * Host only; no CUDA call. */
 int bse_precision_supported(int32_t precision);
 

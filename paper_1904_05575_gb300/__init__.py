@@ -439,7 +439,7 @@ def matrix_to_numpy(t, n: int) -> np.ndarray:
 
 
 def mixed_available() -> bool:
-    """True when this build serves the split-precision tensor-core build."""
+    """True when this library serves the split-precision tensor-core build."""
     return bool(load().bse_precision_supported(BSE_PREC_BF16X6))
 
 

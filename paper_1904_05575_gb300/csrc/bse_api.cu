@@ -406,7 +406,7 @@ int lowest_excitons(int32_t n, const bse_c128* A, const bse_c128* B, int64_t ld,
                       matvec_precision == BSE_PREC_BF16X3,
                   "unknown matvec precision " + std::to_string(matvec_precision));
     BSE_CHECK_ARG(matvec_precision == BSE_PREC_FP64 || mixed_supported(matvec_precision),
-                  "this build has no tensor-core path");
+                  "this library has no tensor-core path");
     BSE_CHECK_ARG(((uintptr_t)A & 15) == 0 && ((uintptr_t)B & 15) == 0,
                   "A and B must be 16-byte aligned");
     if (V0 || k0) {
@@ -444,7 +444,7 @@ extern "C" int bse_mlp_create(void** mlp, int32_t n_features, int32_t hidden, ui
     BSE_CHECK_ARG(mlp != nullptr, "mlp is NULL");
     *mlp = nullptr;
     if (n_features != 4 || hidden != 128)
-      throw Error(BSE_ERR_UNSUPPORTED, "this build provides n_features = 4 and hidden = 128");
+      throw Error(BSE_ERR_UNSUPPORTED, "this library provides n_features = 4 and hidden = 128");
     *mlp = mlp_create(seed);
   });
 }

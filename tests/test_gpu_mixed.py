@@ -22,7 +22,7 @@ def bse():
     build.build()
     import paper_1904_05575_gb300 as m
     m.load()
-    assert m.mixed_available(), "this build must serve the BF16x6 tensor-core path"
+    assert m.mixed_available(), "the library must serve the BF16x6 tensor-core path"
     return m
 
 
