@@ -74,9 +74,12 @@ typedef enum {
  *   m_vv  [nk][nk][nv][nv][ng] m_vv[k][k'][v][v'] = M_{v'v,k'}(G, k-k') of Eq. wrrm
  *   m_cc  [nk][nk][nc][nc][ng] m_cc[k][k'][c][c'] = M_{c'c,k'}(G', k-k') of Eq. wrrm
  *   n_vc  [nk][nk][nv][nc][ng] n_vc[k][k'][v][c'] = N_{v c',k}(G', -k'-k) of Eq.
- *                              wrabar; the first factor N_{c v'} of that equation
- *                              is read as n_vc[k'][k][v'][c].  Unused (may be
- *                              NULL) when coupling == 0.
+ *                              wrabar, the modified element with the ket
+ *                              time-reversed: int phi*_{vk}(r) e^{-i(G'+q)r}
+ *                              phi*_{c'k'}(r) dr, q = -k-k'; the first factor
+ *                              N_{c v'} of that equation is read as
+ *                              n_vc[k'][k][v'][c].  Unused (may be NULL) when
+ *                              coupling == 0.
  *   w     [nq_w][ng][ng]       W_GG'(q), Hermitian, row-major (G' contiguous)
  *   q_minus, q_plus [nk][nk]   index of k-k' and of -k-k' into w, in [0, nq_w)
  *   v_bar [ng]                 4 pi / |G+Q|^2 with the G = 0 term set to 0

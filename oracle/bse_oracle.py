@@ -25,7 +25,11 @@ Readings of the paper taken here (each listed in the design notes):
 
 Parity status: build_A_B, reduce_sqrt, solve_full, oscillator_strengths and
 eps_M are pinned by the tests in tests/test_oracle_pins.py (closed forms,
-brute force, sum rules, gauge invariance); block_A_B is pinned to build_A_B
+brute force, sum rules, gauge invariance, and the real-space double integrals
+of Eq. wij for V, W^rr and W^ra, the last between a resonant and an
+anti-resonant basis function built from time-reversal-symmetric Bloch
+functions, which fixes the sign of W^ra in B, the conjugated N factor and the
+orientation of W); block_A_B is pinned to build_A_B
 block by block (tests/test_oracle_blocks.py); transition_coefficients,
 eps_tensor, loss_function and structure_factor by tests/test_oracle_spectra.py
 (contraction to the pinned scalar spectrum, a one-transition case worked by
@@ -87,7 +91,9 @@ def direct_Wrr(m_vv: np.ndarray, m_cc: np.ndarray, w: np.ndarray,
 def direct_Wra(n_vc: np.ndarray, w: np.ndarray, q_plus: np.ndarray, kap: float) -> np.ndarray:
     """W^ra_{(k v c),(k' v' c')} = kappa sum_{G G'} conj(N^cv[k,k',c,v',G])
     W[q+(k,k')]_{G G'} N^vc[k,k',v,c',G']   (Eq. wrabar), with
-    N^cv[k,k',c,v'] read as n_vc[k',k,v',c]."""
+    N^cv[k,k',c,v'] read as n_vc[k',k,v',c].  n_vc[k,k',v,c'](G) is the
+    modified plane-wave element with the ket time-reversed,
+    int phi*_{v k}(r) e^{-i(G+q)r} phi*_{c' k'}(r) dr with q = -k-k'."""
     nk, _, nv, nc, ng = n_vc.shape
     out = np.zeros((nk, nv, nc, nk, nv, nc), np.complex128)
     for k in range(nk):

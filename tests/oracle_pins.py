@@ -14,6 +14,9 @@ test_oracle_mutants.py can plant mistakes in a copy and see a pin fail.
   pin_xmy               (A-B)(X-Y) = E (X+Y) and (X+Y)^H (X-Y) = 1
   pin_gauge_tda         complex unitary rotation of degenerate bands: A' = U^H A U
   pin_gauge_full        real orthogonal rotation: A' = U^T A U, B' = U^T B U
+  pin_real_space        V and W^rr as the real-space double integrals of Eqs. vij, wij
+  pin_real_space_wra    W^ra (B) as Eq. wij between a resonant and an anti-resonant
+                        basis function, with time-reversal-symmetric Bloch functions
 """
 from __future__ import annotations
 
@@ -359,3 +362,123 @@ def pin_real_space(O):
 
 
 ALL_PINS.append(pin_real_space)
+
+
+# ----------------------------------------------------------------------------
+# real-space pin of the coupling block: W^ra as the double integral of Eq. wij
+# between a resonant and an anti-resonant basis function
+# ----------------------------------------------------------------------------
+def _real_space_tr_case(seed=4, nv=2, nc=2, ncell=3, ngrid=3, a=4.0):
+    """Bloch functions with time-reversal symmetry, phi_{n,-k}(r) = phi*_{n,k}(r)
+    (the property the basis of Eqs. 2particlebasis_qsym_res/ares relies on),
+    on the real-space grid of an ngrid^3 supercell, and a screened interaction
+    w(r, r') that is symmetric in r <-> r' (as the static w of a system with
+    time-reversal symmetry is), given by its Fourier components w_GG'(q) of
+    Eq. wft.  Plane waves on the grid are e^{i f r} with f = G + q on the
+    lattice (b / ngrid) Z^3, periodic over ncell * b: the cell G box and the k
+    grid cover one period exactly, so every frequency has one (G, q) label."""
+    rng = np.random.default_rng(seed)
+    nk = ngrid ** 3
+    L = ngrid * a
+    nr1 = ngrid * ncell
+    x = np.arange(nr1) * (L / nr1)
+    r = np.stack(np.meshgrid(x, x, x, indexing="ij"), -1).reshape(-1, 3)
+    vc = L ** 3
+    dv = vc / len(r)
+    b = 2 * np.pi / a
+    gi = np.arange(ncell) - ncell // 2
+    gint = np.stack(np.meshgrid(gi, gi, gi, indexing="ij"), -1).reshape(-1, 3)
+    gvec = gint * b
+    ng = len(gvec)
+    kint = bi.k_grid(ngrid)
+    kvec = kint * (b / ngrid)
+    qm, qp, neg = bi.pair_maps(ngrid)
+
+    # time-reversal pairs: draw phi_k for one k of each pair {k, -k} and set
+    # phi_{-k} = conj(phi_k); at k = -k (the Gamma point here) phi is real
+    def draw(nb, k):
+        c = rng.standard_normal((nb, ng)) + 1j * rng.standard_normal((nb, ng))
+        c /= (1.0 + (gvec ** 2).sum(1))[None, :]
+        return (c @ np.exp(1j * gvec @ r.T)) * np.exp(1j * r @ kvec[k])[None, :]
+
+    phv, phc = [None] * nk, [None] * nk
+    for k in range(nk):
+        if phv[k] is not None:
+            continue
+        fv, fc = draw(nv, k), draw(nc, k)
+        if neg[k] == k:
+            fv, fc = fv.real.astype(np.complex128), fc.real.astype(np.complex128)
+        phv[k], phc[k] = fv, fc
+        phv[neg[k]], phc[neg[k]] = fv.conj(), fc.conj()
+    for k in range(nk):   # phi_{-k} = phi_k^* holds on the grid
+        assert np.allclose(phv[neg[k]], phv[k].conj()) and np.allclose(phc[neg[k]], phc[k].conj())
+
+    # w over grid frequencies F = ngrid * G + q (integers mod nr1): Hermitian,
+    # block-diagonal in the q class, then symmetrised so that
+    # w(r, r') = w(r', r), i.e. w_F,F' = w_-F',-F
+    fint = (ngrid * gint[:, None, :] + kint[None, :, :]).reshape(-1, 3)      # [(G, q)]
+    fidx = {tuple(np.mod(f, nr1)): i for i, f in enumerate(fint)}
+    minus = np.array([fidx[tuple(np.mod(-f, nr1))] for f in fint])
+    qcls = np.tile(np.arange(nk), ng)
+    nf = len(fint)
+    z = rng.standard_normal((nf, nf)) + 1j * rng.standard_normal((nf, nf))
+    wf = 0.5 * (z + z.conj().T) + 3.0 * np.eye(nf)
+    wf = np.where(qcls[:, None] == qcls[None, :], wf, 0.0)
+    wf = 0.5 * (wf + wf.T[np.ix_(minus, minus)])
+    assert np.allclose(wf, wf.conj().T)
+    w = np.empty((nk, ng, ng), np.complex128)
+    for q in range(nk):
+        sel = np.arange(ng) * nk + q                 # the frequencies G + q, G in box order
+        w[q] = wf[np.ix_(sel, sel)]
+    fvec = fint * (b / ngrid)
+    E = np.exp(1j * r @ fvec.T)                       # [nr, nf]
+    kern_w = (E @ wf @ E.conj().T) / vc               # Eq. wft
+    assert np.allclose(kern_w, kern_w.T, atol=1e-12 * np.abs(kern_w).max())
+
+    # n_vc[k][k'][v][c'](G) = int phi*_{v k}(r) e^{-i (G + q) r} phi*_{c' k'}(r) dr
+    # with q = q+(k, k') = -k - k' on the grid: the modified plane-wave matrix
+    # element N of the LAPW section with its ket state conjugated, |(c' k')^*>
+    n_vc = np.empty((nk, nk, nv, nc, ng), np.complex128)
+    for k in range(nk):
+        for kp in range(nk):
+            qv = kvec[qp[k, kp]]
+            ph = np.exp(-1j * (gvec + qv[None, :]) @ r.T)              # [ng, nr]
+            n_vc[k, kp] = np.einsum("ir,gr,jr->ijg", phv[k].conj(), ph, phc[kp].conj()) * dv
+    p = dict(e_v=np.zeros((nk, nv)), e_c=np.ones((nk, nc)),
+             m_x=np.zeros((nk, nv, nc, ng), np.complex128),
+             m_vv=np.zeros((nk, nk, nv, nv, ng), np.complex128),
+             m_cc=np.zeros((nk, nk, nc, nc, ng), np.complex128),
+             n_vc=n_vc, w=w, q_minus=qm, q_plus=qp, v_bar=np.zeros(ng),
+             omega_cell=a ** 3, nk=nk, nv=nv, nc=nc, ng=ng)
+    return p, phv, phc, neg, kern_w, dv
+
+
+def pin_real_space_wra(O):
+    """Eq. wij with i resonant and j anti-resonant:
+         W^ra_{a a'} = int int Ups^r*_a(r, r') w(r, r') Ups^a_a'(r, r')
+       Ups^r_a(r, r')  = phi_{v k}(r) phi*_{c k}(r')          (Eq. 2particlebasis_qsym_res)
+       Ups^a_a'(r, r') = phi_{c', -k'}(r) phi*_{v', -k'}(r')   (Eq. 2particlebasis_qsym_ares)
+    at zero momentum transfer, evaluated as a double sum on the grid with the
+    anti-resonant functions taken at -k' directly; B = 2 gx V - gc W^ra
+    (Eq. couplingblock) with gx = 0, gc = 1 must equal -W^ra (x Ha)."""
+    p, phv, phc, neg, kern_w, dv = _real_space_tr_case()
+    nk, nv, nc = p["nk"], p["nv"], p["nc"]
+    n = nk * nv * nc
+    W_rs = np.zeros((n, n), np.complex128)
+    for k in range(nk):
+        for kp in range(nk):
+            km = neg[kp]
+            # r: phi*_{v k}(r) phi_{c', -k'}(r);  r': phi_{c k}(r') phi*_{v', -k'}(r')
+            d1 = (phv[k][:, None, :].conj() * phc[km][None, :, :]).reshape(nv * nc, -1)   # [v, c']
+            d2 = (phc[k][:, None, :] * phv[km][None, :, :].conj()).reshape(nc * nv, -1)   # [c, v']
+            blk = (d1 @ kern_w @ d2.T).reshape(nv, nc, nc, nv) * dv * dv * HA
+            # blk[v, c', c, v'] -> rows (v, c), columns (v', c')
+            W_rs[k * nv * nc:(k + 1) * nv * nc, kp * nv * nc:(kp + 1) * nv * nc] = \
+                blk.transpose(0, 2, 3, 1).reshape(nv * nc, nv * nc)
+    scale = np.abs(W_rs).max()
+    assert np.allclose(W_rs, W_rs.conj().T, atol=1e-11 * scale), "W^ra Hermitian (time reversal)"
+    _, B = O.build_A_B(p, gamma_x=0.0, gamma_c=1.0, coupling=True)
+    assert np.allclose(B, -W_rs, rtol=0, atol=1e-11 * scale), "coupling block = -Eq. wij (r, a)"
+
+
+ALL_PINS.append(pin_real_space_wra)

@@ -22,6 +22,13 @@ MUTANTS = {
     "wrr_conj_on_cc": ('np.conj(m_vv[k, kp]), inner', 'm_vv[k, kp], np.conj(inner)'),
     "wrr_qplus": ("wq = w[q_minus[k, kp]]", "wq = w[q_minus[kp, k]]"),
     "wra_no_pair_swap": ("first = np.conj(n_vc[kp, k])", "first = np.conj(n_vc[k, kp])"),
+    "wra_sign": ("B = 2.0 * gamma_x * V - gamma_c * Wra", "B = 2.0 * gamma_x * V + gamma_c * Wra"),
+    "wra_conj_on_second": ("first = np.conj(n_vc[kp, k])          # [v', c, G]\n"
+                           "            second = n_vc[k, kp]",
+                           "first = n_vc[kp, k]          # [v', c, G]\n"
+                           "            second = np.conj(n_vc[k, kp])"),
+    "wra_w_transposed": ('inner = np.einsum("gh,vyh->vyg", wq, second',
+                         'inner = np.einsum("hg,vyh->vyg", wq, second'),
     "kappa_no_nk": ("HARTREE_EV / (nk * omega_cell)", "HARTREE_EV / omega_cell"),
     "energy_sign": ("e[k, v, c] = e_c[k, c] - e_v[k, v]", "e[k, v, c] = e_v[k, v] - e_c[k, c]"),
     "xpy_power": ("xpy = (r @ z) / np.sqrt(e)[None, :]", "xpy = (r @ z) * np.sqrt(e)[None, :]"),
