@@ -1,21 +1,30 @@
 #!/usr/bin/env python
 """Benchmark of the BSE hot path on one GB300 (or N, one process per GPU).
 
-One step = one pass of the whole path over one momentum transfer of the
-optical-limit workload (Q = 0, full BSE, Nk = 64 on a 4x4x4 grid, Nv = Nc = 4,
-N = 1024, NG = 181): the Hamiltonian build (exchange + direct W^rr + direct
-W^ra + assembly of A and B), the Cholesky-form reduction, the FP64
-eigensolve and the oscillator-strength / eps_M spectrum.  Inputs are seeded
-synthetic arrays resident in HBM (0.61 GB, larger than the 129 MB L2).
+Default workload (the largest single-GPU configuration): the
+molecular-crystal-like case, Q = 0, full BSE, Nk = 64 on a 4x4x4 grid,
+Nv = Nc = 20, N = 25,600 (51,200 full), NG = 500, W with strong
+off-diagonal structure; 39.8 GB of seeded synthetic inputs drawn on the GPU
+and resident in HBM (far larger than the 129 MB L2).  One step = one build of
+A and B (exchange + direct W^rr + direct W^ra + assembly) through a plan
+created once (BF16x6 tensor-core contractions, FP64 assembly).
 
 value: algorithmic build TFLOP/s (8 flops per complex multiply-add, no
-padding) of the build phase, timed with CUDA events on the launching stream.
-ms_per_step: the whole step (time to spectrum).  N > 1: every rank builds
-and solves its own momentum transfer (Q replicas, no collective), value sums
-the flops of all ranks over the slowest rank's time.
+padding, every (k, k') block counted) of the build, timed with CUDA events on
+the launching stream.  ms_per_step: the build.  After the timed region, once:
+the FP64 GPU build and the error of the mixed build against it; the time to
+the lowest 16 excitons (mixed build + block Davidson with tensor-core
+matvecs) against the plain FP64 GPU path (FP64 build + Davidson with FP64
+matvecs); the end-to-end build through the public API from pinned host
+buffers (inputs copied in, A and B copied out); the CPU oracle on sampled
+(k, k') blocks; and, as extra keys, the optical-limit workload's (Nk = 64,
+Nv = Nc = 4, N = 1,024, NG = 181) time to spectrum, mixed against FP64.
+N > 1: every rank builds its own momentum transfer (Q replicas, no
+collective), value sums the flops of all ranks over the slowest rank's time.
 
---impl reference times the CPU oracle (the plain FP64 restatement of the
-paper the CUDA path is checked against) on the host cores, same metric.
+--config c1/c2/c3/c4/c4s select the other workloads.  --impl reference
+times the CPU oracle (the plain FP64 restatement of the paper the CUDA path
+is checked against) on the host cores, same metric.
 """
 from __future__ import annotations
 
@@ -35,24 +44,37 @@ METRIC = ("BSE kernel-build TFLOP/s and time-to-spectrum, mixed vs FP64 GPU at "
           "≤1 meV error")
 WORKLOAD = ("optical limit Q=0, full (non-TDA) BSE, Nk=64 (4x4x4), Nv=4, Nc=4, N=1024 "
             "(2048 full), NG=181")
+WORKLOAD_C5 = ("molecular-crystal-like Q=0, full (non-TDA) BSE, Nk=64 (4x4x4), Nv=20, Nc=20, "
+               "N=25600 (51200 full), NG=500, strong off-diagonal W")
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 FP64_PEAK_TFLOPS = 1.25     # GB300 FP64 (CUDA-core and tensor) nominal rate
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# c2 workload's kernels, from the ncu captures summarised in profiles/; None
-# until re-taken after a kernel changes
-TRAFFIC_BYTES = {
-    "mixed_direct_fused": 832.4e6,     # one launch = one build (profiles/mixed_build_c2_kernels.md)
-    "mixed_split": 630.3e6,            # the 5 launches of one build (one W split serves both terms)
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per build of a
+# kernel phase, from one ncu capture of the kernel on the named workload,
+# with a digest of the sources that kernel is compiled from: when those
+# sources have changed since the capture the figure no longer describes the
+# kernel and is reported as null.
+KERNEL_SOURCES = ("paper_1904_05575_gb300/csrc/build_mixed.cu", "paper_1904_05575_gb300/csrc/tc_gemm.cuh",
+                  "paper_1904_05575_gb300/csrc/tc_direct.cuh", "paper_1904_05575_gb300/csrc/bits.cuh",
+                  "paper_1904_05575_gb300/csrc/bse_internal.h")
+TRAFFIC = {
+    # workload: {phase: (bytes per build, sources digest at capture)}
 }
-# the c4 core-level build's stage-2 kernels, per build (8 slab launches each):
-# the capture of one 16-row slab of the same recipe on a 4x4x4 grid (1,024
-# pair blocks) scaled by the 262,144 pair blocks of c4
-# (profiles/mixed_build_c4_slab_kernels.md)
-TRAFFIC_BYTES_C4 = {
-    "mixed_stage2_wrr": 2072.9e6 * 256,
-    "mixed_stage2_wra": 338.6e6 * 256,
-}
+
+
+def sources_digest():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def captured_traffic(workload):
+    """{phase: bytes per build} of the captures still valid for the current sources."""
+    dig = sources_digest()
+    return {k: b for k, (b, sha) in TRAFFIC.get(workload, {}).items() if sha == dig}
 
 
 def build_flops(nk, nv, nc, ng, coupling=True):
@@ -71,19 +93,42 @@ def stage1_flops(nk, nv, nc, ng):
     return 8.0 * nk * nk * ng * ng * min(nv * nv, nc * nc), 8.0 * nk * nk * ng * ng * nv * nc
 
 
-def split_bytes(nk, nv, nc, ng, pieces=3):
+def built_pairs(nk, hermitian):
+    """(k, k') blocks of a direct term the build computes: all Nk^2, or the
+    Nk (Nk + 1) / 2 blocks k <= k' of a Hermitian plan."""
+    return nk * (nk + 1) // 2 if hermitian else nk * nk
+
+
+def split_bytes(nk, nv, nc, ng, pieces=3, hermitian=False, tc_stage2=None):
     """Bytes the operand split must move per build: every complex128 element
-    of M_x (twice: the two exchange operands), W (once, or twice when W^rr
-    applies it conjugate-transposed to the valence side) and the stage-1 side
-    rows of both direct terms read once (16 B), and written as 2 x pieces BF16
-    planes over K padded to 16 (the W rows padded to 32)."""
+    read once (16 B) and written as BF16 planes over K padded to 16 (W rows
+    padded to 32): 2 x pieces planes for a GEMM's row operand, 3 x pieces
+    (-Im, Re, Im) for its column operand.  Rows: M_x twice (the exchange's
+    row and column operands), W (once, or twice when W^rr applies it
+    conjugate-transposed to the valence side; column operand), the stage-1
+    side rows of both direct terms (row operand) and, for a term whose second
+    contraction runs on the tensor cores, its other pair side (the column
+    operand for W^rr with T on (c, c'), else the row operand)."""
     kp = -(-ng // 16) * 16
     ngp = -(-ng // 32) * 32
     n = nk * nv * nc
-    rows_side = min(nv * nv, nc * nc) + nv * nc
+    npair = built_pairs(nk, hermitian)
+    (rt_rr, rx_rr), (rt_ra, rx_ra) = term_rows(nv, nc)
+    if tc_stage2 is None:
+        tc_stage2 = min(rt_rr, rx_rr) >= 64
     w_splits = 1 if nc * nc <= nv * nv else 2
-    read = 16 * ng * (2 * n + w_splits * nk * ng + nk * nk * rows_side)
-    write = 4 * pieces * kp * (2 * n + w_splits * nk * ngp + nk * nk * rows_side)
+    a_rows = n + npair * (rt_rr + rt_ra)
+    b_rows = n
+    read_rows = 2 * n + npair * (rt_rr + rt_ra)
+    if tc_stage2:
+        read_rows += npair * (rx_rr + rx_ra)
+        if nc * nc <= nv * nv:
+            b_rows += npair * rx_rr
+        else:
+            a_rows += npair * rx_rr
+        a_rows += npair * rx_ra
+    read = 16 * ng * (read_rows + w_splits * nk * ng)
+    write = 4 * pieces * kp * a_rows + 6 * pieces * kp * (b_rows + w_splits * nk * ngp)
     return read + write
 
 
@@ -208,11 +253,20 @@ def term_rows(nv, nc):
     return rr, (nv * nc, nv * nc)
 
 
-def build_rooflines(bse, prec, phases, steps, shapes, peaks):
+def upper_fraction(nk):
+    """Share of the N^2 elements in the blocks k <= k' (the exchange of a
+    whole problem with enough tiles, and every direct term of a Hermitian
+    plan, computes those)."""
+    return (nk + 1) / (2.0 * nk)
+
+
+def build_rooflines(bse, prec, phases, steps, shapes, peaks, hermitian=False, workload=None,
+                    upper_exchange=True):
     """Rooflines of the two longest build kernels (phases), from the
-    library's CUDA-event phase timing over the timed region; each phase is
-    one launch per build except the splits and the CUDA-core stage 2 (one per
-    array / term)."""
+    library's CUDA-event phase timing over the timed region.  The work of
+    each is what that kernel computes per build: the exchange over the blocks
+    k <= k' (mirrors completed), the direct terms over all (k, k') blocks or,
+    in a Hermitian plan, the blocks k <= k'."""
     def per_build(name):
         cnt, ms = phases.get(name, (0, float("nan")))
         return ms / steps
@@ -229,16 +283,21 @@ def build_rooflines(bse, prec, phases, steps, shapes, peaks):
     peak_t = peaks["bf16_tflops"] / products
     tensor_src = f"{peaks['source']} bf16 burst / {products} piece products"
     hbm_src = f"{peaks['source']} HBM copy bandwidth"
-    s1 = sum(sum(stage1_flops(*sh)) for sh in shapes)
-    ex = sum(8.0 * (sh[0] * sh[1] * sh[2]) ** 2 * sh[3] for sh in shapes)
-    s2 = sum(2 * 8.0 * sh[3] * (sh[0] * sh[1] * sh[2]) ** 2 for sh in shapes)
-    # CUDA-core stage 2 per term: X read as complex128, T as FP32 complex, the
-    # A or B entries read and written once
+    s1 = s2 = ex = cmp_bytes = 0.0
     s2_term = [0.0, 0.0]
     for nk, nv, nc, ng in shapes:
+        fr = built_pairs(nk, hermitian) / (nk * nk)
         n = nk * nv * nc
+        s1 += fr * sum(stage1_flops(nk, nv, nc, ng))
+        s2 += fr * 2 * 8.0 * ng * n * n
+        ex += (upper_fraction(nk) if upper_exchange else 1.0) * 8.0 * n * n * ng
+        # completion: the blocks k > k' of A and B read from their mirrors and written
+        low = (1.0 - upper_fraction(nk)) * n * n
+        cmp_bytes += 2 * 2 * 16 * low
+        # CUDA-core stage 2 per term: X read as complex128, T as FP32 complex, the
+        # A or B entries read and written once
         for i, (rt, rx) in enumerate(term_rows(nv, nc)):
-            s2_term[i] += nk * nk * ng * (16 * rx + 8 * rt) + 32 * n * n
+            s2_term[i] += fr * (nk * nk * ng * (16 * rx + 8 * rt) + 32 * n * n)
     s2_bytes = sum(s2_term)
     kinds = {
         "mixed_direct_fused": ("gemm_split_bf16_direct: stage-1 GEMM + pair contraction, tcgen05",
@@ -252,14 +311,11 @@ def build_rooflines(bse, prec, phases, steps, shapes, peaks):
         "mixed_stage2_wra": ("k_stage2 family: W^ra stage-2 contraction, CUDA cores", "hbm",
                              s2_term[1]),
         "mixed_split": ("k_split: operand split, HBM pass", "hbm",
-                        sum(split_bytes(*sh, pieces=pieces) for sh in shapes)),
+                        sum(split_bytes(*sh, pieces=pieces, hermitian=hermitian) for sh in shapes)),
+        "hermitian_complete": ("k_hermitian_complete: blocks k > k' from their mirrors", "hbm",
+                               cmp_bytes),
     }
-    # the captured DRAM bytes describe the c2 and c4 workloads alone
-    traffic = {}
-    if shapes == [(64, 4, 4, 181)] and products == 6:
-        traffic = TRAFFIC_BYTES
-    elif shapes == [(512, 2, 20, 300)] and products == 6:
-        traffic = TRAFFIC_BYTES_C4
+    traffic = captured_traffic(workload) if workload else {}
     # the per-term stage-2 phases, where timed, replace their sum
     per_term = "mixed_stage2_wrr" in phases or "mixed_stage2_wra" in phases
     found = sorted(((per_build(k), k) for k in kinds
@@ -284,40 +340,345 @@ def build_rooflines(bse, prec, phases, steps, shapes, peaks):
     return out[0], out[1]
 
 
+def _host_block_view(p, rows, k, kp):
+    """block_inputs for a problem drawn with k_rows=rows (pair arrays indexed
+    by position in rows): the (k, k') block, k and k' both in rows."""
+    import bse_inputs as bi
+    r, rp = rows.index(k), rows.index(kp)
+    h = dict(p, m_vv={(k, kp): p["m_vv"][r, kp]}, m_cc={(k, kp): p["m_cc"][r, kp]},
+             n_vc={(k, kp): p["n_vc"][r, kp], (kp, k): p["n_vc"][rp, k]})
+    return bi.block_inputs(h, k, kp)
+
+
 def run_reference(args):
     world, rank, _ = dist_setup(args)
     if rank != 0:
         return 0
+    import numpy as np
     import bse_inputs as bi
     from oracle import bse_oracle as O
-    if args.config not in ("c1", "c2"):
-        raise SystemExit(f"--impl reference times the oracle on whole problems (c1, c2); the "
-                         f"{args.config} workload is sampled block by block by the cpu_baseline "
-                         f"leg of the GPU arm instead")
-    p = bi.make_problem(args.config)
-    flops = build_flops(p["nk"], p["nv"], p["nc"], p["ng"])
-    for _ in range(args.warmup):
-        oracle_step(p, O)
-    tb, tt = [], []
-    for _ in range(args.steps):
-        b, t = oracle_step(p, O)
-        tb.append(b)
-        tt.append(t)
-    value = flops / statistics.mean(tb) / 1e12
+    if args.config in ("c1", "c2"):
+        p = bi.make_problem(args.config)
+        flops = build_flops(p["nk"], p["nv"], p["nc"], p["ng"])
+        for _ in range(args.warmup):
+            oracle_step(p, O)
+        tb, tt = [], []
+        for _ in range(args.steps):
+            b, t = oracle_step(p, O)
+            tb.append(b)
+            tt.append(t)
+        value = flops / statistics.mean(tb) / 1e12
+        ms = 1e3 * statistics.mean(tt)
+        sample = f"full workload, {args.steps} steps of build+reduce+spectrum"
+        workload = WORKLOAD if args.config == "c2" else args.config
+    else:
+        # the oracle on the (k, k') blocks among a few seeded k rows of the
+        # workload (host generator, drawn once, untimed); a step is every
+        # block among those rows, the build's flops scaled by blocks / Nk^2
+        cfg = bi.CONFIGS[args.config]
+        rng = np.random.default_rng(11)
+        rows = sorted(int(x) for x in rng.choice(cfg.nk, size=min(4, cfg.nk), replace=False))
+        p = bi.make_problem(cfg, k_rows=rows)
+        blocks = [(k, kp) for k in rows for kp in rows]
+        flops = build_flops(p["nk"], p["nv"], p["nc"], p["ng"]) * len(blocks) / p["nk"] ** 2
+        views = [_host_block_view(p, rows, k, kp) for k, kp in blocks]
+        for _ in range(args.warmup):
+            for v in views:
+                O.block_A_B(v)
+        tb = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            for v in views:
+                O.block_A_B(v)
+            tb.append(time.perf_counter() - t0)
+        value = flops / statistics.mean(tb) / 1e12
+        ms = 1e3 * statistics.mean(tb)
+        sample = (f"{len(blocks)} (k,k') blocks among k rows {rows} per step (block_A_B, numpy "
+                  f"FP64), flops = the build's x {len(blocks)}/Nk^2")
+        workload = WORKLOAD_C5 if args.config == "c5" else args.config
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * statistics.mean(tt), "higher_is_better": True,
+        "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.config == "c2" else args.config,
-                   "precision": "fp64 (numpy, host)"},
+        "config": {"workload": workload, "precision": "fp64 (numpy, host)"},
         "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cpu_cores(),
-                         "kind": "oracle",
-                         "sample": f"full workload, {args.steps} steps of build+reduce+spectrum"},
+                         "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_sampled_blocks(p, flops, shape_nk, seconds=10.0, label="Q 0"):
+    """The oracle on seeded (k, k') blocks of a device-resident problem for
+    about `seconds` of host time; algorithmic flops of a block = the build's
+    over Nk^2."""
+    import numpy as np
+    import bse_inputs as bi
+    from oracle import bse_oracle as O
+    rng = np.random.default_rng(11)
+    host = dict(p)
+    for key in ("w", "m_x", "v_bar", "e_v", "e_c", "q_minus", "q_plus"):
+        host[key] = p[key].cpu().numpy()
+    nb, t_cpu = 0, 0.0
+    while t_cpu < seconds and nb < 4096:
+        k, kp = (int(x) for x in rng.integers(0, shape_nk, 2))
+        blk = bi.block_inputs(host, k, kp)
+        t0 = time.perf_counter()
+        O.block_A_B(blk)
+        t_cpu += time.perf_counter() - t0
+        nb += 1
+    return {"value": nb * flops / shape_nk ** 2 / t_cpu / 1e12, "unit": "TFLOP/s",
+            "cores": cpu_cores(), "kind": "oracle",
+            "sample": f"{nb} seeded (k,k') blocks of {label} (block_A_B, numpy FP64)",
+            "build_s": t_cpu}
+
+
+def _rel_fro(X, Y, chunk=2048):
+    """||X - Y||_F / ||Y||_F over the first n columns-major rows, in column
+    chunks (no full-size temporaries)."""
+    import torch
+    num = den = 0.0
+    for j in range(0, X.shape[0], chunk):
+        a, b = X[j:j + chunk], Y[j:j + chunk]
+        num += torch.linalg.norm(a - b).item() ** 2
+        den += torch.linalg.norm(b).item() ** 2
+    return (num / den) ** 0.5
+
+
+def c2_time_to_spectrum(bse, bi, prec, steps=10, warmup=3):
+    """The optical-limit workload's time to spectrum (mixed build + FP64
+    reduction, eigensolve, spectrum) against the plain FP64 GPU path, and
+    the energy error between them."""
+    import torch
+    stream = torch.cuda.current_stream()
+    p = bi.make_problem("c2")
+    nk, nv, nc, ng = p["nk"], p["nv"], p["nc"], p["ng"]
+    n = nk * nv * nc
+    d = bse.upload_problem(p)
+    st = bse.make_problem_struct(d)
+    S = torch.empty((n, n), dtype=torch.complex128, device="cuda")
+    L = torch.empty_like(S)
+    E = torch.empty(n, dtype=torch.float64, device="cuda")
+    osc = torch.empty_like(E)
+    om = torch.as_tensor(p["omega"]).cuda()
+    eps = torch.empty(len(p["omega"]), dtype=torch.complex128, device="cuda")
+    rho = torch.as_tensor(p["rho"]).cuda()
+    vc = nk * p["omega_cell"]
+    plan = bse.Plan([st], precision=prec, autotune=True)
+
+    def run(fp64):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        if fp64:
+            bse.bse_build_kernel([st], bse.BSE_PREC_FP64)
+        else:
+            plan.execute()
+        e1.record(stream)
+        bse.bse_reduce(n, d["A"], d["B"], S, L)
+        bse.bse_spectrum(n, S, L, rho, p["c_q"], vc, om, p["delta"], E, osc, eps)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), e0.elapsed_time(e2)
+
+    for _ in range(warmup):
+        run(False)
+    mixed = [run(False) for _ in range(steps)]
+    E_mixed = E.clone()
+    run(True)
+    fp64 = [run(True) for _ in range(3)]
+    plan.status()
+    plan.close()
+    t_mx = statistics.mean(x[1] for x in mixed)
+    t_64 = statistics.mean(x[1] for x in fp64)
+    return {"workload": WORKLOAD, "build_ms": statistics.mean(x[0] for x in mixed),
+            "build_tflops": build_flops(nk, nv, nc, ng) / (statistics.mean(x[0] for x in mixed)
+                                                           * 1e-3) / 1e12,
+            "time_to_spectrum_ms": t_mx, "fp64_build_ms": statistics.mean(x[0] for x in fp64),
+            "fp64_time_to_spectrum_ms": t_64, "speedup_time_to_spectrum": t_64 / t_mx,
+            "max_dE_meV_vs_fp64": (E_mixed - E).abs().max().item() * 1e3}
+
+
+def run_headline(args, bse, bi, prec, world, rank, local):
+    """The largest single-GPU workload (c5), build-only steps; see the module
+    docstring."""
+    import torch
+    dev = "cuda"
+    stream = torch.cuda.current_stream()
+    seed = 20190411 + rank
+    herm = not args.all_blocks
+    p = bi.make_problem_torch(args.config, q_index=args.q, seed=seed)
+    nk, nv, nc, ng = p["nk"], p["nv"], p["nc"], p["ng"]
+    n = nk * nv * nc
+    flops = build_flops(nk, nv, nc, ng)
+    d = bse.upload_problem(p)
+    st = bse.make_problem_struct(d)
+    torch.cuda.synchronize()
+    plan = bse.Plan([st], precision=prec, autotune=True, hermitian=herm)
+    for _ in range(args.warmup):
+        plan.execute()
+    torch.cuda.synchronize()
+    plan.status()
+
+    # ---- timed region: `steps` builds ----
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = bse.bse_kernel_launches()
+    bse.bse_phase_timing(True)
+    for e0, e1 in evs:
+        e0.record(stream)
+        plan.execute()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    bse.bse_phase_timing(False)
+    launches = bse.bse_kernel_launches() - launches0
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    plan.status()
+    phases = bse.bse_phase_report()
+    build_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+    t_build = max_over_ranks([statistics.mean(build_ms)], dev, world)[0]
+    value = weak_scaling_value(world, flops, t_build)
+    computed = flops
+    if herm:   # direct terms over the blocks k <= k' (both stages)
+        fr = built_pairs(nk, True) / nk ** 2
+        s1 = sum(stage1_flops(nk, nv, nc, ng))
+        s2 = 2 * 8.0 * ng * n * n
+        computed = flops - (1 - fr) * (s1 + s2)
+    computed -= (1 - upper_fraction(nk)) * 8.0 * n * n * ng   # exchange over k <= k'
+    extra = {"build_ms": t_build, "build_ms_min": min(build_ms),
+             "computed_flops_per_build": computed,
+             "computed_tflops": computed / (t_build * 1e-3) / 1e12,
+             "build_api": ("bse_plan_execute (plan created once, "
+                           + ("BSE_PLAN_HERMITIAN: direct terms over the blocks k <= k', "
+                              "the rest completed from the mirrors; " if herm else "")
+                           + f"stage-1 tile width autotuned: {plan.tile_cols} columns)"),
+             "phase_ms_per_step": {k: v[1] / args.steps for k, v in phases.items()}}
+
+    # ---- once: the plain FP64 GPU build and the error against it ----
+    E_mx = torch.empty(args.nev, dtype=torch.float64, device=dev)
+    E_64 = torch.empty(args.nev, dtype=torch.float64, device=dev)
+    A64, B64 = torch.empty_like(d["A"]), torch.empty_like(d["B"])
+    st64 = bse.make_problem_struct(dict(d, A=A64, B=B64))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    bse.bse_build_kernel([st64], bse.BSE_PREC_FP64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fp64_ms = e0.elapsed_time(e1)
+    extra.update({"fp64_build_ms": fp64_ms,
+                  "fp64_build_tflops": flops / (fp64_ms * 1e-3) / 1e12,
+                  "speedup_vs_fp64_build": fp64_ms / t_build,
+                  "A_rel_fro_vs_fp64": _rel_fro(d["A"], A64),
+                  "B_rel_fro_vs_fp64": _rel_fro(d["B"], B64)})
+
+    # ---- once: time to the lowest excitons, mixed against plain FP64 ----
+    if args.nev > 0:
+        tol = args.dav_tol or 1e-5
+        runs, iters = [], 0
+        for _ in range(2):      # the first call also sets up the matvec workspace
+            e0.record(stream)
+            plan.execute()
+            iters = bse.bse_lowest_excitons(n, d["A"], d["B"], args.nev, E_mx, None, tol_ev=tol,
+                                            max_iter=args.dav_max_iter, matvec_precision=prec)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            runs.append(e0.elapsed_time(e1))
+        e0.record(stream)
+        iters64 = bse.bse_lowest_excitons(n, A64, B64, args.nev, E_64, None, tol_ev=tol,
+                                          max_iter=args.dav_max_iter,
+                                          matvec_precision=bse.BSE_PREC_FP64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dav64 = e0.elapsed_time(e1)
+        extra["lowest_excitons"] = {
+            "nev": args.nev, "residual_tol_ev": tol,
+            "method": "mixed build + block Davidson (tensor-core matvecs, diagonal preconditioner)",
+            "time_to_lowest_excitons_ms": runs[-1], "first_call_ms": runs[0],
+            "davidson_iterations": iters,
+            "fp64_method": "FP64 build + block Davidson (FP64 matvecs)",
+            "fp64_time_to_lowest_excitons_ms": fp64_ms + dav64, "fp64_davidson_iterations": iters64,
+            "speedup_vs_fp64": (fp64_ms + dav64) / runs[-1],
+            "max_dE_meV_vs_fp64": (E_mx - E_64).abs().max().item() * 1e3,
+            "lowest_E_eV": [round(x, 6) for x in E_mx[:4].tolist()]}
+    del A64, B64, st64
+    torch.cuda.empty_cache()
+
+    # ---- end to end through the public API with pinned host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        keys = ("e_v", "e_c", "m_x", "m_vv", "m_cc", "n_vc", "w", "q_minus", "q_plus", "v_bar")
+        host = {}
+        for k in keys:
+            host[k] = torch.empty(d[k].shape, dtype=d[k].dtype, pin_memory=True)
+            host[k].copy_(d[k])
+        A_h = torch.empty(d["A"].shape, dtype=d["A"].dtype, pin_memory=True)
+        B_h = torch.empty(d["B"].shape, dtype=d["B"].dtype, pin_memory=True)
+        h2d = sum(t.numel() * t.element_size() for t in host.values())
+        d2h = 2 * A_h.numel() * A_h.element_size()
+        e2e_ms = []
+        for i in range(1 + args.e2e_steps):
+            e0.record(stream)
+            for k, t in host.items():
+                d[k].copy_(t, non_blocking=True)
+            plan.execute()
+            A_h.copy_(d["A"], non_blocking=True)
+            B_h.copy_(d["B"], non_blocking=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if i > 0:
+                e2e_ms.append(e0.elapsed_time(e1))
+        plan.status()
+        t_e2e = max_over_ranks([statistics.mean(e2e_ms)], dev, world)[0]
+        e2e = {"value": weak_scaling_value(world, flops, t_e2e), "unit": "TFLOP/s",
+               "ms_per_step": t_e2e, "steps": args.e2e_steps,
+               "what": "inputs copied in from pinned host memory, build, A and B copied out",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        del host, A_h, B_h
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_sampled_blocks(p, flops, nk, label=f"Q {args.q}")
+
+    peaks = load_peaks()
+    roofline, roofline_secondary = build_rooflines(bse, prec, phases, args.steps,
+                                                   [(nk, nv, nc, ng)], peaks, hermitian=herm,
+                                                   workload=args.config)
+    plan.close()
+    del d, p, st
+    torch.cuda.empty_cache()
+    if not args.no_c2:
+        extra["optical_limit_c2"] = c2_time_to_spectrum(bse, bi, prec)
+
+    if rank == 0:
+        input_gb = 16 * (n * ng + 3 * nk * nk * nv * nc * ng + nk * ng * ng) / 1e9
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_build,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "bf16x6": "bf16x6(f32 acc)", "bf16x3": "bf16x3(f32 acc)"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_C5 if args.config == "c5" else args.config,
+                       "precision": args.precision, "step": "one build of A and B",
+                       "hermitian_plan": herm,
+                       "l2": f"inputs larger than L2 ({input_gb:.1f} GB resident in HBM)",
+                       "parallelism": f"Q replicas x{world}"},
+            "roofline": roofline, "roofline_secondary": roofline_secondary,
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": launches, "peaks": peaks,
+        }
+        line.update(extra)
+        print(json.dumps(line), flush=True)
     return 0
 
 
@@ -468,7 +829,8 @@ def run_c4(args, bse, bi, prec, world, rank, local):
 
     peaks = load_peaks()
     roofline, roofline_secondary = build_rooflines(bse, prec, phases, args.steps,
-                                                   [(nk, nv, nc, ng)], peaks)
+                                                   [(nk, nv, nc, ng)], peaks, workload=args.config,
+                                                   upper_exchange=False)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
@@ -500,7 +862,15 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2")
+    ap.add_argument("--config", default="c5",
+                    help="c5 (default: the largest single-GPU workload), c1, c2, c3, c4, c4s")
+    ap.add_argument("--q", type=int, default=0, help="c5: the momentum transfer index built")
+    ap.add_argument("--all-blocks", action="store_true",
+                    help="c5: compute every (k, k') block (no BSE_PLAN_HERMITIAN)")
+    ap.add_argument("--e2e-steps", type=int, default=3,
+                    help="c5: timed end-to-end steps (after one untimed)")
+    ap.add_argument("--no-c2", action="store_true",
+                    help="c5: skip the optical-limit time-to-spectrum extra keys")
     ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "bf16x6", "bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -553,6 +923,11 @@ def main():
     prec = prec_map[args.precision]
 
     # each rank: its own momentum transfers (Q replicas), resident in HBM
+    if args.config in ("c5", "c5s"):
+        rc = run_headline(args, bse, bi, prec, world, rank, local)
+        if world > 1:
+            dist.destroy_process_group()
+        return rc
     if args.config in ("c4", "c4s"):
         rc = run_c4(args, bse, bi, prec, world, rank, local)
         if world > 1:
@@ -743,7 +1118,10 @@ def main():
 
     # ---- roofline of the dominant build kernel (phase timing, live) ----
     peaks = load_peaks()
-    roofline, roofline_secondary = build_rooflines(bse, prec, phases, args.steps, shapes, peaks)
+    roofline, roofline_secondary = build_rooflines(bse, prec, phases, args.steps, shapes, peaks,
+                                                   workload=args.config,
+                                                   upper_exchange=sum(sh[0] * sh[1] * sh[2]
+                                                                      for sh in shapes) >= 2048)
 
     # ---- end to end through the public API with host buffers ----
     e2e = None

@@ -113,6 +113,12 @@ CONFIGS: Dict[str, BSEConfig] = {
     "c5": BSEConfig("c5", grid=4, nv=20, nc=20, ng=500,
                     q_abs=tuple(0.1 * i for i in range(8)),
                     w_decay=0.2, w_diag=1.05, w_scale=0.002),
+    # the molecular-crystal-like recipe on a 2x2x2 grid (N = 3,200, 0.6 GB of
+    # pair elements): the same pair-block and plane-wave shapes as c5 for
+    # profiling captures of its kernels
+    "c5s": BSEConfig("c5s", grid=2, nv=20, nc=20, ng=500,
+                     q_abs=tuple(0.1 * i for i in range(8)),
+                     w_decay=0.2, w_diag=1.05, w_scale=0.002),
 }
 
 

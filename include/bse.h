@@ -121,9 +121,12 @@ typedef struct {
  * BSE, Sec. "BSE in matrix form", Eq. chimatrixq).  probs is a HOST array of
  * nprob descriptors (device pointers inside).  precision selects the
  * contraction arithmetic.  Reads q_minus / q_plus back to the host to check
- * their range (a sync on cuda_stream); the rest is asynchronous.
+ * their range, and reads every input array once on the device to check that
+ * it holds no NaN or infinity (a sync on cuda_stream); the rest is
+ * asynchronous.
  * Errors: BSE_ERR_ARG (sizes, NULL pointers, ld < N, q index out of range,
- * unknown precision), BSE_ERR_NOMEM, BSE_ERR_CUDA, BSE_ERR_UNSUPPORTED. */
+ * a non-finite input value (the message names the arrays), unknown
+ * precision), BSE_ERR_NOMEM, BSE_ERR_CUDA, BSE_ERR_UNSUPPORTED. */
 int bse_build_kernel(const bse_problem* probs, int32_t nprob, int32_t precision,
                      void* cuda_stream);
 
@@ -131,7 +134,8 @@ int bse_build_kernel(const bse_problem* probs, int32_t nprob, int32_t precision,
  * Many momentum transfers (each its own BSE, Eq. chimatrixq) prepared once and
  * then built repeatedly.  bse_plan_create validates every problem (reading
  * q_minus / q_plus back to the host: their contents are fixed for the plan's
- * lifetime), groups the k pairs of every problem by q, allocates all scratch
+ * lifetime; the input arrays are scanned for NaN and infinity once, at
+ * creation), groups the k pairs of every problem by q, allocates all scratch
  * (cudaMalloc, owned by the plan) and, with BSE_PLAN_AUTOTUNE, times the
  * candidate tile widths of the stage-1 tensor-core GEMM and keeps the fastest
  * (remembered per padded NG for the process).  bse_plan_execute enqueues the
@@ -158,12 +162,39 @@ int bse_build_kernel(const bse_problem* probs, int32_t nprob, int32_t precision,
  * valence x 20 conduction bands), its second contraction (over G') also runs
  * on the tensor cores: stage 1 writes T as split BF16 planes and one
  * persistent launch multiplies each pair block; BSE_PLAN_CUDA_CORE_STAGE2
- * keeps the FP32 CUDA-core contraction instead. */
-enum { BSE_PLAN_AUTOTUNE = 1, BSE_PLAN_UNFUSED = 2, BSE_PLAN_CUDA_CORE_STAGE2 = 4 };
+ * keeps the FP32 CUDA-core contraction instead.
+ *
+ * BSE_PLAN_HERMITIAN: A and B are Hermitian (Eq. Hetr), so the plan computes
+ * the direct terms (Eqs. wrrm, wrabar) only for the blocks (k, k') with
+ * k <= k' (every block of rows k v c and columns k' v' c') and sets each
+ * element of a block k > k' to the conjugate of its mirror, which halves the
+ * direct-term work.  The caller asserts the input symmetries under which the
+ * full definitions give Hermitian A and B: W(q) Hermitian and W(-q) =
+ * conj(W(q)) (q_minus[k'][k] the index of -q_minus[k][k']), and
+ * m_vv[k'][k][v'][v] = conj(m_vv[k][k'][v][v']), likewise m_cc (B needs only
+ * W(q) Hermitian).  m_vv and m_cc blocks with k > k' are then not read.
+ * Whole problems only (k_count 0 or nk; BSE_ERR_UNSUPPORTED for a slab);
+ * ignored by BSE_PREC_FP64 plans.  Without the flag every block is computed
+ * from its own inputs.
+ *
+ * The exchange term V (Eq. vrrofM) is Hermitian for any M_x: where a problem
+ * has at least two exchange tiles per SM, only its blocks k <= k' are
+ * computed and the rest completed from the mirrors (with or without the
+ * flag). */
+enum { BSE_PLAN_AUTOTUNE = 1, BSE_PLAN_UNFUSED = 2, BSE_PLAN_CUDA_CORE_STAGE2 = 4,
+       BSE_PLAN_HERMITIAN = 8 };
 int bse_plan_create(const bse_problem* probs, int32_t nprob, int32_t precision, int32_t flags,
                     void** plan, void* cuda_stream);
 int bse_plan_execute(void* plan, void* cuda_stream);
 int bse_plan_status(void* plan, void* cuda_stream);
+/* Clock budget of every bounded wait inside the plan's tensor-core launches
+ * (default about 2 s): a wait that runs longer records a timeout, the launch
+ * winds down (copies and MMAs already issued complete first) and returns,
+ * and bse_plan_status reports BSE_ERR_TIMEOUT; A and B are then incomplete.
+ * seconds in (0, 60], converted with the device's peak SM clock; applies to
+ * the following executes.  FP64 plans have no bounded waits.  Errors:
+ * BSE_ERR_ARG. */
+int bse_plan_set_wait_limit(void* plan, double seconds);
 /* output-column tile width the plan's stage-1 GEMM uses (0 for FP64 plans) */
 int bse_plan_tile_cols(const void* plan);
 /* 1 if the plan's direct terms run as the fused launch, else 0 */
@@ -194,7 +225,8 @@ void bse_plan_destroy(void* plan);
  *     overlaps on the GPU (other streams, other host threads) race on it and
  *     must be serialised by the caller;
  *   - like bse_build_kernel it reads q_minus / q_plus back to the host to
- *     check their range (a sync on cuda_stream).
+ *     check their range (a sync on cuda_stream); it does not scan the inputs
+ *     for NaN or infinity (that scan needs a workspace word).
  * Errors: BSE_ERR_ARG, BSE_ERR_CUDA. */
 int bse_build_kernel_fp64_static(const bse_problem* prob, void* cuda_stream);
 

@@ -21,6 +21,7 @@ BSE_PREC_FP64, BSE_PREC_BF16X6, BSE_PREC_BF16X3 = 0, 2, 3
 BSE_PLAN_AUTOTUNE = 1
 BSE_PLAN_UNFUSED = 2
 BSE_PLAN_CUDA_CORE_STAGE2 = 4
+BSE_PLAN_HERMITIAN = 8
 HARTREE_EV = 27.211386245988
 
 STATUS_NAMES = {0: "BSE_OK", -1: "BSE_ERR_ARG", -2: "BSE_ERR_CUDA", -3: "BSE_ERR_NOMEM",
@@ -61,7 +62,7 @@ EXPORTED = ("bse_build_kernel", "bse_reduce", "bse_spectrum", "bse_last_error", 
             "bse_mlp_predict", "bse_xpy", "bse_mlp_trajectory_samples", "bse_plan_create",
             "bse_plan_execute", "bse_plan_status", "bse_plan_tile_cols", "bse_plan_destroy",
             "bse_plan_fused", "bse_spectrum_tensor", "bse_loss_function",
-            "bse_lowest_excitons_from", "bse_rpa_screening")
+            "bse_lowest_excitons_from", "bse_rpa_screening", "bse_plan_set_wait_limit")
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -104,6 +105,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.bse_plan_fused.argtypes = [vp]
     lib.bse_plan_destroy.argtypes = [vp]
     lib.bse_plan_destroy.restype = None
+    lib.bse_plan_set_wait_limit.argtypes = [vp, dbl]
+    lib.bse_plan_set_wait_limit.restype = ctypes.c_int
     for name in ("bse_plan_create", "bse_plan_execute", "bse_plan_status", "bse_plan_tile_cols",
                  "bse_plan_fused"):
         getattr(lib, name).restype = ctypes.c_int
@@ -551,13 +554,14 @@ class Plan:
 
     def __init__(self, problems: Sequence[bse_problem], precision: int = BSE_PREC_BF16X6,
                  autotune: bool = False, fused: bool = True, tc_stage2: bool = True,
-                 stream=None):
+                 hermitian: bool = False, stream=None):
         lib = load()
         self._problems = list(problems)
         arr = (bse_problem * len(self._problems))(*self._problems)
         h = ctypes.c_void_p()
         flags = ((BSE_PLAN_AUTOTUNE if autotune else 0) | (0 if fused else BSE_PLAN_UNFUSED)
-                 | (0 if tc_stage2 else BSE_PLAN_CUDA_CORE_STAGE2))
+                 | (0 if tc_stage2 else BSE_PLAN_CUDA_CORE_STAGE2)
+                 | (BSE_PLAN_HERMITIAN if hermitian else 0))
         _check(lib.bse_plan_create(arr, len(self._problems), int(precision), flags,
                                    ctypes.byref(h), _stream(stream)))
         self.handle = h
@@ -567,6 +571,10 @@ class Plan:
 
     def status(self, stream=None) -> None:
         _check(load().bse_plan_status(self.handle, _stream(stream)))
+
+    def set_wait_limit(self, seconds: float) -> None:
+        """Clock budget of the bounded device waits of later executes."""
+        _check(load().bse_plan_set_wait_limit(self.handle, float(seconds)))
 
     @property
     def tile_cols(self) -> int:

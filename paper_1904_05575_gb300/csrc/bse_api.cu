@@ -3,6 +3,7 @@
 // exception crosses this boundary.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -114,7 +115,81 @@ void keep_pool_memory() {
   done[dev] = true;
 }
 
-Problem validate(const bse_problem& p, int index, cudaStream_t s) {
+// Non-finite input scan: bit `bit` of *flag is set if any double of the
+// array is a NaN or an infinity (exponent field all ones).  16-byte words,
+// grid-stride.
+__global__ void __launch_bounds__(256) k_nonfinite16(const uint4* __restrict__ p, int64_t nwords,
+                                                     int bit, int* flag) {
+  bool bad = false;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nwords;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint4 w = __ldg(p + i);
+    bad = bad || ((w.y >> 20) & 0x7FFu) == 0x7FFu || ((w.w >> 20) & 0x7FFu) == 0x7FFu;
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1 << bit);
+}
+
+__global__ void k_nonfinite8(const double* __restrict__ p, int64_t n, int bit, int* flag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t hi = (uint32_t)(__double_as_longlong(p[i]) >> 32);
+    if (((hi >> 20) & 0x7FFu) == 0x7FFu) atomicOr(flag, 1 << bit);
+  }
+}
+
+// Every input array of the problem read once on the device: BSE_ERR_ARG
+// naming the arrays that hold a NaN or an infinity.  Syncs.
+void check_finite(const bse_problem& p, int64_t kn, const std::string& at, cudaStream_t s) {
+  const int64_t n = (int64_t)p.nk * p.nv * p.nc, ng = p.ng, nk = p.nk;
+  struct Arr { const void* ptr; int64_t doubles; const char* name; };
+  std::vector<Arr> arrs = {{p.e_v, nk * p.nv, "e_v"}, {p.e_c, nk * p.nc, "e_c"},
+                           {p.m_x, 2 * n * ng, "m_x"}, {p.v_bar, ng, "v_bar"}};
+  if (p.gamma_c != 0.0) {
+    arrs.push_back({p.m_vv, 2 * kn * nk * p.nv * p.nv * ng, "m_vv"});
+    arrs.push_back({p.m_cc, 2 * kn * nk * p.nc * p.nc * ng, "m_cc"});
+    arrs.push_back({p.w, 2 * (int64_t)p.nq_w * ng * ng, "w"});
+    if (p.coupling) arrs.push_back({p.n_vc, 2 * nk * nk * p.nv * p.nc * ng, "n_vc"});
+  }
+  int* flag = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&flag), sizeof(int), s) != cudaSuccess) {
+    (void)cudaGetLastError();
+    throw Error(BSE_ERR_NOMEM, "workspace allocation failed (input scan)");
+  }
+  int h = 0;
+  try {
+    BSE_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), s));
+    for (size_t i = 0; i < arrs.size(); ++i) {
+      const Arr& a = arrs[i];
+      if (a.doubles % 2 == 0 && (reinterpret_cast<uintptr_t>(a.ptr) & 15) == 0) {
+        const int64_t words = a.doubles / 2;
+        const int grid = (int)std::min<int64_t>((words + 255) / 256, 152 * 8);
+        k_nonfinite16<<<std::max(grid, 1), 256, 0, s>>>(static_cast<const uint4*>(a.ptr), words,
+                                                        (int)i, flag);
+      } else {
+        const int grid = (int)std::min<int64_t>((a.doubles + 255) / 256, 152 * 8);
+        k_nonfinite8<<<std::max(grid, 1), 256, 0, s>>>(static_cast<const double*>(a.ptr),
+                                                       a.doubles, (int)i, flag);
+      }
+      BSE_CUDA(cudaGetLastError());
+      note_launches(1);
+    }
+    BSE_CUDA(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BSE_CUDA(cudaFreeAsync(flag, s));
+    flag = nullptr;
+    BSE_CUDA(cudaStreamSynchronize(s));
+  } catch (...) {
+    if (flag) cudaFreeAsync(flag, s);
+    throw;
+  }
+  if (h) {
+    std::string names;
+    for (size_t i = 0; i < arrs.size(); ++i)
+      if (h & (1 << i)) names += std::string(names.empty() ? "" : ", ") + arrs[i].name;
+    throw Error(BSE_ERR_ARG, at + "non-finite value (NaN or infinity) in " + names);
+  }
+}
+
+Problem validate(const bse_problem& p, int index, cudaStream_t s, bool scan = true) {
   const std::string at = "probs[" + std::to_string(index) + "]: ";
   BSE_CHECK_ARG(p.nk >= 1 && p.nv >= 1 && p.nc >= 1 && p.ng >= 1 && p.nq_w >= 1,
                 at + "nk, nv, nc, ng and nq_w must all be >= 1");
@@ -145,6 +220,7 @@ Problem validate(const bse_problem& p, int index, cudaStream_t s) {
                     aligned(p.q_minus, 4) && aligned(p.q_plus, 4),
                 at + "real arrays must be 8-byte and q maps 4-byte aligned");
   Problem pr;
+  if (scan) check_finite(p, p.k_count > 0 ? p.k_count : p.nk, at, s);
   if (p.gamma_c != 0.0) {
     pr.qm_host = check_q_map(p.q_minus, p.nk, p.nq_w, "q_minus", s);
     if (p.coupling) pr.qp_host = check_q_map(p.q_plus, p.nk, p.nq_w, "q_plus", s);
@@ -187,7 +263,7 @@ extern "C" int bse_build_kernel(const bse_problem* probs, int32_t nprob, int32_t
 extern "C" int bse_build_kernel_fp64_static(const bse_problem* prob, void* cuda_stream) {
   return guarded([&] {
     BSE_CHECK_ARG(prob != nullptr, "prob is NULL");
-    const Problem pr = validate(*prob, 0, static_cast<cudaStream_t>(cuda_stream));
+    const Problem pr = validate(*prob, 0, static_cast<cudaStream_t>(cuda_stream), false);
     build_fp64_static(pr, static_cast<cudaStream_t>(cuda_stream));
   });
 }
@@ -201,7 +277,8 @@ extern "C" int bse_plan_create(const bse_problem* probs, int32_t nprob, int32_t 
     BSE_CHECK_ARG(precision == BSE_PREC_FP64 || precision == BSE_PREC_BF16X6 ||
                       precision == BSE_PREC_BF16X3,
                   "unknown precision " + std::to_string(precision));
-    BSE_CHECK_ARG((flags & ~(BSE_PLAN_AUTOTUNE | BSE_PLAN_UNFUSED | BSE_PLAN_CUDA_CORE_STAGE2)) == 0,
+    BSE_CHECK_ARG((flags & ~(BSE_PLAN_AUTOTUNE | BSE_PLAN_UNFUSED | BSE_PLAN_CUDA_CORE_STAGE2 |
+                             BSE_PLAN_HERMITIAN)) == 0,
                   "unknown plan flags");
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     keep_pool_memory();
@@ -234,6 +311,14 @@ extern "C" int bse_plan_tile_cols(const void* plan) {
 
 extern "C" int bse_plan_fused(const void* plan) {
   return plan ? plan_fused(static_cast<const BatchPlan*>(plan)) : 0;
+}
+
+extern "C" int bse_plan_set_wait_limit(void* plan, double seconds) {
+  return guarded([&] {
+    BSE_CHECK_ARG(plan != nullptr, "plan is NULL");
+    BSE_CHECK_ARG(seconds > 0.0 && seconds <= 60.0, "wait limit must be in (0, 60] seconds");
+    plan_set_wait(static_cast<BatchPlan*>(plan), seconds);
+  });
 }
 
 extern "C" void bse_plan_destroy(void* plan) { plan_destroy(static_cast<BatchPlan*>(plan)); }

@@ -143,6 +143,7 @@ void plan_execute(BatchPlan* plan, cudaStream_t s);
 int plan_status(BatchPlan* plan, cudaStream_t s);
 int plan_tile_cols(const BatchPlan* plan);
 int plan_fused(const BatchPlan* plan);
+void plan_set_wait(BatchPlan* plan, double seconds);
 void plan_destroy(BatchPlan* plan);
 
 // Reduction and spectrum.

@@ -75,6 +75,7 @@ struct SplitArgs {
   int pair_nb = 0;          // SPLIT_PAIRS: rows_per = nb^2 rows (b, b') stored as (b', b)
   int64_t src_ld = 0;       // SPLIT_DENSE: source row stride (0: K)
   int zero_diag = 0;        // SPLIT_DENSE: element k == row stored as zero
+  int bneg = 0;             // B-operand layout: 3P planes (-Im, Re, Im) per piece
 };
 
 // One thread per (output row, 8 consecutive k): every element is read as two
@@ -130,8 +131,16 @@ __global__ void __launch_bounds__(256) k_split(SplitArgs a) {
       vr.z = hr[p][4] | (hr[p][5] << 16); vr.w = hr[p][6] | (hr[p][7] << 16);
       vi.x = hi[p][0] | (hi[p][1] << 16); vi.y = hi[p][2] | (hi[p][3] << 16);
       vi.z = hi[p][4] | (hi[p][5] << 16); vi.w = hi[p][6] | (hi[p][7] << 16);
-      *reinterpret_cast<uint4*>(a.out + (int64_t)p * plane + o) = vr;
-      *reinterpret_cast<uint4*>(a.out + (int64_t)(P + p) * plane + o) = vi;
+      if (a.bneg) {   // planes 3p: -Im (both BF16 signs flipped), 3p + 1: Re, 3p + 2: Im
+        const uint4 vn = make_uint4(vi.x ^ 0x80008000u, vi.y ^ 0x80008000u, vi.z ^ 0x80008000u,
+                                    vi.w ^ 0x80008000u);
+        *reinterpret_cast<uint4*>(a.out + (int64_t)(3 * p) * plane + o) = vn;
+        *reinterpret_cast<uint4*>(a.out + (int64_t)(3 * p + 1) * plane + o) = vr;
+        *reinterpret_cast<uint4*>(a.out + (int64_t)(3 * p + 2) * plane + o) = vi;
+      } else {
+        *reinterpret_cast<uint4*>(a.out + (int64_t)p * plane + o) = vr;
+        *reinterpret_cast<uint4*>(a.out + (int64_t)(P + p) * plane + o) = vi;
+      }
     }
   }
 }
@@ -151,47 +160,101 @@ void launch_split(const SplitArgs& a, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // epilogues of the tensor-core GEMM
 // ---------------------------------------------------------------------------
-// V[alpha][alpha'] -> A, B (column-major FP64).  V is Hermitian (Eq. vrrofM);
-// with `tri`, only tiles touching the lower triangle are computed: the
-// epilogue writes (alpha, alpha') for alpha' <= alpha and its conjugate at
-// (alpha', alpha) for alpha' < alpha, and skips the tile's upper-triangle
-// elements (their mirror is written from the lower tile).  Every element is
-// written once; the diagonal of V is stored real.
+// V[alpha][alpha'] -> A, B (column-major FP64).  V is Hermitian (Eq. vrrofM)
+// and so are A and B (Eq. Hetr): with `upper`, only tiles touching the blocks
+// k <= k' are computed and the epilogue writes the elements of those blocks
+// (alpha in block k, alpha' in block k', k = alpha / (nv nc)); the blocks
+// k > k' are filled afterwards from their mirror by k_hermitian_complete.
+// The diagonal of V is stored real.  Lanes are consecutive rows of one
+// column: every store is coalesced.
 struct ExchangeEpi {
   double2 *A, *B;
   int64_t ld;
   float scale;         // 2 gamma_x kappa (the product is formed in FP32, then widened exactly)
   const double *e_v, *e_c;
   int nv, nc;
-  int tri;
+  int upper;
   __device__ __forceinline__ void operator()(const tc::Tile& t, int row, int c0, const float* re,
                                              const float* im) const {
-    const int64_t al = t.out_row0 + row;
+    const int al = t.out_row0 + row;              // N < 2^30 (checked at validation)
+    const int nb = nv * nc;
+    const int kal = al / nb;
+    // block k' of column ap is >= k of the row exactly when ap >= k nb
+    const int ap_min = upper ? kal * nb : 0;
+    double2* a_col = A + al + (int64_t)(t.n0 + c0) * ld;
+    double2* b_col = B ? B + al + (int64_t)(t.n0 + c0) * ld : nullptr;
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
       const int col = c0 + j;
-      const int64_t ap = t.n0 + col;
-      if (col < t.n_valid && (!tri || ap <= al)) {
+      const int ap = t.n0 + col;
+      if (col < t.n_valid && ap >= ap_min) {
         double2 val = make_double2(f32_to_f64_bits(scale * re[j]), f32_to_f64_bits(scale * im[j]));
-        const int64_t off = al + ap * ld;
-        if (tri && ap < al) {
-          const double2 mir = make_double2(val.x, -val.y);
-          const int64_t moff = ap + al * ld;
-          if (B) B[moff] = mir;
-          A[moff] = mir;
-        }
         if (al == ap) val.y = 0.0;   // the diagonal of a Hermitian V is real
-        if (B) B[off] = val;
+        if (b_col) b_col[(int64_t)j * ld] = val;
         if (al == ap) {
-          const int64_t kk = al / (nv * nc);
-          const int v = (int)((al / nc) % nv), c = (int)(al % nc);
-          val.x += e_c[kk * nc + c] - e_v[kk * nv + v];
+          const int r = al - kal * nb, v = r / nc, c = r - v * nc;
+          val.x += e_c[kal * nc + c] - e_v[kal * nv + v];
         }
-        A[off] = val;
+        a_col[(int64_t)j * ld] = val;
       }
     }
   }
 };
+
+// Hermitian completion (Eq. Hetr: A and B Hermitian): every element of a block
+// k > k' is set to the conjugate of its mirror in block (k', k).  Tiles of
+// 32 x 32 elements of the lower half, staged through shared memory so that
+// the reads (a run of rows of one source column) and the writes (a run of
+// rows of one destination column) are both coalesced.  Elements of the
+// diagonal blocks are left alone.
+struct CompleteArgs {
+  double2* M;       // A or B, column-major
+  int64_t ld;
+  int n, nb;        // N; rows per k block (nv nc)
+};
+
+__global__ void __launch_bounds__(256) k_hermitian_complete(CompleteArgs a) {
+  __shared__ double2 t[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t nt = (a.n + 31) / 32;
+  const int64_t ntiles = nt * (nt + 1) / 2;
+  for (int64_t L = blockIdx.x; L < ntiles; L += gridDim.x) {
+    // tile (tr, tc), tr >= tc, of the lower triangle of the tile grid (an FP32
+    // estimate of the row, corrected with integers: no FP64 arithmetic)
+    int64_t tr = (int64_t)((sqrtf(8.f * (float)L + 1.f) - 1.f) * 0.5f);
+    while (tr * (tr + 1) / 2 > L) --tr;
+    while ((tr + 1) * (tr + 2) / 2 <= L) ++tr;
+    const int64_t tcol = L - tr * (tr + 1) / 2;
+    const int r0 = (int)(tr * 32), c0 = (int)(tcol * 32);
+    const int rlast = min(r0 + 31, a.n - 1);
+    if (rlast / a.nb <= c0 / a.nb) continue;   // no element below the diagonal blocks
+    // source: (c, r) for c in [c0, c0+32), r in [r0, r0+32): column r, rows c
+    for (int j = ty; j < 32; j += 8) {
+      const int r = r0 + j, c = c0 + tx;
+      if (r < a.n && c < a.n) t[j][tx] = a.M[c + (int64_t)r * a.ld];
+    }
+    __syncthreads();
+    // destination: (r, c) = conj of the source (c, r), column c, rows r
+    for (int j = ty; j < 32; j += 8) {
+      const int c = c0 + j, r = r0 + tx;
+      if (r < a.n && c < a.n && r / a.nb > c / a.nb) {
+        const double2 v = t[tx][j];
+        a.M[r + (int64_t)c * a.ld] = make_double2(v.x, -v.y);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+void launch_hermitian_complete(double2* M, int64_t ld, int n, int nb, cudaStream_t s) {
+  if (!M || n <= nb) return;
+  const int64_t nt = (n + 31) / 32;
+  const int64_t ntiles = nt * (nt + 1) / 2;
+  const int grid = (int)std::min<int64_t>(ntiles, 152 * 8);
+  k_hermitian_complete<<<grid, 256, 0, s>>>(CompleteArgs{M, ld, n, nb});
+  BSE_CUDA(cudaGetLastError());
+  note_launches(1);
+}
 
 // Stage-1 output per direct term (Tile::prob = term): FP32 T[G][row] for the
 // CUDA-core stage 2, or, for a term whose stage 2 runs on the tensor cores,
@@ -203,6 +266,8 @@ struct TOut {
   __nv_bfloat16* planes;      // split path
   int64_t plane_rows;
   int Kp, pieces, conj;
+  int bneg = 0;               // planes in the B-operand layout (3P: -Im, Re, Im per piece)
+  int64_t row_off = 0;        // row of the planes = stage-1 row + row_off
 };
 
 struct TEpiMulti {
@@ -221,6 +286,7 @@ struct TEpiMulti {
     // padded K is not written (columns past NG hold zeros from set-up)
     const int64_t plane = o.plane_rows * o.Kp;
     const uint32_t flip = o.conj ? 0x80000000u : 0u;
+    const int64_t rp = r + o.row_off;
 #pragma unroll
     for (int g8 = 0; g8 < 4; ++g8) {
       const int col = t.n0 + c0 + 8 * g8;
@@ -247,7 +313,7 @@ struct TEpiMulti {
           hi[q][e] = b3[q];
         }
       }
-      const int64_t off = r * o.Kp + col;
+      const int64_t off = rp * o.Kp + col;
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
         if (q < o.pieces) {
@@ -256,8 +322,16 @@ struct TEpiMulti {
           vr.z = hr[q][4] | (hr[q][5] << 16); vr.w = hr[q][6] | (hr[q][7] << 16);
           vi.x = hi[q][0] | (hi[q][1] << 16); vi.y = hi[q][2] | (hi[q][3] << 16);
           vi.z = hi[q][4] | (hi[q][5] << 16); vi.w = hi[q][6] | (hi[q][7] << 16);
-          *reinterpret_cast<uint4*>(o.planes + (int64_t)q * plane + off) = vr;
-          *reinterpret_cast<uint4*>(o.planes + (int64_t)(o.pieces + q) * plane + off) = vi;
+          if (o.bneg) {
+            const uint4 vn = make_uint4(vi.x ^ 0x80008000u, vi.y ^ 0x80008000u,
+                                        vi.z ^ 0x80008000u, vi.w ^ 0x80008000u);
+            *reinterpret_cast<uint4*>(o.planes + (int64_t)(3 * q) * plane + off) = vn;
+            *reinterpret_cast<uint4*>(o.planes + (int64_t)(3 * q + 1) * plane + off) = vr;
+            *reinterpret_cast<uint4*>(o.planes + (int64_t)(3 * q + 2) * plane + off) = vi;
+          } else {
+            *reinterpret_cast<uint4*>(o.planes + (int64_t)q * plane + off) = vr;
+            *reinterpret_cast<uint4*>(o.planes + (int64_t)(o.pieces + q) * plane + off) = vi;
+          }
         }
       }
     }
@@ -344,6 +418,7 @@ struct Stage2Args {
   const float2* T;
   int64_t t_ld;
   const int* slot_of_pair;
+  const int* pair_of = nullptr;   // index -> pair of the pairs built (NULL: every pair)
   int rows_x, rows_t, ng, nk, nv, nc;
   int64_t t_row0 = 0;    // first T row of this term (batched plans)
   int k_begin = 0;       // first k row of the slab: pair p = (k - k_begin) nk + k'
@@ -351,6 +426,12 @@ struct Stage2Args {
   double2* out;          // A or B
   int64_t ld;
 };
+
+// i-th pair block of a stage-2 launch: every pair of the slab, or the listed
+// ones (the blocks k <= k' of a Hermitian build)
+__device__ __forceinline__ int s2_pair(const Stage2Args& a, int i) {
+  return a.pair_of ? a.pair_of[i] : i;
+}
 
 // asynchronous global -> shared copies (zero-filled when pred is false)
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool pred) {
@@ -380,7 +461,7 @@ __global__ void __launch_bounds__((TX / RX) * (TT / RT)) k_stage2(Stage2Args a) 
   __shared__ __align__(16) uint4 Xr[2][TX][GC];      // raw FP64 complex
   __shared__ __align__(16) float2 Tr[2][GC][TT];     // FP32 complex
   __shared__ float2 Xs[TX][GC + 1];                  // converted X of the current chunk
-  const int p = blockIdx.x;
+  const int p = s2_pair(a, blockIdx.x);
   const int k = a.k_begin + p / a.nk, kp = p % a.nk;
   const int rx0 = blockIdx.y * TX, rt0 = blockIdx.z * TT;
   const int64_t xp = a.x_transpose_pair ? (int64_t)kp * a.nk + k : (int64_t)p;
@@ -513,7 +594,7 @@ __global__ void __launch_bounds__(256) k_stage2_pipe(Stage2Args a) {
   __shared__ __align__(16) uint4 Xr[2][16][GC];      // raw FP64 complex
   __shared__ __align__(16) float2 Tr[2][GC][16];     // FP32 complex
   __shared__ float2 Xs[16][GC + 1];                  // converted X of the current chunk
-  const int p = blockIdx.x;
+  const int p = s2_pair(a, blockIdx.x);
   const int k = a.k_begin + p / a.nk, kp = p % a.nk;
   const int64_t xp = a.x_transpose_pair ? (int64_t)kp * a.nk + k : (int64_t)p;
   const uint4* X = reinterpret_cast<const uint4*>(a.x) + xp * a.rows_x * a.ng;
@@ -635,15 +716,17 @@ __global__ void __launch_bounds__(SK_ROWS) k_stage2_skinny(Stage2Args a, int64_t
     const int64_t R = row0 + tid;
     int64_t off = -1;
     if (R < total_rows) {
-      const int p = (int)(R / rows_x), r = (int)(R - (int64_t)p * rows_x);
+      const int i = (int)(R / rows_x), r = (int)(R - (int64_t)i * rows_x);
+      const int p = s2_pair(a, i);
       const int k = a.k_begin + p / nk, kp = p % nk;
       const int64_t xp = a.x_transpose_pair ? (int64_t)kp * nk + k : (int64_t)p;
       off = (xp * rows_x + r) * a.ng;
     }
     xoff[tid] = off;
     if (tid < SK_PAIRS) {
-      const int64_t p = p_first + tid;
-      toff[tid] = p * rows_x < total_rows ? a.t_row0 + (int64_t)a.slot_of_pair[p] * a.rows_t : -1;
+      const int64_t i = p_first + tid;
+      toff[tid] = i * rows_x < total_rows
+                      ? a.t_row0 + (int64_t)a.slot_of_pair[s2_pair(a, (int)i)] * a.rows_t : -1;
     }
   }
   __syncthreads();
@@ -722,7 +805,8 @@ __global__ void __launch_bounds__(SK_ROWS) k_stage2_skinny(Stage2Args a, int64_t
     __syncthreads();   // the next prefetch overwrites this buffer
   }
   if (R >= total_rows) return;
-  const int p = (int)(R / rows_x), rx = (int)(R - (int64_t)p * rows_x);
+  const int i = (int)(R / rows_x), rx = (int)(R - (int64_t)i * rows_x);
+  const int p = s2_pair(a, i);
   const int k = a.k_begin + p / nk, kp = p % nk;
   const int nv = a.nv, nc = a.nc;
   const float sc = (float)a.scale;
@@ -789,9 +873,9 @@ __global__ void __launch_bounds__(256) k_stage2_multi(Stage2Args a, int npair, i
   const int rx_n = a.rows_x, rt_n = a.rows_t, per = rx_n * rt_n;
   const int p0 = blockIdx.x * pb;
   if (tid < pb) {
-    const int p = p0 + tid;
     int64_t xb = -1, tb = -1;
-    if (p < npair) {
+    if (p0 + tid < npair) {
+      const int p = s2_pair(a, p0 + tid);
       const int k = a.k_begin + p / a.nk, kp = p % a.nk;
       const int64_t xp = a.x_transpose_pair ? (int64_t)kp * a.nk + k : (int64_t)p;
       xb = xp * rx_n * a.ng;
@@ -871,7 +955,7 @@ __global__ void __launch_bounds__(256) k_stage2_multi(Stage2Args a, int npair, i
     __syncthreads();   // the next prefetch overwrites this buffer
   }
   if (!active || xbase[q] < 0) return;
-  const int p = p0 + q;
+  const int p = s2_pair(a, p0 + q);
   const int k = a.k_begin + p / a.nk, kp = p % a.nk;
   const int nv = a.nv, nc = a.nc, rx = ri, rt = rj;
   int vi, ci, vp, cp;
@@ -1043,7 +1127,7 @@ tc::GemmShape make_shape(int nt, int Kp, int pieces, int seg = 8, int whole = 12
   sh.acc_bufs = 8 * nt <= 512 ? 2 : 1;
   const int cols = 4 * nt * sh.acc_bufs;
   sh.tmem_cols = cols <= 128 ? 128 : cols <= 256 ? 256 : 512;
-  const uint32_t sb = 2u * pieces * (tc::a_plane_bytes() + tc::b_plane_bytes(nt));
+  const uint32_t sb = tc::stage_bytes(sh);
   const size_t budget = 220 * 1024;
   int st = (int)((budget - 2048) / sb);
   sh.stages = std::max(1, std::min(st, 6));
@@ -1151,7 +1235,7 @@ struct ExParams {
   float scale;
   const double *e_v, *e_c;
   int nv, nc;
-  int tri;        // lower-triangle tiles only (see ExchangeEpi)
+  int upper;      // the blocks k <= k' only (see ExchangeEpi)
 };
 
 struct ExchangeBatchEpi {   // ExchangeEpi with per-problem outputs
@@ -1159,7 +1243,7 @@ struct ExchangeBatchEpi {   // ExchangeEpi with per-problem outputs
   __device__ __forceinline__ void operator()(const tc::Tile& t, int row, int c0, const float* re,
                                              const float* im) const {
     const ExParams q = params[t.prob];
-    ExchangeEpi e{q.A, q.B, q.ld, q.scale, q.e_v, q.e_c, q.nv, q.nc, q.tri};
+    ExchangeEpi e{q.A, q.B, q.ld, q.scale, q.e_v, q.e_c, q.nv, q.nc, q.upper};
     e(t, row, c0, re, im);
   }
 };
@@ -1173,7 +1257,13 @@ std::map<int, int> g_tuned_nt;
 struct BatchPlan {
   int precision = 0, pieces = 3, planes = 6, ng = 0, Kp = 0, ng_pad = 0, nt_x = 0, nt_g = 0;
   int device = 0;
+  std::mutex use_mutex;   // held by bse_build_kernel through a cached plan's execute and status
+  long long wait = tc::WAIT_CYCLES;   // clock budget of each pipeline wait in its GEMM launches
   std::vector<Problem> probs;
+  // Hermitian build (BSE_PLAN_HERMITIAN): direct terms over the blocks k <= k'
+  // only, the blocks k > k' of A and B completed from their mirrors
+  bool half = false;
+  std::vector<int> upper_probs;   // problems whose exchange wrote the blocks k <= k' only
   // exchange
   int64_t x_rows = 0;
   std::vector<int64_t> x_row0;
@@ -1191,21 +1281,27 @@ struct BatchPlan {
     bool w_conj_transpose = false;
     DevMem perm, slot;
     Stage2Args s2{};
-    std::vector<int32_t> qh;
+    std::vector<int32_t> qh;   // q index of each pair built, in pair-list order
+    std::vector<int> act_h;    // the pairs built: every pair of the slab, or k <= k'
+    std::vector<int> slot_h;   // pair -> stage-1 slot (-1: not built)
+    DevMem act;
+    int nact = 0;
     // stage 2 on the tensor cores (large pair blocks)
     bool tc2 = false;
     bool rows_t_side = false;   // stage-2 tile rows are the T side (W^rr with T on (c, c'))
     int side_nb = 0, x_nb = 0;  // (b, b') rows stored (b', b) in the stage-1 side / x2 planes
-    int64_t x2_row0 = 0;     // first row of this term's pair side in the x2 planes
+    int64_t x2_row0 = 0;     // first row of this term's pair side in its x2 array
+    int64_t t_row0 = 0;      // first row of this term's T in its T array
     DevMem x2perm;           // pair -> pair whose side rows are read (identity, or (k', k))
   };
   std::vector<Term> terms;
   int64_t a_rows = 0, w_rows = 0;
   DevMem wsplit, asplit, tbuf, stiles;
   int n_stiles = 0;
-  // stage 2 on the tensor cores for terms with large pair blocks
-  int64_t x2_rows = 0;
-  DevMem x2split, tplanes, touts, s2tiles, s2tiles_t, s2params;
+  // stage 2 on the tensor cores for terms with large pair blocks: T and the
+  // other pair side in the layout of their operand role (A: 2P planes, B: 3P)
+  int64_t ta_rows = 0, tb_rows = 0, x2a_rows = 0, x2b_rows = 0;
+  DevMem ta, tb, x2a, x2b, touts, s2tiles, s2tiles_t, s2params;
   int n_s2tiles = 0, n_s2tiles_t = 0, nt2 = 0;
   tc::GemmShape sh_2{};
   CUtensorMap ma_2{}, mb_2{}, ma_2t{}, mb_2t{};   // rows = X side / rows = T side
@@ -1254,15 +1350,17 @@ void plan_splits(BatchPlan& pl, cudaStream_t s) {
     sb.conj = 0;
     sb.kscale = nullptr;
     sb.out = pl.xb.as<__nv_bfloat16>();
+    sb.bneg = 1;
     launch_split(sb, s);
   }
   for (BatchPlan::Term& t : pl.terms) {
     const bse_problem& p = pl.probs[t.prob].p;
-    const int npair = (int)pl.probs[t.prob].slab_pairs();
+    const int npair = t.nact;
     SplitArgs sw{reinterpret_cast<const double2*>(p.w), SPLIT_W, nullptr, pl.ng_pad,
                  t.w_conj_transpose ? 1 : 0, pl.ng, pl.Kp, p.nq_w * pl.ng_pad, pl.pieces,
                  t.w_conj_transpose ? 1 : 0, nullptr, pl.wsplit.as<__nv_bfloat16>(), pl.w_rows,
                  t.w_row0};
+    sw.bneg = 1;
     if (t.w_owner) launch_split(sw, s);
     SplitArgs sa{reinterpret_cast<const double2*>(t.side), SPLIT_PAIRS, t.perm.as<int>(),
                  t.rows_side, 0, pl.ng, pl.Kp, npair * t.rows_side, pl.pieces, 0, nullptr,
@@ -1272,15 +1370,33 @@ void plan_splits(BatchPlan& pl, cudaStream_t s) {
     if (t.tc2) {   // the other pair side, in pair order, conjugated as opX
       SplitArgs sx{t.s2.x, SPLIT_PAIRS, t.x2perm.as<int>(), t.s2.rows_x, 0, pl.ng, pl.Kp,
                    npair * t.s2.rows_x, pl.pieces, t.s2.conj_x, nullptr,
-                   pl.x2split.as<__nv_bfloat16>(), pl.x2_rows, t.x2_row0};
+                   (t.rows_t_side ? pl.x2b : pl.x2a).as<__nv_bfloat16>(),
+                   t.rows_t_side ? pl.x2b_rows : pl.x2a_rows, t.x2_row0};
       sx.pair_nb = t.x_nb;
+      sx.bneg = t.rows_t_side ? 1 : 0;   // the B operand when T forms the tile rows
       launch_split(sx, s);
     }
   }
 }
 
+// blocks k > k' of A and B from their mirrors, for the problems whose
+// exchange wrote only the blocks k <= k' (or every problem of a Hermitian plan)
+void plan_complete(BatchPlan& pl, bool all, cudaStream_t s) {
+  Phase ph("hermitian_complete", s);
+  for (size_t i = 0; i < pl.probs.size(); ++i) {
+    if (!all && std::find(pl.upper_probs.begin(), pl.upper_probs.end(), (int)i) == pl.upper_probs.end())
+      continue;
+    const bse_problem& p = pl.probs[i].p;
+    const int n = (int)pl.probs[i].n, nb = p.nv * p.nc;
+    launch_hermitian_complete(reinterpret_cast<double2*>(p.A), p.ld, n, nb, s);
+    if (p.coupling) launch_hermitian_complete(reinterpret_cast<double2*>(p.B), p.ld, n, nb, s);
+  }
+}
+
 void plan_execute_mixed(BatchPlan& pl, cudaStream_t s) {
-  BSE_CUDA(cudaMemsetAsync(pl.err.ptr, 0, sizeof(int), s));
+  // (the status word is cleared at creation and by plan_status, not here: a
+  // timeout in any execute since the last status call stays visible)
+  pl.sh_x.wait = pl.sh_g.wait = pl.sh_2.wait = pl.wait;
   {
     Phase ph("mixed_split", s);
     plan_splits(pl, s);
@@ -1290,37 +1406,42 @@ void plan_execute_mixed(BatchPlan& pl, cudaStream_t s) {
     launch_gemm(pl.ma_x, pl.mb_x, pl.xtiles.as<tc::Tile>(), pl.n_xtiles, pl.sh_x,
                 ExchangeBatchEpi{pl.exparams.as<ExParams>()}, pl.err.as<int>(), s);
   }
-  if (pl.terms.empty()) return;
-  if (pl.fused) {
-    Phase ph("mixed_direct_fused", s);
-    launch_direct(pl.ma_s, pl.mb_s, pl.stiles.as<tc::Tile>(), pl.n_stiles, pl.sh_g,
-                  pl.s2terms.as<tc::S2Term>(), pl.err.as<int>(), s);
-    return;
-  }
-  {
-    Phase ph("mixed_stage1_gemm", s);
-    launch_gemm(pl.ma_s, pl.mb_s, pl.stiles.as<tc::Tile>(), pl.n_stiles, pl.sh_g,
-                TEpiMulti{pl.touts.as<TOut>()}, pl.err.as<int>(), s);
-  }
-  bool any_cuda_core = false;
-  for (const BatchPlan::Term& t : pl.terms) any_cuda_core = any_cuda_core || !t.tc2;
-  if (any_cuda_core) {
-    Phase ph("mixed_stage2", s);
-    for (BatchPlan::Term& t : pl.terms) {
-      if (t.tc2) continue;
-      Phase pt(t.s2.mode == S2_RA ? "mixed_stage2_wra" : "mixed_stage2_wrr", s);
-      launch_stage2(t.s2, (int)pl.probs[t.prob].slab_pairs(), s);
+  // every block of A and B holds its exchange part before the direct terms
+  // subtract from it, unless those run over the blocks k <= k' alone
+  if (!pl.half && !pl.upper_probs.empty()) plan_complete(pl, false, s);
+  if (!pl.terms.empty()) {
+    if (pl.fused) {
+      Phase ph("mixed_direct_fused", s);
+      launch_direct(pl.ma_s, pl.mb_s, pl.stiles.as<tc::Tile>(), pl.n_stiles, pl.sh_g,
+                    pl.s2terms.as<tc::S2Term>(), pl.err.as<int>(), s);
+    } else {
+      {
+        Phase ph("mixed_stage1_gemm", s);
+        launch_gemm(pl.ma_s, pl.mb_s, pl.stiles.as<tc::Tile>(), pl.n_stiles, pl.sh_g,
+                    TEpiMulti{pl.touts.as<TOut>()}, pl.err.as<int>(), s);
+      }
+      bool any_cuda_core = false;
+      for (const BatchPlan::Term& t : pl.terms) any_cuda_core = any_cuda_core || !t.tc2;
+      if (any_cuda_core) {
+        Phase ph("mixed_stage2", s);
+        for (BatchPlan::Term& t : pl.terms) {
+          if (t.tc2) continue;
+          Phase pt(t.s2.mode == S2_RA ? "mixed_stage2_wra" : "mixed_stage2_wrr", s);
+          launch_stage2(t.s2, t.nact, s);
+        }
+      }
+      if (pl.n_s2tiles || pl.n_s2tiles_t) {
+        Phase ph("mixed_stage2_tc", s);
+        if (pl.n_s2tiles)
+          launch_gemm(pl.ma_2, pl.mb_2, pl.s2tiles.as<tc::Tile>(), pl.n_s2tiles, pl.sh_2,
+                      S2TcEpi{pl.s2params.as<S2TcParams>()}, pl.err.as<int>(), s);
+        if (pl.n_s2tiles_t)
+          launch_gemm(pl.ma_2t, pl.mb_2t, pl.s2tiles_t.as<tc::Tile>(), pl.n_s2tiles_t, pl.sh_2,
+                      S2TcEpi{pl.s2params.as<S2TcParams>()}, pl.err.as<int>(), s);
+      }
     }
   }
-  if (pl.n_s2tiles || pl.n_s2tiles_t) {
-    Phase ph("mixed_stage2_tc", s);
-    if (pl.n_s2tiles)
-      launch_gemm(pl.ma_2, pl.mb_2, pl.s2tiles.as<tc::Tile>(), pl.n_s2tiles, pl.sh_2,
-                  S2TcEpi{pl.s2params.as<S2TcParams>()}, pl.err.as<int>(), s);
-    if (pl.n_s2tiles_t)
-      launch_gemm(pl.ma_2t, pl.mb_2t, pl.s2tiles_t.as<tc::Tile>(), pl.n_s2tiles_t, pl.sh_2,
-                  S2TcEpi{pl.s2params.as<S2TcParams>()}, pl.err.as<int>(), s);
-  }
+  if (pl.half) plan_complete(pl, true, s);
 }
 
 void plan_set_tiles(BatchPlan& pl, int nt) {
@@ -1330,7 +1451,8 @@ void plan_set_tiles(BatchPlan& pl, int nt) {
   std::vector<tc::Tile> st = stage1_tiles(pl, nt);
   pl.n_stiles = (int)st.size();
   pl.stiles = upload_mem(st);
-  pl.mb_s = make_plane_map(pl.wsplit.as<__nv_bfloat16>(), pl.Kp, (int)pl.w_rows, pl.planes, nt);
+  pl.mb_s = make_plane_map(pl.wsplit.as<__nv_bfloat16>(), pl.Kp, (int)pl.w_rows,
+                           tc::b_planes(pl.pieces), nt);
 }
 
 // time the stage-1 GEMM at each candidate tile width and keep the fastest
@@ -1416,6 +1538,11 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
   pl->precision = precision;
   pl->probs = std::move(probs);
   if (precision == BSE_PREC_FP64) return pl.release();
+  pl->half = (flags & BSE_PLAN_HERMITIAN) != 0;
+  if (pl->half)
+    for (const Problem& pr : pl->probs)
+      if (pr.kn != pr.p.nk)
+        throw Error(BSE_ERR_UNSUPPORTED, "a Hermitian plan builds whole problems (no k-row slabs)");
   const int ng = pl->probs.front().p.ng;
   for (const Problem& pr : pl->probs)
     if (pr.p.ng != ng)
@@ -1426,6 +1553,7 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
   pl->Kp = round_up(ng, tc::BK);
   pl->ng_pad = round_up(ng, 32);
   pl->err = DevMem(sizeof(int));
+  BSE_CUDA(cudaMemsetAsync(pl->err.ptr, 0, sizeof(int), s));
 
   // exchange operands of all problems, stacked
   std::vector<tc::Tile> xt;
@@ -1449,27 +1577,33 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
   for (size_t i = 0; i < pl->probs.size(); ++i) {
     const Problem& pr = pl->probs[i];
     const bse_problem& p = pr.p;
-    const int n = (int)pr.n;
-    // a k-row slab computes its own rows of V for every column (no mirror)
-    const int tri = tri_all && pr.kn == p.nk;
+    const int n = (int)pr.n, nb = p.nv * p.nc;
+    // whole problems with enough tiles: the blocks k <= k' only, the rest
+    // completed from the mirrors; a k-row slab computes its own rows of V
+    // for every column
+    const int upper = tri_all && pr.kn == p.nk;
+    if (upper) pl->upper_probs.push_back((int)i);
     const int r0 = (int)pr.row0(), r1 = (int)(pr.row0() + pr.rows());
     pl->x_row0.push_back(pl->x_rows);
     for (int m0 = r0; m0 < r1; m0 += tc::BM)
-      for (int n0 = 0; n0 < n && (!tri || n0 < m0 + tc::BM); n0 += pl->nt_x)
+      for (int n0 = 0; n0 < n; n0 += pl->nt_x) {
+        if (upper && m0 / nb > (std::min(n0 + pl->nt_x, n) - 1) / nb) continue;
         xt.push_back({(int)(pl->x_rows + m0), std::min(tc::BM, r1 - m0), (int)(pl->x_rows + n0), n0,
                       std::min(pl->nt_x, n - n0), m0, (int)i});
+      }
     xp.push_back({reinterpret_cast<double2*>(p.A), p.coupling ? reinterpret_cast<double2*>(p.B) : nullptr,
-                  p.ld, (float)(2.0 * p.gamma_x * pr.kappa), p.e_v, p.e_c, p.nv, p.nc, tri});
+                  p.ld, (float)(2.0 * p.gamma_x * pr.kappa), p.e_v, p.e_c, p.nv, p.nc, upper});
     pl->x_rows += n;
   }
   pl->xa = DevMem((size_t)pl->planes * pl->x_rows * pl->Kp * 2);
-  pl->xb = DevMem((size_t)pl->planes * pl->x_rows * pl->Kp * 2);
+  pl->xb = DevMem((size_t)tc::b_planes(pl->pieces) * pl->x_rows * pl->Kp * 2);
   pl->n_xtiles = (int)xt.size();
   pl->xtiles = upload_mem(xt);
   pl->exparams = upload_mem(xp);
   pl->sh_x = make_shape(pl->nt_x, pl->Kp, pl->pieces);
   pl->ma_x = make_plane_map(pl->xa.as<__nv_bfloat16>(), pl->Kp, (int)pl->x_rows, pl->planes, tc::BM);
-  pl->mb_x = make_plane_map(pl->xb.as<__nv_bfloat16>(), pl->Kp, (int)pl->x_rows, pl->planes, pl->nt_x);
+  pl->mb_x = make_plane_map(pl->xb.as<__nv_bfloat16>(), pl->Kp, (int)pl->x_rows,
+                            tc::b_planes(pl->pieces), pl->nt_x);
 
   // direct terms of all problems, stacked
   for (size_t i = 0; i < pl->probs.size(); ++i) {
@@ -1510,14 +1644,27 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
         a.out = reinterpret_cast<double2*>(p.B);
       }
       a.rows_t = t.rows_side;
+      // the pairs built: every (k, k') of the slab, or k <= k' in a Hermitian
+      // plan (the blocks k > k' are the conjugate transposes, Eq. Hetr)
+      const std::vector<int32_t> q_all(t.qh);
+      t.qh.clear();
+      for (int pp = 0; pp < npair; ++pp) {
+        const int k = pr.kb + pp / p.nk, kp = pp % p.nk;
+        if (pl->half && k > kp) continue;
+        t.act_h.push_back(pp);
+        t.qh.push_back(q_all[pp]);
+      }
+      t.nact = (int)t.act_h.size();
       std::vector<int> perm, gstart;
-      group_pairs(t.qh, p.nq_w, perm, gstart);
-      std::vector<int> slot(npair);
-      for (int j = 0; j < npair; ++j) slot[perm[j]] = j;
+      group_pairs(t.qh, p.nq_w, perm, gstart);   // slot -> index into act_h
+      for (int& x : perm) x = t.act_h[x];         // slot -> pair
+      t.slot_h.assign(npair, -1);
+      for (int j = 0; j < t.nact; ++j) t.slot_h[perm[j]] = j;
       t.perm = upload_mem(perm);
-      t.slot = upload_mem(slot);
+      t.slot = upload_mem(t.slot_h);
+      t.act = upload_mem(t.act_h);
       t.a_row0 = pl->a_rows;
-      pl->a_rows += (int64_t)npair * t.rows_side;
+      pl->a_rows += (int64_t)t.nact * t.rows_side;
       if (term == 1 && !pl->terms.empty() && pl->terms.back().prob == (int)i &&
           !pl->terms.back().w_conj_transpose) {
         // W^ra uses W(q) as stored, like a W^rr term that applies it to the
@@ -1529,6 +1676,7 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
         pl->w_rows += (int64_t)p.nq_w * pl->ng_pad;
       }
       a.slot_of_pair = t.slot.as<int>();
+      a.pair_of = pl->half ? t.act.as<int>() : nullptr;
       a.ng = ng;
       a.nk = p.nk;
       a.k_begin = pr.kb;
@@ -1546,7 +1694,7 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
     // (the fused epilogue contracts whole-K tiles: no K segments)
     pl->fused = (flags & BSE_PLAN_UNFUSED) == 0 && ksegs_for(pl->Kp) == 1;
     for (const BatchPlan::Term& t : pl->terms) pl->fused = pl->fused && fused_fits(t.s2);
-    pl->wsplit = DevMem((size_t)pl->planes * pl->w_rows * pl->Kp * 2);
+    pl->wsplit = DevMem((size_t)tc::b_planes(pl->pieces) * pl->w_rows * pl->Kp * 2);
     pl->asplit = DevMem((size_t)pl->planes * pl->a_rows * pl->Kp * 2);
     if (pl->fused) {
       // the pair side of every term as a 2-D FP64 tensor [pairs * rows_x][2 ng],
@@ -1610,14 +1758,12 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
                             pl->a_rows, pl->Kp, pl->pieces, t.s2.conj_t});
       }
       if (any_tc2) {
-        // columns of T past NG are never written: zero once
-        const size_t tp_bytes = (size_t)pl->planes * pl->a_rows * pl->Kp * 2;
-        pl->tplanes = DevMem(tp_bytes);
-        BSE_CUDA(cudaMemsetAsync(pl->tplanes.ptr, 0, tp_bytes, s));
-        for (size_t ti = 0; ti < pl->terms.size(); ++ti)
-          if (pl->terms[ti].tc2) outs[ti].planes = pl->tplanes.as<__nv_bfloat16>();
-        // pair sides in pair order, and the tiles of every pair block, oriented
-        // so that the tile rows run over c fastest (see S2TcEpi)
+        // Each term's second contraction is one tensor-core GEMM per pair block,
+        // oriented so that the tile rows run over c fastest (see S2TcEpi): T
+        // rows as the A operand (W^rr with T on (c, c')) or as the B operand.
+        // The A operand is stored in 2P planes, the B operand in 3P (see
+        // tc_gemm.cuh), so T and the other pair side go to the arrays of
+        // their role: tA / x2B for the first orientation, x2A / tB for the other.
         std::vector<S2TcParams> prm;
         std::vector<tc::Tile> tiles, tiles_t;
         int max_cols = 0;
@@ -1628,6 +1774,33 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
           t.side_nb = a.mode == S2_RR_CC ? a.nc : 0;
           t.x_nb = a.mode == S2_RR_VV ? a.nc : 0;        // X rows (c, c') -> (c', c)
           max_cols = std::max(max_cols, t.rows_t_side ? a.rows_x : a.rows_t);
+          int64_t& trows = t.rows_t_side ? pl->ta_rows : pl->tb_rows;
+          int64_t& xrows = t.rows_t_side ? pl->x2b_rows : pl->x2a_rows;
+          t.t_row0 = trows;
+          trows += (int64_t)t.nact * a.rows_t;
+          t.x2_row0 = xrows;
+          xrows += (int64_t)t.nact * a.rows_x;
+        }
+        if (std::max({pl->ta_rows, pl->tb_rows, pl->x2a_rows, pl->x2b_rows}) > INT32_MAX)
+          throw Error(BSE_ERR_UNSUPPORTED, "tensor-core stage-2 rows exceed 2^31");
+        const int ap = tc::a_planes(pl->pieces), bp = tc::b_planes(pl->pieces);
+        // columns of T past NG are never written: zero once
+        const size_t ta_bytes = (size_t)ap * pl->ta_rows * pl->Kp * 2;
+        const size_t tb_bytes = (size_t)bp * pl->tb_rows * pl->Kp * 2;
+        pl->ta = DevMem(ta_bytes);
+        pl->tb = DevMem(tb_bytes);
+        if (ta_bytes) BSE_CUDA(cudaMemsetAsync(pl->ta.ptr, 0, ta_bytes, s));
+        if (tb_bytes) BSE_CUDA(cudaMemsetAsync(pl->tb.ptr, 0, tb_bytes, s));
+        pl->x2a = DevMem((size_t)ap * pl->x2a_rows * pl->Kp * 2);
+        pl->x2b = DevMem((size_t)bp * pl->x2b_rows * pl->Kp * 2);
+        for (size_t ti = 0; ti < pl->terms.size(); ++ti) {
+          const BatchPlan::Term& t = pl->terms[ti];
+          if (!t.tc2) continue;
+          TOut& o = outs[ti];
+          o.planes = (t.rows_t_side ? pl->ta : pl->tb).as<__nv_bfloat16>();
+          o.plane_rows = t.rows_t_side ? pl->ta_rows : pl->tb_rows;
+          o.bneg = t.rows_t_side ? 0 : 1;
+          o.row_off = t.t_row0 - t.a_row0;
         }
         // stage 2 products feed A and B directly: K segments of at most 4 steps
         pl->nt2 = tile_cols(round_up(max_cols, 32), pl->Kp, 4, 4);
@@ -1658,18 +1831,16 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
           }
           prm.push_back(q);
           if (!t.tc2) continue;
-          const int npair = (int)pl->probs[t.prob].slab_pairs();
-          std::vector<int> xp(npair);
-          for (int pr = 0; pr < npair; ++pr)   // (k', k) of the whole array, k = k_begin + pr / nk
-            xp[pr] = a.x_transpose_pair ? (pr % a.nk) * a.nk + a.k_begin + pr / a.nk : pr;
+          std::vector<int> xp(t.nact);
+          for (int j = 0; j < t.nact; ++j) {   // (k', k) of the whole array, k = k_begin + pr / nk
+            const int pr = t.act_h[j];
+            xp[j] = a.x_transpose_pair ? (pr % a.nk) * a.nk + a.k_begin + pr / a.nk : pr;
+          }
           t.x2perm = upload_mem(xp);
-          t.x2_row0 = pl->x2_rows;
-          pl->x2_rows += (int64_t)npair * a.rows_x;
-          std::vector<int> slot(npair);
-          BSE_CUDA(cudaMemcpy(slot.data(), a.slot_of_pair, npair * sizeof(int), cudaMemcpyDeviceToHost));
-          for (int pr = 0; pr < npair; ++pr) {
-            const int64_t xr = t.x2_row0 + (int64_t)pr * a.rows_x;      // X rows of the pair
-            const int64_t tr = t.a_row0 + (int64_t)slot[pr] * a.rows_t;  // T rows of the pair
+          for (int j = 0; j < t.nact; ++j) {
+            const int pr = t.act_h[j];
+            const int64_t xr = t.x2_row0 + (int64_t)j * a.rows_x;            // X rows of the pair
+            const int64_t tr = t.t_row0 + (int64_t)t.slot_h[pr] * a.rows_t;  // T rows of the pair
             if (t.rows_t_side) {
               for (int m0 = 0; m0 < a.rows_t; m0 += tc::BM)
                 for (int n0 = 0; n0 < a.rows_x; n0 += pl->nt2)
@@ -1685,23 +1856,21 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
             }
           }
         }
-        if (pl->x2_rows > INT32_MAX)
-          throw Error(BSE_ERR_UNSUPPORTED, "tensor-core stage-2 rows exceed 2^31");
-        pl->x2split = DevMem((size_t)pl->planes * pl->x2_rows * pl->Kp * 2);
         pl->n_s2tiles = (int)tiles.size();
         pl->s2tiles = upload_mem(tiles);
         pl->n_s2tiles_t = (int)tiles_t.size();
         pl->s2tiles_t = upload_mem(tiles_t);
         pl->s2params = upload_mem(prm);
         pl->sh_2 = make_shape(pl->nt2, pl->Kp, pl->pieces, 4, 4);
-        pl->ma_2 = make_plane_map(pl->x2split.as<__nv_bfloat16>(), pl->Kp, (int)pl->x2_rows,
-                                  pl->planes, tc::BM);
-        pl->mb_2 = make_plane_map(pl->tplanes.as<__nv_bfloat16>(), pl->Kp, (int)pl->a_rows,
-                                  pl->planes, pl->nt2);
-        pl->ma_2t = make_plane_map(pl->tplanes.as<__nv_bfloat16>(), pl->Kp, (int)pl->a_rows,
-                                   pl->planes, tc::BM);
-        pl->mb_2t = make_plane_map(pl->x2split.as<__nv_bfloat16>(), pl->Kp, (int)pl->x2_rows,
-                                   pl->planes, pl->nt2);
+        if (pl->n_s2tiles) {
+          pl->ma_2 = make_plane_map(pl->x2a.as<__nv_bfloat16>(), pl->Kp, (int)pl->x2a_rows, ap, tc::BM);
+          pl->mb_2 = make_plane_map(pl->tb.as<__nv_bfloat16>(), pl->Kp, (int)pl->tb_rows, bp, pl->nt2);
+        }
+        if (pl->n_s2tiles_t) {
+          pl->ma_2t = make_plane_map(pl->ta.as<__nv_bfloat16>(), pl->Kp, (int)pl->ta_rows, ap, tc::BM);
+          pl->mb_2t = make_plane_map(pl->x2b.as<__nv_bfloat16>(), pl->Kp, (int)pl->x2b_rows, bp,
+                                     pl->nt2);
+        }
       }
       pl->touts = upload_mem(outs);
     }
@@ -1734,6 +1903,7 @@ int plan_status(BatchPlan* pl, cudaStream_t s) {
   }
   int herr = 0;
   BSE_CUDA(cudaMemcpyAsync(&herr, pl->err.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+  BSE_CUDA(cudaMemsetAsync(pl->err.ptr, 0, sizeof(int), s));
   BSE_CUDA(cudaStreamSynchronize(s));
   return herr ? BSE_ERR_TIMEOUT : BSE_OK;
 }
@@ -1741,6 +1911,13 @@ int plan_status(BatchPlan* pl, cudaStream_t s) {
 int plan_tile_cols(const BatchPlan* pl) { return pl->nt_g; }
 
 int plan_fused(const BatchPlan* pl) { return pl->fused ? 1 : 0; }
+
+void plan_set_wait(BatchPlan* pl, double seconds) {
+  int khz = 0;
+  BSE_CUDA(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, pl->device));
+  const double cycles = seconds * 1e3 * (khz > 0 ? khz : 2000000);
+  pl->wait = std::max<long long>(1, (long long)cycles);
+}
 
 void plan_destroy(BatchPlan* pl) { delete pl; }
 
@@ -1757,7 +1934,7 @@ constexpr size_t kPlanCache = 4;
 
 struct CachedPlan {
   std::vector<uint64_t> key;
-  std::unique_ptr<BatchPlan> plan;
+  std::shared_ptr<BatchPlan> plan;   // shared with the callers using it (eviction-safe)
 };
 std::mutex g_cache_mutex;
 std::vector<CachedPlan> g_cache;   // most recent last
@@ -1805,7 +1982,7 @@ void build_mixed_batch(const std::vector<Problem>& probs, int precision, cudaStr
     for (const Problem& pr : probs)
       if (pr.p.ng == ng) group.push_back(pr);
     const std::vector<uint64_t> key = plan_key(group, precision);
-    BatchPlan* plan = nullptr;
+    std::shared_ptr<BatchPlan> plan;
     {
       std::lock_guard<std::mutex> lock(g_cache_mutex);
       for (size_t i = 0; i < g_cache.size(); ++i)
@@ -1813,19 +1990,22 @@ void build_mixed_batch(const std::vector<Problem>& probs, int precision, cudaStr
           CachedPlan c = std::move(g_cache[i]);
           g_cache.erase(g_cache.begin() + i);
           g_cache.push_back(std::move(c));
-          plan = g_cache.back().plan.get();
+          plan = g_cache.back().plan;
           break;
         }
     }
     if (!plan) {
-      std::unique_ptr<BatchPlan> created(plan_create(group, precision, 0, s));
+      std::shared_ptr<BatchPlan> created(plan_create(group, precision, 0, s));
       std::lock_guard<std::mutex> lock(g_cache_mutex);
       if (g_cache.size() >= kPlanCache) g_cache.erase(g_cache.begin());
-      g_cache.push_back(CachedPlan{key, std::move(created)});
-      plan = g_cache.back().plan.get();
+      g_cache.push_back(CachedPlan{key, created});
+      plan = created;
     }
-    plan_execute(plan, s);
-    if (plan_status(plan, s) != BSE_OK)
+    // a cached plan's scratch and status word serve one build at a time:
+    // callers on other host threads (or streams) wait for the one using it
+    std::lock_guard<std::mutex> use(plan->use_mutex);
+    plan_execute(plan.get(), s);
+    if (plan_status(plan.get(), s) != BSE_OK)
       throw Error(BSE_ERR_TIMEOUT, "tensor-core GEMM: a bounded pipeline wait expired");
   }
 }
@@ -1898,8 +2078,9 @@ TcMatvec* tc_matvec_create(int n, const bse_c128* A, const bse_c128* B, int64_t 
   const size_t mat_bytes = (size_t)m->planes * n * m->Kp * 2;
   m->ap = DevMem(mat_bytes);
   if (B) m->bp = DevMem(mat_bytes);
-  m->vp = DevMem((size_t)m->planes * m->kmax_rows * m->Kp * 2);
-  BSE_CUDA(cudaMemsetAsync(m->vp.ptr, 0, (size_t)m->planes * m->kmax_rows * m->Kp * 2, s));
+  const size_t v_bytes = (size_t)tc::b_planes(m->pieces) * m->kmax_rows * m->Kp * 2;
+  m->vp = DevMem(v_bytes);
+  BSE_CUDA(cudaMemsetAsync(m->vp.ptr, 0, v_bytes, s));
   m->tiles = DevMem((size_t)m->max_tiles * sizeof(tc::Tile));
   m->err = DevMem(sizeof(int));
   BSE_CUDA(cudaMemsetAsync(m->err.ptr, 0, sizeof(int), s));
@@ -1913,7 +2094,8 @@ TcMatvec* tc_matvec_create(int n, const bse_c128* A, const bse_c128* B, int64_t 
   }
   m->ma_a = make_plane_map(m->ap.as<__nv_bfloat16>(), m->Kp, n, m->planes, tc::BM);
   if (B) m->ma_b = make_plane_map(m->bp.as<__nv_bfloat16>(), m->Kp, n, m->planes, tc::BM);
-  m->mb_v = make_plane_map(m->vp.as<__nv_bfloat16>(), m->Kp, m->kmax_rows, m->planes, m->nt);
+  m->mb_v = make_plane_map(m->vp.as<__nv_bfloat16>(), m->Kp, m->kmax_rows,
+                           tc::b_planes(m->pieces), m->nt);
   return m.release();
 }
 
@@ -1923,6 +2105,7 @@ void tc_matvec_apply(TcMatvec* m, const bse_c128* V, int k, bse_c128* AV, bse_c1
   if (k > m->kmax) throw Error(BSE_ERR_UNSUPPORTED, "tensor-core matvec block wider than planned");
   SplitArgs sv{reinterpret_cast<const double2*>(V), SPLIT_DENSE, nullptr, 0, 0, m->n, m->Kp, k,
                m->pieces, 0, nullptr, m->vp.as<__nv_bfloat16>(), m->kmax_rows, 0};
+  sv.bneg = 1;   // the B operand of the matvec GEMMs
   launch_split(sv, s);
   std::vector<tc::Tile> tl;
   for (int m0 = 0; m0 < m->n; m0 += tc::BM)

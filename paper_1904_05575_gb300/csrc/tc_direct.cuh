@@ -61,7 +61,7 @@ struct S2Term {
 };
 
 __host__ __device__ inline uint32_t s2_extra_bytes(int stages) {
-  return S2_XSLOTS * S2_RAW_BYTES + 2 * S2_XF_BYTES + (2 * stages + 4 + 2 * S2_XSLOTS) * 8 + 16;
+  return S2_XSLOTS * S2_RAW_BYTES + 2 * S2_XF_BYTES + (2 * stages + 5 + 2 * S2_XSLOTS) * 8 + 16;
 }
 __host__ inline size_t s2_smem_bytes(const GemmShape& s) {
   return 1024 + (size_t)s.stages * stage_bytes(s) + s2_extra_bytes(s.stages);
@@ -212,12 +212,13 @@ __device__ __forceinline__ bool direct_unit(const EpiCtx& cx, EpiState& st, int 
     const int buf = st.local & 1;
     const int use = st.local >> 1;
     int okt = 0;
-    if (cx.lane == 0) okt = mbar_wait(&cx.pp.tmem_full[buf], use & 1, cx.abort_flag, cx.err) ? 1 : 0;
+    if (cx.lane == 0)
+      okt = mbar_wait(&cx.pp.tmem_full[buf], use & 1, cx.abort_flag, cx.err, cx.sh.wait) ? 1 : 0;
     okt = __shfl_sync(0xffffffffu, okt, 0);
     const uint32_t lane_base =
         cx.tmem_base + (uint32_t)buf * 4u * nt + ((uint32_t)(cx.quarter * 32) << 16);
     for (int c = 0; c < tl.n_valid; c += S2_GB) {
-      const bool okx = okt && mbar_wait(&cx.xfull[st.xs], st.xph, cx.abort_flag, cx.err);
+      const bool okx = okt && mbar_wait(&cx.xfull[st.xs], st.xph, cx.abort_flag, cx.err, cx.sh.wait);
       const int g0 = tl.n0 + c;
       uint8_t* xfb = cx.xf + (size_t)st.xb * S2_XF_BYTES;
       if (okx) {   // complex128 -> FP32 (Re, -Im), each element once
@@ -343,7 +344,7 @@ gemm_split_bf16_direct(const __grid_constant__ CUtensorMap tmA,
   pp.smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   pp.sbytes = stage_bytes(sh);
-  pp.a_bytes = 2u * sh.pieces * a_plane_bytes();
+  pp.a_bytes = (uint32_t)a_planes(sh.pieces) * a_plane_bytes();
   uint8_t* xraw = pp.smem + (size_t)sh.stages * pp.sbytes;   // [S2_XSLOTS][S2_RAW_BYTES]
   uint8_t* xf = xraw + S2_XSLOTS * S2_RAW_BYTES;              // [2][S2_XF_BYTES]
   pp.full = reinterpret_cast<uint64_t*>(xf + 2 * S2_XF_BYTES);
@@ -352,7 +353,8 @@ gemm_split_bf16_direct(const __grid_constant__ CUtensorMap tmA,
   pp.tmem_empty = pp.tmem_full + 2;
   uint64_t* xfull = pp.tmem_empty + 2;
   uint64_t* xempty = xfull + S2_XSLOTS;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(xempty + S2_XSLOTS);
+  pp.drain = xempty + S2_XSLOTS;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(pp.drain + 1);
   __shared__ volatile int abort_flag;
 
   const int warp = threadIdx.x >> 5;
@@ -371,6 +373,7 @@ gemm_split_bf16_direct(const __grid_constant__ CUtensorMap tmA,
       mbar_init(&xfull[b], 1);
       mbar_init(&xempty[b], 1);
     }
+    mbar_init(pp.drain, 1);
     abort_flag = 0;
     fence_barrier_init();
   }
@@ -419,7 +422,7 @@ gemm_split_bf16_direct(const __grid_constant__ CUtensorMap tmA,
         const Tile tl = tiles[t];
         for (int g0 = tl.n0; g0 < tl.n0 + tl.n_valid; g0 += S2_GB) {
           int w = 1;
-          if (lane == 0) w = mbar_wait(&xempty[xs], xph ^ 1, &abort_flag, err) ? 1 : 0;
+          if (lane == 0) w = mbar_wait(&xempty[xs], xph ^ 1, &abort_flag, err, sh.wait) ? 1 : 0;
           w = __shfl_sync(0xffffffffu, w, 0);
           if (!w) {
             ok = false;

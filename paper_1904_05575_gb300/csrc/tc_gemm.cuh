@@ -2,13 +2,20 @@
 //
 //   C[m][n] = sum_k A[m][k] * B[n][k]      (complex, FP32 accumulation)
 //
-// Both operands are stored pre-split as BF16 planes: plane (comp * P + piece)
-// holds piece `piece` of the real (comp 0) or imaginary (comp 1) part, so
-// x = x_0 + x_1 + x_2 with each x_i a BF16 number.  For each K step of 16 the
-// kernel issues, for every piece pair (i, j) with i + j < P, the four real
-// products of a complex multiply-add:
-//   re += A_re,i B_re,j - A_im,i B_im,j        im += A_re,i B_im,j + A_im,i B_re,j
-// (the minus sign through the instruction descriptor's negate-A bit).
+// Both operands are stored pre-split as BF16 planes, x = x_0 + x_1 + x_2 with
+// each x_i a BF16 number.  The A operand (tile rows) has 2P planes: plane
+// (comp * P + piece) holds piece `piece` of the real (comp 0) or imaginary
+// (comp 1) part.  The B operand (tile columns) has 3P planes, three per
+// piece: plane 3 j holds -Im_j, 3 j + 1 Re_j and 3 j + 2 Im_j, so that the
+// nt rows of Re_j followed by those of Im_j, and the nt rows of -Im_j
+// followed by those of Re_j, are each one operand of 2 nt rows.  For each K
+// step of 16 the kernel issues, for every piece pair (i, j) with i + j < P,
+// two MMAs of N = 2 nt into the accumulator pair [re | im] (nt columns each):
+//   [re | im] += A_re,i [B_re,j ; B_im,j]^T  +  A_im,i [-B_im,j ; B_re,j]^T
+// i.e. re += A_re,i B_re,j - A_im,i B_im,j and im += A_re,i B_im,j + A_im,i B_re,j,
+// half as many instructions of twice the width as four MMAs of N = nt, and a
+// third fewer shared-memory bytes per multiply-add (the A planes are read
+// once per pair of products instead of once per product).
 // The leading products (i = j = 0) go to a "main" pair of TMEM accumulators
 // and all correction products (i + j > 0, 2^-8 smaller) to a separate pair:
 // the tensor core's FP32 accumulation loses low bits at every accumulate
@@ -25,8 +32,12 @@
 //   warps 2-5  epilogue: tcgen05.ld of D_re / D_im, then the store functor
 // Shared-memory tiles are K-major with the 32-byte swizzle (one K step of 16
 // BF16 = 32 bytes per row), the layout TMA writes and the MMA descriptor
-// reads.  Every wait on an mbarrier is bounded by a clock budget; on expiry
-// the thread records BSE_TC_TIMEOUT in *err and every role winds down.
+// reads.  Every pipeline wait on an mbarrier is bounded by a clock budget
+// (GemmShape::wait, set at run time); on expiry the thread records
+// ERR_TIMEOUT in *err and every role winds down: the producer waits for the
+// copies it issued to land and the MMA issuer for the MMAs it issued to
+// complete (each with the fixed budget WAIT_CYCLES), then TMEM is released
+// and the kernel returns.
 #pragma once
 
 #include <cuda.h>
@@ -40,7 +51,8 @@ constexpr int BM = 128;             // tile rows (UMMA M)
 constexpr int BK = 16;              // K elements per stage (32 bytes of BF16)
 constexpr int NUM_THREADS = 192;    // 6 warps
 constexpr int ERR_TIMEOUT = 1;
-constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
+constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz: default budget, and the
+                                                  // bound of every wind-down wait
 
 struct Tile {
   int a_row0;    // first row in the A planes
@@ -91,14 +103,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Bounded wait for the phase with the given parity.  Returns false (after
-// recording the timeout) if the budget runs out or another role has already
-// failed.
+// recording the timeout) if `budget` clock cycles pass or another role has
+// already failed.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                          int* err) {
+                                          int* err, long long budget) {
   long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (*abort_flag) return false;
-    if (clock64() - t0 > WAIT_CYCLES) {
+    if (clock64() - t0 > budget) {
       *abort_flag = 1;
       atomicOr(err, ERR_TIMEOUT);
       return false;
@@ -198,12 +210,17 @@ struct GemmShape {    // stages <= 8
   uint32_t tmem_cols;
   int group = 1;   // consecutive tiles a CTA takes as one work unit
   int ksegs = 1;   // K segments per tile (> 1 needs nt <= 64 and acc_bufs == 2)
+  long long wait = WAIT_CYCLES;   // clock-cycle budget of each pipeline wait
 };
 
 __host__ __device__ inline uint32_t a_plane_bytes() { return BM * BK * 2; }
 __host__ __device__ inline uint32_t b_plane_bytes(int nt) { return (uint32_t)nt * BK * 2; }
+// planes of each operand: A 2P (Re, Im), B 3P (-Im, Re, Im)
+__host__ __device__ inline int a_planes(int pieces) { return 2 * pieces; }
+__host__ __device__ inline int b_planes(int pieces) { return 3 * pieces; }
 __host__ __device__ inline uint32_t stage_bytes(const GemmShape& s) {
-  return 2u * s.pieces * (a_plane_bytes() + b_plane_bytes(s.nt));
+  return (uint32_t)a_planes(s.pieces) * a_plane_bytes() +
+         (uint32_t)b_planes(s.pieces) * b_plane_bytes(s.nt);
 }
 __host__ inline size_t gemm_smem_bytes(const GemmShape& s) {
   return 1024 /* alignment slack */ + (size_t)s.stages * stage_bytes(s) + 64 * 8;   // + barriers
@@ -223,6 +240,7 @@ struct Pipe {
   uint64_t* empty;        // [stages] MMAs that read the stage completed
   uint64_t* tmem_full;    // [2] accumulator set ready for the epilogue
   uint64_t* tmem_empty;   // [2] epilogue done with the set (4 warp arrivals)
+  uint64_t* drain;        // [1] every MMA of this CTA completed (before TMEM is released)
   uint32_t sbytes, a_bytes;
 };
 
@@ -242,7 +260,7 @@ __device__ __forceinline__ void producer_role(const Pipe& pp, const CUtensorMap*
     for (int t = u * sh.group; t < min(ntiles, (u + 1) * sh.group) && ok; ++t) {
       const Tile tl = tiles[t];
       for (int kc = 0; kc < sh.kchunks; ++kc) {
-        if (!mbar_wait(&pp.empty[stage], phase ^ 1, abort_flag, err)) {
+        if (!mbar_wait(&pp.empty[stage], phase ^ 1, abort_flag, err, sh.wait)) {
           ok = false;
           break;
         }
@@ -279,7 +297,7 @@ __device__ __forceinline__ void mma_role(const Pipe& pp, uint32_t tmem_base, int
   int local = 0;
   const int nbuf = sh.acc_bufs;
   const uint32_t nt = (uint32_t)sh.nt;
-  const uint32_t id_pos = idesc_bf16(sh.nt, false), id_neg = idesc_bf16(sh.nt, true);
+  const uint32_t id2 = idesc_bf16(2 * sh.nt, false);   // N = 2 nt: [re | im] at once
   // descriptors of stage 0, plane 0; the start-address field (bytes >> 4, 14 bits)
   // is advanced by plain adds for other stages and planes (all below 256 KB)
   const uint32_t sa0 = smem_u32(pp.smem);
@@ -293,27 +311,25 @@ __device__ __forceinline__ void mma_role(const Pipe& pp, uint32_t tmem_base, int
      for (int k0 = 0; k0 < sh.kchunks; k0 += seg_len, ++local) {
       const int buf = nbuf == 2 ? (local & 1) : 0;
       const int use = nbuf == 2 ? (local >> 1) : local;    // earlier uses of this buffer
-      if (use > 0 && !mbar_wait(&pp.tmem_empty[buf], (use - 1) & 1, abort_flag, err)) {
+      if (use > 0 && !mbar_wait(&pp.tmem_empty[buf], (use - 1) & 1, abort_flag, err, sh.wait)) {
         ok = false;
         break;
       }
       tc_fence_after();
       const uint32_t base = tmem_base + (uint32_t)buf * 4u * nt;
-      const uint32_t m_re = base, m_im = base + nt;               // main
-      const uint32_t c_re = base + 2 * nt, c_im = base + 3 * nt;  // corrections
+      const uint32_t m_ri = base;            // main [re | im], nt columns each
+      const uint32_t c_ri = base + 2 * nt;   // corrections [re | im]
       for (int kc = k0; kc < min(sh.kchunks, k0 + seg_len); ++kc) {
-        if (!mbar_wait(&pp.full[stage], phase, abort_flag, err)) {
+        if (!mbar_wait(&pp.full[stage], phase, abort_flag, err, sh.wait)) {
           ok = false;
           break;
         }
         tc_fence_after();
         const uint64_t da = da0 + (uint64_t)stage * dstage, db = db0 + (uint64_t)stage * dstage;
         const uint32_t first = kc == k0 ? 0u : 1u;
-        // leading products
-        mma_bf16(m_re, da, db, id_pos, first);
-        mma_bf16(m_re, da + P * dpa, db + P * dpb, id_neg, 1);
-        mma_bf16(m_im, da, db + P * dpb, id_pos, first);
-        mma_bf16(m_im, da + P * dpa, db, id_pos, 1);
+        // leading products: A_re,0 [B_re,0; B_im,0] + A_im,0 [-B_im,0; B_re,0]
+        mma_bf16(m_ri, da, db + 1 * dpb, id2, first);
+        mma_bf16(m_ri, da + P * dpa, db, id2, 1);
         // correction products i + j in [1, P)
         uint32_t acc_c = first;
 #pragma unroll
@@ -321,12 +337,8 @@ __device__ __forceinline__ void mma_role(const Pipe& pp, uint32_t tmem_base, int
 #pragma unroll
           for (int j = 0; i + j < P; ++j) {
             if (i + j == 0) continue;
-            const uint64_t a_re = da + i * dpa, a_im = da + (P + i) * dpa;
-            const uint64_t b_re = db + j * dpb, b_im = db + (P + j) * dpb;
-            mma_bf16(c_re, a_re, b_re, id_pos, acc_c);
-            mma_bf16(c_re, a_im, b_im, id_neg, 1);
-            mma_bf16(c_im, a_re, b_im, id_pos, acc_c);
-            mma_bf16(c_im, a_im, b_re, id_pos, 1);
+            mma_bf16(c_ri, da + i * dpa, db + (3 * j + 1) * dpb, id2, acc_c);
+            mma_bf16(c_ri, da + (P + i) * dpa, db + (3 * j) * dpb, id2, 1);
             acc_c = 1;
           }
         }
@@ -340,6 +352,13 @@ __device__ __forceinline__ void mma_role(const Pipe& pp, uint32_t tmem_base, int
       mma_commit(&pp.tmem_full[buf]);
      }
     }
+  }
+  // every MMA issued above completes before the block releases TMEM (after a
+  // normal finish the epilogue has waited for them already; after an abort
+  // it has not)
+  mma_commit(pp.drain);
+  const long long t0 = clock64();
+  while (!mbar_try_wait(pp.drain, 0) && clock64() - t0 < WAIT_CYCLES) {
   }
 }
 
@@ -358,12 +377,13 @@ gemm_split_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
   pp.smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   pp.sbytes = stage_bytes(sh);
-  pp.a_bytes = 2u * sh.pieces * a_plane_bytes();
+  pp.a_bytes = (uint32_t)a_planes(sh.pieces) * a_plane_bytes();
   pp.full = reinterpret_cast<uint64_t*>(pp.smem + (size_t)sh.stages * pp.sbytes);
   pp.empty = pp.full + sh.stages;
   pp.tmem_full = pp.empty + sh.stages;
   pp.tmem_empty = pp.tmem_full + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(pp.tmem_empty + 2);
+  pp.drain = pp.tmem_empty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(pp.drain + 1);
   __shared__ volatile int abort_flag;
 
   const int warp = threadIdx.x >> 5;
@@ -379,6 +399,7 @@ gemm_split_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       mbar_init(&pp.tmem_full[b], 1);
       mbar_init(&pp.tmem_empty[b], 4);
     }
+    mbar_init(pp.drain, 1);
     abort_flag = 0;
     fence_barrier_init();
   }
@@ -405,7 +426,7 @@ gemm_split_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         const int buf = nbuf == 2 ? (local & 1) : 0;
         const int use = nbuf == 2 ? (local >> 1) : local;
         int ok = 0;
-        if (lane == 0) ok = mbar_wait(&pp.tmem_full[buf], use & 1, &abort_flag, err) ? 1 : 0;
+        if (lane == 0) ok = mbar_wait(&pp.tmem_full[buf], use & 1, &abort_flag, err, sh.wait) ? 1 : 0;
         ok = __shfl_sync(0xffffffffu, ok, 0);
         if (!ok) {
           alive = false;
@@ -425,7 +446,8 @@ gemm_split_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
               ++local;
               const int bs = local & 1, us = local >> 1;
               int oks = 0;
-              if (lane == 0) oks = mbar_wait(&pp.tmem_full[bs], us & 1, &abort_flag, err) ? 1 : 0;
+              if (lane == 0)
+                oks = mbar_wait(&pp.tmem_full[bs], us & 1, &abort_flag, err, sh.wait) ? 1 : 0;
               oks = __shfl_sync(0xffffffffu, oks, 0);
               if (!oks) {
                 alive = false;

@@ -57,6 +57,8 @@ def test_host_side_argument_errors(lib):
     assert lib2.bse_build_kernel(arr, 1, 0, None) == bse.BSE_ERR_ARG
     assert b"nk" in lib2.bse_last_error()
     assert lib2.bse_build_kernel(arr, 1, 99, None) == bse.BSE_ERR_ARG
+    # a plan's wait limit: NULL plan or a limit outside (0, 60] s
+    assert lib2.bse_plan_set_wait_limit(None, 1.0) == bse.BSE_ERR_ARG
     # a complex128 array that is not 16-byte aligned is refused before any launch
     q = bse.bse_problem(nk=1, nv=1, nc=1, ng=1, nq_w=1, omega_cell=1.0, ld=1, gamma_x=1.0,
                         gamma_c=0.0, coupling=0, e_v=0x1000, e_c=0x1000, m_x=0x1008,
