@@ -29,7 +29,14 @@
 // One CTA per SM, persistent over a list of 128-row tiles:
 //   warp 0     TMA producer: one 3-D box per operand per stage (all planes)
 //   warp 1     TMEM allocation and MMA issue (one elected thread)
-//   warps 2-5  epilogue: tcgen05.ld of D_re / D_im, then the store functor
+//   warps 2-9  epilogue: tcgen05.ld of D_re / D_im, then the store functor;
+//              two warps per TMEM lane quarter (a warp reaches the 32 lanes
+//              32 (warp % 4) ...), each taking every other 32-column chunk,
+//              so that the stores of one tile (FP64 read-modify-writes, split
+//              planes) run on twice as many warps and overlap the next tile's
+//              MMAs (timing variants showed the 4-warp epilogue bounding the
+//              launch: without MMAs or without operand copies the launches
+//              were only 6-20 % shorter)
 // Shared-memory tiles are K-major with the 32-byte swizzle (one K step of 16
 // BF16 = 32 bytes per row), the layout TMA writes and the MMA descriptor
 // reads.  Every pipeline wait on an mbarrier is bounded by a clock budget
@@ -49,7 +56,8 @@ namespace tc {
 
 constexpr int BM = 128;             // tile rows (UMMA M)
 constexpr int BK = 16;              // K elements per stage (32 bytes of BF16)
-constexpr int NUM_THREADS = 192;    // 6 warps
+constexpr int NUM_THREADS = 320;    // 10 warps: producer, MMA issuer, 8 epilogue
+constexpr int EPI_WARPS = 8;        // two per TMEM lane quarter, alternate 32-column chunks
 constexpr int ERR_TIMEOUT = 1;
 constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz: default budget, and the
                                                   // bound of every wind-down wait
@@ -239,7 +247,7 @@ struct Pipe {
   uint64_t* full;         // [stages] operand bytes landed
   uint64_t* empty;        // [stages] MMAs that read the stage completed
   uint64_t* tmem_full;    // [2] accumulator set ready for the epilogue
-  uint64_t* tmem_empty;   // [2] epilogue done with the set (4 warp arrivals)
+  uint64_t* tmem_empty;   // [2] epilogue done with the set (EPI_WARPS warp arrivals)
   uint64_t* drain;        // [1] every MMA of this CTA completed (before TMEM is released)
   uint32_t sbytes, a_bytes;
 };
@@ -397,7 +405,7 @@ gemm_split_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&pp.tmem_full[b], 1);
-      mbar_init(&pp.tmem_empty[b], 4);
+      mbar_init(&pp.tmem_empty[b], EPI_WARPS);
     }
     mbar_init(pp.drain, 1);
     abort_flag = 0;
@@ -414,15 +422,17 @@ gemm_split_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
   } else if (warp == 1) {
     if (lane == 0) mma_role<P>(pp, tmem_base, ntiles, sh, &abort_flag, err);
   } else {
-    // ---------------- epilogue (warps 2..5) ----------------
-    const int quarter = warp & 3;    // TMEM lanes this warp may access
+    // ---------------- epilogue (warps 2..9) ----------------
+    const int quarter = warp & 3;          // TMEM lanes this warp may access
+    const int half = (warp - 2) >> 2;      // chunks c0 = 32 (half + 2 i)
     const int row = quarter * 32 + lane;
     int local = 0;
     const int units = num_units(ntiles, sh.group);
     bool alive = true;
     for (int u = blockIdx.x; u < units && alive; u += gridDim.x) {
       for (int t = u * sh.group; t < min(ntiles, (u + 1) * sh.group); ++t, ++local) {
-        // one lane waits, the warp follows (the tcgen05.ld below is warp-collective)
+        // one lane waits, the warp follows (the tcgen05.ld below is warp-collective);
+        // a warp without a chunk still waits and arrives, keeping the count per phase
         const int buf = nbuf == 2 ? (local & 1) : 0;
         const int use = nbuf == 2 ? (local >> 1) : local;
         int ok = 0;
@@ -436,11 +446,13 @@ gemm_split_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         tc_fence_after();
         const Tile tl = tiles[t];
         if constexpr (SEG) {
-          // K segments: sum (main + correction) of each segment in FP32 registers
-          // (nt <= 64: two chunks of 32 columns), then one store
-          float run_re[64], run_im[64], a[32], b[32];
+          // K segments (nt <= 64: at most one chunk per warp): sum (main +
+          // correction) of each segment in FP32 registers, then one store
+          const int c0 = 32 * half;
+          const bool mine = c0 < sh.nt;
+          float run_re[32], run_im[32], a[32], b[32];
 #pragma unroll
-          for (int j = 0; j < 64; ++j) run_re[j] = run_im[j] = 0.f;
+          for (int j = 0; j < 32; ++j) run_re[j] = run_im[j] = 0.f;
           for (int sgm = 0; sgm < sh.ksegs; ++sgm) {
             if (sgm > 0) {   // the next segment's accumulator set
               ++local;
@@ -459,34 +471,28 @@ gemm_split_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             const int bs = local & 1;
             const uint32_t lb =
                 tmem_base + (uint32_t)bs * 4u * (uint32_t)sh.nt + ((uint32_t)(quarter * 32) << 16);
+            if (mine) {
+              tmem_ld32(lb + (uint32_t)c0, a);
+              tmem_ld32(lb + (uint32_t)(2 * sh.nt + c0), b);
 #pragma unroll
-            for (int ch = 0; ch < 2; ++ch) {
-              if (ch * 32 < sh.nt) {
-                tmem_ld32(lb + (uint32_t)(ch * 32), a);
-                tmem_ld32(lb + (uint32_t)(2 * sh.nt + ch * 32), b);
+              for (int j = 0; j < 32; ++j) run_re[j] += a[j] + b[j];
+              tmem_ld32(lb + (uint32_t)(sh.nt + c0), a);
+              tmem_ld32(lb + (uint32_t)(3 * sh.nt + c0), b);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) run_re[ch * 32 + j] += a[j] + b[j];
-                tmem_ld32(lb + (uint32_t)(sh.nt + ch * 32), a);
-                tmem_ld32(lb + (uint32_t)(3 * sh.nt + ch * 32), b);
-#pragma unroll
-                for (int j = 0; j < 32; ++j) run_im[ch * 32 + j] += a[j] + b[j];
-              }
+              for (int j = 0; j < 32; ++j) run_im[j] += a[j] + b[j];
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&pp.tmem_empty[bs]);
           }
           if (!alive) break;
-#pragma unroll
-          for (int ch = 0; ch < 2; ++ch)
-            if (ch * 32 < sh.nt && row < tl.m_valid && ch * 32 < tl.n_valid)
-              epi(tl, row, ch * 32, run_re + ch * 32, run_im + ch * 32);
+          if (mine && row < tl.m_valid && c0 < tl.n_valid) epi(tl, row, c0, run_re, run_im);
           continue;
         }
         float re[32], im[32], cr[32], ci[32];
         const uint32_t lane_base =
             tmem_base + (uint32_t)buf * 4u * (uint32_t)sh.nt + ((uint32_t)(quarter * 32) << 16);
-        for (int c0 = 0; c0 < sh.nt; c0 += 32) {
+        for (int c0 = 32 * half; c0 < sh.nt; c0 += 64) {
           tmem_ld32(lane_base + (uint32_t)c0, re);
           tmem_ld32(lane_base + (uint32_t)(sh.nt + c0), im);
           tmem_ld32(lane_base + (uint32_t)(2 * sh.nt + c0), cr);
