@@ -148,6 +148,52 @@ def reciprocal_vectors(ng: int, a: float = A_LAT_BOHR) -> np.ndarray:
         nmax += 2
 
 
+def reciprocal_coords(ng: int) -> np.ndarray:
+    """Integer coordinates [ng, 3] (in the reciprocal basis) of the vectors of
+    reciprocal_vectors(ng), same order."""
+    b = 2.0 * np.pi / A_LAT_BOHR * np.array([[-1, 1, 1], [1, -1, 1], [1, 1, -1]], float)
+    return np.rint(reciprocal_vectors(ng) @ np.linalg.inv(b)).astype(np.int64)
+
+
+def wavefunction_coefficients(grid: int, nv: int, nc: int, npw: int, seed: int = 20190411,
+                              decay: float = 1.0) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """Seeded plane-wave coefficients of nv valence and nc conduction Bloch
+    functions at every k of the grid^3 grid, over the basis of the first npw
+    reciprocal vectors (a closed shell, so G -> -G maps it onto itself):
+    returns (cv [nk, nv, npw], cc [nk, nc, npw], basis [npw, 3] integer
+    coordinates).  Complex normal coefficients damped by 1 / (1 + decay |G|^2),
+    orthonormal over the nv + nc bands of each k, with the time-reversal
+    relation C_{n,-k}(G) = conj(C_{n,k}(-G)) (phi_{n,-k} = phi_{n,k}^*); at
+    k = -k the functions are real (C(-G) = conj(C(G)))."""
+    nk = grid ** 3
+    basis = reciprocal_coords(npw)
+    g2 = (reciprocal_vectors(npw) ** 2).sum(1)
+    damp = 1.0 / (1.0 + decay * g2)
+    lut = {tuple(g): i for i, g in enumerate(basis)}
+    minus = np.array([lut[tuple(-g)] for g in basis])
+    _, _, neg = pair_maps(grid)
+    nb = nv + nc
+    coef = np.empty((nk, nb, npw), np.complex128)
+    done = np.zeros(nk, bool)
+    for k in range(nk):
+        if done[k]:
+            continue
+        z = _cnormal(_rng(seed, "coefficients", k), (nb, npw)) * damp
+        real_k = neg[k] == k
+        if real_k:   # C(-G) = conj(C(G)): a real function
+            z = 0.5 * (z + np.conj(z[:, minus]))
+        # Gram-Schmidt; for a real function the overlaps are real, so keep them real
+        for i in range(nb):
+            for j in range(i):
+                ov = np.vdot(z[j], z[i])
+                z[i] -= (ov.real if real_k else ov) * z[j]
+            z[i] /= np.linalg.norm(z[i])
+        coef[k] = z
+        coef[neg[k]] = np.conj(z[:, minus])
+        done[k] = done[neg[k]] = True
+    return coef[:, :nv], coef[:, nv:], basis
+
+
 def k_grid(n: int) -> np.ndarray:
     """Integer coordinates [nk, 3] of the Gamma-centred n^3 grid, k = (i*n + j)*n + l."""
     r = np.arange(n)

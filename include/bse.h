@@ -181,8 +181,16 @@ int bse_build_kernel(const bse_problem* probs, int32_t nprob, int32_t precision,
  * has at least two exchange tiles per SM, only its blocks k <= k' are
  * computed and the rest completed from the mirrors (with or without the
  * flag). */
+/*
+ * BSE_PLAN_FP64_DIAGONAL: after the split-precision build the diagonal of A
+ * (and B) is recomputed in FP64 and overwritten (Eqs. emat, vrrofM, wrrm,
+ * wrabar at alpha = alpha', the diagonal (k, k) pair blocks: W applied to the
+ * block's vectors by the FP64 GEMM kernel, the plane-wave sums reduced in
+ * FP64 by one warp per transition), stored real.  Costs 8 NG^2 (Nc + Nv Nc)
+ * FP64 flops per k row (the W^ra part dominates); scratch allocated at
+ * creation.  Ignored by BSE_PREC_FP64 plans. */
 enum { BSE_PLAN_AUTOTUNE = 1, BSE_PLAN_UNFUSED = 2, BSE_PLAN_CUDA_CORE_STAGE2 = 4,
-       BSE_PLAN_HERMITIAN = 8 };
+       BSE_PLAN_HERMITIAN = 8, BSE_PLAN_FP64_DIAGONAL = 16 };
 int bse_plan_create(const bse_problem* probs, int32_t nprob, int32_t precision, int32_t flags,
                     void** plan, void* cuda_stream);
 int bse_plan_execute(void* plan, void* cuda_stream);
@@ -288,12 +296,18 @@ int bse_spectrum_tensor(int32_t n, const bse_c128* Z, const bse_c128* L, int64_t
  * k + q (eV; every e_c_kq - e_v > 0), m [nk][nv][nc][ng] the pair elements
  * M_vc(k, q)(G), v [ng] = 4 pi / |G+q|^2 (>= 0, Hartree atomic units), w_out
  * [ng][ng] row-major, the layout of one q of bse_problem.w.  Device pointers;
- * m and w_out 16-byte aligned.  X on cuBLAS (ZGEMM), eps^-1 by cuSOLVER LU.
- * Syncs.  Errors: BSE_ERR_ARG (sizes, NULL, a non-positive gap), BSE_ERR_NOMEM,
- * BSE_ERR_CUDA (also a singular eps). */
+ * m and w_out 16-byte aligned.  precision (bse_precision) selects the
+ * arithmetic of the X contraction, on the library's own kernels:
+ * BSE_PREC_FP64 the FP64 GEMM kernel over ranges of at most 1,024
+ * transitions, BSE_PREC_BF16X6 / BF16X3 the tensor cores (the transitions
+ * split into BF16 pieces, FP32 accumulation over ranges of 512 transitions);
+ * the partial sums are added in FP64.  eps and w are formed in FP64, eps^-1
+ * by cuSOLVER LU.  Syncs.  Errors: BSE_ERR_ARG (sizes, NULL, a non-positive
+ * gap, unknown precision), BSE_ERR_NOMEM, BSE_ERR_CUDA (also a singular eps),
+ * BSE_ERR_TIMEOUT (a bounded wait of the tensor-core GEMM expired). */
 int bse_rpa_screening(int32_t nk, int32_t nv, int32_t nc, int32_t ng, double omega_cell,
                       const double* e_v, const double* e_c_kq, const bse_c128* m, const double* v,
-                      bse_c128* w_out, void* cuda_stream);
+                      int32_t precision, bse_c128* w_out, void* cuda_stream);
 
 /* Electron energy-loss function L(w) = -Im 1/eps_M(w) (Eq. Lofeps) and the
  * dynamical structure factor S(Q, w) = -(1/pi) v_G(q)^{-1} Im 1/eps_M(q, w)

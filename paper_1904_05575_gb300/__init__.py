@@ -22,6 +22,7 @@ BSE_PLAN_AUTOTUNE = 1
 BSE_PLAN_UNFUSED = 2
 BSE_PLAN_CUDA_CORE_STAGE2 = 4
 BSE_PLAN_HERMITIAN = 8
+BSE_PLAN_FP64_DIAGONAL = 16
 HARTREE_EV = 27.211386245988
 
 STATUS_NAMES = {0: "BSE_OK", -1: "BSE_ERR_ARG", -2: "BSE_ERR_CUDA", -3: "BSE_ERR_NOMEM",
@@ -93,7 +94,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.bse_lowest_excitons_from.argtypes = [i32, vp, vp, i64, i32, dbl, i32, i32, vp, i32, vp,
                                              i32, vp, vp, ctypes.POINTER(i32), vp]
     lib.bse_lowest_excitons_from.restype = ctypes.c_int
-    lib.bse_rpa_screening.argtypes = [i32, i32, i32, i32, dbl, vp, vp, vp, vp, vp, vp]
+    lib.bse_rpa_screening.argtypes = [i32, i32, i32, i32, dbl, vp, vp, vp, vp, i32, vp, vp]
     lib.bse_rpa_screening.restype = ctypes.c_int
     lib.bse_xpy.argtypes = [i32, i32, vp, vp, i64, vp, vp, vp]
     lib.bse_xpy.restype = ctypes.c_int
@@ -361,10 +362,12 @@ def exciton_bands(problems: Sequence[tuple], nev: int, tol_ev: float = 1e-4, max
     return np.stack(out), iters
 
 
-def bse_rpa_screening(e_v, e_c_kq, m, v, omega_cell: float, w_out, stream=None) -> None:
+def bse_rpa_screening(e_v, e_c_kq, m, v, omega_cell: float, w_out, stream=None,
+                      precision: int = BSE_PREC_FP64) -> None:
     """Static RPA screened interaction w = v eps^-1 for one q (include/bse.h):
     e_v [nk, nv], e_c_kq [nk, nc] float64, m [nk, nv, nc, ng] complex128,
-    v [ng] float64, w_out [ng, ng] complex128 (row-major), CUDA tensors."""
+    v [ng] float64, w_out [ng, ng] complex128 (row-major), CUDA tensors;
+    precision of the polarisability contraction (FP64 or a tensor-core split)."""
     import torch
     nk, nv, nc, ng = m.shape
     if tuple(e_v.shape) != (nk, nv) or tuple(e_c_kq.shape) != (nk, nc) or tuple(v.shape) != (ng,):
@@ -374,7 +377,8 @@ def bse_rpa_screening(e_v, e_c_kq, m, v, omega_cell: float, w_out, stream=None) 
     f64, c128 = torch.float64, torch.complex128
     _check(load().bse_rpa_screening(nk, nv, nc, ng, float(omega_cell), _ptr(e_v, f64, "e_v"),
                                     _ptr(e_c_kq, f64, "e_c_kq"), _ptr(m, c128, "m"),
-                                    _ptr(v, f64, "v"), _ptr(w_out, c128, "w_out"), _stream(stream)))
+                                    _ptr(v, f64, "v"), int(precision), _ptr(w_out, c128, "w_out"),
+                                    _stream(stream)))
 
 
 def bse_phase_timing(enable: bool) -> None:
@@ -554,14 +558,15 @@ class Plan:
 
     def __init__(self, problems: Sequence[bse_problem], precision: int = BSE_PREC_BF16X6,
                  autotune: bool = False, fused: bool = True, tc_stage2: bool = True,
-                 hermitian: bool = False, stream=None):
+                 hermitian: bool = False, fp64_diagonal: bool = False, stream=None):
         lib = load()
         self._problems = list(problems)
         arr = (bse_problem * len(self._problems))(*self._problems)
         h = ctypes.c_void_p()
         flags = ((BSE_PLAN_AUTOTUNE if autotune else 0) | (0 if fused else BSE_PLAN_UNFUSED)
                  | (0 if tc_stage2 else BSE_PLAN_CUDA_CORE_STAGE2)
-                 | (BSE_PLAN_HERMITIAN if hermitian else 0))
+                 | (BSE_PLAN_HERMITIAN if hermitian else 0)
+                 | (BSE_PLAN_FP64_DIAGONAL if fp64_diagonal else 0))
         _check(lib.bse_plan_create(arr, len(self._problems), int(precision), flags,
                                    ctypes.byref(h), _stream(stream)))
         self.handle = h

@@ -278,7 +278,7 @@ extern "C" int bse_plan_create(const bse_problem* probs, int32_t nprob, int32_t 
                       precision == BSE_PREC_BF16X3,
                   "unknown precision " + std::to_string(precision));
     BSE_CHECK_ARG((flags & ~(BSE_PLAN_AUTOTUNE | BSE_PLAN_UNFUSED | BSE_PLAN_CUDA_CORE_STAGE2 |
-                             BSE_PLAN_HERMITIAN)) == 0,
+                             BSE_PLAN_HERMITIAN | BSE_PLAN_FP64_DIAGONAL)) == 0,
                   "unknown plan flags");
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     keep_pool_memory();
@@ -366,9 +366,12 @@ extern "C" int bse_loss_function(int32_t n_omega, const bse_c128* eps, double v_
 
 extern "C" int bse_rpa_screening(int32_t nk, int32_t nv, int32_t nc, int32_t ng,
                                  double omega_cell, const double* e_v, const double* e_c_kq,
-                                 const bse_c128* m, const double* v, bse_c128* w_out,
-                                 void* cuda_stream) {
+                                 const bse_c128* m, const double* v, int32_t precision,
+                                 bse_c128* w_out, void* cuda_stream) {
   return guarded([&] {
+    BSE_CHECK_ARG(precision == BSE_PREC_FP64 || precision == BSE_PREC_BF16X6 ||
+                      precision == BSE_PREC_BF16X3,
+                  "unknown precision " + std::to_string(precision));
     BSE_CHECK_ARG(nk >= 1 && nv >= 1 && nc >= 1 && ng >= 1, "nk, nv, nc and ng must be >= 1");
     BSE_CHECK_ARG((int64_t)nk * nv * nc <= 2147483647LL, "nk*nv*nc is too large");
     BSE_CHECK_ARG(std::isfinite(omega_cell) && omega_cell > 0.0, "omega_cell must be > 0");
@@ -388,7 +391,8 @@ extern "C" int bse_rpa_screening(int32_t nk, int32_t nv, int32_t nc, int32_t ng,
                         "e_c_kq - e_v must be > 0 for every transition (k " + std::to_string(k) +
                             ", v " + std::to_string(a) + ", c " + std::to_string(b) + ")");
     keep_pool_memory();
-    rpa_screening_fp64(nk, nv, nc, ng, omega_cell, e_v, e_c_kq, m, v, w_out, s);
+    Phase ph("rpa_screening", s);
+    rpa_screening(nk, nv, nc, ng, omega_cell, e_v, e_c_kq, m, v, precision, w_out, s);
   });
 }
 

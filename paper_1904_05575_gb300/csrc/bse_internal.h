@@ -107,6 +107,12 @@ constexpr size_t kFp64StaticScratchBytes = (size_t)16 << 20;
 size_t fp64_static_scratch_need(const Problem& pr);
 void build_fp64_static(const Problem& pr, cudaStream_t stream);
 
+// Exact FP64 diagonal of A (and B) over the problem's rows (diag_fp64.cu):
+// overwrites A_aa, B_aa with the FP64 sums; workspace of diag_fp64_workspace
+// bytes (device).
+size_t diag_fp64_workspace(const Problem& pr);
+void diag_fp64(const Problem& pr, bse_c128* workspace, cudaStream_t stream);
+
 // Split-precision tensor-core build (tcgen05) of several problems through a
 // cached batched plan.  Writes every A (and B) completely.  Syncs.
 void build_mixed_batch(const std::vector<Problem>& probs, int precision, cudaStream_t stream);
@@ -157,9 +163,13 @@ void spectrum_tensor_fp64(int n, const bse_c128* Z, const bse_c128* L, int64_t l
                           cudaStream_t s);
 void loss_fp64(int n_omega, const bse_c128* eps, double v_inv, double* loss_out, double* sqw_out,
                cudaStream_t s);
-void rpa_screening_fp64(int nk, int nv, int nc, int ng, double omega_cell, const double* e_v,
-                        const double* e_c_kq, const bse_c128* m, const double* v, bse_c128* w_out,
-                        cudaStream_t s);
+void rpa_screening(int nk, int nv, int nc, int ng, double omega_cell, const double* e_v,
+                   const double* e_c_kq, const bse_c128* m, const double* v, int precision,
+                   bse_c128* w_out, cudaStream_t s);
+// X[G][G'] = sum_a conj(m_a(G)) m_a(G') / (e_c - e_v) (row-major, FP64 result) on the
+// tensor cores in the split precision `precision` (build_mixed.cu)
+void rpa_x_mixed(int nk, int nv, int nc, int ng, const double* e_v, const double* e_c_kq,
+                 const bse_c128* m, int precision, double2* x_out, cudaStream_t s);
 void spectrum_fp64(int n, bse_c128* S, const bse_c128* L, int64_t ld, const bse_c128* rho,
                    double c_q, double vc, int n_omega, const double* omega, double delta,
                    double* E_out, double* osc_out, bse_c128* eps_out, cudaStream_t stream);

@@ -76,6 +76,7 @@ struct SplitArgs {
   int64_t src_ld = 0;       // SPLIT_DENSE: source row stride (0: K)
   int zero_diag = 0;        // SPLIT_DENSE: element k == row stored as zero
   int bneg = 0;             // B-operand layout: 3P planes (-Im, Re, Im) per piece
+  int tdense = 0;           // SPLIT_DENSE read transposed: row r, element k at src[k * src_ld + r]
 };
 
 // One thread per (output row, 8 consecutive k): every element is read as two
@@ -89,8 +90,14 @@ __global__ void __launch_bounds__(256) k_split(SplitArgs a) {
   const uint4* src = reinterpret_cast<const uint4*>(a.src);   // one complex128 per uint4
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int row = (int)(i / kg), k0 = (int)(i % kg) * 8;
+    int row = (int)(i / kg), k0 = (int)(i % kg) * 8;
     int64_t off = (int64_t)row * (a.src_ld ? a.src_ld : a.K), kstride = 1;
+    if (a.tdense) {   // consecutive threads on consecutive rows: coalesced reads
+      row = (int)(i % a.rows);
+      k0 = (int)(i / a.rows) * 8;
+      off = row;
+      kstride = a.src_ld;
+    }
     if (a.mode == SPLIT_PAIRS) {
       const int slot = row / a.rows_per;
       int j = row % a.rows_per;
@@ -1264,6 +1271,8 @@ struct BatchPlan {
   // only, the blocks k > k' of A and B completed from their mirrors
   bool half = false;
   std::vector<int> upper_probs;   // problems whose exchange wrote the blocks k <= k' only
+  // BSE_PLAN_FP64_DIAGONAL: the diagonal of A and B recomputed in FP64 after the build
+  std::vector<DevMem> diag_ws;
   // exchange
   int64_t x_rows = 0;
   std::vector<int64_t> x_row0;
@@ -1442,6 +1451,11 @@ void plan_execute_mixed(BatchPlan& pl, cudaStream_t s) {
     }
   }
   if (pl.half) plan_complete(pl, true, s);
+  if (!pl.diag_ws.empty()) {
+    Phase ph("fp64_diagonal", s);
+    for (size_t i = 0; i < pl.probs.size(); ++i)
+      diag_fp64(pl.probs[i], pl.diag_ws[i].as<bse_c128>(), s);
+  }
 }
 
 void plan_set_tiles(BatchPlan& pl, int nt) {
@@ -1539,6 +1553,8 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
   pl->probs = std::move(probs);
   if (precision == BSE_PREC_FP64) return pl.release();
   pl->half = (flags & BSE_PLAN_HERMITIAN) != 0;
+  if (flags & BSE_PLAN_FP64_DIAGONAL)
+    for (const Problem& pr : pl->probs) pl->diag_ws.emplace_back(diag_fp64_workspace(pr));
   if (pl->half)
     for (const Problem& pr : pl->probs)
       if (pr.kn != pr.p.nk)
@@ -2127,5 +2143,118 @@ void tc_matvec_apply(TcMatvec* m, const bse_c128* V, int k, bse_c128* AV, bse_c1
 }
 
 void tc_matvec_destroy(TcMatvec* m) { delete m; }
+
+// ---------------------------------------------------------------------------
+// Static RPA screening: the polarisability sum of the RPA dielectric matrix
+// (the equation for eps^RPA before Eq. wggq) at omega = 0 for an insulator,
+//   X[G][G'] = sum_a conj(mt_a(G)) mt_a(G'),  mt_a = m_a / sqrt(e_c - e_v),
+// a = (k v c), on the tensor cores: both operands are the transposed pair
+// elements (rows G, K = the transitions, scaled by (e_c - e_v)^-1/2 when
+// split), the K range is cut into tiles of 512 transitions (4 segments of
+// 8 K steps accumulated afresh, as in the build), each tile writes an FP32
+// partial sum and one kernel adds the partials in FP64 in a fixed order.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int RPA_KSTEPS = 32;   // K steps per tile (512 transitions)
+
+struct RpaPartialEpi {
+  float2* part;   // [splits][ng][ng] row-major partial sums
+  int ng;
+  __device__ __forceinline__ void operator()(const tc::Tile& t, int row, int c0, const float* re,
+                                             const float* im) const {
+    float2* dst = part + ((int64_t)t.prob * ng + t.out_row0 + row) * ng + t.n0 + c0;
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (c0 + j < t.n_valid) dst[j] = make_float2(re[j], im[j]);
+  }
+};
+
+__global__ void k_rpa_inv_sqrt_gap(int64_t ntr, int nv, int nc, const double* e_v,
+                                   const double* e_c_kq, double* f) {
+  for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < ntr;
+       a += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(a % nc), v = (int)((a / nc) % nv);
+    const int64_t k = a / ((int64_t)nv * nc);
+    f[a] = 1.0 / sqrt(e_c_kq[k * nc + c] - e_v[k * nv + v]);
+  }
+}
+
+__global__ void k_rpa_reduce(const float2* part, int splits, int64_t nn, double2* x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double sx = 0.0, sy = 0.0;
+    for (int s = 0; s < splits; ++s) {
+      const float2 p = part[(int64_t)s * nn + i];
+      sx += (double)p.x;
+      sy += (double)p.y;
+    }
+    x[i] = make_double2(sx, sy);
+  }
+}
+}  // namespace
+
+void rpa_x_mixed(int nk, int nv, int nc, int ng, const double* e_v, const double* e_c_kq,
+                 const bse_c128* m, int precision, double2* x_out, cudaStream_t s) {
+  const int pieces = precision == BSE_PREC_BF16X6 ? 3 : 2;
+  const int64_t ntr = (int64_t)nk * nv * nc;
+  const int kspan = RPA_KSTEPS * tc::BK;                  // transitions per tile
+  const int64_t kp = (ntr + kspan - 1) / kspan * kspan;   // padded K (zeros past ntr)
+  if (kp > INT32_MAX) throw Error(BSE_ERR_UNSUPPORTED, "too many transitions for the RPA GEMM");
+  const int splits = (int)(kp / kspan);
+  const int nt = tile_cols(round_up(ng, 32), kspan);
+  const tc::GemmShape sh = make_shape(nt, kspan, pieces);
+  DevMem f((size_t)ntr * sizeof(double));
+  DevMem ap((size_t)tc::a_planes(pieces) * ng * kp * 2);
+  DevMem bp((size_t)tc::b_planes(pieces) * ng * kp * 2);
+  DevMem part((size_t)splits * ng * ng * sizeof(float2));
+  DevMem err(sizeof(int));
+  BSE_CUDA(cudaMemsetAsync(err.ptr, 0, sizeof(int), s));
+  {
+    Phase ph("rpa_split", s);
+    k_rpa_inv_sqrt_gap<<<(int)std::min<int64_t>((ntr + 255) / 256, 152 * 8), 256, 0, s>>>(
+        ntr, nv, nc, e_v, e_c_kq, f.as<double>());
+    BSE_CUDA(cudaGetLastError());
+    note_launches(1);
+    // rows G, K = transitions: element (G, a) is m[a][G] (transposed read)
+    SplitArgs sa{reinterpret_cast<const double2*>(m), SPLIT_DENSE, nullptr, 0, 0, (int)ntr,
+                 (int)kp, ng, pieces, 1, f.as<double>(), ap.as<__nv_bfloat16>(), ng, 0};
+    sa.tdense = 1;
+    sa.src_ld = ng;
+    launch_split(sa, s);
+    SplitArgs sb = sa;
+    sb.conj = 0;
+    sb.bneg = 1;
+    sb.out = bp.as<__nv_bfloat16>();
+    launch_split(sb, s);
+  }
+  std::vector<tc::Tile> tiles;
+  for (int sp = 0; sp < splits; ++sp)
+    for (int m0 = 0; m0 < ng; m0 += tc::BM)
+      for (int n0 = 0; n0 < ng; n0 += nt)
+        tiles.push_back({m0, std::min(tc::BM, ng - m0), n0, n0, std::min(nt, ng - n0), m0, sp,
+                         sp * RPA_KSTEPS});
+  DevMem dtiles = upload_mem(tiles);
+  const CUtensorMap ma = make_plane_map(ap.as<__nv_bfloat16>(), (int)kp, ng, tc::a_planes(pieces),
+                                        tc::BM);
+  const CUtensorMap mb = make_plane_map(bp.as<__nv_bfloat16>(), (int)kp, ng, tc::b_planes(pieces),
+                                        nt);
+  {
+    Phase ph("rpa_x_gemm", s);
+    launch_gemm(ma, mb, dtiles.as<tc::Tile>(), (int)tiles.size(), sh, RpaPartialEpi{part.as<float2>(), ng},
+                err.as<int>(), s);
+  }
+  {
+    Phase ph("rpa_reduce", s);
+    const int64_t nn = (int64_t)ng * ng;
+    k_rpa_reduce<<<(int)std::min<int64_t>((nn + 255) / 256, 152 * 8), 256, 0, s>>>(
+        part.as<float2>(), splits, nn, x_out);
+    BSE_CUDA(cudaGetLastError());
+    note_launches(1);
+  }
+  int herr = 0;
+  BSE_CUDA(cudaMemcpyAsync(&herr, err.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+  BSE_CUDA(cudaStreamSynchronize(s));   // also keeps the workspace alive until used
+  if (herr) throw Error(BSE_ERR_TIMEOUT, "RPA tensor-core GEMM: a bounded pipeline wait expired");
+}
 
 }  // namespace bse

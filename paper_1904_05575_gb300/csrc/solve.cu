@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "bse_internal.h"
+#include "zgemm.cuh"
 
 namespace bse {
 namespace {
@@ -450,6 +451,40 @@ void loss_fp64(int n_omega, const bse_c128* eps, double v_inv, double* loss_out,
 // ---------------------------------------------------------------------------
 namespace {
 
+// Partial polarisability sums of the FP64 path, one K range of kc transitions
+// per batch entry b: part[b][G][G'] = sum_{a in range b} conj(mt[a][G]) mt[a][G']
+struct RpaXProb {
+  int M, N, K;            // ng, ng, kc
+  const bse_c128* mt;     // [ntr][ng]
+  int64_t ntr;
+  double2* part;          // [batches][ng][ng]
+  __device__ cplx a(int b, int m, int k) const {
+    const int64_t t = (int64_t)b * K + k;
+    return t < ntr ? conj(ldc(mt + t * M + m)) : cmake(0.0, 0.0);
+  }
+  __device__ cplx b(int b, int n, int k) const {
+    const int64_t t = (int64_t)b * K + k;
+    return t < ntr ? ldc(mt + t * N + n) : cmake(0.0, 0.0);
+  }
+  __device__ void store(int b, int m, int n, cplx v) const {
+    part[((int64_t)b * M + m) * N + n] = make_double2(v.x, v.y);
+  }
+};
+
+// x[i] = sum over batches of part[b][i], in batch order
+__global__ void k_rpa_sum64(const double2* part, int batches, int64_t nn, double2* x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double sx = 0.0, sy = 0.0;
+    for (int b = 0; b < batches; ++b) {
+      const double2 p = part[(int64_t)b * nn + i];
+      sx += p.x;
+      sy += p.y;
+    }
+    x[i] = make_double2(sx, sy);
+  }
+}
+
 // mt[a][G] = m[a][G] / sqrt(e_c_kq[k][c] - e_v[k][v]), a = (k v c)
 __global__ void k_rpa_scale(int64_t total, int nv, int nc, int ng, const double* e_v,
                             const double* e_c_kq, const double2* m, double2* mt) {
@@ -493,27 +528,38 @@ __global__ void k_rpa_w(int ng, const double* v, const double2* inv, double2* w)
 
 }  // namespace
 
-void rpa_screening_fp64(int nk, int nv, int nc, int ng, double omega_cell, const double* e_v,
-                        const double* e_c_kq, const bse_c128* m, const double* v, bse_c128* w_out,
-                        cudaStream_t s) {
+void rpa_screening(int nk, int nv, int nc, int ng, double omega_cell, const double* e_v,
+                   const double* e_c_kq, const bse_c128* m, const double* v, int precision,
+                   bse_c128* w_out, cudaStream_t s) {
+  const int64_t ntr = (int64_t)nk * nv * nc;
+  // X[G][G'] (row-major) into eps, by the library's own kernels: tensor cores
+  // in split precision, or the FP64 GEMM kernel over K ranges of at most
+  // 1,024 transitions with the partials added in FP64
+  DeviceBuffer eps((size_t)ng * ng * sizeof(bse_c128), s);
+  if (precision != BSE_PREC_FP64) {
+    rpa_x_mixed(nk, nv, nc, ng, e_v, e_c_kq, m, precision, eps.as<double2>(), s);
+  } else {
+    Phase ph("rpa_x_fp64", s);
+    DeviceBuffer mt((size_t)ntr * ng * sizeof(bse_c128), s);
+    k_rpa_scale<<<grid_for(ntr * ng, 256), 256, 0, s>>>(ntr * ng, nv, nc, ng, e_v, e_c_kq,
+                                                       reinterpret_cast<const double2*>(m),
+                                                       mt.as<double2>());
+    BSE_CUDA(cudaGetLastError());
+    note_launches(1);
+    const int kc = (int)std::min<int64_t>(ntr, 1024);
+    const int batches = (int)((ntr + kc - 1) / kc);
+    DeviceBuffer part((size_t)batches * ng * ng * sizeof(bse_c128), s);
+    RpaXProb P{ng, ng, kc, mt.as<bse_c128>(), ntr, part.as<double2>()};
+    launch_zgemm(P, batches, s);
+    k_rpa_sum64<<<grid_for((int64_t)ng * ng, 256), 256, 0, s>>>(part.as<double2>(), batches,
+                                                                (int64_t)ng * ng, eps.as<double2>());
+    BSE_CUDA(cudaGetLastError());
+    note_launches(1);
+  }
   std::lock_guard<std::mutex> lock(g_handle_mutex);
   Handles& h = handles_for_current_device();
   BSE_CUSOLVER(cusolverDnSetStream(h.solver, s));
   BSE_CUBLAS(cublasSetStream(h.blas, s));
-  const int64_t ntr = (int64_t)nk * nv * nc;
-  DeviceBuffer mt((size_t)ntr * ng * sizeof(bse_c128), s);
-  k_rpa_scale<<<grid_for(ntr * ng, 256), 256, 0, s>>>(ntr * ng, nv, nc, ng, e_v, e_c_kq,
-                                                     reinterpret_cast<const double2*>(m),
-                                                     mt.as<double2>());
-  BSE_CUDA(cudaGetLastError());
-  // Mt row-major [ntr][ng] is, column-major, the ng x ntr matrix C; C C^H in
-  // column-major storage is X in row-major storage:
-  // (C C^H)[G'][G] = sum_a Mt[a][G'] conj(Mt[a][G]) = X[G][G'] at G' + G ng
-  DeviceBuffer eps((size_t)ng * ng * sizeof(bse_c128), s);
-  const cuDoubleComplex one = make_cuDoubleComplex(1.0, 0.0), zero = make_cuDoubleComplex(0.0, 0.0);
-  BSE_CUBLAS(cublasZgemm(h.blas, CUBLAS_OP_N, CUBLAS_OP_C, ng, ng, (int)ntr, &one,
-                         mt.as<cuDoubleComplex>(), ng, mt.as<cuDoubleComplex>(), ng, &zero,
-                         eps.as<cuDoubleComplex>(), ng));
   DeviceBuffer rhs((size_t)ng * ng * sizeof(bse_c128), s);
   const double two_kappa = 2.0 * kHartreeEv / ((double)nk * omega_cell);
   k_rpa_eps<<<grid_for((int64_t)ng * ng, 256), 256, 0, s>>>(ng, two_kappa, v, eps.as<double2>(),
@@ -539,7 +585,7 @@ void rpa_screening_fp64(int nk, int nv, int nc, int ng, double omega_cell, const
   k_rpa_w<<<grid_for((int64_t)ng * ng, 256), 256, 0, s>>>(ng, v, rhs.as<double2>(),
                                                          reinterpret_cast<double2*>(w_out));
   BSE_CUDA(cudaGetLastError());
-  note_launches(3);
+  note_launches(2);   // k_rpa_eps and k_rpa_w (the LU solve is cuSOLVER's)
   BSE_CUDA(cudaStreamSynchronize(s));   // the workspace is stream-ordered
 }
 

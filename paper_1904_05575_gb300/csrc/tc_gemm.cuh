@@ -70,6 +70,7 @@ struct Tile {
   int n_valid;   // real output columns (<= nt)
   int out_row0;  // first output row
   int prob;      // problem of a batched launch (0 otherwise)
+  int kc0 = 0;   // first K step of the tile's K range (split K: partial sums per range)
 };
 
 // ---------------------------------------------------------------------------
@@ -274,8 +275,8 @@ __device__ __forceinline__ void producer_role(const Pipe& pp, const CUtensorMap*
         }
         mbar_expect_tx(&pp.full[stage], pp.sbytes);
         uint8_t* sa = pp.smem + (size_t)stage * pp.sbytes;
-        tma_load_3d(sa, tmA, kc * BK, tl.a_row0, 0, &pp.full[stage]);
-        tma_load_3d(sa + pp.a_bytes, tmB, kc * BK, tl.b_row0, 0, &pp.full[stage]);
+        tma_load_3d(sa, tmA, (tl.kc0 + kc) * BK, tl.a_row0, 0, &pp.full[stage]);
+        tma_load_3d(sa + pp.a_bytes, tmB, (tl.kc0 + kc) * BK, tl.b_row0, 0, &pp.full[stage]);
         pending[stage] = (int)phase;
         if (++stage == sh.stages) {
           stage = 0;

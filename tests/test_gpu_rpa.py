@@ -33,19 +33,30 @@ def _case(seed, nk, nv, nc, ng):
     return e_v, e_c, m, v
 
 
-@pytest.mark.parametrize("shape", [(8, 2, 3, 15), (8, 4, 4, 59), (1, 1, 1, 1)], ids=str)
-def test_rpa_screening_matches_oracle(bse, shape):
+# shapes: small, several K ranges of the FP64 kernel (1,024) and of the tensor-core
+# GEMM (512) with a ragged last range, NG past one 128-row tile, a single element
+SHAPES = [(8, 2, 3, 15), (8, 4, 4, 59), (64, 4, 5, 181), (1, 1, 1, 1)]
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (2, 2e-6)], ids=["fp64", "bf16x6"])
+@pytest.mark.parametrize("shape", SHAPES, ids=str)
+def test_rpa_screening_matches_oracle(bse, shape, prec, tol):
     import torch
     nk, nv, nc, ng = shape
     e_v, e_c, m, v = _case(7, nk, nv, nc, ng)
     omega = bi.OMEGA_CELL
-    w_ref = R.screened_w(R.rpa_epsilon(e_v, e_c, m, v, omega), v)
+    eps_ref = R.rpa_epsilon(e_v, e_c, m, v, omega)
+    w_ref = R.screened_w(eps_ref, v)
     t = {k: torch.as_tensor(x).cuda() for k, x in (("e_v", e_v), ("e_c", e_c), ("m", m), ("v", v))}
     w = torch.empty((ng, ng), dtype=torch.complex128, device="cuda")
-    bse.bse_rpa_screening(t["e_v"], t["e_c"], t["m"], t["v"], omega, w)
+    bse.bse_rpa_screening(t["e_v"], t["e_c"], t["m"], t["v"], omega, w, precision=prec)
     torch.cuda.synchronize()
     err = np.linalg.norm(w.cpu().numpy() - w_ref) / np.linalg.norm(w_ref)
-    assert err < 1e-12, err
+    assert err < tol, err
+    # the screening weakens the bare potential: w - v is the (negative) correction
+    corr_ref = w_ref - np.diag(v)
+    err_c = np.linalg.norm(w.cpu().numpy() - np.diag(v) - corr_ref) / np.linalg.norm(corr_ref)
+    assert err_c < (1e-10 if prec == 0 else 1e-5), err_c
 
 
 def test_rpa_screening_rejects_a_negative_gap(bse):
