@@ -682,6 +682,105 @@ def run_headline(args, bse, bi, prec, world, rank, local):
     return 0
 
 
+def run_c3_all(args, bse, bi, prec, world, rank, local):
+    """All 16 momentum transfers of the finite-momentum batch (Nk = 512 on an
+    8x8x8 grid, NG = 113, uneven (Nv, Nc) windows, N from 2,048 to 12,288):
+    their 326 GB of complex128 inputs exceed the device, so the Q are packed
+    in order into groups of at most --c3-group-gb of inputs; each group's
+    inputs are drawn on the GPU (untimed) and built by one Hermitian plan
+    (every Q's exchange tiles in one persistent launch, all its direct terms
+    in the next), executed `warmup` times and timed `steps` times.  A step
+    is the build of all 16 Q: ms_per_step is the sum over groups of the mean
+    group time."""
+    import torch
+    cfg = bi.CONFIGS["c3"]
+    nq = len(cfg.q_abs)
+    seed = 20190411 + rank
+    stream = torch.cuda.current_stream()
+    unit = cfg.nk * cfg.nk * cfg.ng * 16
+
+    def qbytes(q):
+        nv, nc = cfg.window(q)
+        return unit * (nv * nv + nc * nc + nv * nc)
+
+    groups, cur, cur_b = [], [], 0.0
+    for q in range(nq):
+        if cur and cur_b + qbytes(q) > args.c3_group_gb * 1e9:
+            groups.append(cur)
+            cur, cur_b = [], 0.0
+        cur.append(q)
+        cur_b += qbytes(q)
+    groups.append(cur)
+    sampler = ClockSampler(local)
+    sampler.start()
+    total_ms, flops, launches, per_group = 0.0, 0.0, 0, []
+    phases_all = {}
+    for g in groups:
+        probs = [bi.make_problem_torch(cfg, q_index=q, seed=seed) for q in g]
+        ds = [bse.upload_problem(p) for p in probs]
+        sts = [bse.make_problem_struct(d) for d in ds]
+        torch.cuda.synchronize()
+        plan = bse.Plan(sts, precision=prec, autotune=True, hermitian=not args.all_blocks)
+        for _ in range(args.warmup):
+            plan.execute()
+        torch.cuda.synchronize()
+        plan.status()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        l0 = bse.bse_kernel_launches()
+        bse.bse_phase_timing(True)
+        for e0, e1 in evs:
+            e0.record(stream)
+            plan.execute()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        bse.bse_phase_timing(False)
+        launches += bse.bse_kernel_launches() - l0
+        plan.status()
+        for k, v in bse.bse_phase_report().items():
+            c, ms = phases_all.get(k, (0, 0.0))
+            phases_all[k] = (c + v[0], ms + v[1])
+        ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in evs)
+        f = sum(build_flops(p["nk"], p["nv"], p["nc"], p["ng"]) for p in probs)
+        per_group.append({"q": g, "windows": [list(cfg.window(q)) for q in g],
+                          "n": [p["nk"] * p["nv"] * p["nc"] for p in probs],
+                          "input_gb": round(sum(qbytes(q) for q in g) / 1e9, 1),
+                          "build_ms": ms, "tflops": f / (ms * 1e-3) / 1e12})
+        total_ms += ms
+        flops += f
+        plan.close()
+        del plan, sts, ds, probs
+        torch.cuda.empty_cache()
+    clocks = sampler.stop()
+    t = max_over_ranks([total_ms], "cuda", world)[0]
+    value = weak_scaling_value(world, flops, t)
+    peaks = load_peaks()
+    shapes = [(cfg.nk,) + tuple(cfg.window(q)) + (cfg.ng,) for q in range(nq)]
+    roofline, roofline_secondary = build_rooflines(bse, prec, phases_all, args.steps, shapes, peaks,
+                                                   hermitian=not args.all_blocks, workload="c3")
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "bf16x6": "bf16x6(f32 acc)", "bf16x3": "bf16x3(f32 acc)"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": "finite-momentum batch: all 16 Q along [100], Nk=512 (8x8x8), "
+                                   "NG=113, uneven windows, N 2048..12288, built in groups of Q "
+                                   "(inputs drawn on the GPU per group)",
+                       "precision": args.precision, "hermitian_plan": not args.all_blocks,
+                       "l2": "inputs larger than L2 (tens of GB per group)",
+                       "parallelism": f"Q replicas x{world}"},
+            "groups": per_group,
+            "phase_ms_per_step": {k: v[1] / args.steps for k, v in phases_all.items()},
+            "roofline": roofline, "roofline_secondary": roofline_secondary,
+            "cpu_baseline": None, "e2e": None, "clocks": clocks, "gpu_launches": launches,
+            "peaks": peaks,
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_c4(args, bse, bi, prec, world, rank, local):
     """Core-level workload (c4: Nk=512, Nv=2 core levels, Nc=20, NG=300,
     N=20,480, full BSE; c4s: the same recipe on a 4x4x4 grid): c4's pair
@@ -869,6 +968,8 @@ def main():
                     help="c5: compute every (k, k') block (no BSE_PLAN_HERMITIAN)")
     ap.add_argument("--e2e-steps", type=int, default=3,
                     help="c5: timed end-to-end steps (after one untimed)")
+    ap.add_argument("--c3-group-gb", type=float, default=120.0,
+                    help="c3 --qs all: complex128 input gigabytes per group of Q")
     ap.add_argument("--no-c2", action="store_true",
                     help="c5: skip the optical-limit time-to-spectrum extra keys")
     ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "bf16x6", "bf16x3"])
@@ -925,6 +1026,11 @@ def main():
     # each rank: its own momentum transfers (Q replicas), resident in HBM
     if args.config in ("c5", "c5s"):
         rc = run_headline(args, bse, bi, prec, world, rank, local)
+        if world > 1:
+            dist.destroy_process_group()
+        return rc
+    if args.config == "c3" and args.qs == "all":
+        rc = run_c3_all(args, bse, bi, prec, world, rank, local)
         if world > 1:
             dist.destroy_process_group()
         return rc

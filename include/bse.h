@@ -226,8 +226,10 @@ void bse_plan_destroy(void* plan);
  *     nk^2 * max(min(nv^2, nc^2), nv*nc if coupling) * ng * 16 bytes, is
  *     rejected with BSE_ERR_ARG before any launch;
  *   - the first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress, no allocation); make that first call before any
- *     stream capture on that device;
+ *     (cudaGetSymbolAddress, no allocation) and keeps it for the process;
+ *     make that first call before any stream capture on that device, and do
+ *     not use this entry point after a device reset (cudaDeviceReset) without
+ *     restarting the process: the kept address belongs to the old context;
  *   - all calls share the one array and it keeps the previous call's
  *     contents (nothing in it needs to start at zero); calls whose work
  *     overlaps on the GPU (other streams, other host threads) race on it and
@@ -308,6 +310,33 @@ int bse_spectrum_tensor(int32_t n, const bse_c128* Z, const bse_c128* L, int64_t
 int bse_rpa_screening(int32_t nk, int32_t nv, int32_t nc, int32_t ng, double omega_cell,
                       const double* e_v, const double* e_c_kq, const bse_c128* m, const double* v,
                       int32_t precision, bse_c128* w_out, void* cuda_stream);
+
+/* Plane-wave pair matrix elements from wavefunction coefficients (the
+ * elements M and N of the LAPW section, interstitial part: the whole element
+ * for Bloch functions expanded in plane waves, phi_{nk}(r) =
+ * sum_{G in S} C_{nk}(G) e^{i(k+G)r} with unit-norm plane waves), in FP64:
+ *   M(a, b; G, s) = sum_{G1 in S} conj(a(G1)) b(G1 + G + s)
+ *   N(a, b; G, s) = sum_{G1 in S} conj(a(G1)) conj(b(-G1 - G - s))
+ * (b = 0 outside S; s the reciprocal vector that brings k + q back onto the
+ * grid), producing the build's inputs at Q = 0 in the layouts of bse_problem:
+ *   m_x[k][v][c](G)       = <c k| e^{-iGr} |v k>                    = M(C_ck, C_vk; G, 0)
+ *   m_vv[k][k'][v][v'](G) = <v' k'| e^{-i(G+q)r} |v k>, q = k - k'  = M(C_v'k', C_vk; G, s)
+ *   m_cc[k][k'][c][c'](G) likewise with conduction bands
+ *   n_vc[k][k'][v][c'](G) = <v k| e^{-i(G+q)r} |(c' k')^*>, q = -k - k'
+ * grid: the k grid is grid^3 points, k = (i grid + j) grid + l at integer
+ * coordinates (i, j, l) / grid of the reciprocal basis (the order of
+ * bse_problem's q maps); cv [nk][nv][npw], cc [nk][nc][npw] device
+ * coefficients; basis [npw][3] and gout [ng][3] HOST int32 coordinates of the
+ * plane-wave basis S (distinct) and of the output vectors G in the reciprocal
+ * basis.  k_begin / k_count select the k rows of m_vv and m_cc as in
+ * bse_problem (0, 0: all); m_x and n_vc are whole.  Any output may be NULL
+ * (not computed), not all.  Syncs.  Errors: BSE_ERR_ARG, BSE_ERR_UNSUPPORTED
+ * (coordinates beyond 30 from the origin, a basis too large for the kernel's
+ * shared memory), BSE_ERR_NOMEM, BSE_ERR_CUDA. */
+int bse_pair_elements(int32_t grid, int32_t nv, int32_t nc, int32_t npw, int32_t ng,
+                      const bse_c128* cv, const bse_c128* cc, const int32_t* basis,
+                      const int32_t* gout, int32_t k_begin, int32_t k_count, bse_c128* m_x,
+                      bse_c128* m_vv, bse_c128* m_cc, bse_c128* n_vc, void* cuda_stream);
 
 /* Electron energy-loss function L(w) = -Im 1/eps_M(w) (Eq. Lofeps) and the
  * dynamical structure factor S(Q, w) = -(1/pi) v_G(q)^{-1} Im 1/eps_M(q, w)

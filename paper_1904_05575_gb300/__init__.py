@@ -63,7 +63,8 @@ EXPORTED = ("bse_build_kernel", "bse_reduce", "bse_spectrum", "bse_last_error", 
             "bse_mlp_predict", "bse_xpy", "bse_mlp_trajectory_samples", "bse_plan_create",
             "bse_plan_execute", "bse_plan_status", "bse_plan_tile_cols", "bse_plan_destroy",
             "bse_plan_fused", "bse_spectrum_tensor", "bse_loss_function",
-            "bse_lowest_excitons_from", "bse_rpa_screening", "bse_plan_set_wait_limit")
+            "bse_lowest_excitons_from", "bse_rpa_screening", "bse_plan_set_wait_limit",
+            "bse_pair_elements")
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -107,6 +108,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.bse_plan_destroy.argtypes = [vp]
     lib.bse_plan_destroy.restype = None
     lib.bse_plan_set_wait_limit.argtypes = [vp, dbl]
+    lib.bse_pair_elements.argtypes = [i32, i32, i32, i32, i32, vp, vp, vp, vp, i32, i32, vp, vp,
+                                      vp, vp, vp]
+    lib.bse_pair_elements.restype = ctypes.c_int
     lib.bse_plan_set_wait_limit.restype = ctypes.c_int
     for name in ("bse_plan_create", "bse_plan_execute", "bse_plan_status", "bse_plan_tile_cols",
                  "bse_plan_fused"):
@@ -379,6 +383,36 @@ def bse_rpa_screening(e_v, e_c_kq, m, v, omega_cell: float, w_out, stream=None,
                                     _ptr(e_c_kq, f64, "e_c_kq"), _ptr(m, c128, "m"),
                                     _ptr(v, f64, "v"), int(precision), _ptr(w_out, c128, "w_out"),
                                     _stream(stream)))
+
+
+def bse_pair_elements(grid: int, cv, cc, basis, gout, m_x=None, m_vv=None, m_cc=None, n_vc=None,
+                      k_begin: int = 0, k_count: int = 0, stream=None) -> None:
+    """Pair matrix elements from plane-wave coefficients (include/bse.h):
+    cv [nk, nv, npw], cc [nk, nc, npw] complex128 CUDA tensors; basis [npw, 3]
+    and gout [ng, 3] integer coordinates (host, any integer array); outputs
+    complex128 CUDA tensors of the bse_problem shapes, or None."""
+    import torch
+    nk, nv, npw = cv.shape
+    nc = cc.shape[1]
+    b = np.ascontiguousarray(basis, np.int32)
+    g = np.ascontiguousarray(gout, np.int32)
+    ng = g.shape[0]
+    if nk != grid ** 3 or tuple(cc.shape) != (nk, nc, npw) or b.shape != (npw, 3) or g.shape[1] != 3:
+        raise ValueError("cv [nk, nv, npw], cc [nk, nc, npw], basis [npw, 3], gout [ng, 3], nk = grid^3")
+    kn = k_count if k_count > 0 else nk
+    shapes = {"m_x": (nk, nv, nc, ng), "m_vv": (kn, nk, nv, nv, ng), "m_cc": (kn, nk, nc, nc, ng),
+              "n_vc": (nk, nk, nv, nc, ng)}
+    outs = {"m_x": m_x, "m_vv": m_vv, "m_cc": m_cc, "n_vc": n_vc}
+    for name, t in outs.items():
+        if t is not None and tuple(t.shape) != shapes[name]:
+            raise ValueError(f"{name} must have shape {shapes[name]}")
+    c128 = torch.complex128
+    ptr = lambda t, name: _ptr(t, c128, name) if t is not None else None
+    _check(load().bse_pair_elements(
+        grid, nv, nc, npw, ng, _ptr(cv, c128, "cv"), _ptr(cc, c128, "cc"),
+        b.ctypes.data_as(ctypes.c_void_p), g.ctypes.data_as(ctypes.c_void_p), int(k_begin),
+        int(k_count), ptr(m_x, "m_x"), ptr(m_vv, "m_vv"), ptr(m_cc, "m_cc"), ptr(n_vc, "n_vc"),
+        _stream(stream)))
 
 
 def bse_phase_timing(enable: bool) -> None:

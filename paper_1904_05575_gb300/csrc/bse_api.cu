@@ -396,6 +396,32 @@ extern "C" int bse_rpa_screening(int32_t nk, int32_t nv, int32_t nc, int32_t ng,
   });
 }
 
+extern "C" int bse_pair_elements(int32_t grid, int32_t nv, int32_t nc, int32_t npw, int32_t ng,
+                                 const bse_c128* cv, const bse_c128* cc, const int32_t* basis,
+                                 const int32_t* gout, int32_t k_begin, int32_t k_count,
+                                 bse_c128* m_x, bse_c128* m_vv, bse_c128* m_cc, bse_c128* n_vc,
+                                 void* cuda_stream) {
+  return guarded([&] {
+    BSE_CHECK_ARG(grid >= 1 && grid <= 64, "grid must be in [1, 64]");
+    BSE_CHECK_ARG(nv >= 1 && nc >= 1 && npw >= 1 && ng >= 1, "nv, nc, npw and ng must be >= 1");
+    const int64_t nk = (int64_t)grid * grid * grid;
+    BSE_CHECK_ARG(nk * nk * std::max(nv, nc) * std::max(nv, nc) <= 2147483647LL,
+                  "too many pair blocks");
+    BSE_CHECK_ARG(cv && cc && basis && gout, "NULL cv, cc, basis or gout");
+    BSE_CHECK_ARG(m_x || m_vv || m_cc || n_vc, "no output requested");
+    BSE_CHECK_ARG(k_begin >= 0 && k_count >= 0 && (int64_t)k_begin + k_count <= nk &&
+                      (k_count > 0 || k_begin == 0),
+                  "k-row slab [k_begin, k_begin + k_count) must lie in [0, nk)");
+    auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+    BSE_CHECK_ARG(al16(cv) && al16(cc) && al16(m_x) && al16(m_vv) && al16(m_cc) && al16(n_vc),
+                  "complex128 arrays must be 16-byte aligned");
+    keep_pool_memory();
+    pair_elements_fp64(grid, nv, nc, npw, ng, cv, cc, basis, gout, k_begin,
+                       k_count > 0 ? k_count : (int)nk, m_x, m_vv, m_cc, n_vc,
+                       static_cast<cudaStream_t>(cuda_stream));
+  });
+}
+
 extern "C" int bse_spectrum(int32_t n, bse_c128* S_inout, const bse_c128* L, int64_t ld,
                             const bse_c128* rho, double c_q, double vc, int32_t n_omega,
                             const double* omega, double delta, double* E_out, double* osc_out,

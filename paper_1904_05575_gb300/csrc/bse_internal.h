@@ -107,6 +107,13 @@ constexpr size_t kFp64StaticScratchBytes = (size_t)16 << 20;
 size_t fp64_static_scratch_need(const Problem& pr);
 void build_fp64_static(const Problem& pr, cudaStream_t stream);
 
+// Pair matrix elements from plane-wave coefficients (pair_elements.cu);
+// basis_h / gout_h are host integer coordinates; NULL outputs are skipped.  Syncs.
+void pair_elements_fp64(int n, int nv, int nc, int npw, int ng, const bse_c128* cv,
+                        const bse_c128* cc, const int32_t* basis_h, const int32_t* gout_h,
+                        int kb, int kn, bse_c128* m_x, bse_c128* m_vv, bse_c128* m_cc,
+                        bse_c128* n_vc, cudaStream_t s);
+
 // Exact FP64 diagonal of A (and B) over the problem's rows (diag_fp64.cu):
 // overwrites A_aa, B_aa with the FP64 sums; workspace of diag_fp64_workspace
 // bytes (device).
