@@ -682,6 +682,88 @@ def run_headline(args, bse, bi, prec, world, rank, local):
     return 0
 
 
+def _eps_peaks(eps_im, omega):
+    """Local maxima of Im eps above 10 % of its largest value."""
+    import numpy as np
+    y = np.asarray(eps_im)
+    idx = [i for i in range(1, len(y) - 1) if y[i] > y[i - 1] and y[i] >= y[i + 1]
+           and y[i] > 0.1 * y.max()]
+    return idx
+
+
+def run_eps_qs(args, bse, bi, prec, world, rank, local):
+    """eps_M at several momentum transfers of a workload, the mixed path (split-
+    precision Hermitian plan + FP64 reduction, eigensolve and spectrum) against
+    the plain FP64 GPU path (FP64 build + the same FP64 steps): per Q the
+    largest exciton-energy difference, the largest relative difference of
+    Im eps_M at its peaks (local maxima above 10 % of the largest) and of the
+    peak positions, and the times.  Each Q's inputs are drawn on the GPU;
+    each path's dense reduction and eigensolve is done once."""
+    import numpy as np
+    import torch
+    qs = [int(x) for x in args.eps_qs.split(",")]
+    stream = torch.cuda.current_stream()
+    rows = []
+    for q in qs:
+        p = bi.make_problem_torch(args.config, q_index=q, seed=20190411 + rank)
+        nk, nv, nc, ng = p["nk"], p["nv"], p["nc"], p["ng"]
+        n = nk * nv * nc
+        d = bse.upload_problem(p)
+        st = bse.make_problem_struct(d)
+        om = torch.as_tensor(p["omega"]).cuda()
+        rho = p["rho"] if torch.is_tensor(p["rho"]) else torch.as_tensor(p["rho"]).cuda()
+        vc = nk * p["omega_cell"]
+        S = torch.empty((n, n), dtype=torch.complex128, device="cuda")
+        L = torch.empty_like(S)
+        out = {}
+        for name in ("fp64", "mixed"):
+            E = torch.empty(n, dtype=torch.float64, device="cuda")
+            osc = torch.empty_like(E)
+            eps = torch.empty(len(p["omega"]), dtype=torch.complex128, device="cuda")
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(stream)
+            if name == "fp64":
+                bse.bse_build_kernel([st], bse.BSE_PREC_FP64)
+            else:
+                plan = bse.Plan([st], precision=prec, hermitian=True)
+                ev[0].record(stream)
+                plan.execute()
+                plan.status()
+            ev[1].record(stream)
+            bse.bse_reduce(n, d["A"], d["B"], S, L)
+            bse.bse_spectrum(n, S, L, rho, p["c_q"], vc, om, p["delta"], E, osc, eps)
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+            if name == "mixed":
+                plan.close()
+            out[name] = {"E": E.cpu().numpy(), "eps": eps.cpu().numpy(),
+                         "build_ms": ev[0].elapsed_time(ev[1]), "total_ms": ev[0].elapsed_time(ev[2])}
+        ef, em = out["fp64"]["E"], out["mixed"]["E"]
+        pf = _eps_peaks(out["fp64"]["eps"].imag, p["omega"])
+        imf, imm = out["fp64"]["eps"].imag, out["mixed"]["eps"].imag
+        pm = _eps_peaks(imm, p["omega"])
+        dpos = max((abs(p["omega"][a] - p["omega"][b]) for a, b in zip(pf, pm)), default=0.0) \
+            if len(pf) == len(pm) else float("nan")
+        rows.append({"q_index": q, "q_abs": float(np.linalg.norm(p["q_vec"])), "n": n,
+                     "max_dE_meV": float(np.abs(ef - em).max() * 1e3),
+                     "lowest_E_eV": float(ef[0]),
+                     "peaks": len(pf),
+                     "max_rel_dIm_eps_at_peaks": float(max((abs(imm[i] - imf[i]) / abs(imf[i])
+                                                            for i in pf), default=0.0)),
+                     "max_rel_d_eps": float(np.abs(out["mixed"]["eps"] - out["fp64"]["eps"]).max()
+                                            / np.abs(out["fp64"]["eps"]).max()),
+                     "peak_shift_eV": dpos,
+                     "fp64_build_ms": out["fp64"]["build_ms"], "mixed_build_ms": out["mixed"]["build_ms"],
+                     "fp64_total_ms": out["fp64"]["total_ms"], "mixed_total_ms": out["mixed"]["total_ms"]})
+        print(json.dumps(rows[-1]), flush=True)
+        del S, L, d, p, st
+        torch.cuda.empty_cache()
+    if rank == 0:
+        print(json.dumps({"metric": "eps_M, mixed vs FP64 GPU path", "config": args.config,
+                          "rows": rows}), flush=True)
+    return 0
+
+
 def run_c3_all(args, bse, bi, prec, world, rank, local):
     """All 16 momentum transfers of the finite-momentum batch (Nk = 512 on an
     8x8x8 grid, NG = 113, uneven (Nv, Nc) windows, N from 2,048 to 12,288):
@@ -968,6 +1050,9 @@ def main():
                     help="c5: compute every (k, k') block (no BSE_PLAN_HERMITIAN)")
     ap.add_argument("--e2e-steps", type=int, default=3,
                     help="c5: timed end-to-end steps (after one untimed)")
+    ap.add_argument("--eps-qs", default=None,
+                    help="comma-separated Q indices: eps_M of the mixed path against the plain "
+                         "FP64 GPU path at each (dense reduction and eigensolve per path)")
     ap.add_argument("--c3-group-gb", type=float, default=120.0,
                     help="c3 --qs all: complex128 input gigabytes per group of Q")
     ap.add_argument("--no-c2", action="store_true",
@@ -1024,6 +1109,11 @@ def main():
     prec = prec_map[args.precision]
 
     # each rank: its own momentum transfers (Q replicas), resident in HBM
+    if args.eps_qs:
+        rc = run_eps_qs(args, bse, bi, prec, world, rank, local)
+        if world > 1:
+            dist.destroy_process_group()
+        return rc
     if args.config in ("c5", "c5s"):
         rc = run_headline(args, bse, bi, prec, world, rank, local)
         if world > 1:
