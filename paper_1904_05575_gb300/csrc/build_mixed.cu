@@ -1051,6 +1051,7 @@ int num_sms() {
   return n;
 }
 
+// d_err: two ints, the error bits and the counter of the dynamic unit hand-out
 template <class Epi>
 void launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb, const tc::Tile* d_tiles, int ntiles,
                  const tc::GemmShape& sh, const Epi& epi, int* d_err, cudaStream_t s) {
@@ -1060,7 +1061,8 @@ void launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb, const tc::Tile* d
   if (seg && (sh.nt > 64 || sh.acc_bufs != 2))
     throw Error(BSE_ERR_UNSUPPORTED, "K-segmented tiles need two accumulator sets of <= 64 columns");
   const int which = (sh.pieces == 3 ? 2 : 0) + (seg ? 1 : 0);
-  void (*const kerns[4])(CUtensorMap, CUtensorMap, const tc::Tile*, int, tc::GemmShape, Epi, int*) = {
+  void (*const kerns[4])(CUtensorMap, CUtensorMap, const tc::Tile*, int, tc::GemmShape, Epi, int*,
+                         int*) = {
       tc::gemm_split_bf16<2, Epi, false>, tc::gemm_split_bf16<2, Epi, true>,
       tc::gemm_split_bf16<3, Epi, false>, tc::gemm_split_bf16<3, Epi, true>};
   auto kern = kerns[which];
@@ -1078,8 +1080,14 @@ void launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb, const tc::Tile* d
     BSE_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn[which]));
   });
   if ((int)smem > max_dyn[which]) throw Error(BSE_ERR_UNSUPPORTED, "tile shape needs too much shared memory");
-  const int grid = std::min<int>(ntiles, num_sms());
-  kern<<<grid, tc::NUM_THREADS, smem, s>>>(ma, mb, d_tiles, ntiles, sh, epi, d_err);
+  const int units = (ntiles + sh.group - 1) / sh.group;
+  const int grid = std::min<int>(units, num_sms());
+  int* units_taken = nullptr;
+  if (units > grid) {   // more than one round of units: hand them out in order of need
+    units_taken = d_err + 1;
+    BSE_CUDA(cudaMemsetAsync(units_taken, 0, sizeof(int), s));
+  }
+  kern<<<grid, tc::NUM_THREADS, smem, s>>>(ma, mb, d_tiles, ntiles, sh, epi, d_err, units_taken);
   BSE_CUDA(cudaGetLastError());
   note_launches(1);
 }
@@ -1568,7 +1576,7 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
   pl->ng = ng;
   pl->Kp = round_up(ng, tc::BK);
   pl->ng_pad = round_up(ng, 32);
-  pl->err = DevMem(sizeof(int));
+  pl->err = DevMem(2 * sizeof(int));
   BSE_CUDA(cudaMemsetAsync(pl->err.ptr, 0, sizeof(int), s));
 
   // exchange operands of all problems, stacked
@@ -2098,7 +2106,7 @@ TcMatvec* tc_matvec_create(int n, const bse_c128* A, const bse_c128* B, int64_t 
   m->vp = DevMem(v_bytes);
   BSE_CUDA(cudaMemsetAsync(m->vp.ptr, 0, v_bytes, s));
   m->tiles = DevMem((size_t)m->max_tiles * sizeof(tc::Tile));
-  m->err = DevMem(sizeof(int));
+  m->err = DevMem(2 * sizeof(int));
   BSE_CUDA(cudaMemsetAsync(m->err.ptr, 0, sizeof(int), s));
   for (int which = 0; which < (B ? 2 : 1); ++which) {
     SplitArgs sa{reinterpret_cast<const double2*>(which ? B : A), SPLIT_DENSE, nullptr, 0, 0, n,
@@ -2207,7 +2215,7 @@ void rpa_x_mixed(int nk, int nv, int nc, int ng, const double* e_v, const double
   DevMem ap((size_t)tc::a_planes(pieces) * ng * kp * 2);
   DevMem bp((size_t)tc::b_planes(pieces) * ng * kp * 2);
   DevMem part((size_t)splits * ng * ng * sizeof(float2));
-  DevMem err(sizeof(int));
+  DevMem err(2 * sizeof(int));
   BSE_CUDA(cudaMemsetAsync(err.ptr, 0, sizeof(int), s));
   {
     Phase ph("rpa_split", s);

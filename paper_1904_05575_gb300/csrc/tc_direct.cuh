@@ -383,11 +383,12 @@ gemm_split_bf16_direct(const __grid_constant__ CUtensorMap tmA,
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   const int units = num_units(ntiles, sh.group);
+  UnitQueue uq_static{};   // no counter: the static order b, b + gridDim.x, ...
 
   if (warp == 0) {
-    if (lane == 0) producer_role(pp, &tmA, &tmB, tiles, ntiles, sh, &abort_flag, err);
+    if (lane == 0) producer_role(pp, &tmA, &tmB, tiles, ntiles, sh, &abort_flag, err, uq_static);
   } else if (warp == 1) {
-    if (lane == 0) mma_role<P>(pp, tmem_base, ntiles, sh, &abort_flag, err);
+    if (lane == 0) mma_role<P>(pp, tmem_base, ntiles, sh, &abort_flag, err, uq_static);
   } else if (warp == 6) {
     // ---------------- pair-side loader ----------------
     int xs = 0;

@@ -242,6 +242,67 @@ __host__ inline size_t gemm_smem_bytes(const GemmShape& s) {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int num_units(int ntiles, int group) { return (ntiles + group - 1) / group; }
 
+// Work-unit hand-out.  Static (no counter): CTA b takes the units b,
+// b + gridDim.x, ... .  Dynamic (a zeroed device counter): the producer takes
+// the next unit with an atomicAdd and passes it to the MMA issuer and the
+// epilogue warps through a ring in shared memory (-1: no more units), so the
+// units in flight are always about the gridDim.x lowest not yet taken.  With
+// the static order a CTA that runs ahead drifts rounds away from the others
+// and the tiles that share an operand tile (a pair block's row tiles, the
+// column tiles of one row tile) no longer run at the same time: the operand
+// is read from DRAM again instead of from L2.
+constexpr int UQ = 4;   // ring depth (units the producer may run ahead)
+struct UnitQueue {
+  int* counter;         // global, zeroed before the launch; NULL = static order
+  volatile int* ring;   // [UQ]
+  uint64_t* full;       // [UQ] unit written (producer)
+  uint64_t* empty;      // [UQ] unit read (the MMA issuer and every epilogue warp)
+};
+struct UnitCursor {     // one consumer's (or the producer's) position
+  int slot = 0;
+  uint32_t phase = 0;
+  int next_static;      // static order: the next unit of this CTA
+};
+
+// The producer's next unit: >= 0 a unit, -1 none left, -2 a wait gave up.
+__device__ __forceinline__ int uq_produce(const UnitQueue& q, UnitCursor& c, int units,
+                                          volatile int* abort_flag, int* err, long long budget) {
+  if (!q.counter) {
+    const int u = c.next_static;
+    c.next_static += gridDim.x;
+    return u < units ? u : -1;
+  }
+  // claim the unit only once its ring entry is free, as late as possible
+  if (!mbar_wait(&q.empty[c.slot], c.phase ^ 1, abort_flag, err, budget)) return -2;
+  int u = atomicAdd(q.counter, 1);
+  if (u >= units) u = -1;
+  q.ring[c.slot] = u;
+  mbar_arrive(&q.full[c.slot]);   // release: the ring entry is visible to the waiters
+  if (++c.slot == UQ) {
+    c.slot = 0;
+    c.phase ^= 1;
+  }
+  return u;
+}
+
+// A consumer's next unit (called by one thread of the consumer).
+__device__ __forceinline__ int uq_consume(const UnitQueue& q, UnitCursor& c, int units,
+                                          volatile int* abort_flag, int* err, long long budget) {
+  if (!q.counter) {
+    const int u = c.next_static;
+    c.next_static += gridDim.x;
+    return u < units ? u : -1;
+  }
+  if (!mbar_wait(&q.full[c.slot], c.phase, abort_flag, err, budget)) return -2;
+  const int u = q.ring[c.slot];
+  mbar_arrive(&q.empty[c.slot]);
+  if (++c.slot == UQ) {
+    c.slot = 0;
+    c.phase ^= 1;
+  }
+  return u;
+}
+
 // Shared-memory pipeline of the operand stages and the TMEM accumulator sets.
 struct Pipe {
   uint8_t* smem;          // stage 0 (1024-byte aligned)
@@ -258,14 +319,18 @@ struct Pipe {
 __device__ __forceinline__ void producer_role(const Pipe& pp, const CUtensorMap* tmA,
                                               const CUtensorMap* tmB, const Tile* tiles, int ntiles,
                                               const GemmShape& sh, volatile int* abort_flag,
-                                              int* err) {
+                                              int* err, const UnitQueue& uq) {
   int stage = 0;
   uint32_t phase = 0;
   int pending[8];   // parity of the latest arming of each stage, -1 = never armed
   for (int s = 0; s < 8; ++s) pending[s] = -1;
   const int units = num_units(ntiles, sh.group);
   bool ok = true;
-  for (int u = blockIdx.x; u < units && ok && !*abort_flag; u += gridDim.x) {
+  UnitCursor cur;
+  cur.next_static = blockIdx.x;
+  while (ok && !*abort_flag) {
+    const int u = uq_produce(uq, cur, units, abort_flag, err, sh.wait);
+    if (u < 0) break;
     for (int t = u * sh.group; t < min(ntiles, (u + 1) * sh.group) && ok; ++t) {
       const Tile tl = tiles[t];
       for (int kc = 0; kc < sh.kchunks; ++kc) {
@@ -300,7 +365,8 @@ __device__ __forceinline__ void producer_role(const Pipe& pp, const CUtensorMap*
 // tiles) accumulates into set local % acc_bufs.
 template <int P>
 __device__ __forceinline__ void mma_role(const Pipe& pp, uint32_t tmem_base, int ntiles,
-                                         const GemmShape& sh, volatile int* abort_flag, int* err) {
+                                         const GemmShape& sh, volatile int* abort_flag, int* err,
+                                         const UnitQueue& uq) {
   int stage = 0;
   uint32_t phase = 0;
   int local = 0;
@@ -315,7 +381,11 @@ __device__ __forceinline__ void mma_role(const Pipe& pp, uint32_t tmem_base, int
   const int units = num_units(ntiles, sh.group);
   const int seg_len = (sh.kchunks + sh.ksegs - 1) / sh.ksegs;
   bool ok = true;
-  for (int u = blockIdx.x; u < units && ok && !*abort_flag; u += gridDim.x) {
+  UnitCursor cur;
+  cur.next_static = blockIdx.x;
+  while (ok && !*abort_flag) {
+    const int u = uq_consume(uq, cur, units, abort_flag, err, sh.wait);
+    if (u < 0) break;
     for (int t = u * sh.group; t < min(ntiles, (u + 1) * sh.group) && ok; ++t) {
      for (int k0 = 0; k0 < sh.kchunks; k0 += seg_len, ++local) {
       const int buf = nbuf == 2 ? (local & 1) : 0;
@@ -376,11 +446,14 @@ __device__ __forceinline__ void mma_role(const Pipe& pp, uint32_t tmem_base, int
 // int col0, const float* re, const float* im) const  for 32 columns at col0.
 // SEG: tiles accumulate K in sh.ksegs segments (compiled only where used, so
 // the register arrays of the segment sums cost nothing elsewhere).
+// units_taken: a device counter zeroed before the launch (dynamic hand-out of
+// the work units), or NULL (static order).
 // ---------------------------------------------------------------------------
 template <int P, class Epi, bool SEG>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
 gemm_split_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                const Tile* __restrict__ tiles, int ntiles, GemmShape sh, Epi epi, int* err) {
+                const Tile* __restrict__ tiles, int ntiles, GemmShape sh, Epi epi, int* err,
+                int* units_taken) {
   extern __shared__ uint8_t smem_raw[];
   Pipe pp;
   pp.smem = reinterpret_cast<uint8_t*>(
@@ -394,6 +467,13 @@ gemm_split_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
   pp.drain = pp.tmem_empty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(pp.drain + 1);
   __shared__ volatile int abort_flag;
+  __shared__ uint64_t uq_full[UQ], uq_empty[UQ];
+  __shared__ int uq_ring[UQ];
+  UnitQueue uq;
+  uq.counter = units_taken;
+  uq.ring = uq_ring;
+  uq.full = uq_full;
+  uq.empty = uq_empty;
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -409,6 +489,10 @@ gemm_split_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       mbar_init(&pp.tmem_empty[b], EPI_WARPS);
     }
     mbar_init(pp.drain, 1);
+    for (int q = 0; q < UQ; ++q) {
+      mbar_init(&uq_full[q], 1);
+      mbar_init(&uq_empty[q], 1 + EPI_WARPS);   // the MMA issuer and each epilogue warp
+    }
     abort_flag = 0;
     fence_barrier_init();
   }
@@ -419,9 +503,9 @@ gemm_split_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
   const uint32_t tmem_base = *tmem_slot;
 
   if (warp == 0) {
-    if (lane == 0) producer_role(pp, &tmA, &tmB, tiles, ntiles, sh, &abort_flag, err);
+    if (lane == 0) producer_role(pp, &tmA, &tmB, tiles, ntiles, sh, &abort_flag, err, uq);
   } else if (warp == 1) {
-    if (lane == 0) mma_role<P>(pp, tmem_base, ntiles, sh, &abort_flag, err);
+    if (lane == 0) mma_role<P>(pp, tmem_base, ntiles, sh, &abort_flag, err, uq);
   } else {
     // ---------------- epilogue (warps 2..9) ----------------
     const int quarter = warp & 3;          // TMEM lanes this warp may access
@@ -430,7 +514,14 @@ gemm_split_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     int local = 0;
     const int units = num_units(ntiles, sh.group);
     bool alive = true;
-    for (int u = blockIdx.x; u < units && alive; u += gridDim.x) {
+    UnitCursor cur;
+    cur.next_static = blockIdx.x;
+    while (alive) {
+      // lane 0 takes the warp's next unit, the warp follows
+      int u = 0;
+      if (lane == 0) u = uq_consume(uq, cur, units, &abort_flag, err, sh.wait);
+      u = __shfl_sync(0xffffffffu, u, 0);
+      if (u < 0) break;
       for (int t = u * sh.group; t < min(ntiles, (u + 1) * sh.group); ++t, ++local) {
         // one lane waits, the warp follows (the tcgen05.ld below is warp-collective);
         // a warp without a chunk still waits and arrives, keeping the count per phase
