@@ -562,7 +562,8 @@ def run_headline(args, bse, bi, prec, world, rank, local):
              "build_api": ("bse_plan_execute (plan created once, "
                            + ("BSE_PLAN_HERMITIAN: direct terms over the blocks k <= k', "
                               "the rest completed from the mirrors; " if herm else "")
-                           + f"stage-1 tile width autotuned: {plan.tile_cols} columns)"),
+                           + f"autotuned: stage-1 tiles of {plan.tile_cols} columns, "
+                           + "stage-2 tiles of {} columns, {}-deep pipeline)".format(*plan.stage2_shape)),
              "phase_ms_per_step": {k: v[1] / args.steps for k, v in phases.items()}}
 
     # ---- once: the plain FP64 GPU build and the error against it ----
@@ -689,6 +690,106 @@ def _eps_peaks(eps_im, omega):
     idx = [i for i in range(1, len(y) - 1) if y[i] > y[i - 1] and y[i] >= y[i + 1]
            and y[i] > 0.1 * y.max()]
     return idx
+
+
+def _dense_lowest(bse, n, A, B, nev):
+    """Lowest nev pairs (E, X+Y [nev, n]) of A, B by the FP64 dense route:
+    reduction, full eigensolve, X+Y of the lowest."""
+    import torch
+    S = torch.empty((n, n), dtype=torch.complex128, device="cuda")
+    L = torch.empty_like(S)
+    bse.bse_reduce(n, A, B, S, L)
+    E = torch.empty(n, dtype=torch.float64, device="cuda")
+    osc = torch.empty_like(E)
+    rho = torch.zeros(n, dtype=torch.complex128, device="cuda")
+    bse.bse_spectrum(n, S, L, rho, 1.0, 1.0, None, 0.05, E, osc, None)
+    X = torch.empty((nev, n), dtype=torch.complex128, device="cuda")
+    bse.bse_xpy(n, nev, S, L, E[:nev].contiguous(), X)
+    return E[:nev].contiguous(), X
+
+
+def run_mlp_family(args, bse, bi, prec, world, rank, local):
+    """The learned Davidson preconditioner on a family of problems along Q
+    (every Q drawn from the streams of Q index 0, so only v(G+Q) and c_Q change):
+    the middle Q of the configuration's line is the unseen one, the other four
+    train the 10-feature network.  Per training Q: the dense FP64 solve's
+    lowest nev pairs, then a Davidson trajectory started from the nearest
+    training Q's X+Y with features from the two nearest.  At the unseen Q: the
+    Davidson iterations and times of the diagonal preconditioner from a cold
+    start and from the nearest Q's X+Y, and of the trained network from the
+    same start, each against the dense solve's energies."""
+    import torch
+    if args.config not in ("c4s", "c2", "c1"):
+        raise SystemExit("--mlp-family draws whole problems: use c4s (or c1 / c2)")
+    cfg = bi.CONFIGS[args.config]
+    nq = len(cfg.q_abs)
+    test_q = nq // 2
+    pool = [q for q in range(nq) if q != test_q]
+    near = lambda q, k: sorted([j for j in pool if j != q],
+                               key=lambda j: abs(cfg.q_abs[j] - cfg.q_abs[q]))[:k]
+    nev, tol = args.nev, args.dav_tol or 1e-4
+    stream = torch.cuda.current_stream()
+    built, pairs = {}, {}
+    for q in range(nq):
+        p = bi.make_problem_torch(args.config, q_index=q, draws_of=0, seed=20190411 + rank)
+        d = bse.upload_problem(p)
+        n = p["nk"] * p["nv"] * p["nc"]
+        plan = bse.Plan([bse.make_problem_struct(d)], precision=prec, hermitian=True)
+        plan.execute()
+        plan.status()
+        plan.close()
+        built[q] = (d["A"], d["B"])
+        pairs[q] = _dense_lowest(bse, n, d["A"], d["B"], nev)
+        del d, p
+    torch.cuda.empty_cache()
+    net = bse.MLP(seed=5, n_features=10)
+    F, C, W = [], [], []
+    t0 = time.perf_counter()
+    for q in pool:
+        net.set_neighbours(torch.stack([pairs[j][1] for j in near(q, 2)]))
+        f, c, w = bse.bse_mlp_trajectory_samples(n, *built[q], *pairs[q], tol_ev=tol, max_iter=80,
+                                                 capacity=min(1 << 22, 160 * nev * n), mlp=net,
+                                                 start=pairs[near(q, 1)[0]][1])
+        F.append(f)
+        C.append(c)
+        W.append(w)
+    F, C, W = (torch.cat(x).contiguous() for x in (F, C, W))
+    t_samples = time.perf_counter() - t0
+    L0, _ = net.loss_grad(F, C, W)
+    t0 = time.perf_counter()
+    L1 = net.train(F, C, W, 600, 2e-3)
+    t_train = time.perf_counter() - t0
+    nbs = near(test_q, 2)
+    net.set_neighbours(torch.stack([pairs[j][1] for j in nbs]))
+    start = pairs[nbs[0]][1]
+    E_ref = pairs[test_q][0]
+    runs = {}
+    for name, pc, st in (("diagonal_cold", 0, None), ("diagonal_from_nearest_q", 0, start),
+                         ("learned_from_nearest_q", 1, start)):
+        E = torch.empty(nev, dtype=torch.float64, device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        converged = True
+        try:
+            it = bse.bse_lowest_excitons(n, *built[test_q], nev, E, None, tol_ev=tol,
+                                         max_iter=args.dav_max_iter, precond=pc,
+                                         mlp=net if pc else None, matvec_precision=prec, start=st)
+        except bse.BSEError as err:     # E holds the last Ritz values
+            if err.status != bse.BSE_ERR_NO_CONV:
+                raise
+            converged, it = False, args.dav_max_iter
+        e1.record(stream)
+        torch.cuda.synchronize()
+        runs[name] = {"iterations": it, "converged": converged, "ms": e0.elapsed_time(e1),
+                      "max_dE_meV_vs_dense": (E - E_ref).abs().max().item() * 1e3}
+    if rank == 0:
+        print(json.dumps({"metric": "learned Davidson preconditioner at an unseen Q",
+                          "config": args.config, "n": n, "nev": nev, "residual_tol_ev": tol,
+                          "q_abs": list(cfg.q_abs), "unseen_q_index": test_q,
+                          "training_q_indices": pool, "samples": int(C.numel()),
+                          "sampling_s": t_samples, "training_s": t_train,
+                          "training_loss": [L0, L1], "runs": runs}), flush=True)
+    return 0
 
 
 def run_eps_qs(args, bse, bi, prec, world, rank, local):
@@ -1050,6 +1151,9 @@ def main():
                     help="c5: compute every (k, k') block (no BSE_PLAN_HERMITIAN)")
     ap.add_argument("--e2e-steps", type=int, default=3,
                     help="c5: timed end-to-end steps (after one untimed)")
+    ap.add_argument("--mlp-family", action="store_true",
+                    help="learned Davidson preconditioner trained at four Q of a family, "
+                         "judged at the fifth (c4s)")
     ap.add_argument("--eps-qs", default=None,
                     help="comma-separated Q indices: eps_M of the mixed path against the plain "
                          "FP64 GPU path at each (dense reduction and eigensolve per path)")
@@ -1109,6 +1213,9 @@ def main():
     prec = prec_map[args.precision]
 
     # each rank: its own momentum transfers (Q replicas), resident in HBM
+    if args.mlp_family:
+        rc = run_mlp_family(args, bse, bi, prec, world, rank, local)
+        return rc
     if args.eps_qs:
         rc = run_eps_qs(args, bse, bi, prec, world, rank, local)
         if world > 1:

@@ -376,7 +376,7 @@ def _hermitian_pair_torch(nk, nb, ng, damp, gen, device):
 
 
 def pair_slab_torch(cfg: BSEConfig | str, k_begin: int, k_count: int, q_index: int = 0,
-                    seed: int = 20190411, device="cuda"):
+                    seed: int = 20190411, device="cuda", draws_of: Optional[int] = None):
     """m_vv and m_cc for the k rows [k_begin, k_begin + k_count) only, drawn on
     a torch device: ([k_count, nk, nv, nv, ng], [k_count, nk, nc, nc, ng]).
 
@@ -386,12 +386,13 @@ def pair_slab_torch(cfg: BSEConfig | str, k_begin: int, k_count: int, q_index: i
     is the conjugate transpose (b <-> b') of block (k', k), and a diagonal block
     is Hermitian in (b, b') with a real diagonal.  So S3 holds across slabs and
     any slab is reproducible on its own (the numbers differ from those of
-    make_problem_torch's whole arrays)."""
+    make_problem_torch's whole arrays).  draws_of as for make_problem_torch."""
     import torch
     if isinstance(cfg, str):
         cfg = CONFIGS[cfg]
     nk, ng = cfg.nk, cfg.ng
     nv, nc = cfg.window(q_index)
+    qd = q_index if draws_of is None else draws_of
     gvec = reciprocal_vectors(ng)
     damp = torch.as_tensor(1.0 / (1.0 + cfg.m_decay * (gvec ** 2).sum(1)), device=device)
     gen = torch.Generator(device=device)
@@ -404,7 +405,7 @@ def pair_slab_torch(cfg: BSEConfig | str, k_begin: int, k_count: int, q_index: i
             k = k_begin + r
             for kp in range(nk):
                 lo, hi = (k, kp) if k <= kp else (kp, k)
-                gen.manual_seed(_key(seed, name, q_index, lo, hi, "slab") % (1 << 62))
+                gen.manual_seed(_key(seed, name, qd, lo, hi, "slab") % (1 << 62))
                 blk = torch.randn((nb, nb, ng), dtype=torch.complex128, device=device, generator=gen)
                 blk *= damp
                 if k == kp:
@@ -418,7 +419,8 @@ def pair_slab_torch(cfg: BSEConfig | str, k_begin: int, k_count: int, q_index: i
 
 
 def make_problem_torch(cfg: BSEConfig | str, q_index: int = 0, seed: int = 20190411,
-                       device="cuda", k_slab: Optional[Tuple[int, int]] = None) -> Dict:
+                       device="cuda", k_slab: Optional[Tuple[int, int]] = None,
+                       draws_of: Optional[int] = None) -> Dict:
     """Draw a full-size problem directly on a torch device, for shapes whose
     inputs are too large to draw on the host (tens of GB).  Same recipe as
     make_problem (distributions, damping, W(q) construction, symmetries S1-S4,
@@ -427,40 +429,43 @@ def make_problem_torch(cfg: BSEConfig | str, q_index: int = 0, seed: int = 20190
     to the host.  Array entries are torch tensors on `device`.
 
     k_slab = (k_begin, k_count) draws m_vv and m_cc for those k rows only
-    (pair_slab_torch); every other array is whole."""
+    (pair_slab_torch); every other array is whole.  draws_of = j draws every
+    random array from the streams of Q index j (a family along Q, as in
+    make_problem)."""
     import torch
     if isinstance(cfg, str):
         cfg = CONFIGS[cfg]
     n, nk = cfg.grid, cfg.nk
     nv, nc = cfg.window(q_index)
+    qd = q_index if draws_of is None else draws_of
     ng = cfg.ng
     gvec = reciprocal_vectors(ng)
     qvec = np.array([cfg.q_abs[q_index], 0.0, 0.0])
     g2 = (gvec ** 2).sum(1)
     damp = torch.as_tensor(1.0 / (1.0 + cfg.m_decay * g2), device=device)
 
-    ge = _torch_gen(device, seed, "energies", q_index, "torch")
+    ge = _torch_gen(device, seed, "energies", qd, "torch")
     lo_v, hi_v = cfg.e_v_range
     lo_c, hi_c = cfg.e_c_range
     e_v = lo_v + (hi_v - lo_v) * torch.rand((nk, nv), dtype=torch.float64, device=device, generator=ge)
     e_c = lo_c + (hi_c - lo_c) * torch.rand((nk, nc), dtype=torch.float64, device=device, generator=ge)
 
     m_x = torch.randn((nk, nv, nc, ng), dtype=torch.complex128, device=device,
-                      generator=_torch_gen(device, seed, "m_x", q_index, "torch"))
+                      generator=_torch_gen(device, seed, "m_x", qd, "torch"))
     m_x *= damp
     if k_slab is None:
-        m_vv = _hermitian_pair_torch(nk, nv, ng, damp, _torch_gen(device, seed, "m_vv", q_index, "torch"), device)
-        m_cc = _hermitian_pair_torch(nk, nc, ng, damp, _torch_gen(device, seed, "m_cc", q_index, "torch"), device)
+        m_vv = _hermitian_pair_torch(nk, nv, ng, damp, _torch_gen(device, seed, "m_vv", qd, "torch"), device)
+        m_cc = _hermitian_pair_torch(nk, nc, ng, damp, _torch_gen(device, seed, "m_cc", qd, "torch"), device)
     else:
-        m_vv, m_cc = pair_slab_torch(cfg, k_slab[0], k_slab[1], q_index, seed, device)
+        m_vv, m_cc = pair_slab_torch(cfg, k_slab[0], k_slab[1], q_index, seed, device, draws_of)
     n_vc = torch.randn((nk, nk, nv, nc, ng), dtype=torch.complex128, device=device,
-                       generator=_torch_gen(device, seed, "n_vc", q_index, "torch"))
+                       generator=_torch_gen(device, seed, "n_vc", qd, "torch"))
     n_vc *= damp
 
     q_minus, q_plus, neg = pair_maps(n)
     gv = torch.as_tensor(gvec, device=device)
     dg = torch.cdist(gv, gv)
-    gw = _torch_gen(device, seed, "w", q_index, "torch")
+    gw = _torch_gen(device, seed, "w", qd, "torch")
     w = torch.empty((nk, ng, ng), dtype=torch.complex128, device=device)
     iu = torch.triu_indices(ng, ng, 1, device=device)
     d = torch.arange(ng, device=device)

@@ -205,6 +205,13 @@ int bse_plan_status(void* plan, void* cuda_stream);
 int bse_plan_set_wait_limit(void* plan, double seconds);
 /* output-column tile width the plan's stage-1 GEMM uses (0 for FP64 plans) */
 int bse_plan_tile_cols(const void* plan);
+/* The tensor-core stage-2 launches' output-column tile width and pipeline
+ * depth (both 0 when the plan has none), host outputs.  With
+ * BSE_PLAN_AUTOTUNE both are timed at creation over the widths {the default,
+ * 32} and the depths {the deepest that fits shared memory, one less}; the
+ * timed launches subtract from blocks of A and B that every execute stores
+ * first.  Errors: BSE_ERR_ARG (NULL). */
+int bse_plan_stage2_shape(const void* plan, int32_t* tile_cols, int32_t* stages);
 /* 1 if the plan's direct terms run as the fused launch, else 0 */
 int bse_plan_fused(const void* plan);
 void bse_plan_destroy(void* plan);
@@ -409,23 +416,57 @@ int bse_lowest_excitons_from(int32_t n, const bse_c128* A, const bse_c128* B, in
                              void* cuda_stream);
 
 /* ---- learned preconditioner for bse_lowest_excitons -------------------------
- * Not in the paper: a per-transition network (4 features -> 128 -> 128 -> 1,
- * ReLU, FP16 weights, FP32 arithmetic) predicting a factor c that rescales the
- * diagonal gain of the Davidson correction, t_a = c r_a / (D_a - E), D the
- * diagonal of A+B (residual of (A+B)(X+Y) = E(X-Y)) or of A-B (the other
- * equation); features [D_a - E, D'_a - E, off-diagonal row norm of A, E/10].
+ * Not in the paper: a per-transition network (F features -> 128 -> 128 -> 1,
+ * ReLU, FP16 weights, FP32 accumulation; the 128 x 128 layer of the forward
+ * pass on the tensor cores) predicting a factor c that rescales the diagonal
+ * gain of the Davidson correction, t_a = c r_a / (D_a - E), D the diagonal of
+ * A+B (residual r of (A+B)(X+Y) = E(X-Y), correcting x = X+Y) or of A-B (the
+ * other equation, correcting x = X-Y).  Feature sets, with D' the other
+ * equation's diagonal and S_a the off-diagonal row norm of A:
+ *   F = 4   [D_a - E, D'_a - E, S_a, E / 10]
+ *   F = 10  [(D_a - E)/10, (D'_a - E)/10, S_a/10, E/100] then, for each of
+ *           the (up to) two neighbour blocks of bse_mlp_set_neighbours, with
+ *           v the neighbour's X+Y of the same exciton, u = v/|v| times the
+ *           unit phase of v^H x, b = r/(D - E) (|D - E| clamped to >= 0.01 eV)
+ *           and d = u - x/|x|: |u_a| sqrt(n), Re(conj(b_a) d_a) sqrt(n)/|b_a|,
+ *           Im(conj(b_a) d_a) sqrt(n)/|b_a| (0 where b_a = 0; 0 for a missing
+ *           second neighbour).
  * An untrained network gives c ~ 1, the diagonal preconditioner.
  * The handle owns device memory on the device current at creation. */
 
-/* Create with deterministic initial weights from seed; n_features must be 4
- * and hidden 128 (BSE_ERR_UNSUPPORTED otherwise). */
+/* Create with deterministic initial weights from seed; n_features 4 or 10,
+ * hidden 128 (BSE_ERR_UNSUPPORTED otherwise). */
 int bse_mlp_create(void** mlp, int32_t n_features, int32_t hidden, uint64_t seed);
 void bse_mlp_destroy(void* mlp);
 int64_t bse_mlp_num_params(const void* mlp);
-/* Parameters in the order W1 [128][4], b1 [128], W2 [128][128], b2, w3 [128],
+/* Parameters in the order W1 [128][F], b1 [128], W2 [128][128], b2, w3 [128],
  * b3 [1] (row-major), as the FP16 values the network uses, to / from host. */
 int bse_mlp_get_params(const void* mlp, float* host, int64_t count);
 int bse_mlp_set_params(void* mlp, const float* host, int64_t count);
+
+/* The neighbouring momentum transfers of the 10-feature set: count (1 or 2)
+ * blocks of [n x nev] column-major complex128 (device, 16-byte aligned), block
+ * i the X+Y of the nev lowest excitons at neighbour Q_i in ascending order,
+ * with the transition order of the problems solved.  The handle keeps the
+ * pointer: the caller keeps the blocks alive and unchanged while solves,
+ * samples or features use the network; nbr = NULL with count = 0 clears.
+ * A 10-feature network without neighbours for the problem's n and at least
+ * its nev excitons is refused (BSE_ERR_ARG) by every call that needs them.
+ * Syncs. */
+int bse_mlp_set_neighbours(void* mlp, int32_t n, int32_t nev, const bse_c128* nbr, int32_t count,
+                           void* cuda_stream);
+
+/* The network's input features for ncol residual columns (all device):
+ * eq [ncol] int32, 0 = residual of the (A+B) equation, 1 = of the (A-B)
+ * equation; lam [ncol] int32, the exciton (column of the neighbour blocks);
+ * theta [ncol] its energy (eV); A, B as for bse_lowest_excitons (B may be
+ * NULL); R and X [n x ncol] column-major (ld n): the residuals and the
+ * vectors they correct (X+Y for eq 0, X-Y for eq 1).  feat_out
+ * [ncol n][F] float32, sample s = c n + a.  Syncs. */
+int bse_mlp_features(const void* mlp, int32_t n, int32_t ncol, const int32_t* eq,
+                     const int32_t* lam, const double* theta, const bse_c128* A,
+                     const bse_c128* B, int64_t ld, const bse_c128* R, const bse_c128* X,
+                     float* feat_out, void* cuda_stream);
 
 /* Training samples from exact pairs (E [nev], X+Y [n x nev] column-major, both
  * device) of the full problem: X-Y = (A+B)(X+Y)/E, both perturbed by eps p
@@ -442,16 +483,20 @@ int bse_mlp_samples(int32_t n, const bse_c128* A, const bse_c128* B, int64_t ld,
 
 /* Training samples from a Davidson trajectory: runs bse_lowest_excitons with
  * the diagonal preconditioner on (A, B) whose exact lowest pairs (E_exact
- * [nev], XpY_exact [n x nev], device) are known; at every iteration each
- * unconverged pair contributes, for both half-size equations, the samples of
- * its residual against the current error (Ritz vector minus the exact vector
- * aligned in phase), defined as in bse_mlp_samples with that error as the
- * step.  Stops at convergence (tol_ev), max_iter or when the next vector's
- * samples would exceed capacity; count_out (host) receives the number
- * written.  Outputs as in bse_mlp_samples (device).  Syncs. */
+ * [nev], XpY_exact [n x nev], device) are known, started from V0 [n x k0]
+ * as bse_lowest_excitons_from does (V0 = NULL, k0 = 0: unit vectors); at
+ * every iteration each unconverged pair contributes, for both half-size
+ * equations, the samples of its residual against the current error (Ritz
+ * vector minus the exact vector aligned in phase): target and weight as in
+ * bse_mlp_samples with that error as the step, features of mlp's set (mlp =
+ * NULL: the 4-feature set; a 10-feature network needs its neighbours).
+ * Stops at convergence (tol_ev), max_iter or when the next vector's samples
+ * would exceed capacity; count_out (host) receives the number written.
+ * feat_out [capacity][F], target_out, weight_out [capacity] (device).  Syncs. */
 int bse_mlp_trajectory_samples(int32_t n, const bse_c128* A, const bse_c128* B, int64_t ld,
                                int32_t nev, const double* E_exact, const bse_c128* XpY_exact,
-                               double tol_ev, int32_t max_iter, int64_t capacity, float* feat_out,
+                               double tol_ev, int32_t max_iter, const void* mlp,
+                               const bse_c128* V0, int32_t k0, int64_t capacity, float* feat_out,
                                float* target_out, float* weight_out, int64_t* count_out,
                                void* cuda_stream);
 

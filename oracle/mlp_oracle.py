@@ -19,6 +19,13 @@ writes out, from their definitions, the quantities its GPU kernels compute:
             and B = 0: the diagonal preconditioner is then exact)
   features  [D_a - E, D'_a - E, S_a, E / 10]: this equation's diagonal, the
             other equation's, the off-diagonal row norm of A, the energy
+  features10  [(D_a - E)/10, (D'_a - E)/10, S_a/10, E/100] then, per
+            neighbouring momentum transfer i (up to two) whose exact X+Y of
+            the same exciton is v_i: with x the vector the residual r corrects
+            (X+Y for the (A+B) equation, X-Y for the other), b = r/(D - E),
+            u = v_i/|v_i| times the unit phase of v_i^H x and d = u - x/|x|,
+            the three values |u_a| sqrt(n), Re(conj(b_a) d_a) sqrt(n)/|b_a|
+            and Im(conj(b_a) d_a) sqrt(n)/|b_a| (zero where b_a = 0)
   network   y = w3 . relu(W2 relu(W1 f + b1) + b2) + b3, factor c = 1 + y
   loss      sum_s w_s (c_s - c*_s)^2 / sum_s w_s
   gradient  backpropagation of that loss (pinned by finite differences in
@@ -48,6 +55,33 @@ def diag_features(A: np.ndarray, B: np.ndarray):
 
 def features(dq: np.ndarray, dother: np.ndarray, s: np.ndarray, e: float) -> np.ndarray:
     return np.stack([dq - e, dother - e, s, np.full_like(dq, e / 10.0)], axis=1)
+
+
+def features10(dq: np.ndarray, dother: np.ndarray, s: np.ndarray, e: float, r: np.ndarray,
+               x: np.ndarray, nbrs) -> np.ndarray:
+    """The 10 features of one residual column r (length n) of energy e that
+    corrects the vector x; nbrs: the neighbours' X+Y of the same exciton (0 to 2
+    vectors; absent ones give zero features)."""
+    n = len(r)
+    cols = [(dq - e) / 10.0, (dother - e) / 10.0, s / 10.0, np.full(n, e / 100.0)]
+    b = r / _clamp(dq - e)
+    bm = np.abs(b)
+    xn = x / np.linalg.norm(x)
+    for i in range(2):
+        if i >= len(nbrs):
+            cols += [np.zeros(n)] * 3
+            continue
+        v = nbrs[i]
+        z = np.vdot(v, x)                      # v^H x
+        ph = z / abs(z) if abs(z) > 0 else 1.0
+        u = v / np.linalg.norm(v) * ph
+        d = u - xn
+        rel = np.conj(b) * d
+        safe = np.where(bm > 0, bm, 1.0)
+        cols += [np.abs(u) * np.sqrt(n),
+                 np.where(bm > 0, rel.real / safe, 0.0) * np.sqrt(n),
+                 np.where(bm > 0, rel.imag / safe, 0.0) * np.sqrt(n)]
+    return np.stack(cols, axis=1)
 
 
 def samples(A, B, E, xpy, noise, eps):

@@ -60,8 +60,10 @@ EXPORTED = ("bse_build_kernel", "bse_reduce", "bse_spectrum", "bse_last_error", 
             "bse_phase_report", "bse_build_kernel_fp64_static", "bse_lowest_excitons",
             "bse_mlp_create", "bse_mlp_destroy", "bse_mlp_num_params", "bse_mlp_get_params",
             "bse_mlp_set_params", "bse_mlp_samples", "bse_mlp_loss_grad", "bse_mlp_train",
-            "bse_mlp_predict", "bse_xpy", "bse_mlp_trajectory_samples", "bse_plan_create",
+            "bse_mlp_predict", "bse_xpy", "bse_mlp_trajectory_samples", "bse_mlp_set_neighbours",
+            "bse_mlp_features", "bse_plan_create",
             "bse_plan_execute", "bse_plan_status", "bse_plan_tile_cols", "bse_plan_destroy",
+            "bse_plan_stage2_shape",
             "bse_plan_fused", "bse_spectrum_tensor", "bse_loss_function",
             "bse_lowest_excitons_from", "bse_rpa_screening", "bse_plan_set_wait_limit",
             "bse_pair_elements")
@@ -104,6 +106,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.bse_plan_execute.argtypes = [vp, vp]
     lib.bse_plan_status.argtypes = [vp, vp]
     lib.bse_plan_tile_cols.argtypes = [vp]
+    lib.bse_plan_stage2_shape.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    lib.bse_plan_stage2_shape.restype = ctypes.c_int
     lib.bse_plan_fused.argtypes = [vp]
     lib.bse_plan_destroy.argtypes = [vp]
     lib.bse_plan_destroy.restype = None
@@ -124,8 +128,12 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.bse_mlp_get_params.argtypes = [vp, f32p, i64]
     lib.bse_mlp_set_params.argtypes = [vp, f32p, i64]
     lib.bse_mlp_samples.argtypes = [i32, vp, vp, i64, i32, vp, vp, vp, dbl, vp, vp, vp, vp]
-    lib.bse_mlp_trajectory_samples.argtypes = [i32, vp, vp, i64, i32, vp, vp, dbl, i32, i64,
-                                               vp, vp, vp, ctypes.POINTER(i64), vp]
+    lib.bse_mlp_trajectory_samples.argtypes = [i32, vp, vp, i64, i32, vp, vp, dbl, i32, vp, vp,
+                                               i32, i64, vp, vp, vp, ctypes.POINTER(i64), vp]
+    lib.bse_mlp_set_neighbours.argtypes = [vp, i32, i32, vp, i32, vp]
+    lib.bse_mlp_set_neighbours.restype = ctypes.c_int
+    lib.bse_mlp_features.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, i64, vp, vp, vp, vp]
+    lib.bse_mlp_features.restype = ctypes.c_int
     lib.bse_mlp_trajectory_samples.restype = ctypes.c_int
     lib.bse_mlp_loss_grad.argtypes = [vp, vp, vp, vp, i64, ctypes.POINTER(dbl), f32p, vp]
     lib.bse_mlp_train.argtypes = [vp, vp, vp, vp, i64, i32, dbl, ctypes.POINTER(dbl), vp]
@@ -492,7 +500,44 @@ class MLP:
         h = ctypes.c_void_p()
         _check(lib.bse_mlp_create(ctypes.byref(h), n_features, hidden, seed))
         self.handle = h
+        self.n_features = n_features
         self.num_params = int(lib.bse_mlp_num_params(h))
+        self._nbr = None
+
+    def set_neighbours(self, nbr, stream=None) -> None:
+        """The 10-feature set's neighbouring-Q X+Y: a CUDA complex128 tensor
+        [count, nev, n] (block i, exciton lambda: column-major n x nev per
+        block), count 1 or 2, kept alive by this object; None clears."""
+        import torch
+        if nbr is None:
+            _check(load().bse_mlp_set_neighbours(self.handle, 0, 0, None, 0, _stream(stream)))
+            self._nbr = None
+            return
+        if nbr.dim() != 3:
+            raise ValueError("nbr must have shape [count, nev, n]")
+        nbr = nbr.contiguous()
+        cnt, nev, n = nbr.shape
+        _check(load().bse_mlp_set_neighbours(self.handle, n, nev,
+                                             _ptr(nbr, torch.complex128, "nbr"), cnt,
+                                             _stream(stream)))
+        self._nbr = nbr
+
+    def features(self, A, B, eq, lam, theta, R, X, stream=None):
+        """Input features (bse_mlp_features) of the residual columns R [ncol, n]
+        correcting X [ncol, n]; eq, lam int32 and theta float64 CUDA tensors of
+        ncol; returns a float32 CUDA tensor [ncol n, F]."""
+        import torch
+        ncol, n = R.shape
+        a, ld = _matrix_ptr(A, n, "A")
+        b = _matrix_ptr(B, n, "B")[0] if B is not None else None
+        feat = torch.empty((ncol * n, self.n_features), dtype=torch.float32, device="cuda")
+        _check(load().bse_mlp_features(self.handle, n, ncol, _ptr(eq, torch.int32, "eq"),
+                                       _ptr(lam, torch.int32, "lam"),
+                                       _ptr(theta, torch.float64, "theta"), a, b, ld,
+                                       _ptr(R, torch.complex128, "R"),
+                                       _ptr(X, torch.complex128, "X"), _ptr(feat),
+                                       _stream(stream)))
+        return feat
 
     def close(self):
         if self.handle:
@@ -564,9 +609,11 @@ def bse_mlp_samples(n: int, A, B, E, XpY, noise, eps: float, stream=None):
 
 
 def bse_mlp_trajectory_samples(n: int, A, B, E, XpY, tol_ev: float = 1e-6, max_iter: int = 60,
-                               capacity: int = 1 << 20, stream=None):
+                               capacity: int = 1 << 20, mlp=None, start=None, stream=None):
     """Samples recorded along a diagonal-preconditioned Davidson run whose exact
-    pairs (E, XpY [nev, n]) are known; returns (feat, target, weight) trimmed."""
+    pairs (E, XpY [nev, n]) are known, with mlp's feature set (None: 4
+    features) and started from start ([k0, n], None: unit vectors); returns
+    (feat, target, weight) trimmed."""
     import torch
     lib = load()
     a, ld = _matrix_ptr(A, n, "A")
@@ -574,13 +621,20 @@ def bse_mlp_trajectory_samples(n: int, A, B, E, XpY, tol_ev: float = 1e-6, max_i
     nev = E.numel()
     if XpY.shape != (nev, n):
         raise ValueError("XpY must have shape [nev, n]")
-    feat = torch.empty((capacity, 4), dtype=torch.float32, device="cuda")
+    nf = mlp.n_features if mlp is not None else 4
+    feat = torch.empty((capacity, nf), dtype=torch.float32, device="cuda")
     target = torch.empty(capacity, dtype=torch.float32, device="cuda")
     weight = torch.empty(capacity, dtype=torch.float32, device="cuda")
     cnt = ctypes.c_int64(0)
+    v0, k0 = None, 0
+    if start is not None:
+        if start.dim() != 2 or start.shape[1] != n:
+            raise ValueError("start must have shape [k0, n] (column-major n x k0)")
+        v0, k0 = _ptr(start, torch.complex128, "start"), start.shape[0]
     _check(lib.bse_mlp_trajectory_samples(n, a, b, ld, nev, _ptr(E, torch.float64, "E"),
                                           _ptr(XpY, torch.complex128, "XpY"), float(tol_ev),
-                                          int(max_iter), int(capacity), _ptr(feat), _ptr(target),
+                                          int(max_iter), mlp.handle if mlp is not None else None,
+                                          v0, k0, int(capacity), _ptr(feat), _ptr(target),
                                           _ptr(weight), ctypes.byref(cnt), _stream(stream)))
     c = cnt.value
     return feat[:c].contiguous(), target[:c].contiguous(), weight[:c].contiguous()
@@ -618,6 +672,13 @@ class Plan:
     @property
     def tile_cols(self) -> int:
         return int(load().bse_plan_tile_cols(self.handle))
+
+    @property
+    def stage2_shape(self):
+        """(tile width, pipeline depth) of the tensor-core stage 2, (0, 0) if none."""
+        t, st = ctypes.c_int32(0), ctypes.c_int32(0)
+        _check(load().bse_plan_stage2_shape(self.handle, ctypes.byref(t), ctypes.byref(st)))
+        return t.value, st.value
 
     @property
     def fused(self) -> bool:

@@ -309,6 +309,16 @@ extern "C" int bse_plan_tile_cols(const void* plan) {
   return plan ? plan_tile_cols(static_cast<const BatchPlan*>(plan)) : 0;
 }
 
+extern "C" int bse_plan_stage2_shape(const void* plan, int32_t* tile_cols, int32_t* stages) {
+  return guarded([&] {
+    BSE_CHECK_ARG(plan && tile_cols && stages, "NULL argument");
+    int t = 0, st = 0;
+    plan_stage2_shape(static_cast<const BatchPlan*>(plan), &t, &st);
+    *tile_cols = t;
+    *stages = st;
+  });
+}
+
 extern "C" int bse_plan_fused(const void* plan) {
   return plan ? plan_fused(static_cast<const BatchPlan*>(plan)) : 0;
 }
@@ -558,9 +568,57 @@ extern "C" int bse_mlp_create(void** mlp, int32_t n_features, int32_t hidden, ui
   return guarded([&] {
     BSE_CHECK_ARG(mlp != nullptr, "mlp is NULL");
     *mlp = nullptr;
-    if (n_features != 4 || hidden != 128)
-      throw Error(BSE_ERR_UNSUPPORTED, "this library provides n_features = 4 and hidden = 128");
-    *mlp = mlp_create(seed);
+    if (!mlp_features_supported(n_features) || hidden != 128)
+      throw Error(BSE_ERR_UNSUPPORTED,
+                  "this library provides n_features = 4 or 10 and hidden = 128");
+    *mlp = mlp_create(n_features, seed);
+  });
+}
+
+extern "C" int bse_mlp_set_neighbours(void* mlp, int32_t n, int32_t nev, const bse_c128* nbr,
+                                      int32_t count, void* cuda_stream) {
+  return guarded([&] {
+    BSE_CHECK_ARG(mlp != nullptr, "mlp is NULL");
+    BSE_CHECK_ARG(nbr == nullptr ? count == 0 : (count == 1 || count == 2),
+                  "neighbour blocks: NULL with count 0, or 1 or 2 blocks");
+    if (nbr) {
+      BSE_CHECK_ARG(n >= 1 && nev >= 1 && nev <= n, "bad n or nev");
+      BSE_CHECK_ARG(((uintptr_t)nbr & 15) == 0, "nbr must be 16-byte aligned");
+    }
+    mlp_set_neighbours(static_cast<MlpNet*>(mlp), n, nev, nbr, count,
+                       static_cast<cudaStream_t>(cuda_stream));
+    BSE_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream)));
+  });
+}
+
+extern "C" int bse_mlp_features(const void* mlp, int32_t n, int32_t ncol, const int32_t* eq,
+                                const int32_t* lam, const double* theta, const bse_c128* A,
+                                const bse_c128* B, int64_t ld, const bse_c128* R,
+                                const bse_c128* X, float* feat_out, void* cuda_stream) {
+  return guarded([&] {
+    BSE_CHECK_ARG(mlp != nullptr, "mlp is NULL");
+    BSE_CHECK_ARG(n >= 1 && ld >= n && ncol >= 1, "bad n, ld or ncol");
+    BSE_CHECK_ARG(eq && lam && theta && A && R && X && feat_out, "NULL argument");
+    const MlpNet* net = static_cast<const MlpNet*>(mlp);
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    if (mlp_num_features(net) == 10) {
+      std::vector<int32_t> lh(ncol);
+      BSE_CUDA(cudaMemcpyAsync(lh.data(), lam, ncol * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      BSE_CUDA(cudaStreamSynchronize(s));
+      int lmax = 0;
+      for (int32_t l : lh) {
+        BSE_CHECK_ARG(l >= 0, "lam must be >= 0");
+        lmax = std::max(lmax, (int)l);
+      }
+      mlp_check_neighbours(net, n, lmax + 1);
+    }
+    keep_pool_memory();
+    DeviceBuffer dp((size_t)n * 8, s), dm((size_t)n * 8, s), sr((size_t)n * 8, s);
+    mlp_diag_features(n, A, B, ld, dp.as<double>(), dm.as<double>(), sr.as<double>(), s);
+    mlp_features(net, n, ncol, eq, lam, theta, dp.as<double>(), dm.as<double>(), sr.as<double>(),
+                 reinterpret_cast<const double2*>(R), n, reinterpret_cast<const double2*>(X), n,
+                 feat_out, s);
+    BSE_CUDA(cudaStreamSynchronize(s));
   });
 }
 
@@ -604,7 +662,8 @@ extern "C" int bse_mlp_samples(int32_t n, const bse_c128* A, const bse_c128* B, 
 extern "C" int bse_mlp_trajectory_samples(int32_t n, const bse_c128* A, const bse_c128* B,
                                           int64_t ld, int32_t nev, const double* E_exact,
                                           const bse_c128* XpY_exact, double tol_ev,
-                                          int32_t max_iter, int64_t capacity, float* feat_out,
+                                          int32_t max_iter, const void* mlp, const bse_c128* V0,
+                                          int32_t k0, int64_t capacity, float* feat_out,
                                           float* target_out, float* weight_out,
                                           int64_t* count_out, void* cuda_stream) {
   return guarded([&] {
@@ -613,12 +672,19 @@ extern "C" int bse_mlp_trajectory_samples(int32_t n, const bse_c128* A, const bs
     BSE_CHECK_ARG(A && E_exact && XpY_exact && feat_out && target_out && weight_out,
                   "NULL argument");
     BSE_CHECK_ARG(capacity >= 0 && max_iter >= 1 && tol_ev > 0.0, "bad capacity, max_iter or tol");
+    if (V0 || k0) {
+      BSE_CHECK_ARG(V0 && k0 >= 1 && k0 <= 4 * nev && k0 <= n,
+                    "a starting block needs V0 and 1 <= k0 <= min(4 nev, n)");
+      BSE_CHECK_ARG(((uintptr_t)V0 & 15) == 0, "V0 must be 16-byte aligned");
+    }
+    if (mlp) mlp_check_neighbours(static_cast<const MlpNet*>(mlp), n, nev);
     keep_pool_memory();
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     std::vector<double> eh(nev);
     BSE_CUDA(cudaMemcpyAsync(eh.data(), E_exact, nev * sizeof(double), cudaMemcpyDeviceToHost, s));
     BSE_CUDA(cudaStreamSynchronize(s));
     TrajectorySink sink;
+    sink.net = static_cast<const MlpNet*>(mlp);
     sink.xpy_exact = XpY_exact;
     sink.e_exact = eh.data();
     sink.capacity = capacity;
@@ -628,7 +694,7 @@ extern "C" int bse_mlp_trajectory_samples(int32_t n, const bse_c128* A, const bs
     DeviceBuffer e_out((size_t)nev * 8, s);
     try {
       davidson_fp64(n, A, B, ld, nev, tol_ev, max_iter, 0, nullptr, e_out.as<double>(), nullptr,
-                    nullptr, s, &sink);
+                    nullptr, s, &sink, BSE_PREC_FP64, V0, k0);
     } catch (const Error& e) {
       if (e.status != BSE_ERR_NO_CONV) throw;   // recording ends with the iteration limit
     }

@@ -155,6 +155,7 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
 void plan_execute(BatchPlan* plan, cudaStream_t s);
 int plan_status(BatchPlan* plan, cudaStream_t s);
 int plan_tile_cols(const BatchPlan* plan);
+void plan_stage2_shape(const BatchPlan* plan, int* tile_cols, int* stages);
 int plan_fused(const BatchPlan* plan);
 void plan_set_wait(BatchPlan* plan, double seconds);
 void plan_destroy(BatchPlan* plan);

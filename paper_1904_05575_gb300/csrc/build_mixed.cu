@@ -1266,6 +1266,7 @@ struct ExchangeBatchEpi {   // ExchangeEpi with per-problem outputs
 // process-wide autotuning results: padded NG -> best output-column tile width
 std::mutex g_tune_mutex;
 std::map<int, int> g_tuned_nt;
+std::map<int64_t, std::pair<int, int>> g_tuned_s2;   // stage-2 (tile width, depth)
 
 }  // namespace
 
@@ -1319,7 +1320,7 @@ struct BatchPlan {
   // other pair side in the layout of their operand role (A: 2P planes, B: 3P)
   int64_t ta_rows = 0, tb_rows = 0, x2a_rows = 0, x2b_rows = 0;
   DevMem ta, tb, x2a, x2b, touts, s2tiles, s2tiles_t, s2params;
-  int n_s2tiles = 0, n_s2tiles_t = 0, nt2 = 0;
+  int n_s2tiles = 0, n_s2tiles_t = 0, nt2 = 0, s2_stages = 0, s2_max_cols = 0;
   tc::GemmShape sh_2{};
   CUtensorMap ma_2{}, mb_2{}, ma_2t{}, mb_2t{};   // rows = X side / rows = T side
   // fused direct term (stage 1 + stage 2 in one launch)
@@ -1466,6 +1467,58 @@ void plan_execute_mixed(BatchPlan& pl, cudaStream_t s) {
   }
 }
 
+// Tensor-core stage 2: products feed A and B directly, K segments of at most
+// 8 steps (at NG = 500, 4-, 8- and 16-step segments give A and B within
+// 3.41e-7, 3.42e-7 and 3.43e-7 of the FP64 build; 8 is 6 % faster than 4).
+int s2_default_cols(const BatchPlan& pl) {
+  return tile_cols(round_up(pl.s2_max_cols, 32), pl.Kp, 8, 8);
+}
+
+// The tensor-core stage-2 tiles at nt2 output columns per tile (the pair
+// blocks' tiles in pair order), pipeline depth stages (0: the deepest that
+// fits shared memory).
+void plan_set_s2_tiles(BatchPlan& pl, int nt2, int stages) {
+  std::vector<tc::Tile> tiles, tiles_t;
+  for (size_t ti = 0; ti < pl.terms.size(); ++ti) {
+    const BatchPlan::Term& t = pl.terms[ti];
+    if (!t.tc2) continue;
+    const Stage2Args& a = t.s2;
+    for (int j = 0; j < t.nact; ++j) {
+      const int pr = t.act_h[j];
+      const int64_t xr = t.x2_row0 + (int64_t)j * a.rows_x;            // X rows of the pair
+      const int64_t tr = t.t_row0 + (int64_t)t.slot_h[pr] * a.rows_t;  // T rows of the pair
+      if (t.rows_t_side) {
+        for (int m0 = 0; m0 < a.rows_t; m0 += tc::BM)
+          for (int n0 = 0; n0 < a.rows_x; n0 += nt2)
+            tiles_t.push_back({(int)(tr + m0), std::min(tc::BM, a.rows_t - m0), (int)(xr + n0), n0,
+                               std::min(nt2, a.rows_x - n0), pr * a.rows_t + m0, (int)ti});
+      } else {
+        for (int m0 = 0; m0 < a.rows_x; m0 += tc::BM)
+          for (int n0 = 0; n0 < a.rows_t; n0 += nt2)
+            tiles.push_back({(int)(xr + m0), std::min(tc::BM, a.rows_x - m0), (int)(tr + n0), n0,
+                             std::min(nt2, a.rows_t - n0), pr * a.rows_x + m0, (int)ti});
+      }
+    }
+  }
+  const int ap = tc::a_planes(pl.pieces), bp = tc::b_planes(pl.pieces);
+  pl.nt2 = nt2;
+  pl.n_s2tiles = (int)tiles.size();
+  pl.s2tiles = upload_mem(tiles);
+  pl.n_s2tiles_t = (int)tiles_t.size();
+  pl.s2tiles_t = upload_mem(tiles_t);
+  pl.sh_2 = make_shape(nt2, pl.Kp, pl.pieces, 8, 8);
+  if (stages > 0) pl.sh_2.stages = std::min(pl.sh_2.stages, stages);
+  pl.s2_stages = pl.sh_2.stages;
+  if (pl.n_s2tiles) {
+    pl.ma_2 = make_plane_map(pl.x2a.as<__nv_bfloat16>(), pl.Kp, (int)pl.x2a_rows, ap, tc::BM);
+    pl.mb_2 = make_plane_map(pl.tb.as<__nv_bfloat16>(), pl.Kp, (int)pl.tb_rows, bp, nt2);
+  }
+  if (pl.n_s2tiles_t) {
+    pl.ma_2t = make_plane_map(pl.ta.as<__nv_bfloat16>(), pl.Kp, (int)pl.ta_rows, ap, tc::BM);
+    pl.mb_2t = make_plane_map(pl.x2b.as<__nv_bfloat16>(), pl.Kp, (int)pl.x2b_rows, bp, nt2);
+  }
+}
+
 void plan_set_tiles(BatchPlan& pl, int nt) {
   pl.nt_g = nt;
   pl.sh_g = pl.fused ? make_shape_direct(nt, pl.Kp, pl.pieces, (pl.ng + nt - 1) / nt)
@@ -1478,7 +1531,7 @@ void plan_set_tiles(BatchPlan& pl, int nt) {
 }
 
 // time the stage-1 GEMM at each candidate tile width and keep the fastest
-void plan_autotune(BatchPlan& pl, cudaStream_t s) {
+void tune_stage1(BatchPlan& pl, cudaStream_t s) {
   const int key = 2 * pl.ng_pad + (pl.fused ? 1 : 0);
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
@@ -1540,6 +1593,70 @@ void plan_autotune(BatchPlan& pl, cudaStream_t s) {
   BSE_CUDA(cudaMemsetAsync(pl.err.ptr, 0, sizeof(int), s));
   std::lock_guard<std::mutex> lock(g_tune_mutex);
   g_tuned_nt[key] = best_nt;
+}
+
+// Time the tensor-core stage-2 launches over the tile widths {default, 32}
+// and pipeline depths {deepest, one less}; keep the fastest.  The timed
+// launches read the stage-1 output of the tuning above and subtract from the
+// blocks of A and B that every execute first stores (exchange), so they leave
+// nothing behind that an execute would read.
+void tune_stage2(BatchPlan& pl, cudaStream_t s) {
+  if (pl.fused || (pl.n_s2tiles == 0 && pl.n_s2tiles_t == 0)) return;
+  const int64_t key = ((int64_t)pl.Kp * 4096 + pl.s2_max_cols) * 4 + pl.pieces;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tuned_s2.find(key);
+    if (it != g_tuned_s2.end()) {
+      plan_set_s2_tiles(pl, it->second.first, it->second.second);
+      return;
+    }
+  }
+  std::vector<std::pair<int, int>> cands;
+  const int d2 = s2_default_cols(pl);
+  for (int nt2 : {d2, 32}) {
+    if (nt2 != d2 && nt2 >= d2) continue;
+    const int deep = make_shape(nt2, pl.Kp, pl.pieces, 8, 8).stages;
+    cands.push_back({nt2, deep});
+    if (deep > 2) cands.push_back({nt2, deep - 1});
+  }
+  cudaEvent_t e0, e1;
+  BSE_CUDA(cudaEventCreate(&e0));
+  BSE_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  std::pair<int, int> pick = cands.front();
+  for (const auto& c : cands) {
+    plan_set_s2_tiles(pl, c.first, c.second);
+    float ms = 0.f;
+    for (int rep = 0; rep < 3; ++rep) {
+      BSE_CUDA(cudaEventRecord(e0, s));
+      if (pl.n_s2tiles)
+        launch_gemm(pl.ma_2, pl.mb_2, pl.s2tiles.as<tc::Tile>(), pl.n_s2tiles, pl.sh_2,
+                    S2TcEpi{pl.s2params.as<S2TcParams>()}, pl.err.as<int>(), s);
+      if (pl.n_s2tiles_t)
+        launch_gemm(pl.ma_2t, pl.mb_2t, pl.s2tiles_t.as<tc::Tile>(), pl.n_s2tiles_t, pl.sh_2,
+                    S2TcEpi{pl.s2params.as<S2TcParams>()}, pl.err.as<int>(), s);
+      BSE_CUDA(cudaEventRecord(e1, s));
+      BSE_CUDA(cudaEventSynchronize(e1));
+      float t = 0.f;
+      BSE_CUDA(cudaEventElapsedTime(&t, e0, e1));
+      if (rep > 0) ms += t;   // first launch warms up
+    }
+    if (ms < best) {
+      best = ms;
+      pick = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  plan_set_s2_tiles(pl, pick.first, pick.second);
+  BSE_CUDA(cudaMemsetAsync(pl.err.ptr, 0, sizeof(int), s));
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_tuned_s2[key] = pick;
+}
+
+void plan_autotune(BatchPlan& pl, cudaStream_t s) {
+  tune_stage1(pl, s);
+  tune_stage2(pl, s);
 }
 
 }  // namespace
@@ -1609,12 +1726,17 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
     if (upper) pl->upper_probs.push_back((int)i);
     const int r0 = (int)pr.row0(), r1 = (int)(pr.row0() + pr.rows());
     pl->x_row0.push_back(pl->x_rows);
-    for (int m0 = r0; m0 < r1; m0 += tc::BM)
-      for (int n0 = 0; n0 < n; n0 += pl->nt_x) {
-        if (upper && m0 / nb > (std::min(n0 + pl->nt_x, n) - 1) / nb) continue;
-        xt.push_back({(int)(pl->x_rows + m0), std::min(tc::BM, r1 - m0), (int)(pl->x_rows + n0), n0,
-                      std::min(pl->nt_x, n - n0), m0, (int)i});
-      }
+    // tiles in groups of kXGroup row tiles, column by column: the CTAs working
+    // at the same time share a few row tiles and each column tile, so both
+    // stay in L2 (row by row, every row tile swept all of M_x through L2)
+    constexpr int kXGroup = 8;
+    for (int g0 = r0; g0 < r1; g0 += kXGroup * tc::BM)
+      for (int n0 = 0; n0 < n; n0 += pl->nt_x)
+        for (int m0 = g0; m0 < std::min(r1, g0 + kXGroup * tc::BM); m0 += tc::BM) {
+          if (upper && m0 / nb > (std::min(n0 + pl->nt_x, n) - 1) / nb) continue;
+          xt.push_back({(int)(pl->x_rows + m0), std::min(tc::BM, r1 - m0), (int)(pl->x_rows + n0),
+                        n0, std::min(pl->nt_x, n - n0), m0, (int)i});
+        }
     xp.push_back({reinterpret_cast<double2*>(p.A), p.coupling ? reinterpret_cast<double2*>(p.B) : nullptr,
                   p.ld, (float)(2.0 * p.gamma_x * pr.kappa), p.e_v, p.e_c, p.nv, p.nc, upper});
     pl->x_rows += n;
@@ -1789,7 +1911,6 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
         // tc_gemm.cuh), so T and the other pair side go to the arrays of
         // their role: tA / x2B for the first orientation, x2A / tB for the other.
         std::vector<S2TcParams> prm;
-        std::vector<tc::Tile> tiles, tiles_t;
         int max_cols = 0;
         for (BatchPlan::Term& t : pl->terms) {
           if (!t.tc2) continue;
@@ -1826,8 +1947,7 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
           o.bneg = t.rows_t_side ? 0 : 1;
           o.row_off = t.t_row0 - t.a_row0;
         }
-        // stage 2 products feed A and B directly: K segments of at most 4 steps
-        pl->nt2 = tile_cols(round_up(max_cols, 32), pl->Kp, 4, 4);
+        pl->s2_max_cols = max_cols;
         for (size_t ti = 0; ti < pl->terms.size(); ++ti) {
           BatchPlan::Term& t = pl->terms[ti];
           const Stage2Args& a = t.s2;
@@ -1861,40 +1981,9 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
             xp[j] = a.x_transpose_pair ? (pr % a.nk) * a.nk + a.k_begin + pr / a.nk : pr;
           }
           t.x2perm = upload_mem(xp);
-          for (int j = 0; j < t.nact; ++j) {
-            const int pr = t.act_h[j];
-            const int64_t xr = t.x2_row0 + (int64_t)j * a.rows_x;            // X rows of the pair
-            const int64_t tr = t.t_row0 + (int64_t)t.slot_h[pr] * a.rows_t;  // T rows of the pair
-            if (t.rows_t_side) {
-              for (int m0 = 0; m0 < a.rows_t; m0 += tc::BM)
-                for (int n0 = 0; n0 < a.rows_x; n0 += pl->nt2)
-                  tiles_t.push_back({(int)(tr + m0), std::min(tc::BM, a.rows_t - m0), (int)(xr + n0),
-                                     n0, std::min(pl->nt2, a.rows_x - n0), pr * a.rows_t + m0,
-                                     (int)ti});
-            } else {
-              for (int m0 = 0; m0 < a.rows_x; m0 += tc::BM)
-                for (int n0 = 0; n0 < a.rows_t; n0 += pl->nt2)
-                  tiles.push_back({(int)(xr + m0), std::min(tc::BM, a.rows_x - m0), (int)(tr + n0),
-                                   n0, std::min(pl->nt2, a.rows_t - n0), pr * a.rows_x + m0,
-                                   (int)ti});
-            }
-          }
         }
-        pl->n_s2tiles = (int)tiles.size();
-        pl->s2tiles = upload_mem(tiles);
-        pl->n_s2tiles_t = (int)tiles_t.size();
-        pl->s2tiles_t = upload_mem(tiles_t);
         pl->s2params = upload_mem(prm);
-        pl->sh_2 = make_shape(pl->nt2, pl->Kp, pl->pieces, 4, 4);
-        if (pl->n_s2tiles) {
-          pl->ma_2 = make_plane_map(pl->x2a.as<__nv_bfloat16>(), pl->Kp, (int)pl->x2a_rows, ap, tc::BM);
-          pl->mb_2 = make_plane_map(pl->tb.as<__nv_bfloat16>(), pl->Kp, (int)pl->tb_rows, bp, pl->nt2);
-        }
-        if (pl->n_s2tiles_t) {
-          pl->ma_2t = make_plane_map(pl->ta.as<__nv_bfloat16>(), pl->Kp, (int)pl->ta_rows, ap, tc::BM);
-          pl->mb_2t = make_plane_map(pl->x2b.as<__nv_bfloat16>(), pl->Kp, (int)pl->x2b_rows, bp,
-                                     pl->nt2);
-        }
+        plan_set_s2_tiles(*pl, s2_default_cols(*pl), 0);
       }
       pl->touts = upload_mem(outs);
     }
@@ -1933,6 +2022,11 @@ int plan_status(BatchPlan* pl, cudaStream_t s) {
 }
 
 int plan_tile_cols(const BatchPlan* pl) { return pl->nt_g; }
+void plan_stage2_shape(const BatchPlan* pl, int* tile_cols, int* stages) {
+  const bool any = pl->n_s2tiles || pl->n_s2tiles_t;
+  *tile_cols = any ? pl->nt2 : 0;
+  *stages = any ? pl->s2_stages : 0;
+}
 
 int plan_fused(const BatchPlan* pl) { return pl->fused ? 1 : 0; }
 

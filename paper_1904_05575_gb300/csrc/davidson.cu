@@ -459,8 +459,9 @@ void record_trajectory(Solver& sv, TrajectorySink& sink, std::unique_ptr<DeviceB
       BSE_CUBLAS(cublasZcopy(sv.h.blas, n, xt.as<cuDoubleComplex>(), 1, st.as<cuDoubleComplex>(), 1));
       BSE_CUBLAS(cublasZaxpy(sv.h.blas, n, &ph, xe, 1, st.as<cuDoubleComplex>(), 1));
       const double2* r = (eq == 0 ? sv.R1 : sv.R2).as<double2>() + (int64_t)lam * n;
-      mlp_record(n, sv.dDp.as<double>(), sv.dDm.as<double>(), sv.dS.as<double>(), E[lam], eq == 0,
-                 r, st.as<double2>(), sink.feat + sink.count * 4, sink.target + sink.count,
+      mlp_record(sink.net, n, sv.dDp.as<double>(), sv.dDm.as<double>(), sv.dS.as<double>(),
+                 E[lam], lam, eq == 0, r, xt.as<double2>(), st.as<double2>(),
+                 sink.feat + sink.count * mlp_num_features(sink.net), sink.target + sink.count,
                  sink.weight + sink.count, s);
       sink.count += n;
     }
@@ -507,6 +508,13 @@ void davidson_fp64(int n, const bse_c128* A, const bse_c128* B, int64_t ld, int 
   // the 2 nev lowest Ritz pairs (thick restart)
   const int mmax = std::min(n, std::max(basis_per_ev() * nev, nev + 96));
   Solver sv(n, nev, mmax, A, B, ld, s, h);
+  // learned preconditioner: per-column records (eq, exciton) and feature scratch
+  std::unique_ptr<DeviceBuffer> pc_cols, pc_feat;
+  if (precond == 1) {
+    mlp_check_neighbours(mlp, n, nev);
+    pc_cols.reset(new DeviceBuffer((size_t)4 * nev * sizeof(int), s));
+    pc_feat.reset(new DeviceBuffer((size_t)n * 2 * nev * mlp_num_features(mlp) * sizeof(float), s));
+  }
   std::unique_ptr<TcMatvec, void (*)(TcMatvec*)> tcm(nullptr, tc_matvec_destroy);
   if (matvec_precision != BSE_PREC_FP64) {
     tcm.reset(tc_matvec_create(n, A, B, ld, matvec_precision, mmax, s));
@@ -623,9 +631,27 @@ void davidson_fp64(int n, const bse_c128* A, const bse_c128* B, int64_t ld, int 
     // both blocks use the same eigenvalue list
     BSE_CUDA(cudaMemcpyAsync(sv.dF.as<double>() + nt, et.data(), nt * 8, cudaMemcpyHostToDevice, s));
     if (precond == 1) {
-      mlp_precondition(mlp, n, 2 * nt, sv.dDp.as<double>(), sv.dDm.as<double>(),
+      // the vectors the residuals correct: X+Y = T[:, k + lam] / E for the (A+B)
+      // equation, X-Y = T[:, lam] / E for the other (scale irrelevant), into BV
+      std::vector<int> cols(4 * nt);
+      for (int i = 0; i < nt; ++i) {
+        BSE_CUDA(cudaMemcpyAsync(sv.BV.as<double2>() + (int64_t)i * n,
+                                 sv.T.as<double2>() + (int64_t)(k + todo[i]) * n, (size_t)n * 16,
+                                 cudaMemcpyDeviceToDevice, s));
+        BSE_CUDA(cudaMemcpyAsync(sv.BV.as<double2>() + (int64_t)(nt + i) * n,
+                                 sv.T.as<double2>() + (int64_t)todo[i] * n, (size_t)n * 16,
+                                 cudaMemcpyDeviceToDevice, s));
+        cols[i] = 0;
+        cols[nt + i] = 1;
+        cols[2 * nt + i] = cols[3 * nt + i] = todo[i];
+      }
+      BSE_CUDA(cudaMemcpyAsync(pc_cols->ptr, cols.data(), cols.size() * sizeof(int),
+                               cudaMemcpyHostToDevice, s));
+      const int* ceq = pc_cols->as<int>();
+      mlp_precondition(mlp, n, 2 * nt, ceq, ceq + 2 * nt, sv.dDp.as<double>(), sv.dDm.as<double>(),
                        sv.dS.as<double>(), sv.dF.as<double>(), sv.AV.as<double2>(), n,
-                       sv.T.as<double2>(), n, s);
+                       sv.BV.as<double2>(), n, pc_feat->as<float>(), sv.T.as<double2>(), n, s);
+      BSE_CUDA(cudaStreamSynchronize(s));   // cols (host) is read by the copy above
     } else {
       k_precond_diag<<<dim3((n + 127) / 128, 2 * nt), 128, 0, s>>>(
           n, 2 * nt, sv.dDp.as<double>(), sv.dDm.as<double>(), sv.dF.as<double>(),

@@ -237,3 +237,31 @@ def test_tensor_core_stage2_matches_oracle_and_cuda_cores(bse, nv, nc, ng):
         assert _rel(x, y) < 1e-6
     tc.close()
     cc.close()
+
+
+@pytest.mark.parametrize("nv,nc,ng", [(8, 8, 300), (8, 9, 59)], ids=str)
+def test_stage2_autotune(bse, nv, nc, ng):
+    """The autotuner times the tensor-core stage 2 over its tile widths and
+    pipeline depths: the chosen shape is one of the candidates, and the build
+    matches the oracle and the default-shape build."""
+    cfg = bi.BSEConfig(f"big-blocks-{nv}-{nc}-{ng}", grid=2, nv=nv, nc=nc, ng=ng, w_scale=0.05)
+    p = bi.make_problem(cfg)
+    A_ref, B_ref = O.build_A_B(p)
+    ds, structs = _upload(bse, [p])
+    plain = bse.Plan(structs, precision=bse.BSE_PREC_BF16X6)
+    nt_d, st_d = plain.stage2_shape
+    assert nt_d in (32, 64, 96, 128) and 2 <= st_d <= 6
+    a = [x.clone() for x in _build(bse, plain, ds)]
+    tuned = bse.Plan(structs, precision=bse.BSE_PREC_BF16X6, autotune=True)
+    nt, st = tuned.stage2_shape
+    assert nt in (32, nt_d) and st <= (st_d if nt == nt_d else 6) and st >= 2
+    b = _build(bse, tuned, ds)
+    _check(bse, [p], [(A_ref, B_ref)], ds, 1e-6)
+    n = p["nk"] * p["nv"] * p["nc"]
+    for x, y in zip(a, b):
+        assert _rel(bse.matrix_to_numpy(x, n), bse.matrix_to_numpy(y, n)) < 1e-12
+    # a plan without a tensor-core stage 2 reports none
+    cc = bse.Plan(structs, precision=bse.BSE_PREC_BF16X6, tc_stage2=False)
+    assert cc.stage2_shape == (0, 0)
+    for pl in (plain, tuned, cc):
+        pl.close()

@@ -72,3 +72,61 @@ def test_sample_targets_diagonal_problem():
     assert np.all(w[~mask] < 1e-15)
     assert np.allclose(F[:, 0], F[:, 1])                 # D+ = D- when B = 0
     assert np.allclose(F[:, 2], 0.0)                     # no off-diagonal coupling
+
+
+def _feat10_case(rng, n=37):
+    dq = rng.uniform(3, 9, n)
+    do = dq + rng.uniform(-0.5, 0.5, n)
+    s = rng.uniform(0, 4, n)
+    r = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    v1 = x + 0.3 * (rng.standard_normal(n) + 1j * rng.standard_normal(n))
+    v2 = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    return dq, do, s, 2.5, r, x, [v1, v2]
+
+
+def test_features10_by_hand():
+    # one transition worked out from the definition with plain scalars
+    rng = np.random.default_rng(5)
+    dq, do, s, e, r, x, nb = _feat10_case(rng, n=5)
+    F = M.features10(dq, do, s, e, r, x, nb)
+    a = 3
+    assert np.isclose(F[a, 0], (dq[a] - e) / 10) and np.isclose(F[a, 3], e / 100)
+    v = nb[1]
+    z = sum(np.conj(v[i]) * x[i] for i in range(5))
+    u_a = v[a] / np.sqrt(sum(abs(t) ** 2 for t in v)) * z / abs(z)
+    d_a = u_a - x[a] / np.sqrt(sum(abs(t) ** 2 for t in x))
+    b_a = r[a] / (dq[a] - e)
+    rel = np.conj(b_a) * d_a / abs(b_a) * np.sqrt(5)
+    assert np.allclose(F[a, 7:10], [abs(u_a) * np.sqrt(5), rel.real, rel.imag])
+
+
+def test_features10_invariances():
+    rng = np.random.default_rng(6)
+    dq, do, s, e, r, x, nb = _feat10_case(rng)
+    F = M.features10(dq, do, s, e, r, x, nb)
+    # a common phase of (r, x) and any phase of a neighbour vector change nothing
+    ph = np.exp(0.7j)
+    F2 = M.features10(dq, do, s, e, r * ph, x * ph, [nb[0] * np.exp(-1.1j), nb[1] * 1j])
+    assert np.allclose(F, F2)
+    # the scale of x and of the neighbours changes nothing either
+    F3 = M.features10(dq, do, s, e, r, 3.0 * x, [0.5 * nb[0], 7.0 * nb[1]])
+    assert np.allclose(F, F3)
+
+
+def test_features10_special_cases():
+    rng = np.random.default_rng(7)
+    dq, do, s, e, r, x, nb = _feat10_case(rng)
+    # a neighbour equal to the current vector: u = x/|x|, d = 0
+    F = M.features10(dq, do, s, e, r, x, [x.copy()])
+    assert np.allclose(F[:, 4], np.abs(x) / np.linalg.norm(x) * np.sqrt(len(x)))
+    assert np.allclose(F[:, 5:7], 0.0)
+    assert np.allclose(F[:, 7:], 0.0)            # no second neighbour
+    # a zero residual component: its direction features are zero
+    r0 = r.copy()
+    r0[4] = 0
+    F0 = M.features10(dq, do, s, e, r0, x, nb)
+    assert np.allclose(F0[4, [5, 6, 8, 9]], 0.0)
+    # sum over a of |u_a|^2 n / n = 1 (u is a unit vector)
+    F1 = M.features10(dq, do, s, e, r, x, nb)
+    assert np.isclose(np.sum(F1[:, 4] ** 2) / len(x), 1.0)
