@@ -48,6 +48,9 @@ WORKLOAD_C5 = ("molecular-crystal-like Q=0, full (non-TDA) BSE, Nk=64 (4x4x4), N
                "N=25600 (51200 full), NG=500, strong off-diagonal W")
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 FP64_PEAK_TFLOPS = 1.25     # GB300 FP64 (CUDA-core and tensor) nominal rate
+# eps by the Lanczos recursion: stop when eps changes by at most this fraction
+# of max |eps| between checks (the 1e-3 bar at the peaks is far above it)
+LANCZOS_TOL = 1e-6
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per build of a
 # kernel phase, from one ncu capture of the kernel on the named workload,
@@ -488,22 +491,47 @@ def c2_time_to_spectrum(bse, bi, prec, steps=10, warmup=3):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1), e0.elapsed_time(e2)
 
+    eps_lz = torch.empty_like(eps)
+
+    def run_lanczos():
+        # eps only: mixed build + the Lanczos recursion (no reduction, no eigensolve)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.execute()
+        k = bse.bse_spectrum_lanczos(n, d["A"], d["B"], rho, p["c_q"], vc, om, p["delta"], eps_lz,
+                                     tol=LANCZOS_TOL)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), k
+
     for _ in range(warmup):
         run(False)
     mixed = [run(False) for _ in range(steps)]
     E_mixed = E.clone()
+    run_lanczos()
+    lanczos = [run_lanczos() for _ in range(steps)]
     run(True)
     fp64 = [run(True) for _ in range(3)]
     plan.status()
     plan.close()
     t_mx = statistics.mean(x[1] for x in mixed)
     t_64 = statistics.mean(x[1] for x in fp64)
+    t_lz = statistics.mean(x[0] for x in lanczos)
+    y = eps.imag.cpu().numpy()
+    pk = [i for i in range(1, len(y) - 1) if y[i] > y[i - 1] and y[i] >= y[i + 1] and y[i] > 0.1 * y.max()]
+    e_lz = eps_lz.cpu().numpy()
+    lz = {"method": "mixed build + Lanczos recursion on (A-B)(A+B), eps only (no eigensolve)",
+          "time_to_eps_ms": t_lz, "lanczos_steps": lanczos[-1][1],
+          "speedup_vs_fp64_time_to_spectrum": t_64 / t_lz,
+          "max_rel_dIm_eps_at_peaks_vs_fp64": float(max(
+              (abs(e_lz.imag[i] - y[i]) / abs(y[i]) for i in pk), default=0.0))}
     return {"workload": WORKLOAD, "build_ms": statistics.mean(x[0] for x in mixed),
             "build_tflops": build_flops(nk, nv, nc, ng) / (statistics.mean(x[0] for x in mixed)
                                                            * 1e-3) / 1e12,
             "time_to_spectrum_ms": t_mx, "fp64_build_ms": statistics.mean(x[0] for x in fp64),
             "fp64_time_to_spectrum_ms": t_64, "speedup_time_to_spectrum": t_64 / t_mx,
-            "max_dE_meV_vs_fp64": (E_mixed - E).abs().max().item() * 1e3}
+            "max_dE_meV_vs_fp64": (E_mixed - E).abs().max().item() * 1e3,
+            "eps_by_lanczos": lz}
 
 
 def run_headline(args, bse, bi, prec, world, rank, local):
@@ -619,6 +647,26 @@ def run_headline(args, bse, bi, prec, world, rank, local):
             "lowest_E_eV": [round(x, 6) for x in E_mx[:4].tolist()]}
     del A64, B64, st64
     torch.cuda.empty_cache()
+
+    # ---- once: time to eps_M on the grid by the Lanczos recursion (mixed
+    # build, then no reduction and no eigensolve) ----
+    if not args.no_lanczos:
+        om = torch.as_tensor(p["omega"]).to(dev)
+        rho = p["rho"] if torch.is_tensor(p["rho"]) else torch.as_tensor(p["rho"]).to(dev)
+        eps_lz = torch.empty(len(p["omega"]), dtype=torch.complex128, device=dev)
+        lz_ms, lz_steps = [], 0
+        for _ in range(2):
+            e0.record(stream)
+            plan.execute()
+            lz_steps = bse.bse_spectrum_lanczos(n, d["A"], d["B"], rho, p["c_q"],
+                                                nk * p["omega_cell"], om, p["delta"], eps_lz,
+                                                tol=LANCZOS_TOL)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            lz_ms.append(e0.elapsed_time(e1))
+        extra["eps_by_lanczos"] = {
+            "method": "mixed build + Lanczos recursion on (A-B)(A+B), eps only (no eigensolve)",
+            "time_to_eps_ms": lz_ms[-1], "lanczos_steps": lz_steps, "tol": LANCZOS_TOL}
 
     # ---- end to end through the public API with pinned host buffers ----
     e2e = None
@@ -794,6 +842,60 @@ def run_mlp_family(args, bse, bi, prec, world, rank, local):
                           "training_q_indices": pool, "samples": int(C.numel()),
                           "sampling_s": t_samples, "training_s": t_train,
                           "training_loss": [L0, L1], "runs": runs}), flush=True)
+    return 0
+
+
+def run_eps_lanczos(args, bse, bi, prec, world, rank, local):
+    """eps_M at one Q by the mixed build + the Lanczos recursion against the
+    plain FP64 GPU path (FP64 build, reduction, eigensolve, spectrum): the
+    largest relative difference of Im eps at its peaks and of eps on the grid,
+    and both times to eps."""
+    import numpy as np
+    import torch
+    q = args.eps_lanczos
+    stream = torch.cuda.current_stream()
+    p = bi.make_problem_torch(args.config, q_index=q, seed=20190411 + rank)
+    n = p["nk"] * p["nv"] * p["nc"]
+    d = bse.upload_problem(p)
+    st = bse.make_problem_struct(d)
+    om = torch.as_tensor(p["omega"]).cuda()
+    rho = p["rho"] if torch.is_tensor(p["rho"]) else torch.as_tensor(p["rho"]).cuda()
+    vc = p["nk"] * p["omega_cell"]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    eps64 = torch.empty(len(p["omega"]), dtype=torch.complex128, device="cuda")
+    ev[0].record(stream)
+    bse.bse_build_kernel([st], bse.BSE_PREC_FP64)
+    S = torch.empty((n, n), dtype=torch.complex128, device="cuda")
+    L = torch.empty_like(S)
+    E = torch.empty(n, dtype=torch.float64, device="cuda")
+    osc = torch.empty_like(E)
+    bse.bse_reduce(n, d["A"], d["B"], S, L)
+    bse.bse_spectrum(n, S, L, rho, p["c_q"], vc, om, p["delta"], E, osc, eps64)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    del S, L
+    torch.cuda.empty_cache()
+    plan = bse.Plan([st], precision=prec, hermitian=True)
+    eps = torch.empty_like(eps64)
+    ev[2].record(stream)
+    plan.execute()
+    steps = bse.bse_spectrum_lanczos(n, d["A"], d["B"], rho, p["c_q"], vc, om, p["delta"], eps,
+                                     tol=1e-8)
+    ev[3].record(stream)
+    torch.cuda.synchronize()
+    plan.status()
+    plan.close()
+    r, e = eps64.cpu().numpy(), eps.cpu().numpy()
+    pk = _eps_peaks(r.imag, p["omega"])
+    row = {"metric": "eps_M by Lanczos (mixed build) vs the FP64 GPU path", "config": args.config,
+           "q_index": q, "n": n, "lanczos_steps": steps, "peaks": len(pk),
+           "max_rel_dIm_eps_at_peaks": float(max((abs(e.imag[i] - r.imag[i]) / abs(r.imag[i])
+                                                  for i in pk), default=0.0)),
+           "max_rel_d_eps": float(np.abs(e - r).max() / np.abs(r).max()),
+           "fp64_time_to_eps_ms": ev[0].elapsed_time(ev[1]),
+           "lanczos_time_to_eps_ms": ev[2].elapsed_time(ev[3])}
+    if rank == 0:
+        print(json.dumps(row), flush=True)
     return 0
 
 
@@ -1156,6 +1258,10 @@ def main():
                     help="c5: compute every (k, k') block (no BSE_PLAN_HERMITIAN)")
     ap.add_argument("--e2e-steps", type=int, default=3,
                     help="c5: timed end-to-end steps (after one untimed)")
+    ap.add_argument("--eps-lanczos", type=int, default=None,
+                    help="one Q index: eps by mixed build + Lanczos against the FP64 GPU path")
+    ap.add_argument("--no-lanczos", action="store_true",
+                    help="c5: skip timing eps by the Lanczos recursion")
     ap.add_argument("--mlp-family", action="store_true",
                     help="learned Davidson preconditioner trained at four Q of a family, "
                          "judged at the fifth (c4s)")
@@ -1221,6 +1327,8 @@ def main():
     if args.mlp_family:
         rc = run_mlp_family(args, bse, bi, prec, world, rank, local)
         return rc
+    if args.eps_lanczos is not None:
+        return run_eps_lanczos(args, bse, bi, prec, world, rank, local)
     if args.eps_qs:
         rc = run_eps_qs(args, bse, bi, prec, world, rank, local)
         if world > 1:

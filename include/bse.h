@@ -277,6 +277,26 @@ int bse_spectrum(int32_t n, bse_c128* S_inout, const bse_c128* L, int64_t ld,
                  const double* omega, double delta, double* E_out, double* osc_out,
                  bse_c128* eps_out, void* cuda_stream);
 
+/* eps on the grid of bse_spectrum without the reduction or the eigensolve.
+ * The exciton sum of bse_spectrum equals (2/vc) Q((w + i delta)^2) with
+ *   Q(z2) = conj(rho)^H (z2 - K)^-1 (A-B) conj(rho),  K = (A-B)(A+B),
+ * (the sum over lambda of |u_lambda|^2 / (z2 - E_lambda^2), S = L^H (A+B) L
+ * being similar to K through L).  K is self-adjoint in the inner product
+ * a^H (A-B)^-1 b, so a Lanczos recursion in that inner product, with two
+ * products by A+B and A-B per step and no factorisation, gives Q as a
+ * continued fraction of its coefficients.  The steps stop when eps changes
+ * by at most tol times max |eps| between checks (every 50 steps; at least
+ * min(100, 2n) steps); steps_out (host, may be NULL) receives the number.
+ * A, B as for bse_reduce (B = NULL: zero), rho, omega, delta, c_q, vc as for
+ * bse_spectrum (delta > 0); eps_out [n_omega] device.  FP64 throughout.
+ * Syncs at each check.  Errors: BSE_ERR_ARG, BSE_ERR_NOT_PD
+ * (conj(rho)^H (A-B) conj(rho) <= 0), BSE_ERR_NO_CONV (max_steps reached;
+ * eps_out holds the last estimate), BSE_ERR_NOMEM, BSE_ERR_CUDA. */
+int bse_spectrum_lanczos(int32_t n, const bse_c128* A, const bse_c128* B, int64_t ld,
+                         const bse_c128* rho, double c_q, double vc, int32_t n_omega,
+                         const double* omega, double delta, double tol, int32_t max_steps,
+                         bse_c128* eps_out, int32_t* steps_out, void* cuda_stream);
+
 /* Cartesian dielectric tensor (Eq. epsmij) from the eigenpairs that
  * bse_spectrum leaves: Z (its S_inout on return, N x N, ld), L from
  * bse_reduce, E [n] its energies.  D: N x 3 column-major (leading dimension

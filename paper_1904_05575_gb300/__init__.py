@@ -63,7 +63,7 @@ EXPORTED = ("bse_build_kernel", "bse_reduce", "bse_spectrum", "bse_last_error", 
             "bse_mlp_predict", "bse_xpy", "bse_mlp_trajectory_samples", "bse_mlp_set_neighbours",
             "bse_mlp_features", "bse_plan_create",
             "bse_plan_execute", "bse_plan_status", "bse_plan_tile_cols", "bse_plan_destroy",
-            "bse_plan_stage2_shape",
+            "bse_plan_stage2_shape", "bse_spectrum_lanczos",
             "bse_plan_fused", "bse_spectrum_tensor", "bse_loss_function",
             "bse_lowest_excitons_from", "bse_rpa_screening", "bse_plan_set_wait_limit",
             "bse_pair_elements")
@@ -82,6 +82,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.bse_build_kernel.argtypes = [ctypes.POINTER(bse_problem), i32, i32, vp]
     lib.bse_reduce.argtypes = [i32, vp, vp, i64, vp, vp, ctypes.POINTER(i32), vp]
     lib.bse_spectrum.argtypes = [i32, vp, vp, i64, vp, dbl, dbl, i32, vp, dbl, vp, vp, vp, vp]
+    lib.bse_spectrum_lanczos.argtypes = [i32, vp, vp, i64, vp, dbl, dbl, i32, vp, dbl, dbl, i32,
+                                         vp, ctypes.POINTER(i32), vp]
+    lib.bse_spectrum_lanczos.restype = ctypes.c_int
     lib.bse_spectrum_tensor.argtypes = [i32, vp, vp, i64, vp, i64, dbl, dbl, i32, vp, dbl, vp, vp,
                                         vp]
     lib.bse_spectrum_tensor.restype = ctypes.c_int
@@ -285,6 +288,28 @@ def bse_spectrum(n: int, S, L, rho, c_q: float, vc: float, omega, delta: float,
                             float(delta), _ptr(E_out, torch.float64, "E_out"),
                             _ptr(osc_out, torch.float64, "osc_out"),
                             _ptr(eps_out, torch.complex128, "eps_out"), _stream(stream)))
+
+
+def bse_spectrum_lanczos(n: int, A, B, rho, c_q: float, vc: float, omega, delta: float, eps_out,
+                         tol: float = 1e-8, max_steps: int = 4000, stream=None) -> int:
+    """eps on the grid by the Lanczos recursion on (A-B)(A+B) (no reduction,
+    no eigensolve); returns the steps taken.  On BSE_ERR_NO_CONV the raised
+    error carries .steps and eps_out holds the last estimate."""
+    import torch
+    lib = load()
+    a, ld = _matrix_ptr(A, n, "A")
+    b = _matrix_ptr(B, n, "B")[0] if B is not None else None
+    steps = ctypes.c_int32(0)
+    st = lib.bse_spectrum_lanczos(n, a, b, ld, _ptr(rho, torch.complex128, "rho"), float(c_q),
+                                  float(vc), omega.numel(), _ptr(omega, torch.float64, "omega"),
+                                  float(delta), float(tol), int(max_steps),
+                                  _ptr(eps_out, torch.complex128, "eps_out"), ctypes.byref(steps),
+                                  _stream(stream))
+    if st != BSE_OK:
+        err = BSEError(st, lib.bse_last_error().decode(errors="replace"))
+        err.steps = steps.value
+        raise err
+    return steps.value
 
 
 def bse_spectrum_tensor(n: int, Z, L, D, c_q: float, vc: float, omega, delta: float, E,
