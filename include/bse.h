@@ -288,14 +288,19 @@ int bse_spectrum(int32_t n, bse_c128* S_inout, const bse_c128* L, int64_t ld,
  * by at most tol times max |eps| between checks (every 50 steps; at least
  * min(100, 2n) steps); steps_out (host, may be NULL) receives the number.
  * A, B as for bse_reduce (B = NULL: zero), rho, omega, delta, c_q, vc as for
- * bse_spectrum (delta > 0); eps_out [n_omega] device.  FP64 throughout.
+ * bse_spectrum (delta > 0); eps_out [n_omega] device.  matvec_precision:
+ * BSE_PREC_FP64 (products in FP64 on CUDA cores) or BSE_PREC_BF16X6 /
+ * BF16X3 (A and B split once into BF16 pieces, products on the tensor
+ * cores with A's diagonal in FP64, as for bse_lowest_excitons; workspace 2 x
+ * 12 N^2 bytes for BF16X6); the recursion itself is FP64.
  * Syncs at each check.  Errors: BSE_ERR_ARG, BSE_ERR_NOT_PD
  * (conj(rho)^H (A-B) conj(rho) <= 0), BSE_ERR_NO_CONV (max_steps reached;
  * eps_out holds the last estimate), BSE_ERR_NOMEM, BSE_ERR_CUDA. */
 int bse_spectrum_lanczos(int32_t n, const bse_c128* A, const bse_c128* B, int64_t ld,
                          const bse_c128* rho, double c_q, double vc, int32_t n_omega,
                          const double* omega, double delta, double tol, int32_t max_steps,
-                         bse_c128* eps_out, int32_t* steps_out, void* cuda_stream);
+                         int32_t matvec_precision, bse_c128* eps_out, int32_t* steps_out,
+                         void* cuda_stream);
 
 /* Cartesian dielectric tensor (Eq. epsmij) from the eigenpairs that
  * bse_spectrum leaves: Z (its S_inout on return, N x N, ld), L from

@@ -83,7 +83,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.bse_reduce.argtypes = [i32, vp, vp, i64, vp, vp, ctypes.POINTER(i32), vp]
     lib.bse_spectrum.argtypes = [i32, vp, vp, i64, vp, dbl, dbl, i32, vp, dbl, vp, vp, vp, vp]
     lib.bse_spectrum_lanczos.argtypes = [i32, vp, vp, i64, vp, dbl, dbl, i32, vp, dbl, dbl, i32,
-                                         vp, ctypes.POINTER(i32), vp]
+                                         i32, vp, ctypes.POINTER(i32), vp]
     lib.bse_spectrum_lanczos.restype = ctypes.c_int
     lib.bse_spectrum_tensor.argtypes = [i32, vp, vp, i64, vp, i64, dbl, dbl, i32, vp, dbl, vp, vp,
                                         vp]
@@ -291,7 +291,8 @@ def bse_spectrum(n: int, S, L, rho, c_q: float, vc: float, omega, delta: float,
 
 
 def bse_spectrum_lanczos(n: int, A, B, rho, c_q: float, vc: float, omega, delta: float, eps_out,
-                         tol: float = 1e-8, max_steps: int = 4000, stream=None) -> int:
+                         tol: float = 1e-8, max_steps: int = 4000,
+                         matvec_precision: int = BSE_PREC_FP64, stream=None) -> int:
     """eps on the grid by the Lanczos recursion on (A-B)(A+B) (no reduction,
     no eigensolve); returns the steps taken.  On BSE_ERR_NO_CONV the raised
     error carries .steps and eps_out holds the last estimate."""
@@ -302,7 +303,7 @@ def bse_spectrum_lanczos(n: int, A, B, rho, c_q: float, vc: float, omega, delta:
     steps = ctypes.c_int32(0)
     st = lib.bse_spectrum_lanczos(n, a, b, ld, _ptr(rho, torch.complex128, "rho"), float(c_q),
                                   float(vc), omega.numel(), _ptr(omega, torch.float64, "omega"),
-                                  float(delta), float(tol), int(max_steps),
+                                  float(delta), float(tol), int(max_steps), int(matvec_precision),
                                   _ptr(eps_out, torch.complex128, "eps_out"), ctypes.byref(steps),
                                   _stream(stream))
     if st != BSE_OK:

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "bse_internal.h"
+#include "lanczos.h"
 #include "mlp.h"
 
 namespace bse {
@@ -454,8 +455,8 @@ extern "C" int bse_spectrum(int32_t n, bse_c128* S_inout, const bse_c128* L, int
 extern "C" int bse_spectrum_lanczos(int32_t n, const bse_c128* A, const bse_c128* B, int64_t ld,
                                     const bse_c128* rho, double c_q, double vc, int32_t n_omega,
                                     const double* omega, double delta, double tol,
-                                    int32_t max_steps, bse_c128* eps_out, int32_t* steps_out,
-                                    void* cuda_stream) {
+                                    int32_t max_steps, int32_t matvec_precision,
+                                    bse_c128* eps_out, int32_t* steps_out, void* cuda_stream) {
   return guarded([&] {
     if (steps_out) *steps_out = 0;
     BSE_CHECK_ARG(n >= 1, "n must be >= 1");
@@ -467,12 +468,18 @@ extern "C" int bse_spectrum_lanczos(int32_t n, const bse_c128* A, const bse_c128
                   "c_q must be finite and delta > 0");
     BSE_CHECK_ARG(std::isfinite(tol) && tol > 0.0, "tol must be > 0");
     BSE_CHECK_ARG(max_steps >= 1, "max_steps must be >= 1");
+    BSE_CHECK_ARG(matvec_precision == BSE_PREC_FP64 || matvec_precision == BSE_PREC_BF16X6 ||
+                      matvec_precision == BSE_PREC_BF16X3,
+                  "unknown matvec precision " + std::to_string(matvec_precision));
+    BSE_CHECK_ARG(matvec_precision == BSE_PREC_FP64 || mixed_supported(matvec_precision),
+                  "this library has no tensor-core path");
     BSE_CHECK_ARG(((uintptr_t)A & 15) == 0 && ((uintptr_t)B & 15) == 0 && ((uintptr_t)rho & 15) == 0,
                   "A, B and rho must be 16-byte aligned");
     keep_pool_memory();
     try {
       const int st = spectrum_lanczos(n, A, B, ld, rho, c_q, vc, n_omega, omega, delta, tol,
-                                      max_steps, eps_out, static_cast<cudaStream_t>(cuda_stream));
+                                      max_steps, matvec_precision, eps_out,
+                                      static_cast<cudaStream_t>(cuda_stream));
       if (steps_out) *steps_out = st;
     } catch (const Error& e) {
       if (e.status == BSE_ERR_NO_CONV && steps_out) *steps_out = max_steps;

@@ -155,12 +155,6 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
 void plan_execute(BatchPlan* plan, cudaStream_t s);
 int plan_status(BatchPlan* plan, cudaStream_t s);
 int plan_tile_cols(const BatchPlan* plan);
-
-// eps_M on a grid by the Lanczos recursion on (A-B)(A+B) (lanczos.cu);
-// returns the steps taken, throws BSE_ERR_NO_CONV / NOT_PD / ARG.
-int spectrum_lanczos(int n, const bse_c128* A, const bse_c128* B, int64_t ld, const bse_c128* rho,
-                     double c_q, double vc, int n_omega, const double* omega, double delta,
-                     double tol, int max_steps, bse_c128* eps_out, cudaStream_t s);
 void plan_stage2_shape(const BatchPlan* plan, int* tile_cols, int* stages);
 int plan_fused(const BatchPlan* plan);
 void plan_set_wait(BatchPlan* plan, double seconds);

@@ -24,9 +24,11 @@
 
 #include <algorithm>
 #include <cmath>
+#include <memory>
 #include <vector>
 
 #include "bse_internal.h"
+#include "lanczos.h"
 
 namespace bse {
 namespace {
@@ -124,6 +126,26 @@ __global__ void k_lanczos_scale(int n, const double* coef, int k, double2* x, do
   y[i] = make_double2(yv.x * f, yv.y * f);
 }
 
+// out = av + s bv (bv NULL: av); dot += Re(sum_i conj(w_i) out_i)
+__global__ void __launch_bounds__(256) k_combine_dot(int n, const double2* av, const double2* bv,
+                                                     double s, double2* out, const double2* w,
+                                                     double* dot) {
+  __shared__ double red[8];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double d = 0.0;
+  if (i < n) {
+    double2 o = av[i];
+    if (bv) {
+      o.x = fma(s, bv[i].x, o.x);
+      o.y = fma(s, bv[i].y, o.y);
+    }
+    out[i] = o;
+    d = w[i].x * o.x + w[i].y * o.y;
+  }
+  d = block_sum(d, red);
+  if (threadIdx.x == 0) atomicAdd(dot, d);
+}
+
 // y = conj(rho)
 __global__ void k_conj(int n, const double2* rho, double2* y) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -182,7 +204,8 @@ __global__ void __launch_bounds__(256) k_eps_change(int n_omega, const double2* 
 // eps on the grid from the recursion above; returns the steps taken.
 int spectrum_lanczos(int n, const bse_c128* A, const bse_c128* B, int64_t ld, const bse_c128* rho,
                      double c_q, double vc, int n_omega, const double* omega, double delta,
-                     double tol, int max_steps, bse_c128* eps_out, cudaStream_t s) {
+                     double tol, int max_steps, int matvec_precision, bse_c128* eps_out,
+                     cudaStream_t s) {
   const double2* A2 = reinterpret_cast<const double2*>(A);
   const double2* B2 = reinterpret_cast<const double2*>(B);
   int dev = 0, sms = 0;
@@ -202,7 +225,24 @@ int spectrum_lanczos(int n, const bse_c128* A, const bse_c128* B, int64_t ld, co
   double* cf = coef.as<double>();
   const int eb = (n + 255) / 256;
   int launches = 0;
+  // split-precision products: A and B split once into BF16 pieces, A x and
+  // B x on the tensor cores (A's diagonal in FP64), FP64 results
+  std::unique_ptr<TcMatvec, void (*)(TcMatvec*)> tcm(nullptr, tc_matvec_destroy);
+  std::unique_ptr<DeviceBuffer> av, bvb;
+  if (matvec_precision != BSE_PREC_FP64) {
+    tcm.reset(tc_matvec_create(n, A, B, ld, matvec_precision, 1, s));
+    av.reset(new DeviceBuffer(vb, s));
+    bvb.reset(new DeviceBuffer(vb, s));
+  }
   auto gemv = [&](double sign, const double2* x, double2* out, const double2* w, double* dot) {
+    if (tcm) {
+      tc_matvec_apply(tcm.get(), reinterpret_cast<const bse_c128*>(x), 1, av->as<bse_c128>(),
+                      B ? bvb->as<bse_c128>() : nullptr, s);
+      k_combine_dot<<<eb, 256, 0, s>>>(n, av->as<double2>(), B ? bvb->as<double2>() : nullptr,
+                                       sign, out, w, dot);
+      launches += 1;
+      return;
+    }
     k_pm_gemv<<<dim3(row_blocks, chunks), kGvRows, 0, s>>>(n, A2, B2, ld, sign, x, chunk,
                                                            part.as<double2>());
     k_sum_partials<<<eb, 256, 0, s>>>(n, chunks, part.as<double2>(), out, w, dot);

@@ -35,8 +35,11 @@ def _gpu_matrix(M):
     return _t(np.ascontiguousarray(M.T))
 
 
+@pytest.mark.parametrize("prec", [0, 2], ids=["fp64", "bf16x6"])
 @pytest.mark.parametrize("cfg", ["c1", FINITE_Q, RAGGED, "c2"], ids=["c1", "finite-q", "ragged", "c2"])
-def test_lanczos_matches_oracle_spectrum(bse, cfg):
+def test_lanczos_matches_oracle_spectrum(bse, cfg, prec):
+    """FP64 products: eps to 1e-7 of the oracle (1e-6 at the peaks); tensor-core
+    products (BF16x6): to 1e-5 (1e-4 at the peaks)."""
     import torch
     p = bi.make_problem(cfg)
     A, B = O.build_A_B(p)
@@ -45,18 +48,20 @@ def test_lanczos_matches_oracle_spectrum(bse, cfg):
     eps = torch.empty(len(p["omega"]), dtype=torch.complex128, device="cuda")
     steps = bse.bse_spectrum_lanczos(n, _gpu_matrix(A), _gpu_matrix(B), _t(p["rho"]), p["c_q"],
                                      p["nk"] * p["omega_cell"], _t(p["omega"]), p["delta"], eps,
-                                     tol=1e-10)
+                                     tol=1e-10, matvec_precision=prec)
     e = eps.cpu().numpy()
     scale = np.abs(eps_ref).max()
-    assert np.abs(e - eps_ref).max() < 1e-7 * scale
+    bound, bound_pk = (1e-7, 1e-6) if prec == 0 else (1e-5, 1e-4)
+    assert np.abs(e - eps_ref).max() < bound * scale
     y = eps_ref.imag
     pk = [i for i in range(1, len(y) - 1) if y[i] > y[i - 1] and y[i] >= y[i + 1] and y[i] > 0.1 * y.max()]
     assert len(pk) > 0
-    assert (np.abs(e[pk] - eps_ref[pk]) / np.abs(eps_ref[pk])).max() < 1e-6
+    assert (np.abs(e[pk] - eps_ref[pk]) / np.abs(eps_ref[pk])).max() < bound_pk
     print(f" [{steps} steps]", end="")
 
 
-def test_lanczos_matches_fp64_path_on_reduced_crystal(bse):
+@pytest.mark.parametrize("prec", [0, 2], ids=["fp64", "bf16x6"])
+def test_lanczos_matches_fp64_path_on_reduced_crystal(bse, prec):
     """The reduced molecular-crystal shape (N = 3,200, NG = 500) at a finite Q:
     the mixed build, then eps by the recursion, against the FP64 build, the
     reduction, the eigensolve and the spectrum; Im eps within 1e-3 at the peaks."""
@@ -82,7 +87,7 @@ def test_lanczos_matches_fp64_path_on_reduced_crystal(bse):
     bse.bse_spectrum(n, S, L, rho, p["c_q"], vc, om, p["delta"], E, osc, eps64)
     eps = torch.empty_like(eps64)
     steps = bse.bse_spectrum_lanczos(n, d["A"], d["B"], rho, p["c_q"], vc, om, p["delta"], eps,
-                                     tol=1e-8)
+                                     tol=1e-8, matvec_precision=prec)
     e, r = eps.cpu().numpy(), eps64.cpu().numpy()
     y = r.imag
     pk = [i for i in range(1, len(y) - 1) if y[i] > y[i - 1] and y[i] >= y[i + 1] and y[i] > 0.1 * y.max()]
