@@ -70,6 +70,12 @@ __global__ void __launch_bounds__(kGvRows) k_pm_gemv(int n, const double2* __res
   if (i < n) partial[(int64_t)blockIdx.y * n + i] = make_double2(ax, ay);
 }
 
+// the dot-product target: coef[2 j + off] for the step j held at jdev, or
+// base itself (jdev NULL)
+__device__ __forceinline__ double* dot_target(double* base, const int* jdev, int off) {
+  return jdev ? base + 2 * (*jdev) + off : base;
+}
+
 __device__ __forceinline__ double block_sum(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -84,7 +90,8 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 
 // out = sum_c partial[c]; dot += Re(sum_i conj(w_i) out_i) (w NULL: no dot)
 __global__ void __launch_bounds__(256) k_sum_partials(int n, int chunks, const double2* partial,
-                                                      double2* out, const double2* w, double* dot) {
+                                                      double2* out, const double2* w, double* dot,
+                                                      const int* jdev, int off) {
   __shared__ double red[8];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double d = 0.0;
@@ -100,26 +107,30 @@ __global__ void __launch_bounds__(256) k_sum_partials(int n, int chunks, const d
   }
   if (w) {
     d = block_sum(d, red);
-    if (threadIdx.x == 0) atomicAdd(dot, d);
+    if (threadIdx.x == 0) atomicAdd(dot_target(dot, jdev, off), d);
   }
 }
 
-// y_new = u - alpha_j y_j - beta_{j-1} y_prev  (coef: alpha at 2j, beta^2 at 2j - 1)
+// y_new = u - alpha_j y_j - beta_{j-1} y_prev  (coef: alpha at 2j, beta^2 at
+// 2j - 1; j the step held at jdev)
 __global__ void k_lanczos_y(int n, const double2* u, const double2* yj, const double2* yprev,
-                            const double* coef, int j, double2* ynew) {
+                            const double* coef, const int* jdev, double2* ynew) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const int j = *jdev;
   const double a = coef[2 * j];
   const double b = j > 0 ? sqrt(fmax(coef[2 * j - 1], 0.0)) : 0.0;
   const double2 uy = u[i], y1 = yj[i], y0 = yprev[i];
   ynew[i] = make_double2(uy.x - a * y1.x - b * y0.x, uy.y - a * y1.y - b * y0.y);
 }
 
-// scale x and y by 1 / sqrt(coef[k]) (k: the entry holding the squared norm)
-__global__ void k_lanczos_scale(int n, const double* coef, int k, double2* x, double2* y) {
+// scale x and y by 1 / sqrt(coef[k]), k = 2 j + 1 for the step held at jdev,
+// or k_fixed (jdev NULL)
+__global__ void k_lanczos_scale(int n, const double* coef, const int* jdev, int k_fixed, double2* x,
+                                double2* y) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const double b2 = coef[k];
+  const double b2 = coef[jdev ? 2 * (*jdev) + 1 : k_fixed];
   const double f = b2 > 0.0 ? 1.0 / sqrt(b2) : 0.0;
   const double2 xv = x[i], yv = y[i];
   x[i] = make_double2(xv.x * f, xv.y * f);
@@ -129,7 +140,7 @@ __global__ void k_lanczos_scale(int n, const double* coef, int k, double2* x, do
 // out = av + s bv (bv NULL: av); dot += Re(sum_i conj(w_i) out_i)
 __global__ void __launch_bounds__(256) k_combine_dot(int n, const double2* av, const double2* bv,
                                                      double s, double2* out, const double2* w,
-                                                     double* dot) {
+                                                     double* dot, const int* jdev, int off) {
   __shared__ double red[8];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double d = 0.0;
@@ -143,8 +154,11 @@ __global__ void __launch_bounds__(256) k_combine_dot(int n, const double2* av, c
     d = w[i].x * o.x + w[i].y * o.y;
   }
   d = block_sum(d, red);
-  if (threadIdx.x == 0) atomicAdd(dot, d);
+  if (threadIdx.x == 0) atomicAdd(dot_target(dot, jdev, off), d);
 }
+
+// the step counter of the recursion: one thread, after a step's last kernel
+__global__ void k_step_inc(int* jdev) { ++*jdev; }
 
 // y = conj(rho)
 __global__ void k_conj(int n, const double2* rho, double2* y) {
@@ -201,7 +215,16 @@ __global__ void __launch_bounds__(256) k_eps_change(int n_omega, const double2* 
 
 }  // namespace
 
+
 // eps on the grid from the recursion above; returns the steps taken.
+//
+// The step index lives on the device (every step kernel reads it, a one-thread
+// kernel advances it), so the kernels of a step take the same arguments at
+// every step but for the buffer rotation, which repeats every 6 steps (v, x
+// swap; y_{j-1}, y_j, y_{j+1} rotate).  With FP64 products, 6 steps are
+// captured once as a CUDA graph and replayed: the launches, not the
+// arithmetic, bound a step at small N.  The tensor-core products synchronise
+// inside each call and run as plain launches.
 int spectrum_lanczos(int n, const bse_c128* A, const bse_c128* B, int64_t ld, const bse_c128* rho,
                      double c_q, double vc, int n_omega, const double* omega, double delta,
                      double tol, int max_steps, int matvec_precision, bse_c128* eps_out,
@@ -219,10 +242,12 @@ int spectrum_lanczos(int n, const bse_c128* A, const bse_c128* B, int64_t ld, co
   const size_t vb = (size_t)n * sizeof(double2);
   DeviceBuffer part((size_t)chunks * vb, s), bv(vb, s), bx(vb, s), by0(vb, s), by1(vb, s),
       by2(vb, s), bu(vb, s), coef((size_t)(2 * max_steps + 2) * sizeof(double), s),
-      ea((size_t)std::max(n_omega, 1) * sizeof(double2), s), diff(2 * sizeof(double), s);
+      ea((size_t)std::max(n_omega, 1) * sizeof(double2), s), diff(2 * sizeof(double), s),
+      jbuf(sizeof(int), s);
   double2 *V = bv.as<double2>(), *X = bx.as<double2>(), *Y0 = by0.as<double2>(),
           *Y1 = by1.as<double2>(), *Y2 = by2.as<double2>(), *U = bu.as<double2>();
   double* cf = coef.as<double>();
+  int* jdev = jbuf.as<int>();
   const int eb = (n + 255) / 256;
   int launches = 0;
   // split-precision products: A and B split once into BF16 pieces, A x and
@@ -234,29 +259,46 @@ int spectrum_lanczos(int n, const bse_c128* A, const bse_c128* B, int64_t ld, co
     av.reset(new DeviceBuffer(vb, s));
     bvb.reset(new DeviceBuffer(vb, s));
   }
-  auto gemv = [&](double sign, const double2* x, double2* out, const double2* w, double* dot) {
+  // out = (A + sign B) x; dot target as for dot_target(dot, jd, off)
+  auto gemv = [&](cudaStream_t st, double sign, const double2* x, double2* out, const double2* w,
+                  double* dot, const int* jd, int off) {
     if (tcm) {
       tc_matvec_apply(tcm.get(), reinterpret_cast<const bse_c128*>(x), 1, av->as<bse_c128>(),
-                      B ? bvb->as<bse_c128>() : nullptr, s);
-      k_combine_dot<<<eb, 256, 0, s>>>(n, av->as<double2>(), B ? bvb->as<double2>() : nullptr,
-                                       sign, out, w, dot);
+                      B ? bvb->as<bse_c128>() : nullptr, st);
+      k_combine_dot<<<eb, 256, 0, st>>>(n, av->as<double2>(), B ? bvb->as<double2>() : nullptr,
+                                        sign, out, w, dot, jd, off);
       launches += 1;
       return;
     }
-    k_pm_gemv<<<dim3(row_blocks, chunks), kGvRows, 0, s>>>(n, A2, B2, ld, sign, x, chunk,
-                                                           part.as<double2>());
-    k_sum_partials<<<eb, 256, 0, s>>>(n, chunks, part.as<double2>(), out, w, dot);
+    k_pm_gemv<<<dim3(row_blocks, chunks), kGvRows, 0, st>>>(n, A2, B2, ld, sign, x, chunk,
+                                                            part.as<double2>());
+    k_sum_partials<<<eb, 256, 0, st>>>(n, chunks, part.as<double2>(), out, w, dot, jd, off);
     launches += 2;
+  };
+  // one step on stream st with the current buffer assignment, then rotate
+  auto step = [&](cudaStream_t st) {
+    gemv(st, +1.0, V, U, V, cf, jdev, 0);                 // u = (A+B) v_j, alpha_j
+    k_lanczos_y<<<eb, 256, 0, st>>>(n, U, Y1, Y0, cf, jdev, Y2);
+    gemv(st, -1.0, Y2, X, Y2, cf, jdev, 1);               // x = (A-B) y, beta_j^2
+    k_lanczos_scale<<<eb, 256, 0, st>>>(n, cf, jdev, 0, X, Y2);
+    k_step_inc<<<1, 1, 0, st>>>(jdev);
+    launches += 3;
+    std::swap(V, X);                                      // v_{j+1}
+    double2* t = Y0;                                      // y_{j-1} <- y_j <- y_{j+1}
+    Y0 = Y1;
+    Y1 = Y2;
+    Y2 = t;
   };
   Phase ph("spectrum_lanczos", s);
   BSE_CUDA(cudaMemsetAsync(cf, 0, (size_t)(2 * max_steps + 2) * sizeof(double), s));
   BSE_CUDA(cudaMemsetAsync(Y0, 0, vb, s));
+  BSE_CUDA(cudaMemsetAsync(jdev, 0, sizeof(int), s));
   // start: y_0 = conj(rho), v_0 = (A-B) y_0, <v_0, v_0> = y_0^H v_0; the
   // squared norm is kept in the last coefficient slot
   double* nv2_dev = cf + 2 * max_steps + 1;
   k_conj<<<eb, 256, 0, s>>>(n, reinterpret_cast<const double2*>(rho), Y1);
   ++launches;
-  gemv(-1.0, Y1, X, Y1, nv2_dev);
+  gemv(s, -1.0, Y1, X, Y1, nv2_dev, nullptr, 0);
   double nv2 = 0.0;
   BSE_CUDA(cudaMemcpyAsync(&nv2, nv2_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
   BSE_CUDA(cudaStreamSynchronize(s));
@@ -265,27 +307,51 @@ int spectrum_lanczos(int n, const bse_c128* A, const bse_c128* B, int64_t ld, co
     throw Error(nv2 == 0.0 ? BSE_ERR_ARG : BSE_ERR_NOT_PD,
                 nv2 == 0.0 ? "rho is zero" : "conj(rho)^H (A-B) conj(rho) <= 0: A-B is not positive definite");
   }
-  k_lanczos_scale<<<eb, 256, 0, s>>>(n, cf, 2 * max_steps + 1, X, Y1);
+  k_lanczos_scale<<<eb, 256, 0, s>>>(n, cf, nullptr, 2 * max_steps + 1, X, Y1);
   ++launches;
   std::swap(V, X);
+
+  // six steps as one graph (FP64 products)
+  constexpr int kGraphSteps = 6;
+  cudaGraphExec_t exec = nullptr;
+  struct GraphGuard {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t e = nullptr;
+    cudaStream_t cs = nullptr;
+    ~GraphGuard() {
+      if (e) cudaGraphExecDestroy(e);
+      if (g) cudaGraphDestroy(g);
+      if (cs) cudaStreamDestroy(cs);
+    }
+  } gg;
+  if (!tcm && max_steps >= kGraphSteps) {
+    BSE_CUDA(cudaStreamCreateWithFlags(&gg.cs, cudaStreamNonBlocking));
+    BSE_CUDA(cudaStreamBeginCapture(gg.cs, cudaStreamCaptureModeThreadLocal));
+    const int l0 = launches;
+    for (int q = 0; q < kGraphSteps; ++q) step(gg.cs);   // the rotation returns to the start
+    BSE_CUDA(cudaStreamEndCapture(gg.cs, &gg.g));
+    BSE_CUDA(cudaGraphInstantiate(&gg.e, gg.g, 0));
+    exec = gg.e;
+    launches = l0;   // captured, not launched; counted per replay below
+  }
+  const int per_graph = tcm ? 0 : kGraphSteps * 7;
   const double pref = c_q * kHartreeEv * 2.0 / vc;
   // eps is compared every `check` steps; at least min_steps are taken (past
   // n steps the recursion only repeats what the Krylov space already holds)
-  const int check = std::max(10, std::min(50, n)), min_steps = std::min(100, 2 * n);
+  const int check = exec ? std::max(kGraphSteps, std::min(48, (n / kGraphSteps) * kGraphSteps))
+                         : std::max(10, std::min(50, n));
+  const int min_steps = std::min(100, 2 * n);
   int steps = 0;
   bool have_prev = false, converged = false;
-  for (int j = 0; j < max_steps; ++j) {
-    gemv(+1.0, V, U, V, cf + 2 * j);                       // u = (A+B) v_j, alpha_j
-    k_lanczos_y<<<eb, 256, 0, s>>>(n, U, Y1, Y0, cf, j, Y2);
-    gemv(-1.0, Y2, X, Y2, cf + 2 * j + 1);                 // x = (A-B) y, beta_j^2
-    k_lanczos_scale<<<eb, 256, 0, s>>>(n, cf, 2 * j + 1, X, Y2);
-    launches += 2;
-    std::swap(V, X);                                       // v_{j+1}
-    double2* t = Y0;                                       // y_{j-1} <- y_j <- y_{j+1}
-    Y0 = Y1;
-    Y1 = Y2;
-    Y2 = t;
-    steps = j + 1;
+  while (steps < max_steps) {
+    if (exec && steps + kGraphSteps <= max_steps) {
+      BSE_CUDA(cudaGraphLaunch(exec, s));
+      launches += per_graph;
+      steps += kGraphSteps;
+    } else {
+      step(s);
+      steps += 1;
+    }
     if (steps % check == 0 || steps == max_steps) {
       double2* cur = have_prev ? ea.as<double2>() : reinterpret_cast<double2*>(eps_out);
       k_lanczos_eps<<<(n_omega + 127) / 128, 128, 0, s>>>(steps, cf, nv2, n_omega, omega, delta,
