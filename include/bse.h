@@ -288,11 +288,12 @@ int bse_spectrum(int32_t n, bse_c128* S_inout, const bse_c128* L, int64_t ld,
  * by at most tol times max |eps| between checks (every 50 steps; at least
  * min(100, 2n) steps); steps_out (host, may be NULL) receives the number.
  * A, B as for bse_reduce (B = NULL: zero), rho, omega, delta, c_q, vc as for
- * bse_spectrum (delta > 0); eps_out [n_omega] device.  matvec_precision:
+ * bse_spectrum (delta > 0); eps_out [n_omega] device.  A+B and A-B are
+ * formed once (workspace 2 x 16 N^2 bytes when B is given).  matvec_precision:
  * BSE_PREC_FP64 (products in FP64 on CUDA cores) or BSE_PREC_BF16X6 /
- * BF16X3 (A and B split once into BF16 pieces, products on the tensor
- * cores with A's diagonal in FP64, as for bse_lowest_excitons; workspace 2 x
- * 12 N^2 bytes for BF16X6); the recursion itself is FP64.
+ * BF16X3 (A+B and A-B split once into BF16 pieces, products on the tensor
+ * cores with the diagonal in FP64, as for bse_lowest_excitons; a further
+ * 2 x 12 N^2 bytes for BF16X6); the recursion itself is FP64.
  * Syncs at each check.  Errors: BSE_ERR_ARG, BSE_ERR_NOT_PD
  * (conj(rho)^H (A-B) conj(rho) <= 0), BSE_ERR_NO_CONV (max_steps reached;
  * eps_out holds the last estimate), BSE_ERR_NOMEM, BSE_ERR_CUDA. */
