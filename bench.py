@@ -62,11 +62,11 @@ KERNEL_SOURCES = ("paper_1904_05575_gb300/csrc/build_mixed.cu", "paper_1904_0557
                   "paper_1904_05575_gb300/csrc/bse_internal.h")
 TRAFFIC = {
     # workload: {phase: (bytes per build, sources digest at capture)}
-    "c5": {"mixed_stage2_tc": (49488502016, "c4cf8213308d36f9"),
-           "mixed_stage1_gemm": (26018308608, "c4cf8213308d36f9"),
-           "mixed_split": (50703839232, "c4cf8213308d36f9"),
-           "mixed_exchange": (13866137088, "c4cf8213308d36f9"),
-           "hermitian_complete": (20564567552, "c4cf8213308d36f9")},
+    "c5": {"mixed_stage2_tc": (49490195712, "dd6654958604b692"),
+           "mixed_stage1_gemm": (26045644800, "dd6654958604b692"),
+           "mixed_split": (50695242240, "dd6654958604b692"),
+           "mixed_exchange": (13866989568, "dd6654958604b692"),
+           "hermitian_complete": (20564305408, "dd6654958604b692")},
 }
 
 

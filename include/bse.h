@@ -67,6 +67,15 @@ typedef enum {
   BSE_PREC_BF16X3 = 3    /* 2 BF16 pieces, 3 products: lower precision */
 } bse_precision;
 
+/* Storage of the complex input arrays m_x, m_vv, m_cc, n_vc and w of a
+ * bse_problem (e_v, e_c, v_bar stay double; A and B complex128). */
+typedef enum {
+  BSE_C128 = 0,   /* interleaved {double re, im}, 16-byte aligned */
+  BSE_C64 = 1     /* interleaved {float re, im}, 8-byte aligned: half the bytes,
+                     the values already FP32 (every split-precision path
+                     rounds its inputs to FP32 before splitting them) */
+} bse_dtype;
+
 /* One momentum transfer Q.  All pointers are device pointers.
  *   e_v   [nk][nv]             valence energies eps_{v,k} (eV)
  *   e_c   [nk][nc]             conduction energies eps_{c,k} (eV), scissor applied
@@ -102,7 +111,17 @@ typedef enum {
  * (the terms of Eqs. vrrofM, wrrm, wrabar are sums over independent (k, k')
  * blocks).  n_vc stays whole: W^ra of row k reads n_vc[k'][k] for every k'.
  * e_v, e_c, m_x, w, q_minus, q_plus, v_bar, A and B keep their full shapes.
- * Requires 0 <= k_begin, k_begin + k_count <= nk; else BSE_ERR_ARG. */
+ * Requires 0 <= k_begin, k_begin + k_count <= nk; else BSE_ERR_ARG.
+ *
+ * in_dtype (BSE_C128 = 0, the default of a zeroed struct, or BSE_C64): the
+ * element type of m_x, m_vv, m_cc, n_vc and w.  BSE_C64 is served by the
+ * split-precision builds (BSE_PREC_BF16X6 / BF16X3, bse_build_kernel and
+ * plans) whose direct terms run on the tensor cores: every pair block with
+ * both sides >= 64 rows, or gamma_c = 0.  It is refused with
+ * BSE_ERR_UNSUPPORTED for BSE_PREC_FP64, bse_build_kernel_fp64_static,
+ * BSE_PLAN_FP64_DIAGONAL, BSE_PLAN_CUDA_CORE_STAGE2 and pair blocks that
+ * would need the CUDA-core stage 2; plans over it never take the fused
+ * direct term. */
 typedef struct {
   int32_t nk, nv, nc, ng, nq_w;
   double omega_cell;                  /* Omega in bohr^3; V_c = nk * Omega */
@@ -115,6 +134,7 @@ typedef struct {
   bse_c128 *A, *B;
   int64_t ld;
   int32_t k_begin, k_count;           /* k-row slab; 0, 0 = all rows */
+  int32_t in_dtype;                   /* bse_dtype of the complex inputs */
 } bse_problem;
 
 /* Build A and B for nprob independent momentum transfers (each Q is its own

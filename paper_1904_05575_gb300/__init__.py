@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libbse.so")
 BSE_OK, BSE_ERR_ARG, BSE_ERR_CUDA, BSE_ERR_NOMEM = 0, -1, -2, -3
 BSE_ERR_NOT_PD, BSE_ERR_NO_CONV, BSE_ERR_TIMEOUT, BSE_ERR_UNSUPPORTED = -4, -5, -6, -7
 BSE_PREC_FP64, BSE_PREC_BF16X6, BSE_PREC_BF16X3 = 0, 2, 3
+BSE_C128, BSE_C64 = 0, 1   # bse_problem.in_dtype
 BSE_PLAN_AUTOTUNE = 1
 BSE_PLAN_UNFUSED = 2
 BSE_PLAN_CUDA_CORE_STAGE2 = 4
@@ -50,6 +51,7 @@ class bse_problem(ctypes.Structure):
         ("v_bar", ctypes.c_void_p),
         ("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("ld", ctypes.c_int64),
         ("k_begin", ctypes.c_int32), ("k_count", ctypes.c_int32),
+        ("in_dtype", ctypes.c_int32),
     ]
 
 
@@ -214,7 +216,11 @@ def make_problem_struct(d: Dict, gamma_x: float = 1.0, gamma_c: float = 1.0,
     B; m_vv and m_cc then hold only those k rows ([k_count, nk, ...]) while
     n_vc stays whole ([nk, nk, ...])."""
     import torch
-    c128, f64, i32 = torch.complex128, torch.float64, torch.int32
+    f64, i32 = torch.float64, torch.int32
+    # the complex inputs' storage: complex128 (BSE_C128) or complex64 (BSE_C64)
+    c128 = d["m_x"].dtype
+    if c128 not in (torch.complex128, torch.complex64):
+        raise TypeError(f"m_x must be complex128 or complex64, got {c128}")
     n = d["nk"] * d["nv"] * d["nc"]
     nk = d["nk"]
     kn = k_count if k_count > 0 else nk
@@ -242,7 +248,8 @@ def make_problem_struct(d: Dict, gamma_x: float = 1.0, gamma_c: float = 1.0,
         w=_ptr(d["w"], c128, "w"), q_minus=_ptr(d["q_minus"], i32, "q_minus"),
         q_plus=_ptr(d["q_plus"], i32, "q_plus") if coupling else None,
         v_bar=_ptr(d["v_bar"], f64, "v_bar"), A=a_ptr, B=b_ptr, ld=ld,
-        k_begin=int(k_begin), k_count=int(k_count))
+        k_begin=int(k_begin), k_count=int(k_count),
+        in_dtype=BSE_C64 if c128 == torch.complex64 else BSE_C128)
 
 
 def bse_build_kernel(problems: Sequence[bse_problem], precision: int = BSE_PREC_FP64,
@@ -481,10 +488,15 @@ def bse_kernel_launches() -> int:
     return int(load().bse_kernel_launches())
 
 
-def upload_problem(p: Dict, device="cuda", ld: Optional[int] = None, pin: bool = False) -> Dict:
+def upload_problem(p: Dict, device="cuda", ld: Optional[int] = None, pin: bool = False,
+                   complex_dtype=None) -> Dict:
     """Copy a bse_inputs problem (numpy arrays, or torch tensors already on a
-    device) to contiguous CUDA tensors and allocate A, B [n, ld]."""
+    device) to contiguous CUDA tensors and allocate A, B [n, ld].
+    complex_dtype = torch.complex64 stores m_x, m_vv, m_cc, n_vc and w as
+    complex64 (BSE_C64; make_problem_struct sets in_dtype from it)."""
     import torch
+    ct = complex_dtype or torch.complex128
+    cn = np.complex64 if ct == torch.complex64 else np.complex128
 
     def dev(x, npt, tt):
         if isinstance(x, torch.Tensor):
@@ -495,7 +507,7 @@ def upload_problem(p: Dict, device="cuda", ld: Optional[int] = None, pin: bool =
     for k in ("e_v", "e_c", "v_bar"):
         out[k] = dev(p[k], np.float64, torch.float64)
     for k in ("m_x", "m_vv", "m_cc", "n_vc", "w"):
-        out[k] = dev(p[k], np.complex128, torch.complex128)
+        out[k] = dev(p[k], cn, ct)
     for k in ("q_minus", "q_plus"):
         out[k] = dev(p[k], np.int32, torch.int32)
     for k in ("nk", "nv", "nc", "ng"):

@@ -130,6 +130,15 @@ __global__ void __launch_bounds__(256) k_nonfinite16(const uint4* __restrict__ p
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1 << bit);
 }
 
+// the same for floats (complex64 inputs)
+__global__ void k_nonfinite4(const float* __restrict__ p, int64_t n, int bit, int* flag) {
+  bool bad = false;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    bad = bad || ((__float_as_uint(p[i]) >> 23) & 0xFFu) == 0xFFu;
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1 << bit);
+}
+
 __global__ void k_nonfinite8(const double* __restrict__ p, int64_t n, int bit, int* flag) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -142,14 +151,17 @@ __global__ void k_nonfinite8(const double* __restrict__ p, int64_t n, int bit, i
 // naming the arrays that hold a NaN or an infinity.  Syncs.
 void check_finite(const bse_problem& p, int64_t kn, const std::string& at, cudaStream_t s) {
   const int64_t n = (int64_t)p.nk * p.nv * p.nc, ng = p.ng, nk = p.nk;
-  struct Arr { const void* ptr; int64_t doubles; const char* name; };
-  std::vector<Arr> arrs = {{p.e_v, nk * p.nv, "e_v"}, {p.e_c, nk * p.nc, "e_c"},
-                           {p.m_x, 2 * n * ng, "m_x"}, {p.v_bar, ng, "v_bar"}};
+  // doubles: the count of 8-byte reals; f32: the complex array holds floats
+  // (complex64), then `doubles` counts its floats
+  struct Arr { const void* ptr; int64_t doubles; const char* name; bool f32; };
+  const bool c64 = p.in_dtype == BSE_C64;
+  std::vector<Arr> arrs = {{p.e_v, nk * p.nv, "e_v", false}, {p.e_c, nk * p.nc, "e_c", false},
+                           {p.m_x, 2 * n * ng, "m_x", c64}, {p.v_bar, ng, "v_bar", false}};
   if (p.gamma_c != 0.0) {
-    arrs.push_back({p.m_vv, 2 * kn * nk * p.nv * p.nv * ng, "m_vv"});
-    arrs.push_back({p.m_cc, 2 * kn * nk * p.nc * p.nc * ng, "m_cc"});
-    arrs.push_back({p.w, 2 * (int64_t)p.nq_w * ng * ng, "w"});
-    if (p.coupling) arrs.push_back({p.n_vc, 2 * nk * nk * p.nv * p.nc * ng, "n_vc"});
+    arrs.push_back({p.m_vv, 2 * kn * nk * p.nv * p.nv * ng, "m_vv", c64});
+    arrs.push_back({p.m_cc, 2 * kn * nk * p.nc * p.nc * ng, "m_cc", c64});
+    arrs.push_back({p.w, 2 * (int64_t)p.nq_w * ng * ng, "w", c64});
+    if (p.coupling) arrs.push_back({p.n_vc, 2 * nk * nk * p.nv * p.nc * ng, "n_vc", c64});
   }
   int* flag = nullptr;
   if (cudaMallocAsync(reinterpret_cast<void**>(&flag), sizeof(int), s) != cudaSuccess) {
@@ -161,7 +173,11 @@ void check_finite(const bse_problem& p, int64_t kn, const std::string& at, cudaS
     BSE_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), s));
     for (size_t i = 0; i < arrs.size(); ++i) {
       const Arr& a = arrs[i];
-      if (a.doubles % 2 == 0 && (reinterpret_cast<uintptr_t>(a.ptr) & 15) == 0) {
+      if (a.f32) {
+        const int grid = (int)std::min<int64_t>((a.doubles + 255) / 256, 152 * 8);
+        k_nonfinite4<<<std::max(grid, 1), 256, 0, s>>>(static_cast<const float*>(a.ptr), a.doubles,
+                                                       (int)i, flag);
+      } else if (a.doubles % 2 == 0 && (reinterpret_cast<uintptr_t>(a.ptr) & 15) == 0) {
         const int64_t words = a.doubles / 2;
         const int grid = (int)std::min<int64_t>((words + 255) / 256, 152 * 8);
         k_nonfinite16<<<std::max(grid, 1), 256, 0, s>>>(static_cast<const uint4*>(a.ptr), words,
@@ -211,12 +227,17 @@ Problem validate(const bse_problem& p, int index, cudaStream_t s, bool scan = tr
     if (p.coupling) BSE_CHECK_ARG(p.n_vc && p.q_plus, at + "NULL n_vc or q_plus");
   }
   if (p.coupling) BSE_CHECK_ARG(p.B, at + "coupling = 1 needs B");
+  BSE_CHECK_ARG(p.in_dtype == BSE_C128 || p.in_dtype == BSE_C64,
+                at + "in_dtype must be BSE_C128 (0) or BSE_C64 (1)");
   // complex128 arrays are read and written 16 bytes at a time (vector loads,
-  // bulk copies), real arrays 8, q maps 4
+  // bulk copies), complex64 inputs 8, real arrays 8, q maps 4
   auto aligned = [](const void* q, uintptr_t a) { return (reinterpret_cast<uintptr_t>(q) & (a - 1)) == 0; };
-  BSE_CHECK_ARG(aligned(p.m_x, 16) && aligned(p.m_vv, 16) && aligned(p.m_cc, 16) &&
-                    aligned(p.n_vc, 16) && aligned(p.w, 16) && aligned(p.A, 16) && aligned(p.B, 16),
-                at + "complex128 arrays must be 16-byte aligned");
+  const uintptr_t ca = p.in_dtype == BSE_C64 ? 8 : 16;
+  BSE_CHECK_ARG(aligned(p.m_x, ca) && aligned(p.m_vv, ca) && aligned(p.m_cc, ca) &&
+                    aligned(p.n_vc, ca) && aligned(p.w, ca),
+                at + (ca == 16 ? "complex128 inputs must be 16-byte aligned"
+                               : "complex64 inputs must be 8-byte aligned"));
+  BSE_CHECK_ARG(aligned(p.A, 16) && aligned(p.B, 16), at + "A and B must be 16-byte aligned");
   BSE_CHECK_ARG(aligned(p.e_v, 8) && aligned(p.e_c, 8) && aligned(p.v_bar, 8) &&
                     aligned(p.q_minus, 4) && aligned(p.q_plus, 4),
                 at + "real arrays must be 8-byte and q maps 4-byte aligned");
@@ -254,6 +275,9 @@ extern "C" int bse_build_kernel(const bse_problem* probs, int32_t nprob, int32_t
     prs.reserve(nprob);
     for (int i = 0; i < nprob; ++i) prs.push_back(validate(probs[i], i, s));
     if (precision == BSE_PREC_FP64) {
+      for (const Problem& pr : prs)
+        if (pr.p.in_dtype != BSE_C128)
+          throw Error(BSE_ERR_UNSUPPORTED, "the FP64 build reads complex128 inputs only");
       for (const Problem& pr : prs) build_fp64(pr, s);
     } else {
       build_mixed_batch(prs, precision, s);
@@ -265,6 +289,8 @@ extern "C" int bse_build_kernel_fp64_static(const bse_problem* prob, void* cuda_
   return guarded([&] {
     BSE_CHECK_ARG(prob != nullptr, "prob is NULL");
     const Problem pr = validate(*prob, 0, static_cast<cudaStream_t>(cuda_stream), false);
+    if (pr.p.in_dtype != BSE_C128)
+      throw Error(BSE_ERR_UNSUPPORTED, "the FP64 build reads complex128 inputs only");
     build_fp64_static(pr, static_cast<cudaStream_t>(cuda_stream));
   });
 }

@@ -77,6 +77,7 @@ struct SplitArgs {
   int zero_diag = 0;        // SPLIT_DENSE: element k == row stored as zero
   int bneg = 0;             // B-operand layout: 3P planes (-Im, Re, Im) per piece
   int tdense = 0;           // SPLIT_DENSE read transposed: row r, element k at src[k * src_ld + r]
+  int c64 = 0;              // src holds complex64 (float re, im) instead of complex128
 };
 
 // One thread per (output row, 8 consecutive k): every element is read as two
@@ -88,6 +89,7 @@ __global__ void __launch_bounds__(256) k_split(SplitArgs a) {
   const int64_t total = (int64_t)a.rows * kg;
   const int64_t plane = (a.plane_rows ? a.plane_rows : (int64_t)a.rows) * a.Kp;
   const uint4* src = reinterpret_cast<const uint4*>(a.src);   // one complex128 per uint4
+  const uint2* src64 = reinterpret_cast<const uint2*>(a.src);  // or one complex64 per uint2
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
     int row = (int)(i / kg), k0 = (int)(i % kg) * 8;
@@ -112,9 +114,20 @@ __global__ void __launch_bounds__(256) k_split(SplitArgs a) {
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const int k = k0 + e;
-      uint4 x = make_uint4(0u, 0u, 0u, 0u);
-      if (k < a.K && off >= 0 && !(a.zero_diag && k == row)) x = __ldg(src + off + (int64_t)k * kstride);
-      uint32_t fr = f64w_to_f32_bits(x.x, x.y), fi = f64w_to_f32_bits(x.z, x.w);
+      const bool take = k < a.K && off >= 0 && !(a.zero_diag && k == row);
+      uint32_t fr = 0u, fi = 0u;
+      if (a.c64) {   // already FP32
+        if (take) {
+          const uint2 x = __ldg(src64 + off + (int64_t)k * kstride);
+          fr = x.x;
+          fi = x.y;
+        }
+      } else {
+        uint4 x = make_uint4(0u, 0u, 0u, 0u);
+        if (take) x = __ldg(src + off + (int64_t)k * kstride);
+        fr = f64w_to_f32_bits(x.x, x.y);
+        fi = f64w_to_f32_bits(x.z, x.w);
+      }
       if (a.kscale && k < a.K) {   // exchange operand only: scale in FP32
         const float sc = (float)a.kscale[k];
         fr = __float_as_uint(__uint_as_float(fr) * sc);
@@ -1363,6 +1376,7 @@ void plan_splits(BatchPlan& pl, cudaStream_t s) {
     SplitArgs sa{reinterpret_cast<const double2*>(p.m_x), SPLIT_DENSE, nullptr, 0, 0, pl.ng,
                  pl.Kp, n, pl.pieces, 1, p.v_bar, pl.xa.as<__nv_bfloat16>(), pl.x_rows,
                  pl.x_row0[i]};
+    sa.c64 = p.in_dtype == BSE_C64;
     launch_split(sa, s);
     SplitArgs sb = sa;
     sb.conj = 0;
@@ -1379,11 +1393,13 @@ void plan_splits(BatchPlan& pl, cudaStream_t s) {
                  t.w_conj_transpose ? 1 : 0, nullptr, pl.wsplit.as<__nv_bfloat16>(), pl.w_rows,
                  t.w_row0};
     sw.bneg = 1;
+    sw.c64 = p.in_dtype == BSE_C64;
     if (t.w_owner) launch_split(sw, s);
     SplitArgs sa{reinterpret_cast<const double2*>(t.side), SPLIT_PAIRS, t.perm.as<int>(),
                  t.rows_side, 0, pl.ng, pl.Kp, npair * t.rows_side, pl.pieces, 0, nullptr,
                  pl.asplit.as<__nv_bfloat16>(), pl.a_rows, t.a_row0};
     sa.pair_nb = t.side_nb;
+    sa.c64 = p.in_dtype == BSE_C64;
     launch_split(sa, s);
     if (t.tc2) {   // the other pair side, in pair order, conjugated as opX
       SplitArgs sx{t.s2.x, SPLIT_PAIRS, t.x2perm.as<int>(), t.s2.rows_x, 0, pl.ng, pl.Kp,
@@ -1392,6 +1408,7 @@ void plan_splits(BatchPlan& pl, cudaStream_t s) {
                    t.rows_t_side ? pl.x2b_rows : pl.x2a_rows, t.x2_row0};
       sx.pair_nb = t.x_nb;
       sx.bneg = t.rows_t_side ? 1 : 0;   // the B operand when T forms the tile rows
+      sx.c64 = p.in_dtype == BSE_C64;
       launch_split(sx, s);
     }
   }
@@ -1678,6 +1695,11 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
   pl->probs = std::move(probs);
   if (precision == BSE_PREC_FP64) return pl.release();
   pl->half = (flags & BSE_PLAN_HERMITIAN) != 0;
+  bool any_c64 = false;
+  for (const Problem& pr : pl->probs) any_c64 = any_c64 || pr.p.in_dtype == BSE_C64;
+  if (any_c64 && (flags & (BSE_PLAN_FP64_DIAGONAL | BSE_PLAN_CUDA_CORE_STAGE2)))
+    throw Error(BSE_ERR_UNSUPPORTED,
+                "complex64 inputs: no exact FP64 diagonal and no CUDA-core stage 2");
   if (flags & BSE_PLAN_FP64_DIAGONAL)
     for (const Problem& pr : pl->probs) pl->diag_ws.emplace_back(diag_fp64_workspace(pr));
   if (pl->half)
@@ -1778,7 +1800,10 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
         a.out = reinterpret_cast<double2*>(p.A);
       } else {
         t.rows_side = nv * nc;
-        t.side = p.n_vc + pair_off * nv * nc * p.ng;   // the slab's rows of the whole n_vc
+        // the slab's rows of the whole n_vc (elements of 16 or 8 bytes)
+        t.side = reinterpret_cast<const bse_c128*>(
+            reinterpret_cast<const char*>(p.n_vc) +
+            pair_off * nv * nc * p.ng * (p.in_dtype == BSE_C64 ? 8 : 16));
         t.w_conj_transpose = false;
         t.qh.assign(pr.qp_host.begin() + pair_off, pr.qp_host.begin() + pair_off + npair);
         a.mode = S2_RA;
@@ -1838,7 +1863,8 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
     if (pl->a_rows > INT32_MAX || pl->w_rows > INT32_MAX)
       throw Error(BSE_ERR_UNSUPPORTED, "batched stage-1 rows exceed 2^31");
     // (the fused epilogue contracts whole-K tiles: no K segments)
-    pl->fused = (flags & BSE_PLAN_UNFUSED) == 0 && ksegs_for(pl->Kp) == 1;
+    // the fused epilogue reads the raw complex128 pair side
+    pl->fused = (flags & BSE_PLAN_UNFUSED) == 0 && ksegs_for(pl->Kp) == 1 && !any_c64;
     for (const BatchPlan::Term& t : pl->terms) pl->fused = pl->fused && fused_fits(t.s2);
     pl->wsplit = DevMem((size_t)tc::b_planes(pl->pieces) * pl->w_rows * pl->Kp * 2);
     pl->asplit = DevMem((size_t)pl->planes * pl->a_rows * pl->Kp * 2);
@@ -1892,6 +1918,11 @@ BatchPlan* plan_create(std::vector<Problem> probs, int precision, int flags, cud
       bool any_fp32 = false, any_tc2 = false;
       for (BatchPlan::Term& t : pl->terms) {
         t.tc2 = (flags & BSE_PLAN_CUDA_CORE_STAGE2) == 0 && t.s2.rows_x >= 64 && t.s2.rows_t >= 64;
+        if (!t.tc2 && pl->probs[t.prob].p.in_dtype == BSE_C64)
+          throw Error(BSE_ERR_UNSUPPORTED,
+                      "complex64 inputs need pair blocks of >= 64 rows on both sides (the "
+                      "tensor-core stage 2); smaller blocks take the CUDA-core stage 2, "
+                      "which reads complex128");
         any_tc2 = any_tc2 || t.tc2;
         any_fp32 = any_fp32 || !t.tc2;
       }
@@ -2080,6 +2111,7 @@ std::vector<uint64_t> plan_key(const std::vector<Problem>& probs, int precision)
     k.push_back(bits[2]);
     k.push_back((uint64_t)p.ld);
     k.push_back(((uint64_t)(uint32_t)p.k_begin << 32) | (uint32_t)p.k_count);
+    k.push_back((uint64_t)(uint32_t)p.in_dtype);
     k.push_back(fnv1a(pr.qp_host, fnv1a(pr.qm_host)));
   }
   return k;
