@@ -305,8 +305,10 @@ int bse_spectrum(int32_t n, bse_c128* S_inout, const bse_c128* L, int64_t ld,
  * a^H (A-B)^-1 b, so a Lanczos recursion in that inner product, with two
  * products by A+B and A-B per step and no factorisation, gives Q as a
  * continued fraction of its coefficients.  The steps stop when eps changes
- * by at most tol times max |eps| between checks (every 50 steps; at least
- * min(100, 2n) steps); steps_out (host, may be NULL) receives the number.
+ * by at most tol times max |eps| between checks (every 48 steps with FP64
+ * products, which run as a CUDA graph of 6 steps, every 50 with tensor-core
+ * products; fewer for n < 50; at least min(100, 2n) steps); steps_out
+ * (host, may be NULL) receives the number.
  * A, B as for bse_reduce (B = NULL: zero), rho, omega, delta, c_q, vc as for
  * bse_spectrum (delta > 0); eps_out [n_omega] device.  A+B and A-B are
  * formed once (workspace 2 x 16 N^2 bytes when B is given).  matvec_precision:
