@@ -126,3 +126,32 @@ def test_problem_struct_shape_checks():
     # TDA does not read n_vc or q_plus
     with pytest.raises(TypeError):
         bse.make_problem_struct(dict(d, n_vc=d["n_vc"][..., :-1]), coupling=False)
+
+
+def test_host_side_argument_errors_newer_entry_points(lib):
+    """The eigensolve-free spectrum, the stage-2 shape query, the learned
+    preconditioner's neighbour and feature calls and the input dtype all
+    check their arguments on the host before any CUDA call."""
+    import paper_1904_05575_gb300 as bse
+    lib2 = bse.load()
+    i32 = ctypes.c_int32
+    assert lib2.bse_spectrum_lanczos(0, None, None, 1, None, 1.0, 1.0, 1, None, 0.1, 1e-8, 100,
+                                     bse.BSE_PREC_FP64, None, None, None) == bse.BSE_ERR_ARG
+    assert lib2.bse_spectrum_lanczos(4, None, None, 4, None, 1.0, 1.0, 1, None, 0.1, 1e-8, 100,
+                                     bse.BSE_PREC_FP64, None, None, None) == bse.BSE_ERR_ARG
+    assert b"NULL" in lib2.bse_last_error()
+    t, st = i32(5), i32(5)
+    assert lib2.bse_plan_stage2_shape(None, ctypes.byref(t), ctypes.byref(st)) == bse.BSE_ERR_ARG
+    assert lib2.bse_mlp_set_neighbours(None, 4, 1, None, 0, None) == bse.BSE_ERR_ARG
+    assert lib2.bse_mlp_features(None, 4, 1, None, None, None, None, None, 4, None, None, None,
+                                 None) == bse.BSE_ERR_ARG
+    # in_dtype outside {BSE_C128, BSE_C64}, and complex64 inputs not 8-byte aligned
+    q = bse.bse_problem(nk=1, nv=1, nc=1, ng=1, nq_w=1, omega_cell=1.0, ld=1, gamma_x=1.0,
+                        gamma_c=0.0, coupling=0, e_v=0x1000, e_c=0x1000, m_x=0x1000,
+                        v_bar=0x1000, A=0x2000, in_dtype=7)
+    assert lib2.bse_build_kernel((bse.bse_problem * 1)(q), 1, 0, None) == bse.BSE_ERR_ARG
+    assert b"in_dtype" in lib2.bse_last_error()
+    q.in_dtype = bse.BSE_C64
+    q.m_x = 0x1004
+    assert lib2.bse_build_kernel((bse.bse_problem * 1)(q), 1, 0, None) == bse.BSE_ERR_ARG
+    assert b"8-byte" in lib2.bse_last_error()
